@@ -1,0 +1,42 @@
+"""The five calibration workloads, as data (no method arithmetic).
+
+Bounds follow the paper's second, narrowed search box (Sec. 3.2): beta in [0, 2],
+gamma in [0, 1], mu in [0, 0.1].  Log-uniform boxes need positive lower bounds,
+so they use beta, gamma >= 1e-3 and mu >= 1e-5.  The fitted initial infectious
+count I0 is searched in [0, 1e6] (linear) or [1, 1e6] (log).  PSO constants are
+the paper's: inertia, cognitive and social coefficients all 0.5 (Sec. 3.3).
+"""
+from __future__ import annotations
+
+PAPER_W = 0.5
+PAPER_C1 = 0.5
+PAPER_C2 = 0.5
+
+
+def bounds(K: int, log: bool):
+    if log:
+        lb = [1e-3] * K + [1e-3, 1e-5, 1.0]
+        ub = [2.0] * K + [1.0, 0.1, 1e6]
+    else:
+        lb = [0.0] * K + [0.0, 0.0, 0.0]
+        ub = [2.0] * K + [1.0, 0.1, 1e6]
+    return lb, ub
+
+
+CONFIGS = {
+    # Plain method in FP64: constant rates (K = 1) plus I0, 30 days, dt = 0.1 day.
+    "c1": dict(name="c1-plain-fp64", series="c1", K=1, days=30, spd=10, M=64, iters=200,
+               precision=64, log=False, seed=0, reeval_topk=0),
+    # One window in FP32 with compensated loss; 4 beta segments (7 params); log-uniform box.
+    "c2": dict(name="c2-single-window-fp32", series="c2", K=4, days=60, spd=10, M=4096, iters=1000,
+               precision=32, log=True, seed=0, reeval_topk=32),
+    # 512 rolling windows of uneven length and swarm size, 6 beta segments (9 params).
+    "c3": dict(name="c3-batched-512-windows-fp32", series="c3", K=6, spd=10, W=512, iters=100,
+               precision=32, log=True, seed=0, L_min=21, L_max=90, M_min=256, M_max=2048, delta=3),
+    # Adjoint gradient over a 90-day window at dt = 0.05 day, checkpoints every 16 steps.
+    "c4": dict(name="c4-adjoint-90d", series="c4", K=4, days=90, spd=20, M=4096, iters=200,
+               precision=32, log=True, seed=0, ckpt=16, polish_topk=32, reeval_topk=32),
+    # 2^20 particles, 10 segments, 120 days at dt = 0.05 day, then a 14-day forecast.
+    "c5": dict(name="c5-large-2^20", series="c5", K=10, days=120, spd=20, M=1 << 20, iters=100,
+               precision=32, log=True, seed=0, horizon=14, forecast_topk=1024, reeval_topk=32),
+}
