@@ -1,0 +1,250 @@
+/*
+ * sird_pso.h -- C ABI of the GB300 (sm_103a) SIRD-by-PSO calibration library.
+ *
+ * The library calibrates the SIRD model of Blaszczyk et al., "On automatic
+ * calibration of the SIRD epidemiological model for COVID-19 data in Poland"
+ * (arXiv 2204.12346), by particle swarm optimisation on one GPU:
+ *
+ *   model       Sec. 2.2, eq. (SIRD): S' = -beta S I / N, I' = beta I S / N - (gamma + mu) I,
+ *               R' = gamma I, D' = mu I, with N = S + I + R + D constant
+ *   beta(t)     Sec. 2.2, eq. (beta): beta1, a linear ramp on [t1, t2), beta2 -- or K equal
+ *               constant segments over the window
+ *   integrator  Sec. 3.1 and 3.3: explicit Euler from the window's first observation
+ *   loss        Sec. 3.1: MXSE / MSE / MAE / MAPE on deceased counts (F_D^C), or the max
+ *               over min-max-normalised I, R, D (F_IRD^C)
+ *   optimiser   Sec. 3.3: PSO (inertia, cognitive, social coefficients; positions outside
+ *               the box are set to the bound)
+ *   forecast    Sec. 4.2: the fitted window extended with the last transmission rate,
+ *               gamma and mu
+ *
+ * Conventions for every entry point:
+ *   - No exception crosses the ABI.  Every call returns sird_status; SIRD_OK is 0.
+ *   - A handle records the first error it meets ("sticky"); later calls on it return
+ *     that status until sird_pso_clear_error().  sird_last_error() gives the message.
+ *   - "device" pointers are CUDA global-memory pointers of the current device;
+ *     "host" pointers are ordinary CPU memory.  The library never frees caller memory.
+ *   - All work of a handle runs on the CUDA stream given at creation (or set later),
+ *     in issue order.  A handle is not thread-safe.
+ *   - Sizes: at most SIRD_MAX_PARAMS parameters, 2^26 particles and 4096 observations
+ *     per window; steps_per_day in 1..1000.
+ */
+#ifndef SIRD_PSO_H
+#define SIRD_PSO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SIRD_MAX_PARAMS 32
+#define SIRD_MAX_OBS 4096
+#define SIRD_MAX_PARTICLES (1 << 26)
+
+typedef enum sird_status {
+    SIRD_OK = 0,
+    SIRD_ERR_ARG = 1,         /* invalid argument: NULL pointer, size out of range, lb > ub,
+                                 non-finite observation, log scale with lb <= 0 */
+    SIRD_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in sird_last_error) */
+    SIRD_ERR_NUMERIC = 3,     /* no finite loss where one is needed (e.g. every particle NaN) */
+    SIRD_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out (the kernel returned early) */
+    SIRD_ERR_STATE = 5,       /* call out of order, or a state blob that does not match the handle */
+    SIRD_ERR_NOMEM = 6,       /* device or host allocation failed */
+    SIRD_ERR_UNSUPPORTED = 7  /* option combination the library does not implement */
+} sird_status;
+
+/* Low-level costs of Sec. 3.1. */
+typedef enum sird_cost { SIRD_COST_MSE = 0, SIRD_COST_MXSE = 1, SIRD_COST_MAE = 2, SIRD_COST_MAPE = 3 } sird_cost;
+
+/* Transmission-rate form: K equal constant segments, or the paper's ramp (eq. (beta)). */
+typedef enum sird_beta_form { SIRD_BETA_PWC = 0, SIRD_BETA_RAMP = 1 } sird_beta_form;
+
+/* Main objective: F_D^C (deaths only) or F_IRD^C (max over I, R, D), Sec. 3.1. */
+typedef enum sird_objective { SIRD_FIT_D = 0, SIRD_FIT_IRD = 1 } sird_objective;
+
+/*
+ * One calibration window (Sec. 3.1).  All pointers are host memory and are copied
+ * by the call that receives the problem.
+ *
+ *   n_obs          tau+1 observations on days 0..n_obs-1 of the window (2..SIRD_MAX_OBS)
+ *   y_D            [n_obs] cumulative deceased.  The Euler scheme starts from D0 = y_D[0].
+ *   y_I, y_R       [n_obs] infectious / recovered, used only by SIRD_FIT_IRD (else NULL)
+ *   N              population (constant); S0 = N - I0 - R0 - D0
+ *   I0             initial infectious when fit_I0 == 0
+ *   R0             initial recovered
+ *   fit_I0         1: I0 is the last entry of theta and is fitted
+ *   beta_form      SIRD_BETA_PWC or SIRD_BETA_RAMP
+ *   K              number of segments for SIRD_BETA_PWC (1..SIRD_MAX_PARAMS-3)
+ *   steps_per_day  Euler steps per day; dt = 1/steps_per_day day
+ *   cost, objective  see the enums
+ *
+ * theta layout (P entries):
+ *   PWC : beta_1..beta_K, gamma, mu [, I0]          segment j covers steps
+ *         [ceil(j*S/K), ceil((j+1)*S/K)) of the S = (n_obs-1)*steps_per_day steps
+ *   RAMP: beta1, beta2, t1, t2, gamma, mu [, I0]    t1, t2 in days from the window start;
+ *         if t1 > t2 the two are swapped.  beta is taken at the left end of each step.
+ */
+typedef struct sird_problem {
+    int n_obs;
+    const double* y_D;
+    const double* y_I;
+    const double* y_R;
+    double N;
+    double I0;
+    double R0;
+    int fit_I0;
+    int beta_form;
+    int K;
+    int steps_per_day;
+    int cost;
+    int objective;
+} sird_problem;
+
+/*
+ * Swarm configuration (Sec. 3.3).  lb, ub, log_scale are host arrays of P entries,
+ * copied at creation.  Dimensions with log_scale[d] != 0 are searched in z = ln(theta)
+ * (needs lb > 0) and clamped in z; the others in theta itself.
+ *
+ *   particles     swarm size M (1..SIRD_MAX_PARTICLES)
+ *   iters         PSO iterations run by sird_pso_calibrate
+ *   w, c1, c2     inertia, cognitive and social coefficients (the paper uses 0.5 each)
+ *   precision     32: FP32 swarm and trajectories (compensated loss); 64: FP64 throughout
+ *   seed          Philox4x32-10 key (64 bits)
+ *   stream_id     fourth Philox counter word; separates independent swarms on one seed
+ *   reeval_topk   FP32 only: at the end, the k best personal bests are re-evaluated in FP64
+ *                 and the best of them is reported (0 = report the FP32 global best as is)
+ *   block_size    threads per block for the swarm kernels (0 = library default; else a
+ *                 multiple of 32 in 32..1024)
+ */
+typedef struct sird_pso_config {
+    int particles;
+    int iters;
+    double w, c1, c2;
+    const double* lb;
+    const double* ub;
+    const int* log_scale;
+    int precision;
+    uint64_t seed;
+    uint32_t stream_id;
+    int reeval_topk;
+    int block_size;
+} sird_pso_config;
+
+/* Result of a calibration (host struct written by the library). */
+typedef struct sird_result {
+    int n_params;
+    double theta[SIRD_MAX_PARAMS];  /* parameters of the reported best (decoded, FP64) */
+    double loss;                    /* FP64 loss of theta, evaluated on the GPU */
+    double loss_search;             /* the personal-best value the search stored for it */
+    double r2_D;                    /* coefficient of determination on D (Sec. 3.1) */
+    int index;                      /* particle whose personal best is reported */
+    int iters_done;                 /* PSO iterations completed */
+} sird_result;
+
+typedef struct sird_pso* sird_pso_t;
+
+/* ---------------------------------------------------------------- lifetime */
+
+/* Validates and copies the problem and configuration, allocates the swarm in device
+ * memory and binds the handle to cuda_stream (a cudaStream_t; NULL = default stream).
+ * On failure *out is NULL and the message is available from sird_last_error(NULL). */
+sird_status sird_pso_create(const sird_problem* problem, const sird_pso_config* config,
+                            void* cuda_stream, sird_pso_t* out);
+/* Waits for the handle's stream, then releases its device memory and graphs.  NULL is a no-op. */
+void sird_pso_destroy(sird_pso_t h);
+/* Message of the handle's sticky error, or of the last failed create when h is NULL. */
+const char* sird_last_error(sird_pso_t h);
+sird_status sird_pso_clear_error(sird_pso_t h);
+sird_status sird_pso_set_stream(sird_pso_t h, void* cuda_stream);
+/* Number of parameters P of the handle's theta layout (0 if h is NULL). */
+int sird_pso_num_params(sird_pso_t h);
+
+/* ---------------------------------------------------------------- fitness */
+
+/*
+ * Loss of M parameter vectors (Sec. 3.1: the Euler trajectory of eq. (SIRD) from the
+ * window start, then the cost on D).  d_theta is device memory, structure-of-arrays
+ * [P][ld] (entry d of vector m at d*ld + m), float for precision 32 and double for 64;
+ * d_loss is device memory [M] of the same type.  Runs on the handle's stream; returns
+ * after the launch.  ld >= M.  Non-finite losses are written as they come out.
+ */
+sird_status sird_pso_eval(sird_pso_t h, const void* d_theta, int M, int ld, void* d_loss, int precision);
+
+/* ---------------------------------------------------------------- swarm */
+
+/* Draws positions and velocities (Philox, iteration 0), evaluates them, sets the
+ * personal bests and the global best.  Asynchronous. */
+sird_status sird_pso_init(sird_pso_t h);
+/* Runs n_iters synchronous PSO iterations (Sec. 3.3): velocity, position, clamp to the
+ * box, evaluation, personal best (strictly smaller loss), global best (lowest index on
+ * ties; NaN counts as +inf).  Needs sird_pso_init or sird_pso_set_state first. */
+sird_status sird_pso_step(sird_pso_t h, int n_iters);
+/* init + config.iters iterations + (FP32) FP64 re-evaluation of the reeval_topk best,
+ * captured once into a CUDA graph and replayed; blocks until the result is on the host. */
+sird_status sird_pso_calibrate(sird_pso_t h, sird_result* out);
+/* Replaces the handle's observations y_D (host [n_obs], same n_obs as at creation; the
+ * first value stays D0 of the Euler scheme) with an asynchronous copy on the handle's
+ * stream, so that one handle (and its captured graph) calibrates window after window.
+ * y_D is copied into a pinned staging buffer before the call returns. */
+sird_status sird_pso_set_observations(sird_pso_t h, const double* y_D, int n_obs);
+/* Measurement hook: makes every later sird_pso_calibrate record the two CUDA events
+ * (cudaEvent_t; NULL to stop) on the handle's stream right before the first PSO
+ * iteration launch and right after the last one.  Re-captures the graph. */
+sird_status sird_pso_set_timing(sird_pso_t h, void* event_iter_begin, void* event_iter_end);
+/* Current best (re-evaluated in FP64 as in calibrate); blocks. */
+sird_status sird_pso_result(sird_pso_t h, sird_result* out);
+/* Waits for the handle's stream and returns the sticky status (device-side errors included). */
+sird_status sird_pso_sync(sird_pso_t h);
+
+/*
+ * Swarm state as a host blob: a header (magic, version, M, P, precision, iteration,
+ * gbest index, seed, stream_id) followed by x, v, pbest as [P][M] and pbest_f [M] in
+ * the swarm's precision.  get_state with buf == NULL writes the size to *size.
+ * set_state restores it exactly (the next step continues bit-identically).
+ */
+sird_status sird_pso_get_state(sird_pso_t h, void* buf, size_t* size);
+sird_status sird_pso_set_state(sird_pso_t h, const void* buf, size_t size);
+
+/* ---------------------------------------------------------------- gradient */
+
+/*
+ * Loss and its exact gradient (discrete adjoint of the Euler map; the paper notes that
+ * PSO is used because no gradient is available, Sec. 3.3 -- the discrete loss does have
+ * one).  d_theta [P][ld], d_loss [M], d_grad [P][ld_grad] (dL/dtheta) and d_grad_u0
+ * [4][ld_grad] (dL/d(S0, I0, R0, D0) with the four taken as independent; may be NULL)
+ * are device memory of the handle's precision type.  Trajectories are recomputed from
+ * checkpoints every ckpt_every steps (1..64).  Costs: MSE, MAE, MAPE, MXSE (sub-gradients
+ * at kinks) on F_D.
+ */
+sird_status sird_loss_grad(sird_pso_t h, const void* d_theta, int M, int ld, void* d_loss,
+                           void* d_grad, int ld_grad, void* d_grad_u0, int precision, int ckpt_every);
+
+/* ---------------------------------------------------------------- forecast */
+
+/*
+ * Deaths forecast (Sec. 4.2): for each of k parameter vectors (host, row-major [k][P]),
+ * integrates the window and `horizon` more days with the last transmission rate, gamma
+ * and mu, and writes D on days n_obs .. n_obs+horizon-1 of the window's numbering to
+ * out_D (host, [k][horizon]).  precision 32 or 64.  Blocks until out_D is written.
+ */
+sird_status sird_forecast(const sird_problem* problem, const double* theta, int k, int horizon,
+                          double* out_D, int precision, void* cuda_stream);
+
+/* ---------------------------------------------------------------- batched */
+
+/*
+ * Calibrates W windows in one persistent launch (the rolling windows of Sec. 3.1).
+ * problems[W], configs[W] are host arrays; every window must share beta_form, K,
+ * steps_per_day, cost, objective, fit_I0, precision (32), w, c1, c2, iters and the
+ * bounds; n_obs, observations, N, I0, R0, particles (<= 2048), seed and stream_id may
+ * differ.  Results go to results[W] (host).  Blocks until done.
+ */
+sird_status sird_pso_calibrate_batched(int W, const sird_problem* problems, const sird_pso_config* configs,
+                                       void* cuda_stream, sird_result* results);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -402,23 +402,29 @@ static void set_gbest(const orc_pso_cfg* cfg, orc_pso_state* st) {
     memcpy(st->gbest, st->pbest + (size_t)g * cfg->P, sizeof(double) * cfg->P);
 }
 
-static void draw(const orc_pso_cfg* cfg, int p, int d, int iter, uint32_t r[4]) {
-    uint32_t ctr[4] = {(uint32_t)p, (uint32_t)d, (uint32_t)iter, cfg->stream};
+/* Philox counter layout: (particle, iteration, dimension pair, stream word).  One
+ * call gives four words; dimension d uses words 2*(d%2) and 2*(d%2)+1 as its (r1, r2)
+ * (at iteration 0: the position and velocity draws). */
+static void draw(const orc_pso_cfg* cfg, int p, int d, int iter, double* u_a, double* u_b) {
+    uint32_t ctr[4] = {(uint32_t)p, (uint32_t)iter, (uint32_t)(d >> 1), cfg->stream};
     uint32_t key[2] = {(uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32)};
+    uint32_t r[4];
     orc_philox4x32_10(ctr, key, r);
+    *u_a = orc_u01(r[2 * (d & 1)]);
+    *u_b = orc_u01(r[2 * (d & 1) + 1]);
 }
 
 void orc_pso_init(const orc_pso_cfg* cfg, const orc_problem* pb, orc_pso_state* st) {
     int M = cfg->M, P = cfg->P;
     for (int p = 0; p < M; ++p) {
         for (int d = 0; d < P; ++d) {
-            uint32_t r[4];
-            draw(cfg, p, d, 0, r);
+            double ua, ub;
+            draw(cfg, p, d, 0, &ua, &ub);
             double range = cfg->zub[d] - cfg->zlb[d];
-            double x = store(cfg, cfg->zlb[d] + range * orc_u01(r[0]));
+            double x = store(cfg, cfg->zlb[d] + range * ua);
             if (x > cfg->zub[d]) x = cfg->zub[d];
             st->x[(size_t)p * P + d] = x;
-            st->v[(size_t)p * P + d] = store(cfg, range * (2.0 * orc_u01(r[1]) - 1.0));
+            st->v[(size_t)p * P + d] = store(cfg, range * (2.0 * ub - 1.0));
         }
         st->pbest_f[p] = store(cfg, orc_objective(cfg, pb, st->x + (size_t)p * P));
     }
@@ -434,9 +440,8 @@ void orc_pso_step(const orc_pso_cfg* cfg, const orc_problem* pb, orc_pso_state* 
         double* v = st->v + (size_t)p * P;
         const double* pb_x = st->pbest + (size_t)p * P;
         for (int d = 0; d < P; ++d) {
-            uint32_t r[4];
-            draw(cfg, p, d, t, r);
-            double r1 = orc_u01(r[0]), r2 = orc_u01(r[1]);
+            double r1, r2;
+            draw(cfg, p, d, t, &r1, &r2);
             double vn = store(cfg, cfg->w * v[d] + cfg->c1 * r1 * (pb_x[d] - x[d]) + cfg->c2 * r2 * (st->gbest[d] - x[d]));
             double xn = store(cfg, x[d] + vn);
             /* out-of-bounds values are set to the bound (Sec. 3.3); the velocity is kept */

@@ -1,0 +1,84 @@
+// kernels.h -- host-side launchers of the calibration kernels (internal to the library).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sird_model.cuh"
+
+namespace sird {
+
+// Swarm in structure-of-arrays layout: entry d of particle p at [d*ld + p].
+template <typename T>
+struct SwarmDev {
+    T* x;
+    T* v;
+    T* pb;      // personal-best positions
+    T* pbf;     // [ld] personal-best values
+    T* gbest;   // [P] global-best position (written by the last block of each iteration)
+    int M, ld;
+};
+
+// Global-best bookkeeping and error word.
+struct ReduceScratch {
+    unsigned long long* gkey;  // FP32 swarms: packed (ordered loss, index), reset to ~0 after use
+    MinPair64* partial;        // FP64 swarms: per-block (loss, index)
+    unsigned int* counter;     // blocks finished in the current launch (reset by the last block)
+    int* gbest_idx;
+    void* gbest_f;             // float or double
+    unsigned* err;             // kErr* bits
+};
+
+template <typename T>
+struct PsoCoeffs {
+    T w, c1, c2;
+    T zlb[kMaxParams], zub[kMaxParams];
+    uint32_t logmask;
+    uint32_t key0, key1, stream_id;
+};
+
+// FP64 result of the re-evaluation of candidate personal bests.
+struct ResultDev {
+    double theta[kMaxParams];
+    double loss;
+    double loss_search;
+    double sse;
+    int index;
+    int count;  // candidates evaluated
+};
+
+// Observations on the device.
+struct ObsDev {
+    const float* yf;     // [n_obs]
+    const float* invyf;  // [n_obs] 1/y or 0
+    const double* yd;    // [n_obs]
+};
+
+size_t smem_bytes_f32(const WindowDev& w, const ModelDev& m, int block, bool with_theta);
+
+cudaError_t launch_eval_f32(const WindowDev& w, const ModelDev& m, const ObsDev& o, const float* theta, int ld,
+                            int M, float* loss, int block, unsigned* err, cudaStream_t s);
+cudaError_t launch_eval_f64(const WindowDev& w, const ModelDev& m, const ObsDev& o, const double* theta, int ld,
+                            int M, double* loss, int block, unsigned* err, cudaStream_t s);
+
+// One PSO iteration (iter >= 1) or the initialisation (iter == 0), fused with the global-best
+// reduction.  All blocks read sw.gbest at their start; the last block to finish rewrites it.
+cudaError_t launch_pso_f32(const WindowDev& w, const ModelDev& m, const ObsDev& o, const PsoCoeffs<float>& c,
+                           const SwarmDev<float>& sw, const ReduceScratch& r, int iter, int block, cudaStream_t s);
+cudaError_t launch_pso_f64(const WindowDev& w, const ModelDev& m, const ObsDev& o, const PsoCoeffs<double>& c,
+                           const SwarmDev<double>& sw, const ReduceScratch& r, int iter, int block, cudaStream_t s);
+
+// Smallest k keys (packed loss, index) of the FP32 personal bests, sorted ascending, into out[k].
+// tmp_a / tmp_b need topk_scratch_keys(M, k) entries each.
+size_t topk_scratch_keys(int M, int k);
+cudaError_t launch_topk_f32(const float* pbf, int M, int k, unsigned long long* tmp_a, unsigned long long* tmp_b,
+                            unsigned long long** out, cudaStream_t s);
+
+// FP64 re-evaluation of candidates (FP32 personal bests named by keys[0..k-1], or the FP64
+// global best when keys == nullptr) and the argmin of them into *res.
+cudaError_t launch_reeval(const WindowDev& w, const ModelDev& m, const ObsDev& o, const PsoCoeffs<float>* c32,
+                          const PsoCoeffs<double>* c64, const void* pb, const void* pbf, int ld,
+                          const unsigned long long* keys, int k, const int* gbest_idx, ResultDev* res,
+                          cudaStream_t s);
+
+}  // namespace sird

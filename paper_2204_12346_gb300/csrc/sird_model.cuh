@@ -1,0 +1,270 @@
+// sird_model.cuh -- per-particle Euler integration of eq. (SIRD) and the window loss.
+//
+// One thread integrates one particle's trajectory in registers; the window's observations
+// sit in shared memory.  Two arithmetic forms:
+//
+//  FP32 (fitness_f32): the state is carried as C = N - S (everyone ever infected), I and D.
+//   Per step, with cb = dt*beta/N, a = dt*(gamma+mu), dm = dt*mu and S = N - C:
+//       g = cb*S - a ;  C += cb*I*S ;  D += dm*I ;  I += g*I
+//   which is the explicit Euler step of eq. (SIRD) rearranged (R is not needed for F_D: it
+//   only receives gamma*I).  Over thousands of steps plain FP32 rounding of these updates
+//   drifts by more than 1e-5 in the loss, so the state is compensated where it pays:
+//     - I: the rounding error of r = fma(g, I, I) is recovered exactly as fma(g, I, I - r)
+//       (I - r is exact) and summed into a low part that is folded back once a day;
+//     - C and D: the day's increments are summed apart from the totals and folded in once a
+//       day, C with an exact TwoSum into a (hi, lo) pair;
+//     - the loss is a Kahan sum.
+//   Nine FP32 instructions per step; the dependence chain through I is one FMA per step.
+//
+//  FP64 (fitness_f64): S, I, D in double precision in the paper's own operation order, with
+//   no contraction into FMA, so the trajectory is the one the equations prescribe bit for bit.
+//
+// Window and coefficient conventions (Sec. 3.1): n = tau+1 observations on days 0..L, Euler
+// starts from D0 = y_0, observation i is compared with the state after i*spd steps,
+// e_i = y_i - Dhat_i.  PWC segment j covers steps [ceil(j*S/K), ceil((j+1)*S/K)).
+#pragma once
+
+#include <climits>
+
+#include "device_common.cuh"
+
+namespace sird {
+
+enum : int { COST_MSE = 0, COST_MXSE = 1, COST_MAE = 2, COST_MAPE = 3 };
+enum : int { BETA_PWC = 0, BETA_RAMP = 1 };
+
+// Window constants shared by every particle of a launch.
+struct WindowDev {
+    int n_obs;      // tau+1
+    int n_kept;     // observations with y != 0 (MAPE denominator)
+    double N, I0, R0, D0, dt;
+    float Nh, Nl;       // N = Nh + Nl
+    float RD0h, RD0l;   // R0 + D0 = RD0h + RD0l
+    float I0f;
+    float cbn_h, cbn_l; // dt/N = cbn_h + cbn_l
+    float dt_h, dt_l;   // dt = dt_h + dt_l
+};
+
+struct ModelDev {
+    int P, K, spd, beta_form, fit_I0, cost;
+};
+
+// First step of PWC segment j: ceil(j*steps/K).
+__device__ __forceinline__ int segment_start(int j, int steps, int K) {
+    return (int)(((long long)j * steps + K - 1) / K);
+}
+
+// ---------------------------------------------------------------- FP32
+
+template <int COST>
+struct LossF32 {
+    Kahan sum;
+    float mx = 0.f;
+    __device__ __forceinline__ void add(float e, float invy) {
+        if (COST == COST_MSE) sum.add(__fmul_rn(e, e));
+        else if (COST == COST_MAE) sum.add(fabsf(e));
+        else if (COST == COST_MAPE) sum.add(__fmul_rn(fabsf(e), invy));
+        else mx = fmaxf(mx, __fmul_rn(e, e));
+    }
+    __device__ __forceinline__ float result(int n, int n_kept) const {
+        if (COST == COST_MSE || COST == COST_MAE) return __fdiv_rn(sum.sum, (float)n);
+        if (COST == COST_MAPE) return n_kept > 0 ? __fdiv_rn(__fmul_rn(100.f, sum.sum), (float)n_kept) : 0.f;
+        return mx;
+    }
+};
+
+// One Euler step in the C-form (see the file comment).  cday / dday are the day's increments;
+// Il collects the rounding errors of I.
+__device__ __forceinline__ void euler_f32(float cb, float a, float dm, float Sday, float& cday, float& dday,
+                                          float& I, float& Il) {
+    const float S = __fsub_rn(Sday, cday);
+    const float g = __fmaf_rn(cb, S, -a);
+    const float t = __fmul_rn(cb, I);
+    cday = __fmaf_rn(t, S, cday);
+    dday = __fmaf_rn(dm, I, dday);
+    const float r = __fmaf_rn(g, I, I);
+    Il = __fmaf_rn(g, I, __fadd_rn(Il, __fsub_rn(I, r)));
+    I = r;
+}
+
+// Folds the day's increments into the totals and returns e_i = y_i - Dhat_i.
+struct DayStateF32 {
+    float Ch, Cl, Sday, Dh;
+    __device__ __forceinline__ void init(const WindowDev& w, float I0, float y0) {
+        two_sum(I0, w.RD0h, Ch, Cl);
+        Cl = __fadd_rn(Cl, w.RD0l);
+        Sday = __fadd_rn(__fsub_rn(w.Nh, Ch), __fsub_rn(w.Nl, Cl));
+        Dh = y0;
+    }
+    __device__ __forceinline__ float close_day(const WindowDev& w, float cday, float dday, float y, float& I,
+                                               float& Il) {
+        // I: fold the low part in (|I| >= |Il|, so Fast2Sum is exact)
+        const float si = __fadd_rn(I, Il);
+        Il = __fsub_rn(Il, __fsub_rn(si, I));
+        I = si;
+        float s, e;
+        two_sum(Ch, cday, s, e);
+        Ch = s;
+        Cl = __fadd_rn(Cl, e);
+        Sday = __fadd_rn(__fsub_rn(w.Nh, Ch), __fsub_rn(w.Nl, Cl));
+        Dh = __fadd_rn(Dh, dday);
+        return __fsub_rn(y, Dh);
+    }
+};
+
+// Loss of one parameter vector, theta_d at th[d*stride].  ys / invys: observations and their
+// reciprocals (0 where y == 0) in shared memory.  SPD > 0 fixes steps per day at compile time.
+template <int SPD, int COST>
+__device__ float fitness_f32(const WindowDev& w, const ModelDev& m, const float* __restrict__ ys,
+                             const float* __restrict__ invys, const float* th, int stride) {
+    const int spd = SPD > 0 ? SPD : m.spd;
+    const int L = w.n_obs - 1;
+    const int steps = L * spd;
+    const int gi = (m.beta_form == BETA_RAMP) ? 4 : m.K;
+    const float gam = th[gi * stride], mu = th[(gi + 1) * stride];
+    float I = m.fit_I0 ? th[(gi + 2) * stride] : w.I0f;
+    float Il = 0.f;
+    const float gm = __fadd_rn(gam, mu);
+    const float a = __fmaf_rn(gm, w.dt_h, __fmul_rn(gm, w.dt_l));
+    const float dm = __fmaf_rn(mu, w.dt_h, __fmul_rn(mu, w.dt_l));
+    DayStateF32 ds;
+    ds.init(w, I, ys[0]);
+    LossF32<COST> loss;  // day 0: e_0 = y_0 - D_0 = 0 contributes nothing
+
+    if (m.beta_form == BETA_RAMP) {
+        // eq. (beta): beta1 before t1, linear to beta2 on [t1, t2), beta2 after (t1 <= t2 by swap)
+        const float b1 = th[0], b2 = th[stride];
+        const float ta = th[2 * stride], tb = th[3 * stride];
+        const float t1 = fminf(ta, tb), t2 = fmaxf(ta, tb);
+        const float slope = (t2 > t1) ? __fdiv_rn(__fsub_rn(b2, b1), __fsub_rn(t2, t1)) : 0.f;
+        const float dtf = __fadd_rn(w.dt_h, w.dt_l);
+        int k = 0;
+        for (int day = 1; day <= L; ++day) {
+            float cday = 0.f, dday = 0.f;
+            for (int s = 0; s < spd; ++s, ++k) {
+                const float t = __fmul_rn((float)k, dtf);
+                float beta = (t < t1) ? b1 : ((t < t2) ? __fmaf_rn(slope, __fsub_rn(t, t1), b1) : b2);
+                const float cb = __fmaf_rn(beta, w.cbn_h, __fmul_rn(beta, w.cbn_l));
+                euler_f32(cb, a, dm, ds.Sday, cday, dday, I, Il);
+            }
+            loss.add(ds.close_day(w, cday, dday, ys[day], I, Il), COST == COST_MAPE ? invys[day] : 0.f);
+        }
+        return loss.result(w.n_obs, w.n_kept);
+    }
+
+    const int K = m.K;
+    int seg = 0;
+    float b = th[0];
+    float cb = __fmaf_rn(b, w.cbn_h, __fmul_rn(b, w.cbn_l));
+    int next_b = (K > 1) ? segment_start(1, steps, K) : INT_MAX;
+    int k = 0;
+    for (int day = 1; day <= L; ++day) {
+        float cday = 0.f, dday = 0.f;
+        if (next_b < k + spd) {  // a segment starts inside this day (same for the whole block)
+            for (int s = 0; s < spd; ++s, ++k) {
+                while (k == next_b) {  // several segments may start on one step when K > steps
+                    ++seg;
+                    b = th[seg * stride];
+                    cb = __fmaf_rn(b, w.cbn_h, __fmul_rn(b, w.cbn_l));
+                    next_b = (seg + 1 < K) ? segment_start(seg + 1, steps, K) : INT_MAX;
+                }
+                euler_f32(cb, a, dm, ds.Sday, cday, dday, I, Il);
+            }
+        } else {
+            if (SPD > 0) {
+#pragma unroll
+                for (int s = 0; s < (SPD > 0 ? SPD : 1); ++s) euler_f32(cb, a, dm, ds.Sday, cday, dday, I, Il);
+            } else {
+                for (int s = 0; s < spd; ++s) euler_f32(cb, a, dm, ds.Sday, cday, dday, I, Il);
+            }
+            k += spd;
+        }
+        loss.add(ds.close_day(w, cday, dday, ys[day], I, Il), COST == COST_MAPE ? invys[day] : 0.f);
+    }
+    return loss.result(w.n_obs, w.n_kept);
+}
+
+// ---------------------------------------------------------------- FP64
+
+template <int COST>
+struct LossF64 {
+    double acc = 0.0, sse = 0.0;
+    __device__ __forceinline__ void add(double y, double yhat) {
+        const double e = __dsub_rn(y, yhat);
+        const double e2 = __dmul_rn(e, e);
+        sse = __dadd_rn(sse, e2);
+        if (COST == COST_MSE) acc = __dadd_rn(acc, e2);
+        else if (COST == COST_MXSE) { if (e2 > acc) acc = e2; }
+        else if (COST == COST_MAE) acc = __dadd_rn(acc, fabs(e));
+        else if (y != 0.0) acc = __dadd_rn(acc, fabs(__ddiv_rn(e, y)));
+    }
+    __device__ __forceinline__ double result(int n, int n_kept) const {
+        if (COST == COST_MSE || COST == COST_MAE) return __ddiv_rn(acc, (double)n);
+        if (COST == COST_MAPE) return n_kept > 0 ? __ddiv_rn(__dmul_rn(100.0, acc), (double)n_kept) : 0.0;
+        return acc;
+    }
+};
+
+// Loss of one parameter vector in FP64 (theta_d at th[d*stride]); *sse_out gets sum e_i^2.
+// Observation i is compared after i*spd steps; the sum runs over days in order.
+template <int COST>
+__device__ double fitness_f64(const WindowDev& w, const ModelDev& m, const double* __restrict__ ys,
+                              const double* th, int stride, double* sse_out) {
+    const int spd = m.spd;
+    const int L = w.n_obs - 1;
+    const int steps = L * spd;
+    const int gi = (m.beta_form == BETA_RAMP) ? 4 : m.K;
+    const double gam = th[gi * stride], mu = th[(gi + 1) * stride];
+    const double I0 = m.fit_I0 ? th[(gi + 2) * stride] : w.I0;
+    const double gm = __dadd_rn(gam, mu);
+    const double dt = w.dt;
+    double S = __dsub_rn(__dsub_rn(__dsub_rn(w.N, I0), w.R0), w.D0);
+    double I = I0, D = w.D0;
+    LossF64<COST> loss;
+    loss.add(ys[0], D);
+
+    const bool ramp = (m.beta_form == BETA_RAMP);
+    double rb1 = 0, rb2 = 0, rt1 = 0, rt2 = 0;
+    if (ramp) {
+        rb1 = th[0];
+        rb2 = th[stride];
+        const double ta = th[2 * stride], tb = th[3 * stride];
+        rt1 = ta < tb ? ta : tb;
+        rt2 = ta < tb ? tb : ta;
+    }
+    const int K = ramp ? 1 : m.K;
+    int seg = 0;
+    double bN = 0.0;
+    int prev_seg = -1;
+    int next_b = (!ramp && K > 1) ? segment_start(1, steps, K) : INT_MAX;
+    for (int k = 0; k < steps; ++k) {
+        if (ramp) {
+            const double t = __ddiv_rn((double)k, (double)spd);
+            double beta;
+            if (t < rt1) beta = rb1;
+            else if (t < rt2) beta = __dadd_rn(rb1, __dmul_rn(__ddiv_rn(__dsub_rn(rb2, rb1), __dsub_rn(rt2, rt1)),
+                                                              __dsub_rn(t, rt1)));
+            else beta = rb2;
+            bN = __ddiv_rn(beta, w.N);
+        } else {
+            while (k == next_b) {
+                ++seg;
+                next_b = (seg + 1 < K) ? segment_start(seg + 1, steps, K) : INT_MAX;
+            }
+            if (k == 0 || seg != prev_seg) bN = __ddiv_rn(th[seg * stride], w.N);
+            prev_seg = seg;
+        }
+        // eq. (SIRD): fS = -(beta/N) S I, fI = (beta/N) I S - (gamma+mu) I, fD = mu I
+        const double fS = __dmul_rn(__dmul_rn(-bN, S), I);
+        const double fI = __dsub_rn(__dmul_rn(__dmul_rn(bN, I), S), __dmul_rn(gm, I));
+        const double fD = __dmul_rn(mu, I);
+        S = __dadd_rn(S, __dmul_rn(dt, fS));
+        I = __dadd_rn(I, __dmul_rn(dt, fI));
+        D = __dadd_rn(D, __dmul_rn(dt, fD));
+        if ((k + 1) % spd == 0) loss.add(ys[(k + 1) / spd], D);
+    }
+    if (sse_out) *sse_out = loss.sse;
+    return loss.result(w.n_obs, w.n_kept);
+}
+
+}  // namespace sird

@@ -1,0 +1,590 @@
+// sird_pso_api.cu -- the C ABI (include/sird_pso.h): validation, device memory, graphs.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sird_pso.h"
+#include "kernels.h"
+
+using namespace sird;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Split {
+    float h, l;
+};
+Split split(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+constexpr uint32_t kStateMagic = 0x44524953u;  // "SIRD"
+constexpr uint32_t kStateVersion = 1;
+
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t M, P, precision, iter, gbest_idx, reserved;
+    uint64_t seed;
+    uint32_t stream_id, reserved2;
+};
+
+int nparams_of(const sird_problem* pb) {
+    return (pb->beta_form == SIRD_BETA_RAMP ? 6 : pb->K + 2) + (pb->fit_I0 ? 1 : 0);
+}
+
+}  // namespace
+
+struct sird_pso {
+    // problem
+    WindowDev win{};
+    ModelDev mdl{};
+    double ss_tot = 0.0;  // sum (y - mean y)^2 of the observed deaths, for R^2
+    // configuration
+    int M = 0, ld = 0, P = 0, iters = 0, precision = 32, block = 128, reeval_k = 0;
+    PsoCoeffs<float> c32{};
+    PsoCoeffs<double> c64{};
+    uint64_t seed = 0;
+    uint32_t stream_id = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;  // library-owned stream the calibration graph is captured on
+    int iter = -1;  // completed iterations; -1 before init
+    // device memory
+    void* d_mem = nullptr;   // swarm
+    void* d_obs = nullptr;   // observations
+    void* d_aux = nullptr;   // reduction scratch, top-k keys, result
+    ObsDev obs{};
+    void *x = nullptr, *v = nullptr, *pb = nullptr, *pbf = nullptr, *gbest = nullptr;
+    ReduceScratch red{};
+    unsigned long long *tk_a = nullptr, *tk_b = nullptr;
+    ResultDev* d_res = nullptr;
+    ResultDev* h_res = nullptr;  // pinned
+    cudaGraphExec_t calib = nullptr;
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // optional timing events (sird_pso_set_timing)
+    double* h_stage = nullptr;                          // pinned staging for observation uploads
+    int n_obs = 0;
+    // errors
+    sird_status sticky = SIRD_OK;
+    std::string msg;
+
+    sird_status fail(sird_status s, const std::string& m) {
+        if (sticky == SIRD_OK) {
+            sticky = s;
+            msg = m;
+        }
+        return s;
+    }
+    sird_status cuda(cudaError_t e, const char* what) {
+        if (e == cudaSuccess) return SIRD_OK;
+        (void)cudaGetLastError();  // the status now lives in the handle; do not leak it into later launches
+        return fail(SIRD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+
+    SwarmDev<float> sw32() const {
+        return {(float*)x, (float*)v, (float*)pb, (float*)pbf, (float*)gbest, M, ld};
+    }
+    SwarmDev<double> sw64() const {
+        return {(double*)x, (double*)v, (double*)pb, (double*)pbf, (double*)gbest, M, ld};
+    }
+
+    cudaError_t enqueue_iter(int t, cudaStream_t s) {
+        if (precision == 32) return launch_pso_f32(win, mdl, obs, c32, sw32(), red, t, block, s);
+        return launch_pso_f64(win, mdl, obs, c64, sw64(), red, t, block, s);
+    }
+    cudaError_t enqueue_result(cudaStream_t s) {
+        if (precision == 32 && reeval_k > 0) {
+            unsigned long long* keys = nullptr;
+            cudaError_t e = launch_topk_f32((const float*)pbf, M, reeval_k, tk_a, tk_b, &keys, s);
+            if (e != cudaSuccess) return e;
+            e = launch_reeval(win, mdl, obs, &c32, nullptr, pb, pbf, ld, keys, reeval_k, nullptr, d_res, s);
+            if (e != cudaSuccess) return e;
+        } else {
+            cudaError_t e = launch_reeval(win, mdl, obs, precision == 32 ? &c32 : nullptr,
+                                          precision == 64 ? &c64 : nullptr, pb, pbf, ld, nullptr, 1, red.gbest_idx,
+                                          d_res, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaMemcpyAsync(h_res, d_res, sizeof(ResultDev), cudaMemcpyDeviceToHost, s);
+    }
+    void fill_result(sird_result* out) const {
+        std::memset(out, 0, sizeof(*out));
+        out->n_params = P;
+        for (int d = 0; d < P; ++d) out->theta[d] = h_res->theta[d];
+        out->loss = h_res->loss;
+        out->loss_search = h_res->loss_search;
+        out->r2_D = ss_tot > 0 ? 1.0 - h_res->sse / ss_tot : NAN;
+        out->index = h_res->index;
+        out->iters_done = iter;
+    }
+};
+
+// ---------------------------------------------------------------- validation
+
+static sird_status check_problem(const sird_problem* pb, std::string& why) {
+    if (!pb) return why = "problem is NULL", SIRD_ERR_ARG;
+    if (pb->n_obs < 2 || pb->n_obs > SIRD_MAX_OBS) return why = "n_obs out of range [2, SIRD_MAX_OBS]", SIRD_ERR_ARG;
+    if (!pb->y_D) return why = "y_D is NULL", SIRD_ERR_ARG;
+    for (int i = 0; i < pb->n_obs; ++i)
+        if (!std::isfinite(pb->y_D[i])) return why = "non-finite observation in y_D", SIRD_ERR_ARG;
+    if (!(pb->N > 0) || !std::isfinite(pb->N)) return why = "N must be finite and positive", SIRD_ERR_ARG;
+    if (!std::isfinite(pb->R0) || !std::isfinite(pb->I0)) return why = "I0/R0 must be finite", SIRD_ERR_ARG;
+    if (pb->steps_per_day < 1 || pb->steps_per_day > 1000) return why = "steps_per_day out of range [1, 1000]", SIRD_ERR_ARG;
+    if ((long long)(pb->n_obs - 1) * pb->steps_per_day > (1LL << 30)) return why = "too many Euler steps", SIRD_ERR_ARG;
+    if (pb->beta_form != SIRD_BETA_PWC && pb->beta_form != SIRD_BETA_RAMP) return why = "unknown beta_form", SIRD_ERR_ARG;
+    if (pb->beta_form == SIRD_BETA_PWC && (pb->K < 1 || pb->K > SIRD_MAX_PARAMS - 3))
+        return why = "K out of range [1, SIRD_MAX_PARAMS-3]", SIRD_ERR_ARG;
+    if (pb->cost < SIRD_COST_MSE || pb->cost > SIRD_COST_MAPE) return why = "unknown cost", SIRD_ERR_ARG;
+    if (pb->fit_I0 != 0 && pb->fit_I0 != 1) return why = "fit_I0 must be 0 or 1", SIRD_ERR_ARG;
+    if (pb->objective == SIRD_FIT_IRD) return why = "F_IRD objective is not implemented on the GPU yet", SIRD_ERR_UNSUPPORTED;
+    if (pb->objective != SIRD_FIT_D) return why = "unknown objective", SIRD_ERR_ARG;
+    return SIRD_OK;
+}
+
+static void fill_window(const sird_problem* pb, WindowDev& w, ModelDev& m) {
+    const int n = pb->n_obs;
+    w.n_obs = n;
+    w.n_kept = 0;
+    for (int i = 0; i < n; ++i) w.n_kept += (pb->y_D[i] != 0.0);
+    w.N = pb->N;
+    w.I0 = pb->I0;
+    w.R0 = pb->R0;
+    w.D0 = pb->y_D[0];
+    w.dt = 1.0 / (double)pb->steps_per_day;
+    Split s = split(pb->N);
+    w.Nh = s.h;
+    w.Nl = s.l;
+    s = split(pb->R0 + pb->y_D[0]);
+    w.RD0h = s.h;
+    w.RD0l = s.l;
+    w.I0f = (float)pb->I0;
+    s = split(w.dt / pb->N);
+    w.cbn_h = s.h;
+    w.cbn_l = s.l;
+    s = split(w.dt);
+    w.dt_h = s.h;
+    w.dt_l = s.l;
+    m.P = nparams_of(pb);
+    m.K = pb->beta_form == SIRD_BETA_PWC ? pb->K : 1;
+    m.spd = pb->steps_per_day;
+    m.beta_form = pb->beta_form;
+    m.fit_I0 = pb->fit_I0;
+    m.cost = pb->cost;
+}
+
+// Observations to the device: float copy, float reciprocals (0 where y == 0), double copy.
+static cudaError_t upload_obs(const sird_problem* pb, void** mem, ObsDev& o, cudaStream_t s) {
+    const int n = pb->n_obs;
+    const size_t nf = (size_t)((n + 3) & ~3);
+    const size_t bytes = nf * 2 * sizeof(float) + (size_t)n * sizeof(double);
+    cudaError_t e = cudaMalloc(mem, bytes);
+    if (e != cudaSuccess) return e;
+    std::vector<unsigned char> host(bytes, 0);
+    float* yf = (float*)host.data();
+    float* inv = yf + nf;
+    double* yd = (double*)(inv + nf);
+    for (int i = 0; i < n; ++i) {
+        yf[i] = (float)pb->y_D[i];
+        inv[i] = pb->y_D[i] != 0.0 ? (float)(1.0 / pb->y_D[i]) : 0.f;
+        yd[i] = pb->y_D[i];
+    }
+    e = cudaMemcpyAsync(*mem, host.data(), bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    o.yf = (const float*)*mem;
+    o.invyf = o.yf + nf;
+    o.yd = (const double*)(o.invyf + nf);
+    return e;
+}
+
+// ---------------------------------------------------------------- lifetime
+
+extern "C" sird_status sird_pso_create(const sird_problem* pb, const sird_pso_config* cfg, void* cuda_stream,
+                                       sird_pso_t* out) {
+    if (!out) return g_create_error = "out is NULL", SIRD_ERR_ARG;
+    *out = nullptr;
+    std::string why;
+    sird_status st = check_problem(pb, why);
+    if (st != SIRD_OK) return g_create_error = why, st;
+    if (!cfg) return g_create_error = "config is NULL", SIRD_ERR_ARG;
+    const int P = nparams_of(pb);
+    if (P > SIRD_MAX_PARAMS) return g_create_error = "too many parameters", SIRD_ERR_ARG;
+    if (cfg->particles < 1 || cfg->particles > SIRD_MAX_PARTICLES) return g_create_error = "particles out of range", SIRD_ERR_ARG;
+    if (cfg->iters < 0) return g_create_error = "iters < 0", SIRD_ERR_ARG;
+    if (cfg->precision != 32 && cfg->precision != 64) return g_create_error = "precision must be 32 or 64", SIRD_ERR_ARG;
+    if (!cfg->lb || !cfg->ub) return g_create_error = "lb/ub is NULL", SIRD_ERR_ARG;
+    if (cfg->block_size != 0 && (cfg->block_size < 32 || cfg->block_size > 1024 || cfg->block_size % 32))
+        return g_create_error = "block_size must be 0 or a multiple of 32 in [32, 1024]", SIRD_ERR_ARG;
+    if (cfg->precision == 64 && cfg->block_size > 256) return g_create_error = "FP64 block_size must be <= 256", SIRD_ERR_ARG;
+    if (cfg->reeval_topk < 0 || cfg->reeval_topk > 1024 || cfg->reeval_topk > cfg->particles)
+        return g_create_error = "reeval_topk out of range [0, min(particles, 1024)]", SIRD_ERR_ARG;
+    for (int d = 0; d < P; ++d) {
+        const bool lg = cfg->log_scale && cfg->log_scale[d];
+        if (!std::isfinite(cfg->lb[d]) || !std::isfinite(cfg->ub[d]) || cfg->lb[d] > cfg->ub[d])
+            return g_create_error = "bounds must be finite with lb <= ub", SIRD_ERR_ARG;
+        if (lg && !(cfg->lb[d] > 0)) return g_create_error = "log_scale needs lb > 0", SIRD_ERR_ARG;
+    }
+
+    sird_pso* h = new (std::nothrow) sird_pso();
+    if (!h) return g_create_error = "host allocation failed", SIRD_ERR_NOMEM;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->n_obs = pb->n_obs;
+    fill_window(pb, h->win, h->mdl);
+    {
+        double mean = 0;
+        for (int i = 0; i < pb->n_obs; ++i) mean += pb->y_D[i];
+        mean /= pb->n_obs;
+        for (int i = 0; i < pb->n_obs; ++i) h->ss_tot += (pb->y_D[i] - mean) * (pb->y_D[i] - mean);
+    }
+    h->M = cfg->particles;
+    h->ld = (cfg->particles + 31) & ~31;
+    h->P = P;
+    h->iters = cfg->iters;
+    h->precision = cfg->precision;
+    h->block = cfg->block_size ? cfg->block_size : (cfg->precision == 32 ? 128 : 64);
+    h->reeval_k = cfg->precision == 32 ? cfg->reeval_topk : 0;
+    h->seed = cfg->seed;
+    h->stream_id = cfg->stream_id;
+    uint32_t logmask = 0;
+    for (int d = 0; d < P; ++d) {
+        const bool lg = cfg->log_scale && cfg->log_scale[d];
+        if (lg) logmask |= 1u << d;
+        const double zl = lg ? std::log(cfg->lb[d]) : cfg->lb[d];
+        const double zu = lg ? std::log(cfg->ub[d]) : cfg->ub[d];
+        h->c64.zlb[d] = zl;
+        h->c64.zub[d] = zu;
+        h->c32.zlb[d] = (float)zl;
+        h->c32.zub[d] = (float)zu;
+    }
+    h->c64.w = cfg->w;
+    h->c64.c1 = cfg->c1;
+    h->c64.c2 = cfg->c2;
+    h->c32.w = (float)cfg->w;
+    h->c32.c1 = (float)cfg->c1;
+    h->c32.c2 = (float)cfg->c2;
+    h->c32.logmask = h->c64.logmask = logmask;
+    h->c32.key0 = h->c64.key0 = (uint32_t)cfg->seed;
+    h->c32.key1 = h->c64.key1 = (uint32_t)(cfg->seed >> 32);
+    h->c32.stream_id = h->c64.stream_id = cfg->stream_id;
+
+    auto bail = [&](cudaError_t e, const char* what) {
+        g_create_error = std::string(what) + ": " + cudaGetErrorString(e);
+        sird_pso_destroy(h);
+        return e == cudaErrorMemoryAllocation ? SIRD_ERR_NOMEM : SIRD_ERR_CUDA;
+    };
+    cudaError_t e = upload_obs(pb, &h->d_obs, h->obs, h->stream);
+    if (e != cudaSuccess) return bail(e, "uploading observations");
+
+    const size_t tsz = h->precision == 32 ? sizeof(float) : sizeof(double);
+    const size_t plane = (size_t)P * h->ld * tsz;
+    const size_t swarm_bytes = 3 * plane + (size_t)h->ld * tsz + SIRD_MAX_PARAMS * tsz;
+    e = cudaMalloc(&h->d_mem, swarm_bytes);
+    if (e != cudaSuccess) return bail(e, "allocating the swarm");
+    unsigned char* base = (unsigned char*)h->d_mem;
+    h->x = base;
+    h->v = base + plane;
+    h->pb = base + 2 * plane;
+    h->pbf = base + 3 * plane;
+    h->gbest = base + 3 * plane + (size_t)h->ld * tsz;
+
+    const size_t grid = (size_t)((h->M + h->block - 1) / h->block);
+    const size_t tk = h->reeval_k > 0 ? topk_scratch_keys(h->M, h->reeval_k) : 0;
+    const size_t aux_bytes = 256 + grid * sizeof(MinPair64) + 2 * tk * sizeof(unsigned long long) + sizeof(ResultDev);
+    e = cudaMalloc(&h->d_aux, aux_bytes);
+    if (e != cudaSuccess) return bail(e, "allocating scratch");
+    unsigned char* a = (unsigned char*)h->d_aux;
+    h->red.gkey = (unsigned long long*)a;
+    h->red.counter = (unsigned int*)(a + 8);
+    h->red.gbest_idx = (int*)(a + 16);
+    h->red.gbest_f = a + 24;
+    h->red.err = (unsigned*)(a + 32);
+    h->red.partial = (MinPair64*)(a + 256);
+    h->tk_a = (unsigned long long*)(a + 256 + grid * sizeof(MinPair64));
+    h->tk_b = h->tk_a + tk;
+    h->d_res = (ResultDev*)(h->tk_b + tk);
+    e = cudaMemsetAsync(h->d_aux, 0, 256, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->red.gkey, 0xFF, sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return bail(e, "initialising scratch");
+    e = cudaMallocHost((void**)&h->h_res, sizeof(ResultDev));
+    if (e != cudaSuccess) return bail(e, "allocating pinned result");
+    *out = h;
+    return SIRD_OK;
+}
+
+extern "C" void sird_pso_destroy(sird_pso_t h) {
+    if (!h) return;
+    if (h->stream || h->d_mem) cudaStreamSynchronize(h->stream);
+    if (h->calib) cudaGraphExecDestroy(h->calib);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    cudaFree(h->d_mem);
+    cudaFree(h->d_obs);
+    cudaFree(h->d_aux);
+    if (h->h_res) cudaFreeHost(h->h_res);
+    if (h->h_stage) cudaFreeHost(h->h_stage);
+    delete h;
+}
+
+extern "C" const char* sird_last_error(sird_pso_t h) {
+    if (!h) return g_create_error.c_str();
+    return h->msg.c_str();
+}
+
+extern "C" sird_status sird_pso_clear_error(sird_pso_t h) {
+    if (!h) return SIRD_ERR_ARG;
+    h->sticky = SIRD_OK;
+    h->msg.clear();
+    return SIRD_OK;
+}
+
+extern "C" sird_status sird_pso_set_stream(sird_pso_t h, void* cuda_stream) {
+    if (!h) return SIRD_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if ((cudaStream_t)cuda_stream != h->stream) {
+        sird_status s = h->cuda(cudaStreamSynchronize(h->stream), "synchronising the old stream");
+        if (s) return s;
+        h->stream = (cudaStream_t)cuda_stream;
+        if (h->calib) {
+            cudaGraphExecDestroy(h->calib);
+            h->calib = nullptr;
+        }
+    }
+    return SIRD_OK;
+}
+
+extern "C" int sird_pso_num_params(sird_pso_t h) { return h ? h->P : 0; }
+
+// ---------------------------------------------------------------- fitness
+
+extern "C" sird_status sird_pso_eval(sird_pso_t h, const void* d_theta, int M, int ld, void* d_loss, int precision) {
+    if (!h) return SIRD_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if (M < 0 || ld < M || (M > 0 && (!d_theta || !d_loss))) return h->fail(SIRD_ERR_ARG, "eval: bad M/ld/pointers");
+    if (precision != 32 && precision != 64) return h->fail(SIRD_ERR_ARG, "eval: precision must be 32 or 64");
+    if (M == 0) return SIRD_OK;
+    const int block = precision == 32 ? 128 : 64;
+    cudaError_t e = precision == 32
+                        ? launch_eval_f32(h->win, h->mdl, h->obs, (const float*)d_theta, ld, M, (float*)d_loss, block,
+                                          h->red.err, h->stream)
+                        : launch_eval_f64(h->win, h->mdl, h->obs, (const double*)d_theta, ld, M, (double*)d_loss,
+                                          block, h->red.err, h->stream);
+    return h->cuda(e, "eval launch");
+}
+
+// ---------------------------------------------------------------- swarm
+
+extern "C" sird_status sird_pso_init(sird_pso_t h) {
+    if (!h) return SIRD_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    sird_status s = h->cuda(h->enqueue_iter(0, h->stream), "init launch");
+    if (s) return s;
+    h->iter = 0;
+    return SIRD_OK;
+}
+
+extern "C" sird_status sird_pso_step(sird_pso_t h, int n_iters) {
+    if (!h) return SIRD_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if (n_iters < 0) return h->fail(SIRD_ERR_ARG, "step: n_iters < 0");
+    if (h->iter < 0) return h->fail(SIRD_ERR_STATE, "step before init/set_state");
+    for (int i = 0; i < n_iters; ++i) {
+        sird_status s = h->cuda(h->enqueue_iter(h->iter + 1, h->stream), "step launch");
+        if (s) return s;
+        ++h->iter;
+    }
+    return SIRD_OK;
+}
+
+extern "C" sird_status sird_pso_sync(sird_pso_t h) {
+    if (!h) return SIRD_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    sird_status s = h->cuda(cudaStreamSynchronize(h->stream), "sync");
+    if (s) return s;
+    unsigned err = 0;
+    s = h->cuda(cudaMemcpy(&err, h->red.err, sizeof(err), cudaMemcpyDeviceToHost), "reading the error word");
+    if (s) return s;
+    if (err & kErrTimeout) return h->fail(SIRD_ERR_TIMEOUT, "a device-side wait ran out");
+    if (err & kErrBounds) return h->fail(SIRD_ERR_ARG, "a device-side index check failed");
+    return SIRD_OK;
+}
+
+extern "C" sird_status sird_pso_set_observations(sird_pso_t h, const double* y_D, int n_obs) {
+    if (!h) return SIRD_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if (!y_D || n_obs != h->n_obs) return h->fail(SIRD_ERR_ARG, "set_observations: y_D NULL or n_obs differs");
+    for (int i = 0; i < n_obs; ++i)
+        if (!std::isfinite(y_D[i])) return h->fail(SIRD_ERR_ARG, "set_observations: non-finite observation");
+    if (y_D[0] != h->win.D0) return h->fail(SIRD_ERR_ARG, "set_observations: y_D[0] (D0) must not change");
+    const size_t nf = (size_t)((n_obs + 3) & ~3);
+    const size_t bytes = nf * 2 * sizeof(float) + (size_t)n_obs * sizeof(double);
+    sird_status s = SIRD_OK;
+    if (!h->h_stage) s = h->cuda(cudaMallocHost((void**)&h->h_stage, bytes), "allocating pinned staging");
+    if (s) return s;
+    s = h->cuda(cudaStreamSynchronize(h->stream), "sync");  // the previous upload may still read the stage
+    if (s) return s;
+    float* yf = (float*)h->h_stage;
+    float* inv = yf + nf;
+    double* yd = (double*)(inv + nf);
+    std::memset(h->h_stage, 0, bytes);
+    int kept = 0;
+    double mean = 0.0, ss = 0.0;
+    for (int i = 0; i < n_obs; ++i) {
+        yf[i] = (float)y_D[i];
+        inv[i] = y_D[i] != 0.0 ? (float)(1.0 / y_D[i]) : 0.f;
+        yd[i] = y_D[i];
+        kept += (y_D[i] != 0.0);
+        mean += y_D[i];
+    }
+    mean /= n_obs;
+    for (int i = 0; i < n_obs; ++i) ss += (y_D[i] - mean) * (y_D[i] - mean);
+    if (kept != h->win.n_kept) return h->fail(SIRD_ERR_ARG, "set_observations: the count of zero observations must not change");
+    h->ss_tot = ss;
+    return h->cuda(cudaMemcpyAsync((void*)h->obs.yf, h->h_stage, bytes, cudaMemcpyHostToDevice, h->stream),
+                   "uploading observations");
+}
+
+extern "C" sird_status sird_pso_set_timing(sird_pso_t h, void* event_iter_begin, void* event_iter_end) {
+    if (!h) return SIRD_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    h->ev_begin = (cudaEvent_t)event_iter_begin;
+    h->ev_end = (cudaEvent_t)event_iter_end;
+    if (h->calib) {
+        cudaGraphExecDestroy(h->calib);
+        h->calib = nullptr;
+    }
+    return SIRD_OK;
+}
+
+extern "C" sird_status sird_pso_result(sird_pso_t h, sird_result* out) {
+    if (!h || !out) return SIRD_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if (h->iter < 0) return h->fail(SIRD_ERR_STATE, "result before init");
+    sird_status s = h->cuda(h->enqueue_result(h->stream), "result launch");
+    if (s) return s;
+    s = sird_pso_sync(h);
+    if (s) return s;
+    h->fill_result(out);
+    return SIRD_OK;
+}
+
+extern "C" sird_status sird_pso_calibrate(sird_pso_t h, sird_result* out) {
+    if (!h || !out) return SIRD_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if (!h->calib) {
+        // captured once on a private stream (the caller's may be the legacy default stream,
+        // which cannot be captured), then launched on the caller's stream
+        if (!h->cap) {
+            sird_status s = h->cuda(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking), "capture stream");
+            if (s) return s;
+        }
+        cudaGraph_t g = nullptr;
+        sird_status s = h->cuda(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+        if (s) return s;
+        cudaError_t e = h->enqueue_iter(0, h->cap);
+        if (e == cudaSuccess && h->ev_begin) e = cudaEventRecordWithFlags(h->ev_begin, h->cap, cudaEventRecordExternal);
+        for (int t = 1; t <= h->iters && e == cudaSuccess; ++t) e = h->enqueue_iter(t, h->cap);
+        if (e == cudaSuccess && h->ev_end) e = cudaEventRecordWithFlags(h->ev_end, h->cap, cudaEventRecordExternal);
+        if (e == cudaSuccess) e = h->enqueue_result(h->cap);
+        cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->calib, g, 0);
+        if (g) cudaGraphDestroy(g);
+        s = h->cuda(e, "capturing the calibration graph");
+        if (s) return s;
+    }
+    sird_status s = h->cuda(cudaGraphLaunch(h->calib, h->stream), "graph launch");
+    if (s) return s;
+    h->iter = h->iters;
+    s = sird_pso_sync(h);
+    if (s) return s;
+    h->fill_result(out);
+    return SIRD_OK;
+}
+
+// ---------------------------------------------------------------- state
+
+extern "C" sird_status sird_pso_get_state(sird_pso_t h, void* buf, size_t* size) {
+    if (!h || !size) return SIRD_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    const size_t tsz = h->precision == 32 ? 4 : 8;
+    const size_t need = sizeof(StateHeader) + (3 * (size_t)h->P + 1) * h->M * tsz;
+    if (!buf) {
+        *size = need;
+        return SIRD_OK;
+    }
+    if (*size < need) return h->fail(SIRD_ERR_ARG, "get_state: buffer too small");
+    if (h->iter < 0) return h->fail(SIRD_ERR_STATE, "get_state before init");
+    sird_status s = h->cuda(cudaStreamSynchronize(h->stream), "sync");
+    if (s) return s;
+    StateHeader hd{kStateMagic, kStateVersion, h->M, h->P, h->precision, h->iter, 0, 0, h->seed, h->stream_id, 0};
+    s = h->cuda(cudaMemcpy(&hd.gbest_idx, h->red.gbest_idx, sizeof(int), cudaMemcpyDeviceToHost), "get_state");
+    if (s) return s;
+    unsigned char* p = (unsigned char*)buf;
+    std::memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    const size_t row = (size_t)h->M * tsz, pitch = (size_t)h->ld * tsz;
+    for (void* src : {h->x, h->v, h->pb}) {
+        s = h->cuda(cudaMemcpy2D(p, row, src, pitch, row, h->P, cudaMemcpyDeviceToHost), "get_state copy");
+        if (s) return s;
+        p += row * h->P;
+    }
+    s = h->cuda(cudaMemcpy(p, h->pbf, row, cudaMemcpyDeviceToHost), "get_state copy");
+    if (s) return s;
+    *size = need;
+    return SIRD_OK;
+}
+
+extern "C" sird_status sird_pso_set_state(sird_pso_t h, const void* buf, size_t size) {
+    if (!h || !buf) return SIRD_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    const size_t tsz = h->precision == 32 ? 4 : 8;
+    const size_t need = sizeof(StateHeader) + (3 * (size_t)h->P + 1) * h->M * tsz;
+    StateHeader hd;
+    if (size < sizeof(hd)) return h->fail(SIRD_ERR_STATE, "set_state: blob too small");
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (hd.magic != kStateMagic || hd.version != kStateVersion || hd.M != h->M || hd.P != h->P ||
+        hd.precision != h->precision || size < need || hd.iter < 0 || hd.gbest_idx < 0 || hd.gbest_idx >= h->M)
+        return h->fail(SIRD_ERR_STATE, "set_state: blob does not match this handle");
+    sird_status s = h->cuda(cudaStreamSynchronize(h->stream), "sync");
+    if (s) return s;
+    const unsigned char* p = (const unsigned char*)buf + sizeof(hd);
+    const size_t row = (size_t)h->M * tsz, pitch = (size_t)h->ld * tsz;
+    for (void* dst : {h->x, h->v, h->pb}) {
+        s = h->cuda(cudaMemcpy2D(dst, pitch, p, row, row, h->P, cudaMemcpyHostToDevice), "set_state copy");
+        if (s) return s;
+        p += row * h->P;
+    }
+    s = h->cuda(cudaMemcpy(h->pbf, p, row, cudaMemcpyHostToDevice), "set_state copy");
+    if (s) return s;
+    // global best = personal best of the recorded index
+    std::vector<unsigned char> g(tsz * h->P), gf(tsz);
+    const unsigned char* pbh = (const unsigned char*)buf + sizeof(hd) + 2 * row * h->P;
+    for (int d = 0; d < h->P; ++d) std::memcpy(&g[d * tsz], pbh + d * row + (size_t)hd.gbest_idx * tsz, tsz);
+    std::memcpy(gf.data(), p + (size_t)hd.gbest_idx * tsz, tsz);
+    s = h->cuda(cudaMemcpy(h->gbest, g.data(), g.size(), cudaMemcpyHostToDevice), "set_state gbest");
+    if (!s) s = h->cuda(cudaMemcpy(h->red.gbest_idx, &hd.gbest_idx, sizeof(int), cudaMemcpyHostToDevice), "set_state");
+    if (!s) s = h->cuda(cudaMemcpy(h->red.gbest_f, gf.data(), tsz, cudaMemcpyHostToDevice), "set_state");
+    if (s) return s;
+    h->iter = hd.iter;
+    return SIRD_OK;
+}
+
+// ---------------------------------------------------------------- not yet built
+
+extern "C" sird_status sird_loss_grad(sird_pso_t h, const void*, int, int, void*, void*, int, void*, int, int) {
+    if (!h) return SIRD_ERR_ARG;
+    return h->fail(SIRD_ERR_UNSUPPORTED, "sird_loss_grad: not built yet");
+}
+
+extern "C" sird_status sird_forecast(const sird_problem*, const double*, int, int, double*, int, void*) {
+    g_create_error = "sird_forecast: not built yet";
+    return SIRD_ERR_UNSUPPORTED;
+}
+
+extern "C" sird_status sird_pso_calibrate_batched(int, const sird_problem*, const sird_pso_config*, void*,
+                                                  sird_result*) {
+    g_create_error = "sird_pso_calibrate_batched: not built yet";
+    return SIRD_ERR_UNSUPPORTED;
+}

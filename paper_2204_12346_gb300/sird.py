@@ -1,0 +1,282 @@
+"""Python binding of the C ABI in ``include/sird_pso.h`` (argument marshalling only).
+
+Every computation runs in the CUDA library ``_build/libsird_pso.so``; this module only
+builds the C structs, passes torch device pointers and the current CUDA stream, and turns
+status codes into exceptions.  There is no CPU fallback: if the library cannot be loaded,
+``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAX_PARAMS = 32
+OK, ERR_ARG, ERR_CUDA, ERR_NUMERIC, ERR_TIMEOUT, ERR_STATE, ERR_NOMEM, ERR_UNSUPPORTED = range(8)
+STATUS_NAMES = ["OK", "ERR_ARG", "ERR_CUDA", "ERR_NUMERIC", "ERR_TIMEOUT", "ERR_STATE", "ERR_NOMEM", "ERR_UNSUPPORTED"]
+COST_MSE, COST_MXSE, COST_MAE, COST_MAPE = 0, 1, 2, 3
+COSTS = {"mse": COST_MSE, "mxse": COST_MXSE, "mae": COST_MAE, "mape": COST_MAPE}
+BETA_PWC, BETA_RAMP = 0, 1
+FIT_D, FIT_IRD = 0, 1
+
+# Symbols the header declares (checked by the ABI test).
+EXPORTS = [
+    "sird_pso_create", "sird_pso_destroy", "sird_last_error", "sird_pso_clear_error", "sird_pso_set_stream",
+    "sird_pso_num_params", "sird_pso_eval", "sird_pso_init", "sird_pso_step", "sird_pso_calibrate",
+    "sird_pso_result", "sird_pso_sync", "sird_pso_get_state", "sird_pso_set_state", "sird_loss_grad",
+    "sird_forecast", "sird_pso_calibrate_batched", "sird_pso_set_observations", "sird_pso_set_timing",
+]
+
+
+class SirdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class Problem(C.Structure):
+    _fields_ = [
+        ("n_obs", C.c_int), ("y_D", C.POINTER(C.c_double)), ("y_I", C.POINTER(C.c_double)),
+        ("y_R", C.POINTER(C.c_double)), ("N", C.c_double), ("I0", C.c_double), ("R0", C.c_double),
+        ("fit_I0", C.c_int), ("beta_form", C.c_int), ("K", C.c_int), ("steps_per_day", C.c_int),
+        ("cost", C.c_int), ("objective", C.c_int),
+    ]
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("particles", C.c_int), ("iters", C.c_int), ("w", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
+        ("lb", C.POINTER(C.c_double)), ("ub", C.POINTER(C.c_double)), ("log_scale", C.POINTER(C.c_int)),
+        ("precision", C.c_int), ("seed", C.c_uint64), ("stream_id", C.c_uint32), ("reeval_topk", C.c_int),
+        ("block_size", C.c_int),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [
+        ("n_params", C.c_int), ("theta", C.c_double * MAX_PARAMS), ("loss", C.c_double),
+        ("loss_search", C.c_double), ("r2_D", C.c_double), ("index", C.c_int), ("iters_done", C.c_int),
+    ]
+
+    def as_dict(self) -> dict:
+        return {"theta": np.array(self.theta[: self.n_params]), "loss": self.loss, "loss_search": self.loss_search,
+                "r2_D": self.r2_D, "index": self.index, "iters_done": self.iters_done}
+
+
+_lib = None
+
+
+def lib():
+    """Loads (building first if needed) the CUDA library.  Raises if it cannot."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not _build.up_to_date():
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not found at {path}")
+        L = C.CDLL(path)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+        L.sird_pso_create.argtypes = [C.POINTER(Problem), C.POINTER(Config), vp, C.POINTER(vp)]
+        L.sird_pso_destroy.argtypes = [vp]
+        L.sird_pso_destroy.restype = None
+        L.sird_last_error.argtypes = [vp]
+        L.sird_last_error.restype = C.c_char_p
+        L.sird_pso_clear_error.argtypes = [vp]
+        L.sird_pso_set_stream.argtypes = [vp, vp]
+        L.sird_pso_num_params.argtypes = [vp]
+        L.sird_pso_eval.argtypes = [vp, vp, ip, ip, vp, ip]
+        L.sird_pso_init.argtypes = [vp]
+        L.sird_pso_step.argtypes = [vp, ip]
+        L.sird_pso_calibrate.argtypes = [vp, C.POINTER(Result)]
+        L.sird_pso_result.argtypes = [vp, C.POINTER(Result)]
+        L.sird_pso_sync.argtypes = [vp]
+        L.sird_pso_get_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+        L.sird_pso_set_state.argtypes = [vp, vp, C.c_size_t]
+        L.sird_loss_grad.argtypes = [vp, vp, ip, ip, vp, vp, ip, vp, ip, ip]
+        L.sird_forecast.argtypes = [C.POINTER(Problem), dp, ip, ip, dp, ip, vp]
+        L.sird_pso_calibrate_batched.argtypes = [ip, C.POINTER(Problem), C.POINTER(Config), vp, C.POINTER(Result)]
+        L.sird_pso_set_observations.argtypes = [vp, dp, ip]
+        L.sird_pso_set_timing.argtypes = [vp, vp, vp]
+        _lib = L
+    return _lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def current_stream_handle(stream=None) -> int:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def make_problem(yD, N, K=1, spd=10, R0=0.0, I0=0.0, fit_I0=True, beta_form=BETA_PWC, cost=COST_MSE,
+                 objective=FIT_D, yI=None, yR=None):
+    """Builds a Problem struct; the returned keep-alive list must outlive the call that uses it."""
+    yD = _f64(yD)
+    keep = [yD]
+    null = C.POINTER(C.c_double)()
+    pI = pR = null
+    if yI is not None:
+        yI = _f64(yI)
+        keep.append(yI)
+        pI = _dptr(yI)
+    if yR is not None:
+        yR = _f64(yR)
+        keep.append(yR)
+        pR = _dptr(yR)
+    pb = Problem(len(yD), _dptr(yD), pI, pR, float(N), float(I0), float(R0), int(fit_I0), int(beta_form), int(K),
+                 int(spd), int(cost), int(objective))
+    return pb, keep
+
+
+def make_config(particles, iters, lb, ub, log_scale=None, w=0.5, c1=0.5, c2=0.5, precision=32, seed=0,
+                stream_id=0, reeval_topk=0, block_size=0):
+    lb, ub = _f64(lb), _f64(ub)
+    keep = [lb, ub]
+    lsp = C.POINTER(C.c_int)()
+    if log_scale is not None:
+        ls = np.ascontiguousarray(np.asarray(log_scale, dtype=np.int32))
+        keep.append(ls)
+        lsp = ls.ctypes.data_as(C.POINTER(C.c_int))
+    cfg = Config(int(particles), int(iters), float(w), float(c1), float(c2), _dptr(lb), _dptr(ub), lsp,
+                 int(precision), int(seed) & (2**64 - 1), int(stream_id) & 0xFFFFFFFF, int(reeval_topk),
+                 int(block_size))
+    return cfg, keep
+
+
+class Calibrator:
+    """One calibration window and its swarm on the GPU (wraps a sird_pso_t handle)."""
+
+    def __init__(self, yD, N, *, K=1, spd=10, R0=0.0, I0=0.0, fit_I0=True, beta_form=BETA_PWC, cost=COST_MSE,
+                 particles=64, iters=100, lb=None, ub=None, log_scale=None, w=0.5, c1=0.5, c2=0.5, precision=32,
+                 seed=0, stream_id=0, reeval_topk=0, block_size=0, stream=None):
+        self._lib = lib()
+        self.problem, k1 = make_problem(yD, N, K, spd, R0, I0, fit_I0, beta_form, cost)
+        self.config, k2 = make_config(particles, iters, lb, ub, log_scale, w, c1, c2, precision, seed, stream_id,
+                                      reeval_topk, block_size)
+        self._keep = k1 + k2
+        self.precision = int(precision)
+        self.M = int(particles)
+        h = C.c_void_p()
+        st = self._lib.sird_pso_create(C.byref(self.problem), C.byref(self.config),
+                                       C.c_void_p(current_stream_handle(stream)), C.byref(h))
+        if st != OK:
+            raise SirdError(st, self._lib.sird_last_error(None).decode())
+        self.h = h
+        self.P = self._lib.sird_pso_num_params(h)
+
+    def _check(self, st):
+        if st != OK:
+            raise SirdError(st, self._lib.sird_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.sird_pso_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream=None):
+        self._check(self._lib.sird_pso_set_stream(self.h, C.c_void_p(current_stream_handle(stream))))
+
+    def eval(self, theta, out=None, precision=None):
+        """Loss of each column of theta ([P, M] or [P, ld] torch CUDA tensor, float32/float64)."""
+        import torch
+
+        precision = precision or (32 if theta.dtype == torch.float32 else 64)
+        dt = torch.float32 if precision == 32 else torch.float64
+        if theta.dtype != dt or not theta.is_cuda or theta.dim() != 2 or theta.shape[0] != self.P:
+            raise ValueError("theta must be a CUDA tensor [P, M] of the requested precision")
+        if theta.stride(1) != 1:
+            raise ValueError("theta rows must be contiguous")
+        M = theta.shape[1]
+        if out is None:
+            out = torch.empty(M, dtype=dt, device=theta.device)
+        self._check(self._lib.sird_pso_eval(self.h, C.c_void_p(theta.data_ptr()), M, theta.stride(0),
+                                            C.c_void_p(out.data_ptr()), precision))
+        return out
+
+    def set_observations(self, yD):
+        """Uploads new observations (same length, same first value) for the next calibration."""
+        y = _f64(yD)
+        self._keep_obs = y
+        self._check(self._lib.sird_pso_set_observations(self.h, _dptr(y), len(y)))
+
+    def set_timing(self, ev_begin=None, ev_end=None):
+        """torch.cuda.Event pair recorded around the iteration launches of every calibrate."""
+        b = C.c_void_p(ev_begin.cuda_event) if ev_begin is not None else None
+        e = C.c_void_p(ev_end.cuda_event) if ev_end is not None else None
+        self._check(self._lib.sird_pso_set_timing(self.h, b, e))
+
+    def init(self):
+        self._check(self._lib.sird_pso_init(self.h))
+        return self
+
+    def step(self, n=1):
+        self._check(self._lib.sird_pso_step(self.h, int(n)))
+        return self
+
+    def sync(self):
+        self._check(self._lib.sird_pso_sync(self.h))
+
+    def calibrate(self) -> dict:
+        r = Result()
+        self._check(self._lib.sird_pso_calibrate(self.h, C.byref(r)))
+        return r.as_dict()
+
+    def result(self) -> dict:
+        r = Result()
+        self._check(self._lib.sird_pso_result(self.h, C.byref(r)))
+        return r.as_dict()
+
+    def get_state(self) -> dict:
+        n = C.c_size_t(0)
+        self._check(self._lib.sird_pso_get_state(self.h, None, C.byref(n)))
+        buf = (C.c_ubyte * n.value)()
+        self._check(self._lib.sird_pso_get_state(self.h, buf, C.byref(n)))
+        raw = bytes(buf)
+        hdr = np.frombuffer(raw[:48], dtype=np.uint32)  # 48-byte header, see include/sird_pso.h
+        M, P, prec, it, gidx = [int(np.int32(v)) for v in hdr[2:7]]
+        dt = np.float32 if prec == 32 else np.float64
+        body = np.frombuffer(raw[48:], dtype=dt)
+        plane = M * P
+        return {"raw": raw, "M": M, "P": P, "precision": prec, "iter": it, "gbest_idx": gidx,
+                "x": body[:plane].reshape(P, M).copy(), "v": body[plane:2 * plane].reshape(P, M).copy(),
+                "pbest": body[2 * plane:3 * plane].reshape(P, M).copy(),
+                "pbest_f": body[3 * plane:3 * plane + M].copy()}
+
+    def set_state(self, x, v, pbest, pbest_f, gbest_idx, iteration, seed=None, stream_id=None):
+        """Loads a swarm state (arrays [P, M] and [M] in the swarm precision)."""
+        dt = np.float32 if self.precision == 32 else np.float64
+        hdr = np.zeros(10, dtype=np.uint32)
+        hdr[0], hdr[1] = 0x44524953, 1
+        hdr[2:8] = [self.M, self.P, self.precision, int(iteration), int(gbest_idx), 0]
+        seed = int(self.config.seed if seed is None else seed)
+        hdr[8] = seed & 0xFFFFFFFF
+        hdr[9] = (seed >> 32) & 0xFFFFFFFF
+        tail = np.array([int(self.config.stream_id if stream_id is None else stream_id), 0], dtype=np.uint32)
+        body = np.concatenate([np.asarray(a, dtype=dt).ravel() for a in (x, v, pbest, pbest_f)])
+        raw = hdr.tobytes() + tail.tobytes() + body.tobytes()
+        buf = (C.c_ubyte * len(raw)).from_buffer_copy(raw)
+        self._check(self._lib.sird_pso_set_state(self.h, buf, len(raw)))

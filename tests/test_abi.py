@@ -1,0 +1,75 @@
+"""The C-ABI library builds for sm_103a, loads, exports what the header declares, and
+rejects bad arguments before touching the GPU (CPU only)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2204_12346_gb300 import build, sird
+
+    build.build()
+    return sird.lib()
+
+
+def test_header_and_exports_agree(L):
+    from paper_2204_12346_gb300 import sird
+
+    header = open(os.path.join(ROOT, "include", "sird_pso.h")).read()
+    header = re.sub(r"/\*.*?\*/", "", header, flags=re.S)
+    declared = set(re.findall(r"\b(sird_\w+)\s*\(", header))
+    assert declared == set(sird.EXPORTS)
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+def _create(L, **over):
+    from paper_2204_12346_gb300 import sird
+
+    y = over.pop("y", np.arange(31, dtype=float))
+    pkw = dict(N=38e6, K=1, spd=10)
+    ckw = dict(particles=64, iters=5, lb=[0, 0, 0, 0], ub=[2, 1, 0.1, 1e6])
+    for k in list(over):
+        if k in ("N", "K", "spd", "cost", "beta_form", "fit_I0", "objective"):
+            pkw[k] = over.pop(k)
+    ckw.update(over)
+    pb, k1 = sird.make_problem(y, **pkw)
+    cfg, k2 = sird.make_config(**ckw)
+    h = C.c_void_p()
+    st = L.sird_pso_create(C.byref(pb), C.byref(cfg), None, C.byref(h))
+    return st, L.sird_last_error(None).decode(), h
+
+
+@pytest.mark.parametrize("over,status", [
+    (dict(y=np.array([0.0])), 1),
+    (dict(y=np.array([0.0, np.nan, 3.0])), 1),
+    (dict(N=-1.0), 1),
+    (dict(spd=0), 1),
+    (dict(K=0), 1),
+    (dict(K=40, lb=[0] * 43, ub=[1] * 43), 1),
+    (dict(cost=9), 1),
+    (dict(objective=1), 7),
+    (dict(particles=0), 1),
+    (dict(precision=16), 1),
+    (dict(block_size=48), 1),
+    (dict(reeval_topk=65), 1),
+    (dict(lb=[0, 0, 0, 2e6]), 1),
+    (dict(log_scale=[1, 1, 1, 1]), 1),
+    (dict(lb=[0, 0, 0, np.inf]), 1),
+])
+def test_create_rejects_bad_arguments_without_a_gpu(L, over, status):
+    st, msg, h = _create(L, **over)
+    assert st == status and msg and not h.value
+
+
+def test_null_handle_calls_are_safe(L):
+    assert L.sird_pso_init(None) == 1
+    assert L.sird_pso_step(None, 1) == 1
+    assert L.sird_pso_num_params(None) == 0
+    L.sird_pso_destroy(None)
