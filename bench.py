@@ -43,6 +43,22 @@ SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 
 
+# DRAM bytes per launch of the dominant kernel from the committed ncu capture
+# (profiles/pso_f32_persistent_c2.md), valid only for the kernel sources it was taken on.
+PROFILED_KERNEL_FILES = ["pso_persistent.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"]
+PROFILED = {"sha": "ea40821fd8e456d2", "traffic_bytes": 727296, "profile": "profiles/pso_f32_persistent_c2.md"}
+
+
+def kernel_sources_sha() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in PROFILED_KERNEL_FILES:
+        with open(os.path.join(ROOT, "paper_2204_12346_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def algorithmic_flops_per_particle_day(spd: int) -> int:
     """8 flops per Euler step (S = N - C, inf = cb*S*I, C += inf, I += inf - a*I, D += dm*I with
     FMA counted as 2) times steps per day, plus 3 for the day's error and its square-sum."""
@@ -192,7 +208,12 @@ def run_ours(args, rank: int, world: int) -> dict | None:
     h2d = n_obs * (4 + 4 + 8)
     d2h = 8 * 32 + 8 * 3 + 8  # ResultDev
     topk_passes = 1 if c.get("reeval_topk", 0) else 0
-    launches = args.steps * (1 + c["iters"] + topk_passes + 1)
+    persistent = cal.launch_mode == sird.LAUNCH_PERSISTENT
+    iter_launches = 1 if persistent else c["iters"]
+    launches = args.steps * (1 + iter_launches + topk_passes + 1)
+    kernel = ("pso_f32_persistent (all iterations in one cooperative launch)" if persistent
+              else "pso_f32_kernel (one fused PSO iteration per launch)")
+    launch_us = statistics.mean(iter_ms) * 1e3 / iter_launches
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -204,9 +225,12 @@ def run_ours(args, rank: int, world: int) -> dict | None:
                          "calibration keep the swarm resident in L2 by design",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP32_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "pso_f32_kernel (fused PSO iteration)",
-                     "avg_launch_us": avg_iter_ms * 1e3,
+                     "frac": achieved_tflops / FP32_PEAK_TFLOPS,
+                     "traffic": (PROFILED["traffic_bytes"] if persistent and args.workload == "c2"
+                                 and kernel_sources_sha() == PROFILED["sha"] else None),
+                     "traffic_source": PROFILED["profile"],
+                     "kernel": kernel, "avg_launch_us": launch_us, "us_per_iteration": avg_iter_ms * 1e3,
+                     "flops_per_launch": flops_per_launch * c["iters"] / iter_launches,
                      "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_total / args.steps},

@@ -60,6 +60,9 @@ typedef enum sird_cost { SIRD_COST_MSE = 0, SIRD_COST_MXSE = 1, SIRD_COST_MAE = 
 /* Transmission-rate form: K equal constant segments, or the paper's ramp (eq. (beta)). */
 typedef enum sird_beta_form { SIRD_BETA_PWC = 0, SIRD_BETA_RAMP = 1 } sird_beta_form;
 
+/* How the swarm iterations are launched (results are identical). */
+typedef enum sird_launch_mode { SIRD_LAUNCH_AUTO = 0, SIRD_LAUNCH_PER_ITER = 1, SIRD_LAUNCH_PERSISTENT = 2 } sird_launch_mode;
+
 /* Main objective: F_D^C (deaths only) or F_IRD^C (max over I, R, D), Sec. 3.1. */
 typedef enum sird_objective { SIRD_FIT_D = 0, SIRD_FIT_IRD = 1 } sird_objective;
 
@@ -116,6 +119,10 @@ typedef struct sird_problem {
  *                 and the best of them is reported (0 = report the FP32 global best as is)
  *   block_size    threads per block for the swarm kernels (0 = library default; else a
  *                 multiple of 32 in 32..1024)
+ *   launch_mode   SIRD_LAUNCH_AUTO, SIRD_LAUNCH_PER_ITER (one kernel per iteration) or
+ *                 SIRD_LAUNCH_PERSISTENT (FP32 only: all iterations in one cooperative launch
+ *                 with the swarm in shared memory; needs every block co-resident).  AUTO
+ *                 picks persistent when it fits.  Both give bit-identical swarms.
  */
 typedef struct sird_pso_config {
     int particles;
@@ -129,6 +136,7 @@ typedef struct sird_pso_config {
     uint32_t stream_id;
     int reeval_topk;
     int block_size;
+    int launch_mode;
 } sird_pso_config;
 
 /* Result of a calibration (host struct written by the library). */
@@ -159,6 +167,9 @@ sird_status sird_pso_clear_error(sird_pso_t h);
 sird_status sird_pso_set_stream(sird_pso_t h, void* cuda_stream);
 /* Number of parameters P of the handle's theta layout (0 if h is NULL). */
 int sird_pso_num_params(sird_pso_t h);
+/* Launch mode the handle uses for its iterations: SIRD_LAUNCH_PER_ITER or
+ * SIRD_LAUNCH_PERSISTENT (what SIRD_LAUNCH_AUTO resolved to); 0 if h is NULL. */
+int sird_pso_launch_mode(sird_pso_t h);
 
 /* ---------------------------------------------------------------- fitness */
 

@@ -80,6 +80,15 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
     return v;
 }
 
+// Warp minimum of packed keys via two 32-bit warp reductions (value, then index among the
+// lanes holding the minimum value); every lane gets the result.
+__device__ __forceinline__ unsigned long long warp_min_key(unsigned long long key) {
+    const uint32_t hi = (uint32_t)(key >> 32);
+    const uint32_t mhi = __reduce_min_sync(0xFFFFFFFFu, hi);
+    const uint32_t lo = __reduce_min_sync(0xFFFFFFFFu, hi == mhi ? (uint32_t)key : 0xFFFFFFFFu);
+    return ((unsigned long long)mhi << 32) | lo;
+}
+
 // FP64 (value, index) pair with NaN as +inf and lowest index on ties.
 struct MinPair64 {
     double f;

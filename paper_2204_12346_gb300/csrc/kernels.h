@@ -27,6 +27,16 @@ struct ReduceScratch {
     int* gbest_idx;
     void* gbest_f;             // float or double
     unsigned* err;             // kErr* bits
+    unsigned* abort;           // persistent kernel: set by a block whose wait ran out
+};
+
+// One block's published best of one iteration (persistent kernel).  Every 64-bit word holds
+// the iteration number in its high half, so a reader knows a word is current without any
+// fence: (tag, ordered loss bits), (tag, particle index), (tag, position bits) x P.
+struct ExchangeSlot {
+    unsigned long long w_loss;
+    unsigned long long w_idx;
+    unsigned long long w_pos[kMaxParams];
 };
 
 template <typename T>
@@ -67,6 +77,16 @@ cudaError_t launch_pso_f32(const WindowDev& w, const ModelDev& m, const ObsDev& 
                            const SwarmDev<float>& sw, const ReduceScratch& r, int iter, int block, cudaStream_t s);
 cudaError_t launch_pso_f64(const WindowDev& w, const ModelDev& m, const ObsDev& o, const PsoCoeffs<double>& c,
                            const SwarmDev<double>& sw, const ReduceScratch& r, int iter, int block, cudaStream_t s);
+
+// All iterations iter0+1 .. iter0+n_iters of an FP32 swarm in one cooperative launch (every
+// block co-resident); slots needs 2 * ceil(M / block) entries.  Resets the slots and the abort
+// flag first.
+size_t smem_bytes_persistent(const WindowDev& w, const ModelDev& m, int block, int grid);
+int persistent_capacity(const WindowDev& w, const ModelDev& m, int block, int grid);
+constexpr int kMaxPersistentBlocks = 128;
+cudaError_t launch_pso_f32_persistent(const WindowDev& w, const ModelDev& m, const ObsDev& o,
+                                      const PsoCoeffs<float>& c, const SwarmDev<float>& sw, const ReduceScratch& r,
+                                      ExchangeSlot* slots, int iter0, int n_iters, int block, cudaStream_t s);
 
 // Smallest k keys (packed loss, index) of the FP32 personal bests, sorted ascending, into out[k].
 // tmp_a / tmp_b need topk_scratch_keys(M, k) entries each.

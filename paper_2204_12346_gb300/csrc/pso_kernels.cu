@@ -117,12 +117,11 @@ __global__ void __launch_bounds__(1024) pso_f32_kernel(WindowDev w, ModelDev m, 
     }
 
     // block minimum -> one atomicMin per block -> the last block publishes the global best
-    key = warp_min_u64(key);
+    key = warp_min_key(key);
     if ((tid & 31) == 0) wk[tid >> 5] = key;
     __syncthreads();
     if (tid < 32) {
-        unsigned long long k2 = (tid < (B + 31) / 32) ? wk[tid] : ~0ull;
-        k2 = warp_min_u64(k2);
+        const unsigned long long k2 = warp_min_key((tid < (B + 31) / 32) ? wk[tid] : ~0ull);
         if (tid == 0) {
             atomicMin(r.gkey, k2);
             __threadfence();

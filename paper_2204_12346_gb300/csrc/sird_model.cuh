@@ -152,25 +152,28 @@ __device__ float fitness_f32(const WindowDev& w, const ModelDev& m, const float*
         return loss.result(w.n_obs, w.n_kept);
     }
 
+    // Segment-major: every segment runs its whole days through one straight-line unrolled day
+    // body (a single coefficient cb per day keeps the step chain short); a day split by a
+    // segment start is finished step by step.  Several segments may start on one day.
     const int K = m.K;
-    int seg = 0;
-    float b = th[0];
-    float cb = __fmaf_rn(b, w.cbn_h, __fmul_rn(b, w.cbn_l));
-    int next_b = (K > 1) ? segment_start(1, steps, K) : INT_MAX;
-    int k = 0;
-    for (int day = 1; day <= L; ++day) {
-        float cday = 0.f, dday = 0.f;
-        if (next_b < k + spd) {  // a segment starts inside this day (same for the whole block)
-            for (int s = 0; s < spd; ++s, ++k) {
-                while (k == next_b) {  // several segments may start on one step when K > steps
-                    ++seg;
-                    b = th[seg * stride];
-                    cb = __fmaf_rn(b, w.cbn_h, __fmul_rn(b, w.cbn_l));
-                    next_b = (seg + 1 < K) ? segment_start(seg + 1, steps, K) : INT_MAX;
-                }
-                euler_f32(cb, a, dm, ds.Sday, cday, dday, I, Il);
+    int k = 0, day = 0, in_day = 0;
+    float cday = 0.f, dday = 0.f;
+    for (int seg = 0; seg < K; ++seg) {
+        const float b = th[seg * stride];
+        const float cb = __fmaf_rn(b, w.cbn_h, __fmul_rn(b, w.cbn_l));
+        const int kend = segment_start(seg + 1, steps, K);
+        while (in_day != 0 && k < kend) {  // finish a day begun by the previous segment
+            euler_f32(cb, a, dm, ds.Sday, cday, dday, I, Il);
+            ++k;
+            if (++in_day == spd) {
+                ++day;
+                in_day = 0;
+                loss.add(ds.close_day(w, cday, dday, ys[day], I, Il), COST == COST_MAPE ? invys[day] : 0.f);
+                cday = 0.f;
+                dday = 0.f;
             }
-        } else {
+        }
+        while (k + spd <= kend) {  // whole days
             if (SPD > 0) {
 #pragma unroll
                 for (int s = 0; s < (SPD > 0 ? SPD : 1); ++s) euler_f32(cb, a, dm, ds.Sday, cday, dday, I, Il);
@@ -178,8 +181,16 @@ __device__ float fitness_f32(const WindowDev& w, const ModelDev& m, const float*
                 for (int s = 0; s < spd; ++s) euler_f32(cb, a, dm, ds.Sday, cday, dday, I, Il);
             }
             k += spd;
+            ++day;
+            loss.add(ds.close_day(w, cday, dday, ys[day], I, Il), COST == COST_MAPE ? invys[day] : 0.f);
+            cday = 0.f;
+            dday = 0.f;
         }
-        loss.add(ds.close_day(w, cday, dday, ys[day], I, Il), COST == COST_MAPE ? invys[day] : 0.f);
+        while (k < kend) {  // start a day the next segment finishes
+            euler_f32(cb, a, dm, ds.Sday, cday, dday, I, Il);
+            ++k;
+            ++in_day;
+        }
     }
     return loss.result(w.n_obs, w.n_kept);
 }

@@ -46,6 +46,9 @@ struct sird_pso {
     double ss_tot = 0.0;  // sum (y - mean y)^2 of the observed deaths, for R^2
     // configuration
     int M = 0, ld = 0, P = 0, iters = 0, precision = 32, block = 128, reeval_k = 0;
+    bool persistent = false;
+    void* d_slots = nullptr;  // abort flag + exchange slots of the persistent kernel
+    ExchangeSlot* slots = nullptr;
     PsoCoeffs<float> c32{};
     PsoCoeffs<double> c64{};
     uint64_t seed = 0;
@@ -94,6 +97,16 @@ struct sird_pso {
     cudaError_t enqueue_iter(int t, cudaStream_t s) {
         if (precision == 32) return launch_pso_f32(win, mdl, obs, c32, sw32(), red, t, block, s);
         return launch_pso_f64(win, mdl, obs, c64, sw64(), red, t, block, s);
+    }
+    // iterations iter0+1 .. iter0+n
+    cudaError_t enqueue_iters(int iter0, int n, cudaStream_t s) {
+        if (n <= 0) return cudaSuccess;
+        if (persistent) return launch_pso_f32_persistent(win, mdl, obs, c32, sw32(), red, slots, iter0, n, block, s);
+        for (int t = iter0 + 1; t <= iter0 + n; ++t) {
+            cudaError_t e = enqueue_iter(t, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
     }
     cudaError_t enqueue_result(cudaStream_t s) {
         if (precision == 32 && reeval_k > 0) {
@@ -218,6 +231,10 @@ extern "C" sird_status sird_pso_create(const sird_problem* pb, const sird_pso_co
     if (cfg->block_size != 0 && (cfg->block_size < 32 || cfg->block_size > 1024 || cfg->block_size % 32))
         return g_create_error = "block_size must be 0 or a multiple of 32 in [32, 1024]", SIRD_ERR_ARG;
     if (cfg->precision == 64 && cfg->block_size > 256) return g_create_error = "FP64 block_size must be <= 256", SIRD_ERR_ARG;
+    if (cfg->launch_mode < SIRD_LAUNCH_AUTO || cfg->launch_mode > SIRD_LAUNCH_PERSISTENT)
+        return g_create_error = "unknown launch_mode", SIRD_ERR_ARG;
+    if (cfg->launch_mode == SIRD_LAUNCH_PERSISTENT && cfg->precision != 32)
+        return g_create_error = "the persistent launch is FP32 only", SIRD_ERR_UNSUPPORTED;
     if (cfg->reeval_topk < 0 || cfg->reeval_topk > 1024 || cfg->reeval_topk > cfg->particles)
         return g_create_error = "reeval_topk out of range [0, min(particles, 1024)]", SIRD_ERR_ARG;
     for (int d = 0; d < P; ++d) {
@@ -310,6 +327,22 @@ extern "C" sird_status sird_pso_create(const sird_problem* pb, const sird_pso_co
     if (e != cudaSuccess) return bail(e, "initialising scratch");
     e = cudaMallocHost((void**)&h->h_res, sizeof(ResultDev));
     if (e != cudaSuccess) return bail(e, "allocating pinned result");
+    if (h->precision == 32 && cfg->launch_mode != SIRD_LAUNCH_PER_ITER) {
+        const int cap = persistent_capacity(h->win, h->mdl, h->block, (int)grid);
+        const bool fits = grid <= (size_t)cap && grid <= (size_t)kMaxPersistentBlocks;
+        if (!fits && cfg->launch_mode == SIRD_LAUNCH_PERSISTENT) {
+            g_create_error = "persistent launch requested but the blocks cannot all be co-resident";
+            sird_pso_destroy(h);
+            return SIRD_ERR_UNSUPPORTED;
+        }
+        if (fits) {
+            e = cudaMalloc(&h->d_slots, 256 + 2 * grid * sizeof(ExchangeSlot));
+            if (e != cudaSuccess) return bail(e, "allocating exchange slots");
+            h->red.abort = (unsigned*)h->d_slots;
+            h->slots = (ExchangeSlot*)((unsigned char*)h->d_slots + 256);
+            h->persistent = true;
+        }
+    }
     *out = h;
     return SIRD_OK;
 }
@@ -322,6 +355,7 @@ extern "C" void sird_pso_destroy(sird_pso_t h) {
     cudaFree(h->d_mem);
     cudaFree(h->d_obs);
     cudaFree(h->d_aux);
+    cudaFree(h->d_slots);
     if (h->h_res) cudaFreeHost(h->h_res);
     if (h->h_stage) cudaFreeHost(h->h_stage);
     delete h;
@@ -356,6 +390,11 @@ extern "C" sird_status sird_pso_set_stream(sird_pso_t h, void* cuda_stream) {
 
 extern "C" int sird_pso_num_params(sird_pso_t h) { return h ? h->P : 0; }
 
+extern "C" int sird_pso_launch_mode(sird_pso_t h) {
+    if (!h) return 0;
+    return h->persistent ? SIRD_LAUNCH_PERSISTENT : SIRD_LAUNCH_PER_ITER;
+}
+
 // ---------------------------------------------------------------- fitness
 
 extern "C" sird_status sird_pso_eval(sird_pso_t h, const void* d_theta, int M, int ld, void* d_loss, int precision) {
@@ -389,11 +428,9 @@ extern "C" sird_status sird_pso_step(sird_pso_t h, int n_iters) {
     if (h->sticky) return h->sticky;
     if (n_iters < 0) return h->fail(SIRD_ERR_ARG, "step: n_iters < 0");
     if (h->iter < 0) return h->fail(SIRD_ERR_STATE, "step before init/set_state");
-    for (int i = 0; i < n_iters; ++i) {
-        sird_status s = h->cuda(h->enqueue_iter(h->iter + 1, h->stream), "step launch");
-        if (s) return s;
-        ++h->iter;
-    }
+    sird_status s = h->cuda(h->enqueue_iters(h->iter, n_iters, h->stream), "step launch");
+    if (s) return s;
+    h->iter += n_iters;
     return SIRD_OK;
 }
 
@@ -484,7 +521,7 @@ extern "C" sird_status sird_pso_calibrate(sird_pso_t h, sird_result* out) {
         if (s) return s;
         cudaError_t e = h->enqueue_iter(0, h->cap);
         if (e == cudaSuccess && h->ev_begin) e = cudaEventRecordWithFlags(h->ev_begin, h->cap, cudaEventRecordExternal);
-        for (int t = 1; t <= h->iters && e == cudaSuccess; ++t) e = h->enqueue_iter(t, h->cap);
+        if (e == cudaSuccess) e = h->enqueue_iters(0, h->iters, h->cap);
         if (e == cudaSuccess && h->ev_end) e = cudaEventRecordWithFlags(h->ev_end, h->cap, cudaEventRecordExternal);
         if (e == cudaSuccess) e = h->enqueue_result(h->cap);
         cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);

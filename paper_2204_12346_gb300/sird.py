@@ -21,13 +21,14 @@ COST_MSE, COST_MXSE, COST_MAE, COST_MAPE = 0, 1, 2, 3
 COSTS = {"mse": COST_MSE, "mxse": COST_MXSE, "mae": COST_MAE, "mape": COST_MAPE}
 BETA_PWC, BETA_RAMP = 0, 1
 FIT_D, FIT_IRD = 0, 1
+LAUNCH_AUTO, LAUNCH_PER_ITER, LAUNCH_PERSISTENT = 0, 1, 2
 
 # Symbols the header declares (checked by the ABI test).
 EXPORTS = [
     "sird_pso_create", "sird_pso_destroy", "sird_last_error", "sird_pso_clear_error", "sird_pso_set_stream",
     "sird_pso_num_params", "sird_pso_eval", "sird_pso_init", "sird_pso_step", "sird_pso_calibrate",
     "sird_pso_result", "sird_pso_sync", "sird_pso_get_state", "sird_pso_set_state", "sird_loss_grad",
-    "sird_forecast", "sird_pso_calibrate_batched", "sird_pso_set_observations", "sird_pso_set_timing",
+    "sird_forecast", "sird_pso_calibrate_batched", "sird_pso_set_observations", "sird_pso_set_timing", "sird_pso_launch_mode",
 ]
 
 
@@ -51,7 +52,7 @@ class Config(C.Structure):
         ("particles", C.c_int), ("iters", C.c_int), ("w", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
         ("lb", C.POINTER(C.c_double)), ("ub", C.POINTER(C.c_double)), ("log_scale", C.POINTER(C.c_int)),
         ("precision", C.c_int), ("seed", C.c_uint64), ("stream_id", C.c_uint32), ("reeval_topk", C.c_int),
-        ("block_size", C.c_int),
+        ("block_size", C.c_int), ("launch_mode", C.c_int),
     ]
 
 
@@ -101,6 +102,7 @@ def lib():
         L.sird_pso_calibrate_batched.argtypes = [ip, C.POINTER(Problem), C.POINTER(Config), vp, C.POINTER(Result)]
         L.sird_pso_set_observations.argtypes = [vp, dp, ip]
         L.sird_pso_set_timing.argtypes = [vp, vp, vp]
+        L.sird_pso_launch_mode.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -141,7 +143,7 @@ def make_problem(yD, N, K=1, spd=10, R0=0.0, I0=0.0, fit_I0=True, beta_form=BETA
 
 
 def make_config(particles, iters, lb, ub, log_scale=None, w=0.5, c1=0.5, c2=0.5, precision=32, seed=0,
-                stream_id=0, reeval_topk=0, block_size=0):
+                stream_id=0, reeval_topk=0, block_size=0, launch_mode=0):
     lb, ub = _f64(lb), _f64(ub)
     keep = [lb, ub]
     lsp = C.POINTER(C.c_int)()
@@ -151,7 +153,7 @@ def make_config(particles, iters, lb, ub, log_scale=None, w=0.5, c1=0.5, c2=0.5,
         lsp = ls.ctypes.data_as(C.POINTER(C.c_int))
     cfg = Config(int(particles), int(iters), float(w), float(c1), float(c2), _dptr(lb), _dptr(ub), lsp,
                  int(precision), int(seed) & (2**64 - 1), int(stream_id) & 0xFFFFFFFF, int(reeval_topk),
-                 int(block_size))
+                 int(block_size), int(launch_mode))
     return cfg, keep
 
 
@@ -160,11 +162,11 @@ class Calibrator:
 
     def __init__(self, yD, N, *, K=1, spd=10, R0=0.0, I0=0.0, fit_I0=True, beta_form=BETA_PWC, cost=COST_MSE,
                  particles=64, iters=100, lb=None, ub=None, log_scale=None, w=0.5, c1=0.5, c2=0.5, precision=32,
-                 seed=0, stream_id=0, reeval_topk=0, block_size=0, stream=None):
+                 seed=0, stream_id=0, reeval_topk=0, block_size=0, launch_mode=0, stream=None):
         self._lib = lib()
         self.problem, k1 = make_problem(yD, N, K, spd, R0, I0, fit_I0, beta_form, cost)
         self.config, k2 = make_config(particles, iters, lb, ub, log_scale, w, c1, c2, precision, seed, stream_id,
-                                      reeval_topk, block_size)
+                                      reeval_topk, block_size, launch_mode)
         self._keep = k1 + k2
         self.precision = int(precision)
         self.M = int(particles)
@@ -175,6 +177,7 @@ class Calibrator:
             raise SirdError(st, self._lib.sird_last_error(None).decode())
         self.h = h
         self.P = self._lib.sird_pso_num_params(h)
+        self.launch_mode = self._lib.sird_pso_launch_mode(h)
 
     def _check(self, st):
         if st != OK:

@@ -249,3 +249,25 @@ def test_one_day_window():
     cal = cal_for(y, 38e6, 1, 10, 32)
     want = O.losses(O.Problem(yD=y, N=38e6, K=1, spd=10), th)
     assert rel_err(gpu_eval(cal, th, 32), want).max() <= TOL32
+
+
+@pytest.mark.parametrize("M,block", [(4096, 128), (1000, 64), (77, 32)])
+def test_persistent_and_per_iteration_launches_agree_bit_for_bit(M, block):
+    y, N, _, _ = window("c2")
+    lb, ub = log_box(4)
+    kw = dict(K=4, spd=10, particles=M, iters=25, lb=lb, ub=ub, log_scale=[1] * 7, precision=32, seed=5,
+              reeval_topk=8, block_size=block)
+    a = sird.Calibrator(y, N, launch_mode=sird.LAUNCH_PER_ITER, **kw)
+    b = sird.Calibrator(y, N, launch_mode=sird.LAUNCH_PERSISTENT, **kw)
+    ra, rb = a.calibrate(), b.calibrate()
+    assert ra["index"] == rb["index"] and ra["loss"] == rb["loss"] and ra["loss_search"] == rb["loss_search"]
+    sa, sb = a.get_state(), b.get_state()
+    for k in ("x", "v", "pbest", "pbest_f", "gbest_idx"):
+        assert np.array_equal(np.asarray(sa[k]), np.asarray(sb[k])), k
+    # stepping in pieces through the persistent kernel continues the same swarm
+    c = sird.Calibrator(y, N, launch_mode=sird.LAUNCH_PERSISTENT, **kw).init()
+    c.step(10)
+    c.step(15)
+    sc = c.get_state()
+    for k in ("x", "v", "pbest", "pbest_f", "gbest_idx"):
+        assert np.array_equal(np.asarray(sa[k]), np.asarray(sc[k])), k
