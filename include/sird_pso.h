@@ -254,6 +254,43 @@ sird_status sird_forecast(const sird_problem* problem, const double* theta, int 
 sird_status sird_pso_calibrate_batched(int W, const sird_problem* problems, const sird_pso_config* configs,
                                        void* cuda_stream, sird_result* results);
 
+/* ---------------------------------------------------------------- no allocation */
+
+#define SIRD_NOALLOC_MAX_OBS 4096
+
+/*
+ * One FP32 PSO iteration (iter >= 1), or the initialisation (iter == 0), on a swarm that the
+ * caller owns, without allocating anything.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they need a step -- a host
+ * framework that owns the whole device budget and lends a plugin only its own buffers, or a
+ * latency-critical loop where a cudaMalloc (which can synchronise the device) is not allowed.
+ *
+ * Same kernel and same results as sird_pso_step with SIRD_LAUNCH_PER_ITER on a handle built
+ * from the same problem and config.  Inputs and outputs are the caller's:
+ *   problem, config  host structs as for sird_pso_create (precision must be 32; only the
+ *                    values of y_D[0] and the count of zeros in y_D are read from y_D)
+ *   d_obs            device [n_obs] float observations of D (the float values of y_D)
+ *   d_x, d_v, d_pbest  device [P][ld] float, read and written (layout of sird_pso_eval)
+ *   d_pbest_f        device [ld] float, read and written
+ *   d_gbest          device [P] float: read as the previous global best, rewritten
+ *   iter             iteration number (the Philox counter word); 0 initialises
+ *   d_gbest_index    device int (may be NULL): receives the new global-best index
+ *   cuda_stream      cudaStream_t (NULL = default stream); the call returns after enqueueing
+ * Its only scratch (the global-best reduction words and, for MAPE, reciprocals of the
+ * observations) is a fixed array of 256 + 4*SIRD_NOALLOC_MAX_OBS bytes that the library keeps
+ * in every device's global memory until the process exits.  The first call on a device looks
+ * up that array's device address (cudaGetSymbolAddress), so make the first call on each device
+ * before any stream capture.  Every call uses the same array: the call clears the words that
+ * must start at zero, but calls that overlap on the GPU (different streams, other threads) race
+ * on it -- serialise them.  n_obs above SIRD_NOALLOC_MAX_OBS is rejected with SIRD_ERR_ARG; the
+ * message is available from sird_last_error(NULL).  No cudaMalloc, cudaFree or other allocating
+ * call is made.
+ */
+sird_status sird_pso_step_f32_noalloc(const sird_problem* problem, const sird_pso_config* config,
+                                      const float* d_obs, float* d_x, float* d_v, float* d_pbest,
+                                      float* d_pbest_f, float* d_gbest, int ld, int iter,
+                                      int* d_gbest_index, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,9 @@ cudaError_t launch_pso_f32_persistent(const WindowDev& w, const ModelDev& m, con
                                       const PsoCoeffs<float>& c, const SwarmDev<float>& sw, const ReduceScratch& r,
                                       ExchangeSlot* slots, int iter0, int n_iters, int block, cudaStream_t s);
 
+// Message returned by sird_last_error(NULL) on this thread.
+void set_global_error(const char* msg);
+
 // Smallest k keys (packed loss, index) of the FP32 personal bests, sorted ascending, into out[k].
 // tmp_a / tmp_b need topk_scratch_keys(M, k) entries each.
 size_t topk_scratch_keys(int M, int k);

@@ -33,6 +33,12 @@ struct StateHeader {
     uint32_t stream_id, reserved2;
 };
 
+}  // namespace
+
+void sird::set_global_error(const char* msg) { g_create_error = msg; }
+
+namespace {
+
 int nparams_of(const sird_problem* pb) {
     return (pb->beta_form == SIRD_BETA_RAMP ? 6 : pb->K + 2) + (pb->fit_I0 ? 1 : 0);
 }

@@ -29,6 +29,7 @@ EXPORTS = [
     "sird_pso_num_params", "sird_pso_eval", "sird_pso_init", "sird_pso_step", "sird_pso_calibrate",
     "sird_pso_result", "sird_pso_sync", "sird_pso_get_state", "sird_pso_set_state", "sird_loss_grad",
     "sird_forecast", "sird_pso_calibrate_batched", "sird_pso_set_observations", "sird_pso_set_timing", "sird_pso_launch_mode",
+    "sird_pso_step_f32_noalloc",
 ]
 
 
@@ -103,6 +104,7 @@ def lib():
         L.sird_pso_set_observations.argtypes = [vp, dp, ip]
         L.sird_pso_set_timing.argtypes = [vp, vp, vp]
         L.sird_pso_launch_mode.argtypes = [vp]
+        L.sird_pso_step_f32_noalloc.argtypes = [C.POINTER(Problem), C.POINTER(Config)] + [vp] * 6 + [ip, ip, vp, vp]
         _lib = L
     return _lib
 
@@ -283,3 +285,22 @@ class Calibrator:
         raw = hdr.tobytes() + tail.tobytes() + body.tobytes()
         buf = (C.c_ubyte * len(raw)).from_buffer_copy(raw)
         self._check(self._lib.sird_pso_set_state(self.h, buf, len(raw)))
+
+
+def step_f32_noalloc(yD, N, obs, x, v, pbest, pbest_f, gbest, iteration, *, gbest_index=None, stream=None,
+                     K=1, spd=10, R0=0.0, I0=0.0, fit_I0=True, beta_form=BETA_PWC, cost=COST_MSE, particles=None,
+                     lb=None, ub=None, log_scale=None, w=0.5, c1=0.5, c2=0.5, seed=0, stream_id=0, block_size=0):
+    """One FP32 PSO iteration on caller-owned torch CUDA buffers, through the entry point that
+    allocates nothing (sird_pso_step_f32_noalloc).  x, v, pbest: [P, ld] float32; pbest_f: [ld];
+    gbest: [P]; obs: [n_obs] float32 observations; gbest_index: optional int32 CUDA tensor [1]."""
+    L = lib()
+    pb, k1 = make_problem(yD, N, K, spd, R0, I0, fit_I0, beta_form, cost)
+    M = int(particles if particles is not None else x.shape[1])
+    cfg, k2 = make_config(M, 1, lb, ub, log_scale, w, c1, c2, 32, seed, stream_id, 0, block_size, 0)
+    ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+    st = L.sird_pso_step_f32_noalloc(C.byref(pb), C.byref(cfg), ptr(obs), ptr(x), ptr(v), ptr(pbest), ptr(pbest_f),
+                                     ptr(gbest), int(x.stride(0)), int(iteration), ptr(gbest_index),
+                                     C.c_void_p(current_stream_handle(stream)))
+    if st != OK:
+        raise SirdError(st, L.sird_last_error(None).decode())
+
