@@ -217,6 +217,12 @@ sird_status sird_pso_sync(sird_pso_t h);
 sird_status sird_pso_get_state(sird_pso_t h, void* buf, size_t* size);
 sird_status sird_pso_set_state(sird_pso_t h, const void* buf, size_t size);
 
+/* The k best personal bests of an FP32 swarm (k <= min(2048, particles)), best first (lowest
+ * index on ties): theta_out (host, [k][P]) decoded in FP64 from the stored positions,
+ * loss_out (host, [k]) their stored FP32 losses.  Blocks.  The forecast ensemble of Sec. 4.2
+ * is built from these. */
+sird_status sird_pso_topk(sird_pso_t h, int k, double* theta_out, double* loss_out);
+
 /* ---------------------------------------------------------------- gradient */
 
 /*

@@ -88,6 +88,16 @@ cudaError_t launch_pso_f32_persistent(const WindowDev& w, const ModelDev& m, con
                                       const PsoCoeffs<float>& c, const SwarmDev<float>& sw, const ReduceScratch& r,
                                       ExchangeSlot* slots, int iter0, int n_iters, int block, cudaStream_t s);
 
+// Deaths forecast of k parameter vectors (theta [P][ld], float or double by precision) into
+// out[k][horizon] (same type): D on days n_obs .. n_obs+horizon-1 of the window's numbering.
+cudaError_t launch_forecast(const WindowDev& w, const ModelDev& m, const void* theta, int ld, int k, int horizon,
+                            void* out, int precision, cudaStream_t s);
+
+// The k personal bests named by keys (FP32 swarm), decoded to theta in FP64: theta_out[k][P],
+// loss_out[k] = their stored FP32 values.
+cudaError_t launch_topk_gather(const unsigned long long* keys, int k, const float* pb, const float* pbf, int ld,
+                               int P, uint32_t logmask, double* theta_out, double* loss_out, cudaStream_t s);
+
 // Message returned by sird_last_error(NULL) on this thread.
 void set_global_error(const char* msg);
 

@@ -364,6 +364,19 @@ __global__ void __launch_bounds__(1024) reeval_kernel(WindowDev w, ModelDev m, O
     }
 }
 
+__global__ void topk_gather_kernel(const unsigned long long* __restrict__ keys, int k, const float* __restrict__ pb,
+                                   const float* __restrict__ pbf, int ld, int P, uint32_t logmask,
+                                   double* __restrict__ theta_out, double* __restrict__ loss_out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= k) return;
+    const int idx = (int)(keys[j] & 0xFFFFFFFFu);
+    for (int d = 0; d < P; ++d) {
+        const double z = (double)pb[(size_t)d * ld + idx];
+        theta_out[(size_t)j * P + d] = ((logmask >> d) & 1u) ? exp(z) : z;
+    }
+    loss_out[j] = (double)pbf[idx];
+}
+
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
@@ -479,6 +492,14 @@ cudaError_t launch_topk_f32(const float* pbf, int M, int k, unsigned long long* 
         src = dst;
         dst = (dst == tmp_a) ? tmp_b : tmp_a;
     }
+}
+
+cudaError_t launch_topk_gather(const unsigned long long* keys, int k, const float* pb, const float* pbf, int ld,
+                               int P, uint32_t logmask, double* theta_out, double* loss_out, cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    (void)cudaGetLastError();
+    topk_gather_kernel<<<(k + 127) / 128, 128, 0, s>>>(keys, k, pb, pbf, ld, P, logmask, theta_out, loss_out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reeval(const WindowDev& w, const ModelDev& m, const ObsDev& o, const PsoCoeffs<float>* c32,

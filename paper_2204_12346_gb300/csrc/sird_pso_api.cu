@@ -621,9 +621,70 @@ extern "C" sird_status sird_loss_grad(sird_pso_t h, const void*, int, int, void*
     return h->fail(SIRD_ERR_UNSUPPORTED, "sird_loss_grad: not built yet");
 }
 
-extern "C" sird_status sird_forecast(const sird_problem*, const double*, int, int, double*, int, void*) {
-    g_create_error = "sird_forecast: not built yet";
-    return SIRD_ERR_UNSUPPORTED;
+extern "C" sird_status sird_forecast(const sird_problem* pb, const double* theta, int k, int horizon, double* out_D,
+                                     int precision, void* cuda_stream) {
+    std::string why;
+    sird_status st = check_problem(pb, why);
+    if (st != SIRD_OK) return g_create_error = why, st;
+    if (!theta || !out_D || k < 1 || k > SIRD_MAX_PARTICLES || horizon < 1 || horizon > 100000)
+        return g_create_error = "forecast: bad theta/out_D/k/horizon", SIRD_ERR_ARG;
+    if (precision != 32 && precision != 64) return g_create_error = "forecast: precision must be 32 or 64", SIRD_ERR_ARG;
+    WindowDev w{};
+    ModelDev m{};
+    fill_window(pb, w, m);
+    const int P = m.P;
+    const size_t tsz = precision == 32 ? 4 : 8;
+    const size_t th_bytes = (size_t)P * k * tsz, out_bytes = (size_t)k * horizon * tsz;
+    std::vector<unsigned char> hth(th_bytes), hout(out_bytes);
+    for (int j = 0; j < k; ++j)
+        for (int d = 0; d < P; ++d) {
+            const double v = theta[(size_t)j * P + d];
+            if (precision == 32) ((float*)hth.data())[(size_t)d * k + j] = (float)v;
+            else ((double*)hth.data())[(size_t)d * k + j] = v;
+        }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    void* dmem = nullptr;
+    cudaError_t e = cudaMalloc(&dmem, th_bytes + out_bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dmem, hth.data(), th_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_forecast(w, m, dmem, k, k, horizon, (unsigned char*)dmem + th_bytes, precision, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hout.data(), (unsigned char*)dmem + th_bytes, out_bytes,
+                                              cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dmem);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return g_create_error = std::string("forecast: ") + cudaGetErrorString(e), SIRD_ERR_CUDA;
+    }
+    for (size_t i = 0; i < (size_t)k * horizon; ++i)
+        out_D[i] = precision == 32 ? (double)((float*)hout.data())[i] : ((double*)hout.data())[i];
+    return SIRD_OK;
+}
+
+extern "C" sird_status sird_pso_topk(sird_pso_t h, int k, double* theta_out, double* loss_out) {
+    if (!h) return SIRD_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if (h->precision != 32) return h->fail(SIRD_ERR_UNSUPPORTED, "topk: FP32 swarms only");
+    if (k < 1 || k > 2048 || k > h->M || !theta_out || !loss_out) return h->fail(SIRD_ERR_ARG, "topk: bad k or outputs");
+    if (h->iter < 0) return h->fail(SIRD_ERR_STATE, "topk before init");
+    const size_t nk = topk_scratch_keys(h->M, k);
+    const size_t bytes = 2 * nk * sizeof(unsigned long long) + (size_t)k * (h->P + 1) * sizeof(double);
+    void* dmem = nullptr;
+    sird_status st = h->cuda(cudaMalloc(&dmem, bytes), "topk scratch");
+    if (st) return st;
+    unsigned long long* a = (unsigned long long*)dmem;
+    unsigned long long* b = a + nk;
+    double* dth = (double*)(b + nk);
+    double* dloss = dth + (size_t)k * h->P;
+    unsigned long long* keys = nullptr;
+    cudaError_t e = launch_topk_f32((const float*)h->pbf, h->M, k, a, b, &keys, h->stream);
+    if (e == cudaSuccess)
+        e = launch_topk_gather(keys, k, (const float*)h->pb, (const float*)h->pbf, h->ld, h->P, h->c32.logmask, dth,
+                               dloss, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(theta_out, dth, (size_t)k * h->P * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(loss_out, dloss, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dmem);
+    return h->cuda(e, "topk");
 }
 
 extern "C" sird_status sird_pso_calibrate_batched(int, const sird_problem*, const sird_pso_config*, void*,

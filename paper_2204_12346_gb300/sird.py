@@ -29,7 +29,7 @@ EXPORTS = [
     "sird_pso_num_params", "sird_pso_eval", "sird_pso_init", "sird_pso_step", "sird_pso_calibrate",
     "sird_pso_result", "sird_pso_sync", "sird_pso_get_state", "sird_pso_set_state", "sird_loss_grad",
     "sird_forecast", "sird_pso_calibrate_batched", "sird_pso_set_observations", "sird_pso_set_timing", "sird_pso_launch_mode",
-    "sird_pso_step_f32_noalloc",
+    "sird_pso_step_f32_noalloc", "sird_pso_topk",
 ]
 
 
@@ -104,6 +104,7 @@ def lib():
         L.sird_pso_set_observations.argtypes = [vp, dp, ip]
         L.sird_pso_set_timing.argtypes = [vp, vp, vp]
         L.sird_pso_launch_mode.argtypes = [vp]
+        L.sird_pso_topk.argtypes = [vp, ip, dp, dp]
         L.sird_pso_step_f32_noalloc.argtypes = [C.POINTER(Problem), C.POINTER(Config)] + [vp] * 6 + [ip, ip, vp, vp]
         _lib = L
     return _lib
@@ -255,6 +256,13 @@ class Calibrator:
         self._check(self._lib.sird_pso_result(self.h, C.byref(r)))
         return r.as_dict()
 
+    def topk(self, k: int):
+        """(theta [k, P], loss [k]) of the k best personal bests, best first."""
+        th = np.zeros((k, self.P))
+        lo = np.zeros(k)
+        self._check(self._lib.sird_pso_topk(self.h, int(k), _dptr(th), _dptr(lo)))
+        return th, lo
+
     def get_state(self) -> dict:
         n = C.c_size_t(0)
         self._check(self._lib.sird_pso_get_state(self.h, None, C.byref(n)))
@@ -285,6 +293,20 @@ class Calibrator:
         raw = hdr.tobytes() + tail.tobytes() + body.tobytes()
         buf = (C.c_ubyte * len(raw)).from_buffer_copy(raw)
         self._check(self._lib.sird_pso_set_state(self.h, buf, len(raw)))
+
+
+def forecast(yD, N, theta, horizon, *, K=1, spd=10, R0=0.0, I0=0.0, fit_I0=True, beta_form=BETA_PWC,
+             precision=64, stream=None) -> np.ndarray:
+    """D on the `horizon` days after the window for each row of theta ([k, P]); returns [k, horizon]."""
+    L = lib()
+    pb, keep = make_problem(yD, N, K, spd, R0, I0, fit_I0, beta_form)
+    th = _f64(np.atleast_2d(theta))
+    out = np.zeros((th.shape[0], int(horizon)))
+    st = L.sird_forecast(C.byref(pb), _dptr(th), th.shape[0], int(horizon), _dptr(out), int(precision),
+                         C.c_void_p(current_stream_handle(stream)))
+    if st != OK:
+        raise SirdError(st, L.sird_last_error(None).decode())
+    return out
 
 
 def step_f32_noalloc(yD, N, obs, x, v, pbest, pbest_f, gbest, iteration, *, gbest_index=None, stream=None,
