@@ -237,6 +237,18 @@ sird_status sird_pso_topk(sird_pso_t h, int k, double* theta_out, double* loss_o
 sird_status sird_loss_grad(sird_pso_t h, const void* d_theta, int M, int ld, void* d_loss,
                            void* d_grad, int ld_grad, void* d_grad_u0, int precision, int ckpt_every);
 
+/*
+ * Gradient polish of an FP32 swarm's k best personal bests (k <= min(1024, particles)): iters
+ * L-BFGS iterations in FP64 on the search coordinates (dL/dz = theta dL/dtheta on log
+ * dimensions; 8 stored pairs), each with one sird_loss_grad evaluation (checkpoints every
+ * ckpt_every steps) and a line search that evaluates 16 step lengths 2^-q in one FP64 launch
+ * and takes the longest one meeting the Armijo condition; positions are clamped to the box.
+ * first_step is the largest change of any search coordinate in the first (steepest-descent)
+ * step.  The best point ever evaluated is reported in *out (FP64 loss; index = the
+ * candidate's particle).  The swarm itself is not changed.  Blocks.
+ */
+sird_status sird_pso_polish(sird_pso_t h, int k, int iters, double first_step, int ckpt_every, sird_result* out);
+
 /* ---------------------------------------------------------------- forecast */
 
 /*

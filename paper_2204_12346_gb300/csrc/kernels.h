@@ -98,6 +98,22 @@ cudaError_t launch_forecast(const WindowDev& w, const ModelDev& m, const void* t
 cudaError_t launch_topk_gather(const unsigned long long* keys, int k, const float* pb, const float* pbf, int ld,
                                int P, uint32_t logmask, double* theta_out, double* loss_out, cudaStream_t s);
 
+// Loss and exact gradient (discrete adjoint) of M parameter vectors in FP64; checkpoints every C
+// steps (1..64) in ckpt (adjoint_ckpt_bytes).
+size_t adjoint_ckpt_bytes(const WindowDev& w, const ModelDev& m, int M, int C);
+cudaError_t launch_loss_grad_f64(const WindowDev& w, const ModelDev& m, const ObsDev& o, const double* theta, int ld,
+                                 int M, double* loss, double* grad, int ldg, double* grad_u0, double* ckpt, int C,
+                                 cudaStream_t s);
+
+// FP64 L-BFGS polish of the k candidates named by keys (FP32 swarm): iters iterations with a
+// parallel line search, best point kept, the best candidate's theta / loss / sse into *res.
+// scratch: polish_scratch_doubles(P, k) doubles.
+size_t polish_scratch_doubles(int P, int k);
+cudaError_t launch_polish(const WindowDev& w, const ModelDev& m, const ObsDev& o, const PsoCoeffs<double>& c,
+                          const unsigned long long* keys, int k, const float* pb, const float* pbf, int ld, int iters,
+                          double first_step, double* scratch, double* ckpt, int ckpt_every, ResultDev* res,
+                          cudaStream_t s);
+
 // Message returned by sird_last_error(NULL) on this thread.
 void set_global_error(const char* msg);
 

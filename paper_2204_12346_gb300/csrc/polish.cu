@@ -1,0 +1,292 @@
+// polish.cu -- FP64 L-BFGS polish of the best PSO candidates with a parallel line search.
+//
+// PSO (Sec. 3.3) needs no gradient; near its optimum the swarm resolves the loss only as far
+// as its search does.  The discrete adjoint gives the exact gradient of the FP64 loss, so the
+// k best personal bests are refined by L-BFGS in the search coordinates (z = ln theta on log
+// dimensions, where dL/dz = theta dL/dtheta), positions clamped to the box.  Each iteration:
+//   1. direction d = -H g by the two-loop recursion over the last kMem (s, y) pairs,
+//   2. kTrials trial points z + 2^-q d (q = 0..kTrials-1) for every candidate, evaluated in ONE
+//      FP64 launch -- on this GPU an FP64 evaluation is latency-bound, so 16 trials cost about
+//      what one does,
+//   3. the largest step that satisfies the Armijo condition (else the best trial if it lowers
+//      the loss, else the candidate stops),
+//   4. the gradient at the accepted point (adjoint launch) and the history update.
+// The best point ever evaluated is reported.
+#include <cmath>
+
+#include "kernels.h"
+
+namespace sird {
+
+namespace {
+
+constexpr int kMem = 8;
+constexpr int kTrials = 16;
+
+// Per-candidate state, structure of arrays with candidate j at [.. * k + j].
+struct PolishState {
+    double *z, *g, *f, *d, *zt, *tht, *ft, *S, *Y, *rho, *best_f, *best_th, *gth, *lnew;
+    int *head, *count, *active, *cand;
+    int P, k;
+};
+
+__device__ __forceinline__ double decode(double z, bool lg) { return lg ? exp(z) : z; }
+
+__global__ void polish_init_kernel(PolishState s, const unsigned long long* __restrict__ keys, const float* __restrict__ pb,
+                                   int ld, uint32_t logmask) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= s.k) return;
+    const int idx = (int)(keys[j] & 0xFFFFFFFFu);
+    s.cand[j] = idx;
+    s.head[j] = 0;
+    s.count[j] = 0;
+    s.active[j] = 1;
+    s.best_f[j] = INFINITY;
+    for (int d = 0; d < s.P; ++d) {
+        const double z = (double)pb[(size_t)d * ld + idx];
+        s.z[(size_t)d * s.k + j] = z;
+        s.tht[(size_t)d * s.k * kTrials + j] = decode(z, (logmask >> d) & 1u);  // slot 0: gradient point
+    }
+}
+
+// After an adjoint launch at the accepted points (theta in tht slot 0, loss lnew, gradient gth):
+// convert the gradient to z, push (s, y) into the history, keep the best point.
+__global__ void polish_accept_kernel(PolishState s, uint32_t logmask, int first) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= s.k) return;
+    const int P = s.P, k = s.k, kt = k * kTrials;
+    const double fnew = s.lnew[j];
+    double sy = 0.0, yy = 0.0, ss = 0.0;
+    for (int d = 0; d < P; ++d) {
+        const bool lg = (logmask >> d) & 1u;
+        const double th = s.tht[(size_t)d * kt + j];
+        const double gz = lg ? th * s.gth[(size_t)d * k + j] : s.gth[(size_t)d * k + j];
+        if (!first) {
+            const double sd = s.zt[(size_t)d * k + j] - s.z[(size_t)d * k + j];
+            const double yd = gz - s.g[(size_t)d * k + j];
+            sy += sd * yd;
+            yy += yd * yd;
+            ss += sd * sd;
+            s.S[((size_t)s.head[j] * P + d) * k + j] = sd;
+            s.Y[((size_t)s.head[j] * P + d) * k + j] = yd;
+        }
+        s.g[(size_t)d * k + j] = gz;
+    }
+    if (!first) {
+        for (int d = 0; d < P; ++d) s.z[(size_t)d * k + j] = s.zt[(size_t)d * k + j];
+        if (sy > 1e-14 * sqrt(ss * yy)) {  // curvature condition: keep the pair
+            s.rho[(size_t)s.head[j] * k + j] = 1.0 / sy;
+            s.head[j] = (s.head[j] + 1) % kMem;
+            if (s.count[j] < kMem) ++s.count[j];
+        }
+    }
+    s.f[j] = fnew;
+    if (fnew < s.best_f[j]) {
+        s.best_f[j] = fnew;
+        for (int d = 0; d < P; ++d) s.best_th[(size_t)d * k + j] = s.tht[(size_t)d * kt + j];
+    }
+}
+
+// Two-loop recursion and the trial points z + 2^-q d, clamped to the box.
+__global__ void polish_direction_kernel(PolishState s, PsoCoeffs<double> c, double first_step) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= s.k) return;
+    const int P = s.P, k = s.k, kt = k * kTrials;
+    double q[kMaxParams], a[kMem];
+    for (int d = 0; d < P; ++d) q[d] = s.g[(size_t)d * k + j];
+    const int cnt = s.count[j];
+    for (int i = 0; i < cnt; ++i) {
+        const int h = (s.head[j] - 1 - i + 2 * kMem) % kMem;
+        double dot = 0.0;
+        for (int d = 0; d < P; ++d) dot += s.S[((size_t)h * P + d) * k + j] * q[d];
+        a[i] = s.rho[(size_t)h * k + j] * dot;
+        for (int d = 0; d < P; ++d) q[d] -= a[i] * s.Y[((size_t)h * P + d) * k + j];
+    }
+    if (cnt > 0) {
+        const int h = (s.head[j] - 1 + kMem) % kMem;
+        double yy = 0.0;
+        for (int d = 0; d < P; ++d) yy += s.Y[((size_t)h * P + d) * k + j] * s.Y[((size_t)h * P + d) * k + j];
+        const double gamma = 1.0 / (s.rho[(size_t)h * k + j] * yy);
+        for (int d = 0; d < P; ++d) q[d] *= gamma;
+    } else {
+        double gmax = 0.0;
+        for (int d = 0; d < P; ++d) gmax = fmax(gmax, fabs(q[d]));
+        const double sc = gmax > 0.0 ? first_step / gmax : 0.0;
+        for (int d = 0; d < P; ++d) q[d] *= sc;
+    }
+    for (int i = cnt - 1; i >= 0; --i) {
+        const int h = (s.head[j] - 1 - i + 2 * kMem) % kMem;
+        double dot = 0.0;
+        for (int d = 0; d < P; ++d) dot += s.Y[((size_t)h * P + d) * k + j] * q[d];
+        const double b = s.rho[(size_t)h * k + j] * dot;
+        for (int d = 0; d < P; ++d) q[d] += (a[i] - b) * s.S[((size_t)h * P + d) * k + j];
+    }
+    double gd = 0.0;
+    for (int d = 0; d < P; ++d) {
+        s.d[(size_t)d * k + j] = -q[d];
+        gd -= q[d] * s.g[(size_t)d * k + j];
+    }
+    if (!(gd < 0.0)) {  // not a descent direction: restart along the scaled steepest descent
+        double gmax = 0.0;
+        for (int d = 0; d < P; ++d) gmax = fmax(gmax, fabs(s.g[(size_t)d * k + j]));
+        const double sc = gmax > 0.0 ? first_step / gmax : 0.0;
+        for (int d = 0; d < P; ++d) s.d[(size_t)d * k + j] = -sc * s.g[(size_t)d * k + j];
+        s.count[j] = 0;
+    }
+    for (int t = 0; t < kTrials; ++t) {
+        const double alpha = ldexp(1.0, -t);
+        for (int d = 0; d < P; ++d) {
+            const double zn = fmin(fmax(s.z[(size_t)d * k + j] + alpha * s.d[(size_t)d * k + j], c.zlb[d]), c.zub[d]);
+            s.tht[(size_t)d * kt + (size_t)t * k + j] = decode(zn, (c.logmask >> d) & 1u);
+        }
+    }
+}
+
+// Armijo choice among the evaluated trials; the accepted theta goes to trial slot 0 and z to zt.
+__global__ void polish_select_kernel(PolishState s, PsoCoeffs<double> c) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= s.k) return;
+    const int P = s.P, k = s.k, kt = k * kTrials;
+    const double f0 = s.f[j];
+    double gd = 0.0;
+    for (int d = 0; d < P; ++d) gd += s.g[(size_t)d * k + j] * s.d[(size_t)d * k + j];
+    int pick = -1;
+    double fbest = f0;
+    int tbest = -1;
+    for (int t = 0; t < kTrials; ++t) {
+        const double ft = s.ft[(size_t)t * k + j];
+        if (pick < 0 && ft <= f0 + 1e-4 * ldexp(1.0, -t) * gd) pick = t;
+        if (ft < fbest) {
+            fbest = ft;
+            tbest = t;
+        }
+    }
+    if (pick < 0) pick = tbest;  // no Armijo step: take the lowest trial if it improves
+    if (pick < 0 || !s.active[j]) {
+        s.active[j] = 0;
+        pick = -1;
+    }
+    for (int d = 0; d < P; ++d) {
+        double zn;
+        if (pick >= 0) {
+            zn = fmin(fmax(s.z[(size_t)d * k + j] + ldexp(1.0, -pick) * s.d[(size_t)d * k + j], c.zlb[d]), c.zub[d]);
+        } else {
+            zn = s.z[(size_t)d * k + j];
+        }
+        s.zt[(size_t)d * k + j] = zn;
+        s.tht[(size_t)d * kt + j] = decode(zn, (c.logmask >> d) & 1u);
+    }
+}
+
+// Best candidate: theta, FP64 loss and sum of squared errors (for R^2) into *res.
+__global__ void polish_pick_kernel(WindowDev w, ModelDev m, ObsDev o, PolishState s, const float* __restrict__ pbf,
+                                   ResultDev* res) {
+    extern __shared__ double dsm[];
+    __shared__ double wf[32];
+    __shared__ int wi[32];
+    const int tid = threadIdx.x, B = blockDim.x, k = s.k;
+    for (int i = tid; i < w.n_obs; i += B) dsm[i] = o.yd[i];
+    double f = tid < k ? s.best_f[tid] : INFINITY;
+    int j = tid < k ? tid : INT_MAX;
+    warp_min_pair(f, j);
+    if ((tid & 31) == 0) {
+        wf[tid >> 5] = f;
+        wi[tid >> 5] = j;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        double f2 = tid < (B + 31) / 32 ? wf[tid] : INFINITY;
+        int j2 = tid < (B + 31) / 32 ? wi[tid] : INT_MAX;
+        warp_min_pair(f2, j2);
+        if (tid == 0 && j2 < k) {
+            double sse = 0.0, fl = 0.0;
+            const double* th = s.best_th + j2;
+            switch (m.cost) {
+                case COST_MSE: fl = fitness_f64<COST_MSE>(w, m, dsm, th, k, &sse); break;
+                case COST_MXSE: fl = fitness_f64<COST_MXSE>(w, m, dsm, th, k, &sse); break;
+                case COST_MAE: fl = fitness_f64<COST_MAE>(w, m, dsm, th, k, &sse); break;
+                default: fl = fitness_f64<COST_MAPE>(w, m, dsm, th, k, &sse); break;
+            }
+            for (int d = 0; d < m.P; ++d) res->theta[d] = th[(size_t)d * k];
+            res->loss = fl;
+            res->sse = sse;
+            res->index = s.cand[j2];
+            res->loss_search = (double)pbf[s.cand[j2]];
+            res->count = k;
+        }
+    }
+}
+
+PolishState carve(double* base, int P, int k) {
+    PolishState s{};
+    s.P = P;
+    s.k = k;
+    const size_t pk = (size_t)P * k;
+    double* q = base;
+    s.z = q; q += pk;
+    s.g = q; q += pk;
+    s.d = q; q += pk;
+    s.zt = q; q += pk;
+    s.gth = q; q += pk;
+    s.best_th = q; q += pk;
+    s.tht = q; q += pk * kTrials;
+    s.S = q; q += pk * kMem;
+    s.Y = q; q += pk * kMem;
+    s.rho = q; q += (size_t)k * kMem;
+    s.f = q; q += k;
+    s.ft = q; q += (size_t)k * kTrials;
+    s.best_f = q; q += k;
+    s.lnew = q; q += k;
+    int* iq = (int*)q;
+    s.head = iq; iq += k;
+    s.count = iq; iq += k;
+    s.active = iq; iq += k;
+    s.cand = iq;
+    return s;
+}
+
+}  // namespace
+
+size_t polish_scratch_doubles(int P, int k) {
+    const size_t pk = (size_t)P * k;
+    return pk * (6 + kTrials + 2 * kMem) + (size_t)k * (kMem + kTrials + 3) + 2 * (size_t)k + 8;
+}
+
+int polish_trials() { return kTrials; }
+
+cudaError_t launch_polish(const WindowDev& w, const ModelDev& m, const ObsDev& o, const PsoCoeffs<double>& c,
+                          const unsigned long long* keys, int k, const float* pb, const float* pbf, int ld, int iters,
+                          double first_step, double* scratch, double* ckpt, int ckpt_every, ResultDev* res,
+                          cudaStream_t st) {
+    const int P = m.P;
+    PolishState s = carve(scratch, P, k);
+    const unsigned grid = (unsigned)((k + 127) / 128);
+    const int kt = k * kTrials;
+    (void)cudaGetLastError();
+    polish_init_kernel<<<grid, 128, 0, st>>>(s, keys, pb, ld, c.logmask);
+    cudaError_t e = cudaGetLastError();
+    // loss and gradient at the starting points (trial slot 0 holds their theta)
+    if (e == cudaSuccess) e = launch_loss_grad_f64(w, m, o, s.tht, kt, k, s.lnew, s.gth, k, nullptr, ckpt, ckpt_every, st);
+    if (e == cudaSuccess) {
+        polish_accept_kernel<<<grid, 128, 0, st>>>(s, c.logmask, 1);
+        e = cudaGetLastError();
+    }
+    for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+        polish_direction_kernel<<<grid, 128, 0, st>>>(s, c, first_step);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_eval_f64(w, m, o, s.tht, kt, kt, s.ft, 64, nullptr, st);
+        if (e != cudaSuccess) break;
+        polish_select_kernel<<<grid, 128, 0, st>>>(s, c);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_loss_grad_f64(w, m, o, s.tht, kt, k, s.lnew, s.gth, k, nullptr, ckpt, ckpt_every, st);
+        if (e != cudaSuccess) break;
+        polish_accept_kernel<<<grid, 128, 0, st>>>(s, c.logmask, 0);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
+    const int block = ((k + 31) / 32) * 32;
+    polish_pick_kernel<<<1, block, (size_t)w.n_obs * sizeof(double), st>>>(w, m, o, s, pbf, res);
+    return cudaGetLastError();
+}
+
+}  // namespace sird

@@ -75,6 +75,8 @@ struct sird_pso {
     cudaGraphExec_t calib = nullptr;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // optional timing events (sird_pso_set_timing)
     double* h_stage = nullptr;                          // pinned staging for observation uploads
+    void* d_ckpt = nullptr;                             // adjoint checkpoints (grown on demand)
+    size_t ckpt_bytes = 0;
     int n_obs = 0;
     // errors
     sird_status sticky = SIRD_OK;
@@ -362,6 +364,7 @@ extern "C" void sird_pso_destroy(sird_pso_t h) {
     cudaFree(h->d_obs);
     cudaFree(h->d_aux);
     cudaFree(h->d_slots);
+    cudaFree(h->d_ckpt);
     if (h->h_res) cudaFreeHost(h->h_res);
     if (h->h_stage) cudaFreeHost(h->h_stage);
     delete h;
@@ -616,9 +619,62 @@ extern "C" sird_status sird_pso_set_state(sird_pso_t h, const void* buf, size_t 
 
 // ---------------------------------------------------------------- not yet built
 
-extern "C" sird_status sird_loss_grad(sird_pso_t h, const void*, int, int, void*, void*, int, void*, int, int) {
+extern "C" sird_status sird_loss_grad(sird_pso_t h, const void* d_theta, int M, int ld, void* d_loss, void* d_grad,
+                                      int ld_grad, void* d_grad_u0, int precision, int ckpt_every) {
     if (!h) return SIRD_ERR_ARG;
-    return h->fail(SIRD_ERR_UNSUPPORTED, "sird_loss_grad: not built yet");
+    if (h->sticky) return h->sticky;
+    if (M < 0 || ld < M || ld_grad < M || (M > 0 && (!d_theta || !d_loss || !d_grad)))
+        return h->fail(SIRD_ERR_ARG, "loss_grad: bad M/ld/pointers");
+    if (ckpt_every < 1 || ckpt_every > 64) return h->fail(SIRD_ERR_ARG, "loss_grad: ckpt_every out of range [1, 64]");
+    if (precision != 64) return h->fail(SIRD_ERR_UNSUPPORTED, "loss_grad: FP64 only");
+    if (M == 0) return SIRD_OK;
+    const size_t need = adjoint_ckpt_bytes(h->win, h->mdl, M, ckpt_every);
+    if (need > h->ckpt_bytes) {
+        sird_status s = h->cuda(cudaStreamSynchronize(h->stream), "sync");
+        if (s) return s;
+        cudaFree(h->d_ckpt);
+        h->d_ckpt = nullptr;
+        h->ckpt_bytes = 0;
+        s = h->cuda(cudaMalloc(&h->d_ckpt, need), "allocating adjoint checkpoints");
+        if (s) return s;
+        h->ckpt_bytes = need;
+    }
+    return h->cuda(launch_loss_grad_f64(h->win, h->mdl, h->obs, (const double*)d_theta, ld, M, (double*)d_loss,
+                                        (double*)d_grad, ld_grad, (double*)d_grad_u0, (double*)h->d_ckpt,
+                                        ckpt_every, h->stream),
+                   "loss_grad launch");
+}
+
+extern "C" sird_status sird_pso_polish(sird_pso_t h, int k, int iters, double first_step, int ckpt_every,
+                                       sird_result* out) {
+    if (!h || !out) return SIRD_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if (h->precision != 32) return h->fail(SIRD_ERR_UNSUPPORTED, "polish: FP32 swarms only");
+    if (k < 1 || k > 1024 || k > h->M || iters < 0 || !(first_step > 0) || ckpt_every < 1 || ckpt_every > 64)
+        return h->fail(SIRD_ERR_ARG, "polish: bad k/iters/first_step/ckpt_every");
+    if (h->iter < 0) return h->fail(SIRD_ERR_STATE, "polish before init");
+    const size_t nk = topk_scratch_keys(h->M, k);
+    const size_t ck = adjoint_ckpt_bytes(h->win, h->mdl, k, ckpt_every);
+    const size_t bytes = 2 * nk * sizeof(unsigned long long) + polish_scratch_doubles(h->P, k) * sizeof(double) + ck;
+    void* dmem = nullptr;
+    sird_status st = h->cuda(cudaMalloc(&dmem, bytes), "polish scratch");
+    if (st) return st;
+    unsigned long long* a = (unsigned long long*)dmem;
+    unsigned long long* b = a + nk;
+    double* scratch = (double*)(b + nk);
+    double* ckpt = scratch + polish_scratch_doubles(h->P, k);
+    unsigned long long* keys = nullptr;
+    cudaError_t e = launch_topk_f32((const float*)h->pbf, h->M, k, a, b, &keys, h->stream);
+    if (e == cudaSuccess)
+        e = launch_polish(h->win, h->mdl, h->obs, h->c64, keys, k, (const float*)h->pb, (const float*)h->pbf, h->ld,
+                          iters, first_step, scratch, ckpt, ckpt_every, h->d_res, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_res, h->d_res, sizeof(ResultDev), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dmem);
+    st = h->cuda(e, "polish");
+    if (st) return st;
+    h->fill_result(out);
+    return SIRD_OK;
 }
 
 extern "C" sird_status sird_forecast(const sird_problem* pb, const double* theta, int k, int horizon, double* out_D,

@@ -29,7 +29,7 @@ EXPORTS = [
     "sird_pso_num_params", "sird_pso_eval", "sird_pso_init", "sird_pso_step", "sird_pso_calibrate",
     "sird_pso_result", "sird_pso_sync", "sird_pso_get_state", "sird_pso_set_state", "sird_loss_grad",
     "sird_forecast", "sird_pso_calibrate_batched", "sird_pso_set_observations", "sird_pso_set_timing", "sird_pso_launch_mode",
-    "sird_pso_step_f32_noalloc", "sird_pso_topk",
+    "sird_pso_step_f32_noalloc", "sird_pso_topk", "sird_pso_polish",
 ]
 
 
@@ -105,6 +105,7 @@ def lib():
         L.sird_pso_set_timing.argtypes = [vp, vp, vp]
         L.sird_pso_launch_mode.argtypes = [vp]
         L.sird_pso_topk.argtypes = [vp, ip, dp, dp]
+        L.sird_pso_polish.argtypes = [vp, ip, ip, C.c_double, ip, C.POINTER(Result)]
         L.sird_pso_step_f32_noalloc.argtypes = [C.POINTER(Problem), C.POINTER(Config)] + [vp] * 6 + [ip, ip, vp, vp]
         _lib = L
     return _lib
@@ -235,6 +236,25 @@ class Calibrator:
         e = C.c_void_p(ev_end.cuda_event) if ev_end is not None else None
         self._check(self._lib.sird_pso_set_timing(self.h, b, e))
 
+    def loss_grad(self, theta, ckpt_every=16, grad_u0=False):
+        """FP64 loss and exact gradient (discrete adjoint) of each column of theta ([P, M] CUDA
+        float64).  Returns (loss [M], grad [P, M]) or (loss, grad, grad_u0 [4, M])."""
+        import torch
+
+        if theta.dtype != torch.float64 or not theta.is_cuda or theta.dim() != 2 or theta.shape[0] != self.P:
+            raise ValueError("theta must be a CUDA float64 tensor [P, M]")
+        if theta.stride(1) != 1:
+            raise ValueError("theta rows must be contiguous")
+        M = theta.shape[1]
+        loss = torch.empty(M, dtype=torch.float64, device=theta.device)
+        grad = torch.empty(self.P, M, dtype=torch.float64, device=theta.device)
+        gu = torch.empty(4, M, dtype=torch.float64, device=theta.device) if grad_u0 else None
+        self._check(self._lib.sird_loss_grad(self.h, C.c_void_p(theta.data_ptr()), M, theta.stride(0),
+                                             C.c_void_p(loss.data_ptr()), C.c_void_p(grad.data_ptr()), M,
+                                             C.c_void_p(gu.data_ptr()) if gu is not None else None, 64,
+                                             int(ckpt_every)))
+        return (loss, grad, gu) if grad_u0 else (loss, grad)
+
     def init(self):
         self._check(self._lib.sird_pso_init(self.h))
         return self
@@ -254,6 +274,13 @@ class Calibrator:
     def result(self) -> dict:
         r = Result()
         self._check(self._lib.sird_pso_result(self.h, C.byref(r)))
+        return r.as_dict()
+
+    def polish(self, k=32, iters=50, first_step=1e-2, ckpt_every=16) -> dict:
+        """FP64 L-BFGS polish of the k best personal bests (discrete-adjoint gradient)."""
+        r = Result()
+        self._check(self._lib.sird_pso_polish(self.h, int(k), int(iters), float(first_step), int(ckpt_every),
+                                              C.byref(r)))
         return r.as_dict()
 
     def topk(self, k: int):
@@ -293,6 +320,27 @@ class Calibrator:
         raw = hdr.tobytes() + tail.tobytes() + body.tobytes()
         buf = (C.c_ubyte * len(raw)).from_buffer_copy(raw)
         self._check(self._lib.sird_pso_set_state(self.h, buf, len(raw)))
+
+
+try:
+    import torch as _torch
+
+    class SirdLoss(_torch.autograd.Function):
+        """FP64 loss of each column of theta ([P, M] CUDA float64) with its exact gradient from
+        the discrete-adjoint kernel: SirdLoss.apply(calibrator, theta[, ckpt_every])."""
+
+        @staticmethod
+        def forward(ctx, cal, theta, ckpt_every=16):
+            loss, grad = cal.loss_grad(theta.detach().contiguous(), ckpt_every=ckpt_every)
+            ctx.save_for_backward(grad)
+            return loss
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (grad,) = ctx.saved_tensors
+            return None, grad * grad_out.unsqueeze(0), None
+except ImportError:  # the binding still loads for CPU-only tooling
+    SirdLoss = None
 
 
 def forecast(yD, N, theta, horizon, *, K=1, spd=10, R0=0.0, I0=0.0, fit_I0=True, beta_form=BETA_PWC,
