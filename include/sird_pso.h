@@ -263,12 +263,30 @@ sird_status sird_forecast(const sird_problem* problem, const double* theta, int 
 /* ---------------------------------------------------------------- batched */
 
 /*
- * Calibrates W windows in one persistent launch (the rolling windows of Sec. 3.1).
- * problems[W], configs[W] are host arrays; every window must share beta_form, K,
- * steps_per_day, cost, objective, fit_I0, precision (32), w, c1, c2, iters and the
- * bounds; n_obs, observations, N, I0, R0, particles (<= 2048), seed and stream_id may
- * differ.  Results go to results[W] (host).  Blocks until done.
+ * Many calibration windows in one persistent launch (the rolling windows of Sec. 3.1): every
+ * block takes the next window from a queue (longest first), runs its whole PSO -- the
+ * initialisation and config.iters iterations, global best within the block -- and re-evaluates
+ * its global best in FP64.  A window's result equals sird_pso_calibrate with reeval_topk = 0,
+ * the same seed and the same stream_id.
+ *
+ * problems[W], configs[W] are host arrays.  Every window must share beta_form, K,
+ * steps_per_day, cost, objective, fit_I0, precision (32), w, c1, c2, iters, the bounds and
+ * log_scale; n_obs, observations, N, I0, R0, particles (1..2048), seed and stream_id may
+ * differ.  configs[0].block_size = 0 lets the library pick the threads per block and the blocks
+ * per SM by timing short trial runs of each candidate (cached in the file named by the
+ * environment variable SIRD_TUNE_CACHE when it is set); otherwise a multiple of 32 in 32..1024
+ * with as many blocks per SM as fit.
  */
+typedef struct sird_batch* sird_batch_t;
+sird_status sird_batch_create(int W, const sird_problem* problems, const sird_pso_config* configs, void* cuda_stream,
+                              sird_batch_t* out);
+/* Runs the batch (captured once into a CUDA graph, replayed after); results[W] on the host.  Blocks. */
+sird_status sird_batch_calibrate(sird_batch_t b, sird_result* results);
+/* Threads per block and blocks per SM the batch runs with (autotuned or given); 0 if b is NULL. */
+int sird_batch_block_size(sird_batch_t b);
+int sird_batch_blocks_per_sm(sird_batch_t b);
+void sird_batch_destroy(sird_batch_t b);
+/* One-shot create + calibrate + destroy.  Errors of the batch calls: sird_last_error(NULL). */
 sird_status sird_pso_calibrate_batched(int W, const sird_problem* problems, const sird_pso_config* configs,
                                        void* cuda_stream, sird_result* results);
 

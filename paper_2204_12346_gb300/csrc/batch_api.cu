@@ -1,0 +1,356 @@
+// batch_api.cu -- C ABI of the batched calibration (many rolling windows, one launch).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/sird_pso.h"
+#include "kernels.h"
+
+using namespace sird;
+
+sird_status sird_check_problem(const sird_problem* pb, std::string& why);
+void sird_fill_window(const sird_problem* pb, WindowDev& w, ModelDev& m);
+
+struct sird_batch {
+    int W = 0, P = 0, iters = 0, n_max = 0, block = 0, grid = 0, per_sm = 0;  // per_sm 0 = occupancy maximum
+    ModelDev mdl{};
+    PsoCoeffs<float> c{};
+    cudaStream_t stream = nullptr, cap = nullptr;
+    void* d_mem = nullptr;
+    BatchWindow* wins = nullptr;
+    int* order = nullptr;
+    float *yf = nullptr, *invy = nullptr, *swarm = nullptr;
+    double* yd = nullptr;
+    unsigned* queue = nullptr;
+    BatchOut* out = nullptr;
+    BatchOut* h_out = nullptr;  // pinned
+    std::vector<double> ss_tot;
+    cudaGraphExec_t graph = nullptr;
+    std::string msg;
+};
+
+namespace {
+
+thread_local std::string g_batch_error;
+
+sird_status berr(sird_status s, const std::string& m) {
+    g_batch_error = m;
+    set_global_error(m.c_str());
+    return s;
+}
+
+// Optional on-disk cache of tuned block sizes: file named by SIRD_TUNE_CACHE, lines "key block".
+std::string tune_key(const sird_batch* b, long long work) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%s|W%d|P%d|spd%d|K%d|cost%d|iters%d|work%lld|n%d", prop.name, b->W, b->P,
+                  b->mdl.spd, b->mdl.K, b->mdl.cost, b->iters, work, b->n_max);
+    std::string k(buf);
+    for (char& ch : k)
+        if (ch == ' ') ch = '_';
+    return k;
+}
+
+int tune_cache_get(const std::string& key) {
+    const char* path = std::getenv("SIRD_TUNE_CACHE");
+    if (!path) return 0;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return 0;
+    char k[512];
+    int v = 0, found = 0;
+    while (std::fscanf(f, "%511s %d", k, &v) == 2)
+        if (key == k) found = v;
+    std::fclose(f);
+    return found;
+}
+
+void tune_cache_put(const std::string& key, int block) {
+    const char* path = std::getenv("SIRD_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d\n", key.c_str(), block);
+    std::fclose(f);
+}
+
+cudaError_t run(sird_batch* b, int iters, int block, int per_sm, cudaStream_t s, bool reeval) {
+    int per = batch_blocks_per_sm(b->mdl, block, b->n_max);
+    if (per <= 0) return cudaErrorInvalidConfiguration;
+    if (per_sm > 0 && per_sm < per) per = per_sm;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::min(b->W, per * nsm);
+    b->grid = grid;
+    return launch_batch(b->wins, b->order, b->W, b->mdl, b->c, b->yf, b->invy, b->yd, b->swarm, b->queue, b->out,
+                        iters, b->n_max, block, grid, reeval, s);
+}
+
+// Times short trial runs (2 iterations) of each candidate (threads per block, blocks per SM)
+// and keeps the fastest.  One block per SM gives a long window a whole SM; more blocks per SM
+// hide latency better when windows are short.
+cudaError_t autotune(sird_batch* b, long long work) {
+    const std::string key = tune_key(b, work);
+    const int cached = tune_cache_get(key);
+    if (cached) {
+        b->block = cached & 0xFFFF;
+        b->per_sm = cached >> 16;
+        return cudaSuccess;
+    }
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return e;
+    float best = 1e30f;
+    int best_block = 128, best_per = 0;
+    for (int block : {128, 256, 512, 1024}) {
+        const int maxper = batch_blocks_per_sm(b->mdl, block, b->n_max);
+        for (int per : {1, 2, maxper}) {
+            if (maxper <= 0 || per > maxper || (per == maxper && per <= 2 && per != maxper)) continue;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // first run warms up
+                e = cudaEventRecord(e0, b->stream);
+                if (e == cudaSuccess) e = run(b, 2, block, per, b->stream, false);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (e != cudaSuccess) break;
+            if (ms < best) {
+                best = ms;
+                best_block = block;
+                best_per = per;
+            }
+        }
+        if (e != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    b->block = best_block;
+    b->per_sm = best_per;
+    tune_cache_put(key, best_block | (best_per << 16));
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" sird_status sird_batch_create(int W, const sird_problem* problems, const sird_pso_config* configs,
+                                         void* cuda_stream, sird_batch_t* out) {
+    if (!out) return berr(SIRD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (W < 1 || W > (1 << 20) || !problems || !configs) return berr(SIRD_ERR_ARG, "bad W or NULL arrays");
+    const sird_problem& p0 = problems[0];
+    const sird_pso_config& c0 = configs[0];
+    std::string why;
+    for (int i = 0; i < W; ++i) {
+        const sird_problem& p = problems[i];
+        const sird_pso_config& c = configs[i];
+        sird_status st = sird_check_problem(&p, why);
+        if (st != SIRD_OK) return berr(st, "window " + std::to_string(i) + ": " + why);
+        if (p.beta_form != p0.beta_form || p.K != p0.K || p.steps_per_day != p0.steps_per_day || p.cost != p0.cost ||
+            p.objective != p0.objective || p.fit_I0 != p0.fit_I0)
+            return berr(SIRD_ERR_ARG, "window " + std::to_string(i) + ": model settings differ from window 0");
+        if (c.precision != 32) return berr(SIRD_ERR_UNSUPPORTED, "batched calibration is FP32 only");
+        if (c.particles < 1 || c.particles > 2048) return berr(SIRD_ERR_ARG, "particles per window out of range [1, 2048]");
+        if (c.iters != c0.iters || c.w != c0.w || c.c1 != c0.c1 || c.c2 != c0.c2 || c.iters < 0)
+            return berr(SIRD_ERR_ARG, "window " + std::to_string(i) + ": PSO coefficients or iterations differ");
+        if (!c.lb || !c.ub) return berr(SIRD_ERR_ARG, "lb/ub is NULL");
+    }
+    const int P = (p0.beta_form == SIRD_BETA_RAMP ? 6 : p0.K + 2) + (p0.fit_I0 ? 1 : 0);
+    for (int i = 0; i < W; ++i)
+        for (int d = 0; d < P; ++d) {
+            const bool lg = configs[i].log_scale && configs[i].log_scale[d];
+            const bool lg0 = c0.log_scale && c0.log_scale[d];
+            if (configs[i].lb[d] != c0.lb[d] || configs[i].ub[d] != c0.ub[d] || lg != lg0)
+                return berr(SIRD_ERR_ARG, "window " + std::to_string(i) + ": bounds differ from window 0");
+        }
+    if (c0.block_size != 0 && (c0.block_size < 32 || c0.block_size > 1024 || c0.block_size % 32))
+        return berr(SIRD_ERR_ARG, "block_size must be 0 (autotune) or a multiple of 32 in [32, 1024]");
+
+    sird_batch* b = new (std::nothrow) sird_batch();
+    if (!b) return berr(SIRD_ERR_NOMEM, "host allocation failed");
+    b->W = W;
+    b->P = P;
+    b->iters = c0.iters;
+    b->stream = (cudaStream_t)cuda_stream;
+    std::vector<BatchWindow> wins(W);
+    std::vector<int> obs_off(W + 1, 0);
+    long long sw_total = 0, work = 0;
+    for (int i = 0; i < W; ++i) {
+        ModelDev m{};
+        sird_fill_window(&problems[i], wins[i].w, m);
+        if (i == 0) b->mdl = m;
+        obs_off[i + 1] = obs_off[i] + ((problems[i].n_obs + 3) & ~3);
+        wins[i].obs_off = obs_off[i];
+        wins[i].M = configs[i].particles;
+        wins[i].ld = (configs[i].particles + 31) & ~31;
+        wins[i].sw_off = sw_total;
+        wins[i].key0 = (uint32_t)configs[i].seed;
+        wins[i].key1 = (uint32_t)(configs[i].seed >> 32);
+        wins[i].stream_id = configs[i].stream_id;
+        sw_total += (long long)(3 * P + 1) * wins[i].ld;
+        b->n_max = std::max(b->n_max, problems[i].n_obs);
+        work += (long long)configs[i].particles * (problems[i].n_obs - 1);
+    }
+    // longest first, so the last windows taken from the queue are short
+    std::vector<int> order(W);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return (long long)wins[a].M * (wins[a].w.n_obs - 1) > (long long)wins[c].M * (wins[c].w.n_obs - 1);
+    });
+    for (int d = 0; d < P; ++d) {
+        const bool lg = c0.log_scale && c0.log_scale[d];
+        if (lg && !(c0.lb[d] > 0)) {
+            delete b;
+            return berr(SIRD_ERR_ARG, "log_scale needs lb > 0");
+        }
+        if (lg) b->c.logmask |= 1u << d;
+        b->c.zlb[d] = (float)(lg ? std::log(c0.lb[d]) : c0.lb[d]);
+        b->c.zub[d] = (float)(lg ? std::log(c0.ub[d]) : c0.ub[d]);
+    }
+    b->c.w = (float)c0.w;
+    b->c.c1 = (float)c0.c1;
+    b->c.c2 = (float)c0.c2;
+    b->ss_tot.resize(W);
+    const size_t nobs = (size_t)obs_off[W];
+    std::vector<float> yf(nobs, 0.f), invy(nobs, 0.f);
+    std::vector<double> yd(nobs, 0.0);
+    for (int i = 0; i < W; ++i) {
+        const sird_problem& p = problems[i];
+        double mean = 0.0;
+        for (int j = 0; j < p.n_obs; ++j) {
+            yf[obs_off[i] + j] = (float)p.y_D[j];
+            invy[obs_off[i] + j] = p.y_D[j] != 0.0 ? (float)(1.0 / p.y_D[j]) : 0.f;
+            yd[obs_off[i] + j] = p.y_D[j];
+            mean += p.y_D[j];
+        }
+        mean /= p.n_obs;
+        double ss = 0.0;
+        for (int j = 0; j < p.n_obs; ++j) ss += (p.y_D[j] - mean) * (p.y_D[j] - mean);
+        b->ss_tot[i] = ss;
+    }
+    auto r256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
+    const size_t bytes = r256(sizeof(BatchWindow) * W) + r256(sizeof(int) * W) + 2 * r256(nobs * sizeof(float)) +
+                         r256(nobs * sizeof(double)) + r256(256) + r256(sizeof(BatchOut) * W) +
+                         r256((size_t)sw_total * sizeof(float));
+    cudaError_t e = cudaMalloc(&b->d_mem, bytes);
+    auto bail = [&](cudaError_t err, const char* what) {
+        std::string m = std::string(what) + ": " + cudaGetErrorString(err);
+        (void)cudaGetLastError();
+        sird_batch_destroy(b);
+        return berr(err == cudaErrorMemoryAllocation ? SIRD_ERR_NOMEM : SIRD_ERR_CUDA, m);
+    };
+    if (e != cudaSuccess) return bail(e, "allocating the batch");
+    unsigned char* q = (unsigned char*)b->d_mem;
+    auto take = [&](size_t n) {
+        unsigned char* r = q;
+        q += (n + 255) & ~(size_t)255;
+        return r;
+    };
+    b->wins = (BatchWindow*)take(sizeof(BatchWindow) * W);
+    b->order = (int*)take(sizeof(int) * W);
+    b->yf = (float*)take(nobs * sizeof(float));
+    b->invy = (float*)take(nobs * sizeof(float));
+    b->yd = (double*)take(nobs * sizeof(double));
+    b->queue = (unsigned*)take(256);
+    b->out = (BatchOut*)take(sizeof(BatchOut) * W);
+    b->swarm = (float*)take((size_t)sw_total * sizeof(float));
+    if ((size_t)(q - (unsigned char*)b->d_mem) > bytes) return bail(cudaErrorInvalidValue, "batch layout");
+    e = cudaMemcpyAsync(b->wins, wins.data(), sizeof(BatchWindow) * W, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->order, order.data(), sizeof(int) * W, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->yf, yf.data(), nobs * sizeof(float), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->invy, invy.data(), nobs * sizeof(float), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->yd, yd.data(), nobs * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bail(e, "uploading the batch");
+    e = cudaMallocHost((void**)&b->h_out, sizeof(BatchOut) * W);
+    if (e != cudaSuccess) return bail(e, "allocating pinned results");
+    if (c0.block_size) {
+        b->block = c0.block_size;
+    } else {
+        e = autotune(b, work);
+        if (e != cudaSuccess) return bail(e, "autotuning");
+    }
+    *out = b;
+    return SIRD_OK;
+}
+
+extern "C" void sird_batch_destroy(sird_batch_t b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->d_mem);
+    if (b->h_out) cudaFreeHost(b->h_out);
+    delete b;
+}
+
+extern "C" int sird_batch_block_size(sird_batch_t b) { return b ? b->block : 0; }
+
+extern "C" int sird_batch_blocks_per_sm(sird_batch_t b) {
+    if (!b) return 0;
+    const int maxper = batch_blocks_per_sm(b->mdl, b->block, b->n_max);
+    return (b->per_sm > 0 && b->per_sm < maxper) ? b->per_sm : maxper;
+}
+
+extern "C" sird_status sird_batch_calibrate(sird_batch_t b, sird_result* results) {
+    if (!b || !results) return berr(SIRD_ERR_ARG, "batch or results is NULL");
+    cudaError_t e = cudaSuccess;
+    if (!b->graph) {
+        if (!b->cap) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+        cudaGraph_t g = nullptr;
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = run(b, b->iters, b->block, b->per_sm, b->cap, true);
+            if (e1 == cudaSuccess)
+                e1 = cudaMemcpyAsync(b->h_out, b->out, sizeof(BatchOut) * b->W, cudaMemcpyDeviceToHost, b->cap);
+            e = cudaStreamEndCapture(b->cap, &g);
+            if (e1 != cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return berr(SIRD_ERR_CUDA, std::string("capturing the batch graph: ") + cudaGetErrorString(e));
+        }
+    }
+    e = cudaGraphLaunch(b->graph, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return berr(SIRD_ERR_CUDA, std::string("batch run: ") + cudaGetErrorString(e));
+    }
+    for (int i = 0; i < b->W; ++i) {
+        sird_result& r = results[i];
+        std::memset(&r, 0, sizeof(r));
+        r.n_params = b->P;
+        for (int d = 0; d < b->P; ++d) r.theta[d] = b->h_out[i].theta[d];
+        r.loss = b->h_out[i].loss64;
+        r.loss_search = (double)b->h_out[i].loss;
+        r.r2_D = b->ss_tot[i] > 0 ? 1.0 - b->h_out[i].sse / b->ss_tot[i] : NAN;
+        r.index = b->h_out[i].index;
+        r.iters_done = b->iters;
+    }
+    return SIRD_OK;
+}
+
+extern "C" sird_status sird_pso_calibrate_batched(int W, const sird_problem* problems, const sird_pso_config* configs,
+                                                  void* cuda_stream, sird_result* results) {
+    if (!results) return berr(SIRD_ERR_ARG, "results is NULL");
+    sird_batch_t b = nullptr;
+    sird_status st = sird_batch_create(W, problems, configs, cuda_stream, &b);
+    if (st != SIRD_OK) return st;
+    st = sird_batch_calibrate(b, results);
+    sird_batch_destroy(b);
+    return st;
+}

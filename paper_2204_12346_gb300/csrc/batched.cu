@@ -1,0 +1,201 @@
+// batched.cu -- many calibration windows in one persistent launch.
+//
+// The paper calibrates every rolling window I_i = [T_i, T_i + tau] separately (Sec. 3.1).  Here
+// W windows of uneven length and swarm size run in one launch: each block takes the next
+// window from an atomic queue (windows sorted longest first, so the tail of the run is made of
+// short ones), runs that window's whole PSO -- initialisation and every iteration -- and takes
+// the next.  A window's swarm never leaves its block, so the synchronous global best is a
+// block-level minimum and no block ever waits for another.  Threads loop over the window's
+// particles (particle j = thread + q * blockDim).
+//
+// Every window uses the same Philox counters, arithmetic and order of updates as a
+// single-window calibration, so its result equals that of sird_pso_calibrate with the same
+// seed and stream word.
+#include <cmath>
+
+#include "kernels.h"
+
+namespace sird {
+
+namespace {
+
+__host__ __device__ __forceinline__ int pad4(int n) { return (n + 3) & ~3; }
+
+template <int SPD, int COST>
+__global__ void __launch_bounds__(1024) pso_batch_f32(const BatchWindow* __restrict__ wins, const int* __restrict__ order,
+                                                     int W, ModelDev m, PsoCoeffs<float> c, const float* __restrict__ yf_all,
+                                                     const float* __restrict__ invy_all, float* __restrict__ swarm,
+                                                     unsigned* __restrict__ queue, BatchOut* __restrict__ out, int iters,
+                                                     int n_max) {
+    extern __shared__ float smem[];
+    __shared__ unsigned long long wk[32];
+    __shared__ int s_win;
+    const int B = blockDim.x, tid = threadIdx.x, P = m.P;
+    float* ys = smem;
+    float* invys = (COST == COST_MAPE) ? ys + pad4(n_max) : ys;
+    float* th_s = smem + pad4(n_max) * (COST == COST_MAPE ? 2 : 1);
+    float* g_s = th_s + P * B;
+    float* lb_s = g_s + kMaxParams;
+    float* ub_s = lb_s + kMaxParams;
+    if (tid < P) {
+        lb_s[tid] = c.zlb[tid];
+        ub_s[tid] = c.zub[tid];
+    }
+    for (;;) {
+        if (tid == 0) {
+            const unsigned q = atomicAdd(queue, 1u);
+            s_win = q < (unsigned)W ? order[q] : -1;
+        }
+        __syncthreads();
+        const int wi = s_win;
+        if (wi < 0) break;
+        const BatchWindow bw = wins[wi];
+        const WindowDev& w = bw.w;
+        for (int i = tid; i < w.n_obs; i += B) {
+            ys[i] = yf_all[bw.obs_off + i];
+            if (COST == COST_MAPE) invys[i] = invy_all[bw.obs_off + i];
+        }
+        float* X = swarm + bw.sw_off;
+        float* V = X + (size_t)P * bw.ld;
+        float* PB = V + (size_t)P * bw.ld;
+        float* PBF = PB + (size_t)P * bw.ld;
+        const int M = bw.M, ld = bw.ld;
+        __syncthreads();
+        unsigned long long gkey = ~0ull;
+        for (int it = 0; it <= iters; ++it) {
+            unsigned long long key = ~0ull;
+            for (int j = tid; j < M; j += B) {
+                uint4 rnd = make_uint4(0, 0, 0, 0);
+                for (int d = 0; d < P; ++d) {
+                    if ((d & 1) == 0)
+                        rnd = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)it, (uint32_t)(d >> 1), bw.stream_id),
+                                            bw.key0, bw.key1);
+                    const float ua = u01f((d & 1) ? rnd.z : rnd.x);
+                    const float ub = u01f((d & 1) ? rnd.w : rnd.y);
+                    const size_t off = (size_t)d * ld + j;
+                    const float lo = lb_s[d], hi = ub_s[d];
+                    float xn, vn;
+                    if (it == 0) {
+                        const float range = __fsub_rn(hi, lo);
+                        xn = fminf(__fmaf_rn(range, ua, lo), hi);
+                        vn = __fmul_rn(range, __fmaf_rn(2.f, ub, -1.f));
+                    } else {
+                        const float x = X[off], v = V[off], pbv = PB[off];
+                        const float t = __fmaf_rn(__fmul_rn(c.c1, ua), __fsub_rn(pbv, x), __fmul_rn(c.w, v));
+                        vn = __fmaf_rn(__fmul_rn(c.c2, ub), __fsub_rn(g_s[d], x), t);
+                        xn = fminf(fmaxf(__fadd_rn(x, vn), lo), hi);
+                    }
+                    X[off] = xn;
+                    V[off] = vn;
+                    th_s[d * B + tid] = ((c.logmask >> d) & 1u) ? expf(xn) : xn;
+                }
+                float f = fitness_f32<SPD, COST>(w, m, ys, invys, th_s + tid, B);
+                if (f != f) f = INFINITY;
+                float best = f;
+                if (it == 0 || f < PBF[j]) {
+                    PBF[j] = f;
+                    for (int d = 0; d < P; ++d) PB[(size_t)d * ld + j] = X[(size_t)d * ld + j];
+                } else {
+                    best = PBF[j];
+                }
+                const unsigned long long kj = argmin_key(best, (uint32_t)j);
+                key = kj < key ? kj : key;
+            }
+            key = warp_min_key(key);
+            if ((tid & 31) == 0) wk[tid >> 5] = key;
+            __syncthreads();
+            gkey = warp_min_key((tid & 31) < (B + 31) / 32 ? wk[tid & 31] : ~0ull);
+            if (tid < P) g_s[tid] = PB[(size_t)tid * ld + (int)(gkey & 0xFFFFFFFFu)];
+            __syncthreads();
+        }
+        if (tid == 0) {
+            out[wi].index = (int)(gkey & 0xFFFFFFFFu);
+            out[wi].loss = from_ordered_bits((uint32_t)(gkey >> 32));
+        }
+        if (tid < P) out[wi].z[tid] = g_s[tid];
+        __syncthreads();  // smem is reused by the next window
+    }
+}
+
+// FP64 re-evaluation of every window's global best (one thread per window).
+__global__ void batch_reeval_kernel(const BatchWindow* __restrict__ wins, int W, ModelDev m, uint32_t logmask,
+                                    const double* __restrict__ yd_all, BatchOut* __restrict__ out) {
+    const int wi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (wi >= W) return;
+    const BatchWindow bw = wins[wi];
+    double th[kMaxParams];
+    for (int d = 0; d < m.P; ++d) {
+        const double z = (double)out[wi].z[d];
+        th[d] = ((logmask >> d) & 1u) ? exp(z) : z;
+        out[wi].theta[d] = th[d];
+    }
+    double sse = 0.0, f = 0.0;
+    const double* ys = yd_all + bw.obs_off;
+    switch (m.cost) {
+        case COST_MSE: f = fitness_f64<COST_MSE>(bw.w, m, ys, th, 1, &sse); break;
+        case COST_MXSE: f = fitness_f64<COST_MXSE>(bw.w, m, ys, th, 1, &sse); break;
+        case COST_MAE: f = fitness_f64<COST_MAE>(bw.w, m, ys, th, 1, &sse); break;
+        default: f = fitness_f64<COST_MAPE>(bw.w, m, ys, th, 1, &sse); break;
+    }
+    out[wi].loss64 = f;
+    out[wi].sse = sse;
+}
+
+}  // namespace
+
+size_t batch_smem_bytes(const ModelDev& m, int block, int n_max) {
+    return ((size_t)pad4(n_max) * (m.cost == COST_MAPE ? 2 : 1) + (size_t)m.P * block + 3 * kMaxParams) *
+           sizeof(float);
+}
+
+#define SIRD_DISPATCH_COST(COSTV, ...)                          \
+    switch (COSTV) {                                            \
+        case COST_MSE: { constexpr int C_ = COST_MSE; __VA_ARGS__; } break;   \
+        case COST_MXSE: { constexpr int C_ = COST_MXSE; __VA_ARGS__; } break; \
+        case COST_MAE: { constexpr int C_ = COST_MAE; __VA_ARGS__; } break;   \
+        default: { constexpr int C_ = COST_MAPE; __VA_ARGS__; } break;        \
+    }
+
+#define SIRD_DISPATCH_SPD(SPDV, ...)                            \
+    switch (SPDV) {                                             \
+        case 10: { constexpr int S_ = 10; __VA_ARGS__; } break; \
+        case 20: { constexpr int S_ = 20; __VA_ARGS__; } break; \
+        default: { constexpr int S_ = 0; __VA_ARGS__; } break;  \
+    }
+
+int batch_blocks_per_sm(const ModelDev& m, int block, int n_max) {
+    const size_t sm = batch_smem_bytes(m, block, n_max);
+    int per = 0;
+    cudaError_t e = cudaSuccess;
+    SIRD_DISPATCH_SPD(m.spd, SIRD_DISPATCH_COST(m.cost, {
+        auto kern = pso_batch_f32<S_, C_>;
+        if (sm > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, block, sm);
+    }));
+    (void)cudaGetLastError();
+    return e == cudaSuccess ? per : 0;
+}
+
+cudaError_t launch_batch(const BatchWindow* wins, const int* order, int W, const ModelDev& m, const PsoCoeffs<float>& c,
+                         const float* yf_all, const float* invy_all, const double* yd_all, float* swarm,
+                         unsigned* queue, BatchOut* out, int iters, int n_max, int block, int grid, bool reeval,
+                         cudaStream_t s) {
+    const size_t sm = batch_smem_bytes(m, block, n_max);
+    (void)cudaGetLastError();
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    SIRD_DISPATCH_SPD(m.spd, SIRD_DISPATCH_COST(m.cost, {
+        auto kern = pso_batch_f32<S_, C_>;
+        if (sm > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e == cudaSuccess)
+            kern<<<grid, block, sm, s>>>(wins, order, W, m, c, yf_all, invy_all, swarm, queue, out, iters, n_max);
+    }));
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess && reeval) {
+        batch_reeval_kernel<<<(W + 63) / 64, 64, 0, s>>>(wins, W, m, c.logmask, yd_all, out);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace sird

@@ -114,6 +114,28 @@ cudaError_t launch_polish(const WindowDev& w, const ModelDev& m, const ObsDev& o
                           double first_step, double* scratch, double* ckpt, int ckpt_every, ResultDev* res,
                           cudaStream_t s);
 
+// ---------------------------------------------------------------- batched windows
+struct BatchWindow {
+    WindowDev w;
+    int obs_off;         // offset of this window's observations in the packed arrays
+    int M, ld;           // particles, leading dimension of its swarm block
+    long long sw_off;    // offset (floats) of its swarm block: x, v, pbest [P][ld], pbest_f [ld]
+    uint32_t key0, key1, stream_id;
+};
+struct BatchOut {
+    float z[kMaxParams];        // global-best position (search coordinates)
+    double theta[kMaxParams];   // decoded in FP64
+    double loss64, sse;         // FP64 re-evaluation
+    float loss;                 // FP32 global-best loss
+    int index;
+};
+size_t batch_smem_bytes(const ModelDev& m, int block, int n_max);
+int batch_blocks_per_sm(const ModelDev& m, int block, int n_max);
+cudaError_t launch_batch(const BatchWindow* wins, const int* order, int W, const ModelDev& m, const PsoCoeffs<float>& c,
+                         const float* yf_all, const float* invy_all, const double* yd_all, float* swarm,
+                         unsigned* queue, BatchOut* out, int iters, int n_max, int block, int grid, bool reeval,
+                         cudaStream_t s);
+
 // Message returned by sird_last_error(NULL) on this thread.
 void set_global_error(const char* msg);
 

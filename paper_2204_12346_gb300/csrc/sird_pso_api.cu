@@ -145,7 +145,7 @@ struct sird_pso {
 
 // ---------------------------------------------------------------- validation
 
-static sird_status check_problem(const sird_problem* pb, std::string& why) {
+sird_status sird_check_problem(const sird_problem* pb, std::string& why) {
     if (!pb) return why = "problem is NULL", SIRD_ERR_ARG;
     if (pb->n_obs < 2 || pb->n_obs > SIRD_MAX_OBS) return why = "n_obs out of range [2, SIRD_MAX_OBS]", SIRD_ERR_ARG;
     if (!pb->y_D) return why = "y_D is NULL", SIRD_ERR_ARG;
@@ -165,7 +165,7 @@ static sird_status check_problem(const sird_problem* pb, std::string& why) {
     return SIRD_OK;
 }
 
-static void fill_window(const sird_problem* pb, WindowDev& w, ModelDev& m) {
+void sird_fill_window(const sird_problem* pb, WindowDev& w, ModelDev& m) {
     const int n = pb->n_obs;
     w.n_obs = n;
     w.n_kept = 0;
@@ -227,7 +227,7 @@ extern "C" sird_status sird_pso_create(const sird_problem* pb, const sird_pso_co
     if (!out) return g_create_error = "out is NULL", SIRD_ERR_ARG;
     *out = nullptr;
     std::string why;
-    sird_status st = check_problem(pb, why);
+    sird_status st = sird_check_problem(pb, why);
     if (st != SIRD_OK) return g_create_error = why, st;
     if (!cfg) return g_create_error = "config is NULL", SIRD_ERR_ARG;
     const int P = nparams_of(pb);
@@ -256,7 +256,7 @@ extern "C" sird_status sird_pso_create(const sird_problem* pb, const sird_pso_co
     if (!h) return g_create_error = "host allocation failed", SIRD_ERR_NOMEM;
     h->stream = (cudaStream_t)cuda_stream;
     h->n_obs = pb->n_obs;
-    fill_window(pb, h->win, h->mdl);
+    sird_fill_window(pb, h->win, h->mdl);
     {
         double mean = 0;
         for (int i = 0; i < pb->n_obs; ++i) mean += pb->y_D[i];
@@ -680,14 +680,14 @@ extern "C" sird_status sird_pso_polish(sird_pso_t h, int k, int iters, double fi
 extern "C" sird_status sird_forecast(const sird_problem* pb, const double* theta, int k, int horizon, double* out_D,
                                      int precision, void* cuda_stream) {
     std::string why;
-    sird_status st = check_problem(pb, why);
+    sird_status st = sird_check_problem(pb, why);
     if (st != SIRD_OK) return g_create_error = why, st;
     if (!theta || !out_D || k < 1 || k > SIRD_MAX_PARTICLES || horizon < 1 || horizon > 100000)
         return g_create_error = "forecast: bad theta/out_D/k/horizon", SIRD_ERR_ARG;
     if (precision != 32 && precision != 64) return g_create_error = "forecast: precision must be 32 or 64", SIRD_ERR_ARG;
     WindowDev w{};
     ModelDev m{};
-    fill_window(pb, w, m);
+    sird_fill_window(pb, w, m);
     const int P = m.P;
     const size_t tsz = precision == 32 ? 4 : 8;
     const size_t th_bytes = (size_t)P * k * tsz, out_bytes = (size_t)k * horizon * tsz;
@@ -743,8 +743,3 @@ extern "C" sird_status sird_pso_topk(sird_pso_t h, int k, double* theta_out, dou
     return h->cuda(e, "topk");
 }
 
-extern "C" sird_status sird_pso_calibrate_batched(int, const sird_problem*, const sird_pso_config*, void*,
-                                                  sird_result*) {
-    g_create_error = "sird_pso_calibrate_batched: not built yet";
-    return SIRD_ERR_UNSUPPORTED;
-}

@@ -29,7 +29,8 @@ EXPORTS = [
     "sird_pso_num_params", "sird_pso_eval", "sird_pso_init", "sird_pso_step", "sird_pso_calibrate",
     "sird_pso_result", "sird_pso_sync", "sird_pso_get_state", "sird_pso_set_state", "sird_loss_grad",
     "sird_forecast", "sird_pso_calibrate_batched", "sird_pso_set_observations", "sird_pso_set_timing", "sird_pso_launch_mode",
-    "sird_pso_step_f32_noalloc", "sird_pso_topk", "sird_pso_polish",
+    "sird_pso_step_f32_noalloc", "sird_pso_topk", "sird_pso_polish", "sird_batch_create", "sird_batch_calibrate",
+    "sird_batch_block_size", "sird_batch_blocks_per_sm", "sird_batch_destroy",
 ]
 
 
@@ -105,6 +106,12 @@ def lib():
         L.sird_pso_set_timing.argtypes = [vp, vp, vp]
         L.sird_pso_launch_mode.argtypes = [vp]
         L.sird_pso_topk.argtypes = [vp, ip, dp, dp]
+        L.sird_batch_create.argtypes = [ip, C.POINTER(Problem), C.POINTER(Config), vp, C.POINTER(vp)]
+        L.sird_batch_calibrate.argtypes = [vp, C.POINTER(Result)]
+        L.sird_batch_block_size.argtypes = [vp]
+        L.sird_batch_blocks_per_sm.argtypes = [vp]
+        L.sird_batch_destroy.argtypes = [vp]
+        L.sird_batch_destroy.restype = None
         L.sird_pso_polish.argtypes = [vp, ip, ip, C.c_double, ip, C.POINTER(Result)]
         L.sird_pso_step_f32_noalloc.argtypes = [C.POINTER(Problem), C.POINTER(Config)] + [vp] * 6 + [ip, ip, vp, vp]
         _lib = L
@@ -341,6 +348,59 @@ try:
             return None, grad * grad_out.unsqueeze(0), None
 except ImportError:  # the binding still loads for CPU-only tooling
     SirdLoss = None
+
+
+class Batch:
+    """Many calibration windows in one persistent launch (wraps a sird_batch_t).
+
+    windows: list of dicts with keys yD, N and optionally R0, I0, particles, seed, stream_id;
+    the model and PSO settings (K, spd, cost, beta_form, fit_I0, iters, lb, ub, log_scale, w,
+    c1, c2, block_size) are shared."""
+
+    def __init__(self, windows, *, K=1, spd=10, cost=COST_MSE, beta_form=BETA_PWC, fit_I0=True, iters=100,
+                 lb=None, ub=None, log_scale=None, w=0.5, c1=0.5, c2=0.5, particles=256, seed=0, block_size=0,
+                 stream=None):
+        self._lib = lib()
+        W = len(windows)
+        self._keep = []
+        pbs = (Problem * W)()
+        cfgs = (Config * W)()
+        for i, win in enumerate(windows):
+            pb, k1 = make_problem(win["yD"], win["N"], K, spd, win.get("R0", 0.0), win.get("I0", 0.0), fit_I0,
+                                  beta_form, cost)
+            cfg, k2 = make_config(int(win.get("particles", particles)), iters, lb, ub, log_scale, w, c1, c2, 32,
+                                  int(win.get("seed", seed)), int(win.get("stream_id", i)), 0,
+                                  block_size if i == 0 else 0, 0)
+            self._keep += k1 + k2
+            pbs[i] = pb
+            cfgs[i] = cfg
+        self._keep += [pbs, cfgs]
+        h = C.c_void_p()
+        st = self._lib.sird_batch_create(W, pbs, cfgs, C.c_void_p(current_stream_handle(stream)), C.byref(h))
+        if st != OK:
+            raise SirdError(st, self._lib.sird_last_error(None).decode())
+        self.h = h
+        self.W = W
+        self.block_size = self._lib.sird_batch_block_size(h)
+        self.blocks_per_sm = self._lib.sird_batch_blocks_per_sm(h)
+
+    def calibrate(self):
+        res = (Result * self.W)()
+        st = self._lib.sird_batch_calibrate(self.h, res)
+        if st != OK:
+            raise SirdError(st, self._lib.sird_last_error(None).decode())
+        return [r.as_dict() for r in res]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.sird_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def forecast(yD, N, theta, horizon, *, K=1, spd=10, R0=0.0, I0=0.0, fit_I0=True, beta_form=BETA_PWC,

@@ -62,3 +62,18 @@ def load_series(name: str) -> dict:
     with open(os.path.join(_GOLDEN, f"series_{name}.json")) as f:
         d = json.load(f)
     return {k: (np.asarray(v, dtype=np.float64) if isinstance(v, list) else v) for k, v in d.items()}
+
+
+def rolling_window_problems(series: dict, layout: dict) -> list:
+    """Cuts windows out of a long stored series: window w covers days T_w .. T_w + L_w; its
+    observed deaths are the noisy cumulative counts on those days (the Euler scheme starts from
+    the first one), R0 is the series' recovered count on day T_w rounded, and its swarm size is
+    layout["M"][w]."""
+    y = series["yD"]
+    R = series["R_true"]
+    out = []
+    for w, (L, M, T) in enumerate(zip(layout["L"], layout["M"], layout["T"])):
+        out.append({"yD": y[T:T + L + 1].copy(), "N": float(series["N"]), "R0": float(np.round(R[T])),
+                    "particles": int(M), "T": int(T), "L": int(L)})
+    return out
+

@@ -1,0 +1,77 @@
+"""Batched calibration of many rolling windows in one launch (GPU only)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2204_12346_gb300 import configs, sird, synth
+from util import f32, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _dev():
+    torch.cuda.set_device(0)
+    O.build()
+
+
+def small_layout():
+    # seven windows of uneven length and ragged swarm sizes cut from the 450-day series
+    return {"L": np.array([21, 34, 25, 40, 22, 30, 27]), "M": np.array([64, 96, 150, 33, 300, 1, 200]),
+            "T": np.array([0, 57, 120, 201, 300, 333, 410])}
+
+
+def shared(K=6):
+    lb, ub = configs.bounds(K, log=True)
+    return dict(K=K, spd=10, lb=lb, ub=ub, log_scale=[1] * len(lb), seed=11)
+
+
+def test_batch_windows_match_single_window_calibrations():
+    ser = synth.load_series("c3")
+    wins = synth.rolling_window_problems(ser, small_layout())
+    kw = shared()
+    batch = sird.Batch(wins, iters=15, **kw)
+    res = batch.calibrate()
+    for i, w in enumerate(wins):
+        cal = sird.Calibrator(w["yD"], w["N"], R0=w["R0"], particles=w["particles"], iters=15, precision=32,
+                              stream_id=i, reeval_topk=0, **kw)
+        r = cal.calibrate()
+        assert res[i]["index"] == r["index"], i
+        assert res[i]["loss_search"] == r["loss_search"], i
+        assert res[i]["loss"] == r["loss"], i
+        assert np.array_equal(res[i]["theta"], r["theta"]), i
+        assert res[i]["r2_D"] == pytest.approx(r["r2_D"], rel=1e-12)
+
+
+def test_batch_block_sizes_agree():
+    ser = synth.load_series("c3")
+    wins = synth.rolling_window_problems(ser, small_layout())
+    out = [sird.Batch(wins, iters=8, block_size=b, **shared()).calibrate() for b in (64, 256)]
+    for a, b in zip(*out):
+        assert a["index"] == b["index"] and a["loss"] == b["loss"]
+    auto = sird.Batch(wins, iters=8, **shared())
+    assert auto.block_size in (128, 256, 512, 1024) and auto.blocks_per_sm >= 1
+
+
+def test_full_512_window_layout_against_the_oracle_at_initialisation():
+    # the batched configuration's layout: 512 windows, 21..90 days, 256..2048 particles, 6 segments
+    c = configs.CONFIGS["c3"]
+    ser = synth.load_series("c3")
+    lay = synth.rolling_windows(W=c["W"], L_min=c["L_min"], L_max=c["L_max"], M_min=c["M_min"], M_max=c["M_max"],
+                                delta=c["delta"], seed=c["seed"])
+    wins = synth.rolling_window_problems(ser, lay)
+    kw = shared(c["K"])
+    res = sird.Batch(wins, iters=0, **kw).calibrate()
+    assert len(res) == 512 and all(np.isfinite(r["loss"]) for r in res)
+    lb, ub = configs.bounds(c["K"], log=True)
+    zlb, zub = f32(np.log(lb)), f32(np.log(ub))
+    for i in np.random.default_rng(0).choice(512, 6, replace=False):
+        w = wins[i]
+        pb = O.Problem(yD=w["yD"], N=w["N"], R0=w["R0"], K=c["K"], spd=10)
+        pso = O.PSO(pb, w["particles"], zlb, zub, logdim=[1] * len(lb), seed=kw["seed"], stream=int(i),
+                    store_f32=True).init()
+        assert rel_err(res[i]["loss_search"], pso.gbest_f) <= 1e-5
+        s = np.sort(pso.pbest_f)
+        if s[1] - s[0] > 3e-5 * s[0]:
+            assert res[i]["index"] == pso.gbest_idx
