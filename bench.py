@@ -1,25 +1,28 @@
 """Benchmark of the calibration hot path on GB300; prints one JSON line.
 
-Workload (default, the single-window FP32 configuration): 60-day window, transmission rate
-piecewise constant over 4 segments (7 parameters with gamma, mu, I0), log-uniform PSO box,
-4096 particles, 1000 PSO iterations, Euler at dt = 0.1 day, FP32 trajectories with a Kahan
-loss, FP64 re-evaluation of the 32 best personal bests.  One step = one full calibration
-(initialisation, 1000 fused PSO iterations, top-k, FP64 re-evaluation) on synthetic deaths
-(Poisson-noised Euler curve at ground-truth rates, N = 38e6).
+Default workload (the batched FP32 configuration): 512 rolling windows cut from a 450-day
+synthetic series, window lengths uniform in 21..90 days, swarms of 256..2048 particles,
+transmission rate piecewise constant over 6 segments (9 parameters with gamma, mu, I0),
+log-uniform PSO box, 100 PSO iterations, Euler at dt = 0.1 day, FP32 trajectories with a Kahan
+loss, one persistent launch captured in a CUDA graph with autotuned block shape, FP64
+re-evaluation of every window's global best.  One step = one such batched calibration.
 
-Metric: particle-day ODE steps per second = particles x days x PSO iterations / second
-(the initial evaluation and the FP64 re-evaluation are extra work, not counted).
+Metric: particle-day ODE steps per second = sum over windows of particles x days, times PSO
+iterations, per second (the initial evaluation and the FP64 re-evaluation are extra work, not
+counted).  The metric's second part, seconds to calibrate at fixed loss, is measured on the
+single 60-day window: the plain FP64 swarm (4096 particles, 1000 iterations) sets the loss
+L_ref; the FP32 swarm followed by the FP64 L-BFGS polish must reach (1 + 1e-6) L_ref.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c2|c1|c5]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c3|c2|c1|c5]
 
-With --gpus N > 1 (one process per GPU under torchrun) every rank calibrates its own
-independent replica (its own Philox stream word, as in repeated calibrations of one
-window); there is no data-path collective, and value = all ranks' particle-days / the
-slowest rank's time (weak scaling).
+With --gpus N > 1 (one process per GPU under torchrun) every rank calibrates its own batch of
+windows (its own Philox stream words); there is no data-path collective, and value = all ranks'
+particle-days / the slowest rank's time (weak scaling).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -42,21 +45,29 @@ UNIT = "particle-days/s"
 SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 
+# DRAM bytes per launch of the dominant kernel from committed ncu captures, valid only for the
+# kernel sources they were taken on (sha256[:16] of the files listed).
+PROFILED = {
+    "c3": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": None,
+           "traffic_bytes": None, "profile": "profiles/pso_batch_f32_c3.md"},
+    "c2": {"files": ["pso_persistent.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"],
+           "sha": "ea40821fd8e456d2", "traffic_bytes": 727296, "profile": "profiles/pso_f32_persistent_c2.md"},
+}
 
-# DRAM bytes per launch of the dominant kernel from the committed ncu capture
-# (profiles/pso_f32_persistent_c2.md), valid only for the kernel sources it was taken on.
-PROFILED_KERNEL_FILES = ["pso_persistent.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"]
-PROFILED = {"sha": "ea40821fd8e456d2", "traffic_bytes": 727296, "profile": "profiles/pso_f32_persistent_c2.md"}
 
-
-def kernel_sources_sha() -> str:
-    import hashlib
-
+def kernel_sources_sha(files) -> str:
     h = hashlib.sha256()
-    for f in PROFILED_KERNEL_FILES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_2204_12346_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    p = PROFILED.get(workload)
+    if not p or p["sha"] is None or kernel_sources_sha(p["files"]) != p["sha"]:
+        return None
+    return p["traffic_bytes"]
 
 
 def algorithmic_flops_per_particle_day(spd: int) -> int:
@@ -65,22 +76,37 @@ def algorithmic_flops_per_particle_day(spd: int) -> int:
     return 8 * spd + 3
 
 
-def workload(name: str):
+def single_window(name: str):
     c = dict(configs.CONFIGS[name])
     ser = synth.load_series(c["series"])
-    days = c["days"]
-    y = ser["yD"][: days + 1]
+    y = ser["yD"][: c["days"] + 1]
     lb, ub = configs.bounds(c["K"], c["log"])
     return c, ser, y, lb, ub
 
 
-def describe(c) -> str:
-    if c["series"] == "c2":
-        return ("single window FP32 + Kahan loss: 60 days, beta piecewise constant over 4 segments (7 params), "
-                "log-uniform PSO box, 4096 particles, 1000 iterations, dt=0.1, FP64 re-evaluation of the 32 best")
-    if c["series"] == "c1":
-        return "plain method FP64: constant beta, gamma, mu + I0, 30 days, 64 particles, 200 iterations, dt=0.1"
-    return f"{c['name']}: K={c['K']}, {c['days']} days, {c['M']} particles, {c['iters']} iterations, spd={c['spd']}"
+def c3_windows(seed_offset: int = 0):
+    c = dict(configs.CONFIGS["c3"])
+    ser = synth.load_series("c3")
+    lay = synth.rolling_windows(W=c["W"], L_min=c["L_min"], L_max=c["L_max"], M_min=c["M_min"], M_max=c["M_max"],
+                                delta=c["delta"], seed=c["seed"])
+    wins = synth.rolling_window_problems(ser, lay)
+    for i, w in enumerate(wins):
+        w["seed"] = c["seed"]
+        w["stream_id"] = seed_offset * c["W"] + i
+    lb, ub = configs.bounds(c["K"], c["log"])
+    return c, wins, lb, ub
+
+
+def describe(name: str) -> str:
+    return {
+        "c3": ("batched FP32: 512 rolling windows of 21..90 days cut from a 450-day series, 256..2048 particles "
+               "per window, beta piecewise constant over 6 segments (9 params), log-uniform PSO box, 100 iterations, "
+               "dt=0.1, one persistent launch in a CUDA graph, autotuned block shape, FP64 re-evaluation per window"),
+        "c2": ("single window FP32 + Kahan loss: 60 days, beta piecewise constant over 4 segments (7 params), "
+               "log-uniform PSO box, 4096 particles, 1000 iterations, dt=0.1, FP64 re-evaluation of the 32 best"),
+        "c1": "plain method FP64: constant beta, gamma, mu + I0, 30 days, 64 particles, 200 iterations, dt=0.1",
+        "c5": "large FP32: 2^20 particles, 10 segments, 120 days, dt=0.05, 100 iterations",
+    }[name]
 
 
 # ------------------------------------------------------------------ clocks
@@ -136,112 +162,8 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ------------------------------------------------------------------ our arm
-
 def flush_l2(buf):
     buf.add_(1.0)  # 256 MiB write, larger than the 129 MB L2
-
-
-def run_ours(args, rank: int, world: int) -> dict | None:
-    import torch
-
-    from paper_2204_12346_gb300 import sird
-
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-    c, ser, y, lb, ub = workload(args.workload)
-    log = [1] * len(lb) if c["log"] else None
-    stream = torch.cuda.Stream()
-    kw = dict(K=c["K"], spd=c["spd"], particles=c["M"], iters=c["iters"], lb=lb, ub=ub, log_scale=log,
-              precision=c["precision"], seed=c["seed"], stream_id=rank, reeval_topk=c.get("reeval_topk", 0))
-    with torch.cuda.stream(stream):
-        cal = sird.Calibrator(y, ser["N"], stream=stream, **kw)
-        ev_it0, ev_it1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev_it0.record(stream)  # torch only reads events it has seen recorded once; the graph re-records them
-        ev_it1.record(stream)
-        cal.set_timing(ev_it0, ev_it1)
-        flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
-        for _ in range(args.warmup):
-            res = cal.calibrate()
-        L = c["days"]
-        units_per_step = c["M"] * L * c["iters"]
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        iter_ms = []
-        _barrier(world)
-        torch.cuda.synchronize()
-        with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
-            for i in range(args.steps):
-                flush_l2(flush)
-                starts[i].record(stream)
-                res = cal.calibrate()
-                ends[i].record(stream)
-                torch.cuda.synchronize()
-                iter_ms.append(ev_it0.elapsed_time(ev_it1))
-        torch.cuda.synchronize()
-        _barrier(world)
-        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-        total_ms = _max_over_ranks(sum(step_ms), world)
-
-        # end to end through the public API with host buffers: upload this step's observations
-        # from host memory, calibrate, read the result back (the result struct is the output)
-        e2e_ms = []
-        y_host = np.asarray(y, dtype=np.float64)
-        for i in range(args.steps):
-            flush_l2(flush)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            cal.set_observations(y_host)
-            r2 = cal.calibrate()
-            e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        e2e_total = _max_over_ranks(sum(e2e_ms), world)
-        assert r2["loss"] == res["loss"]
-
-    if rank != 0:
-        return None
-    value = units_per_step * args.steps * world / (total_ms / 1e3)
-    e2e_value = units_per_step * args.steps * world / (e2e_total / 1e3)
-    spd = c["spd"]
-    flops_per_launch = c["M"] * L * algorithmic_flops_per_particle_day(spd)
-    avg_iter_ms = statistics.mean(iter_ms) / c["iters"]
-    achieved_tflops = flops_per_launch / (avg_iter_ms / 1e3) / 1e12
-    n_obs = L + 1
-    h2d = n_obs * (4 + 4 + 8)
-    d2h = 8 * 32 + 8 * 3 + 8  # ResultDev
-    topk_passes = 1 if c.get("reeval_topk", 0) else 0
-    persistent = cal.launch_mode == sird.LAUNCH_PERSISTENT
-    iter_launches = 1 if persistent else c["iters"]
-    launches = args.steps * (1 + iter_launches + topk_passes + 1)
-    kernel = ("pso_f32_persistent (all iterations in one cooperative launch)" if persistent
-              else "pso_f32_kernel (one fused PSO iteration per launch)")
-    launch_us = statistics.mean(iter_ms) * 1e3 / iter_launches
-    out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if c["precision"] == 32 else "f64", "data": "synthetic",
-        "config": {"workload": describe(c), "name": c["name"], "particles": c["M"], "days": L,
-                   "iterations": c["iters"], "steps_per_day": spd, "params": len(lb),
-                   "l2": "flushed between timed steps (256 MiB write); the 1000 iterations inside one "
-                         "calibration keep the swarm resident in L2 by design",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP32_PEAK_TFLOPS,
-                     "traffic": (PROFILED["traffic_bytes"] if persistent and args.workload == "c2"
-                                 and kernel_sources_sha() == PROFILED["sha"] else None),
-                     "traffic_source": PROFILED["profile"],
-                     "kernel": kernel, "avg_launch_us": launch_us, "us_per_iteration": avg_iter_ms * 1e3,
-                     "flops_per_launch": flops_per_launch * c["iters"] / iter_launches,
-                     "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": e2e_total / args.steps},
-        "gpu_launches": launches,
-        "result": {"loss_fp64": res["loss"], "loss_search": res["loss_search"], "r2_D": res["r2_D"],
-                   "theta": [float(v) for v in res["theta"]]},
-    }
-    out["clocks"] = clk.summary()
-    if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_budget)
-    return out
 
 
 def _barrier(world):
@@ -262,59 +184,264 @@ def _max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def timed_steps(args, world, stream, step_fn, kernel_events):
+    """Runs args.steps steps with an L2 flush before each, timed by CUDA events on `stream`.
+    Returns (total ms max over ranks, per-step kernel ms from kernel_events, clocks, last result)."""
+    import torch
+
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kern_ms = []
+    res = None
+    _barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush_l2(flush)
+            starts[i].record(stream)
+            res = step_fn()
+            ends[i].record(stream)
+            torch.cuda.synchronize()
+            kern_ms.append(kernel_events[0].elapsed_time(kernel_events[1]))
+    torch.cuda.synchronize()
+    _barrier(world)
+    total = _max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world)
+    return total, kern_ms, clk.summary(), res
+
+
+# ------------------------------------------------------------------ seconds to calibrate
+
+def s_to_calibrate() -> dict:
+    """Single 60-day window: wall seconds of the plain FP64 swarm (its final loss is L_ref) vs the
+    FP32 swarm plus FP64 L-BFGS polish until the loss is <= (1 + 1e-6) L_ref."""
+    import torch
+
+    from paper_2204_12346_gb300 import sird
+
+    c, ser, y, lb, ub = single_window("c2")
+    kw = dict(K=c["K"], spd=c["spd"], particles=c["M"], iters=c["iters"], lb=lb, ub=ub,
+              log_scale=[1] * len(lb), seed=c["seed"])
+    c64 = sird.Calibrator(y, ser["N"], precision=64, **kw)
+    c64.calibrate()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r64 = c64.calibrate()
+    t64 = time.perf_counter() - t0
+    target = r64["loss"] * (1 + 1e-6)
+    c32 = sird.Calibrator(y, ser["N"], precision=32, reeval_topk=32, **kw)
+    c32.calibrate()
+    out = {"window": "60 days, 4 segments, 4096 particles, 1000 PSO iterations, dt=0.1", "L_ref": r64["loss"],
+           "target": "(1 + 1e-6) L_ref", "fp64_pso_s": t64}
+    loss = float("inf")
+    for n in (0, 5, 10, 15, 20, 30, 40, 50, 75, 100, 150, 200, 300):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r32 = c32.calibrate()
+        loss = r32["loss"]
+        if n > 0:
+            rp = c32.polish(k=32, iters=n, first_step=1e-2)
+            loss = min(loss, rp["loss"])
+        dt = time.perf_counter() - t0
+        if loss <= target:
+            out.update({"fp32_plus_polish_s": dt, "polish_iters": n, "loss_reached": loss,
+                        "speedup": t64 / dt, "reached": True})
+            return out
+    out.update({"reached": False, "loss_reached": loss})
+    return out
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_c3(args, rank, world):
+    import torch
+
+    from paper_2204_12346_gb300 import sird
+
+    c, wins, lb, ub = c3_windows(rank)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch = sird.Batch(wins, K=c["K"], spd=c["spd"], iters=c["iters"], lb=lb, ub=ub, log_scale=[1] * len(lb),
+                           stream=stream)
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record(stream)  # torch reads only events it has seen recorded; the graph re-records them
+        ev[1].record(stream)
+        batch.set_timing(*ev)
+        for _ in range(args.warmup):
+            batch.calibrate()
+    total_ms, kern_ms, clocks, res = timed_steps(args, world, stream, batch.calibrate, ev)
+
+    # end to end through the public one-shot call with host buffers: upload every window's
+    # observations and settings, calibrate, copy the results back (autotuned shape passed in)
+    e2e = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sird.calibrate_batched(wins, K=c["K"], spd=c["spd"], iters=c["iters"], lb=lb, ub=ub,
+                               log_scale=[1] * len(lb), block_size=batch.block_size, stream=stream)
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = _max_over_ranks(sum(e2e), world)
+    if rank != 0:
+        return None
+    pdays = sum(w["particles"] * w["L"] for w in wins)
+    units = pdays * c["iters"]
+    flops = pdays * algorithmic_flops_per_particle_day(c["spd"]) * (c["iters"] + 1)
+    kms = statistics.mean(kern_ms)
+    achieved = flops / (kms / 1e3) / 1e12
+    h2d = sum(((len(w["yD"]) + 3) // 4 * 4) * 16 for w in wins) + len(wins) * 180
+    d2h = len(wins) * 464
+    out = {
+        "metric": METRIC, "value": units * args.steps * world / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": describe("c3"), "name": c["name"], "windows": len(wins),
+                   "particle_days_per_iteration": pdays, "iterations": c["iters"], "steps_per_day": c["spd"],
+                   "params": len(lb), "block": f"{batch.block_size} threads x {batch.blocks_per_sm} per SM (autotuned)",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"independent batches x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic("c3"),
+                     "traffic_source": PROFILED["c3"]["profile"], "kernel": "pso_batch_f32",
+                     "avg_launch_us": kms * 1e3, "flops_per_launch": flops,
+                     "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+        "e2e": {"value": units * args.steps * world / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_total / args.steps},
+        "gpu_launches": args.steps * 2,
+        "clocks": clocks,
+        "result": {"windows": len(res), "median_r2_D": float(np.median([r["r2_D"] for r in res])),
+                   "window0_loss_fp64": res[0]["loss"]},
+    }
+    if not args.no_s2c:
+        out["s_to_calibrate"] = s_to_calibrate()
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline("c3", budget_s=args.cpu_budget)
+    return out
+
+
+def run_single(args, rank, world):
+    import torch
+
+    from paper_2204_12346_gb300 import sird
+
+    c, ser, y, lb, ub = single_window(args.workload)
+    stream = torch.cuda.Stream()
+    kw = dict(K=c["K"], spd=c["spd"], particles=c["M"], iters=c["iters"], lb=lb, ub=ub,
+              log_scale=[1] * len(lb) if c["log"] else None, precision=c["precision"], seed=c["seed"],
+              stream_id=rank, reeval_topk=c.get("reeval_topk", 0))
+    with torch.cuda.stream(stream):
+        cal = sird.Calibrator(y, ser["N"], stream=stream, **kw)
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record(stream)
+        ev[1].record(stream)
+        cal.set_timing(*ev)
+        for _ in range(args.warmup):
+            cal.calibrate()
+    total_ms, kern_ms, clocks, res = timed_steps(args, world, stream, cal.calibrate, ev)
+    e2e = []
+    y_host = np.asarray(y, dtype=np.float64)
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cal.set_observations(y_host)
+        cal.calibrate()
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = _max_over_ranks(sum(e2e), world)
+    if rank != 0:
+        return None
+    L, spd = c["days"], c["spd"]
+    units = c["M"] * L * c["iters"]
+    persistent = cal.launch_mode == sird.LAUNCH_PERSISTENT
+    iter_launches = 1 if persistent else c["iters"]
+    kms = statistics.mean(kern_ms)
+    flops = c["M"] * L * algorithmic_flops_per_particle_day(spd) * c["iters"]
+    achieved = flops / (kms / 1e3) / 1e12
+    fp64 = c["precision"] == 64
+    peak = 1.25 if fp64 else FP32_PEAK_TFLOPS
+    out = {
+        "metric": METRIC, "value": units * args.steps * world / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
+        "config": {"workload": describe(args.workload), "name": c["name"], "particles": c["M"], "days": L,
+                   "iterations": c["iters"], "steps_per_day": spd, "params": len(lb),
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": profiled_traffic(args.workload) if persistent else None,
+                     "kernel": "pso_f32_persistent" if persistent else ("pso_f64_kernel" if fp64 else "pso_f32_kernel"),
+                     "avg_launch_us": kms * 1e3 / iter_launches, "us_per_iteration": kms * 1e3 / c["iters"],
+                     "peak_basis": ("nominal FP64 1.25 TFLOP/s" if fp64
+                                    else "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz")},
+        "e2e": {"value": units * args.steps * world / (e2e_total / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": (L + 1) * 16, "d2h_bytes_per_step": 288, "ms_per_step": e2e_total / args.steps},
+        "gpu_launches": args.steps * (1 + iter_launches + (1 if c.get("reeval_topk", 0) else 0) + 1),
+        "clocks": clocks,
+        "result": {"loss_fp64": res["loss"], "loss_search": res["loss_search"], "r2_D": res["r2_D"]},
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_budget)
+    return out
+
+
 # ------------------------------------------------------------------ oracle on the host cores
 
 def cpu_baseline(name: str, budget_s: float = 15.0, iters_cap: int | None = None) -> dict:
-    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the workload:
-    the same swarm (all particles) for as many PSO iterations as fit in about budget_s."""
-    import oracle as O
-
-    c, ser, y, lb, ub = workload(name)
-    K = c["K"]
-    logd = [1] * len(lb) if c["log"] else [0] * len(lb)
-    zlb = np.log(lb) if c["log"] else np.array(lb, float)
-    zub = np.log(ub) if c["log"] else np.array(ub, float)
-    pb = O.Problem(yD=y, N=ser["N"], K=K, spd=c["spd"])
-    pso = O.PSO(pb, c["M"], zlb, zub, logdim=logd, seed=c["seed"], store_f32=c["precision"] == 32)
-    t0 = time.perf_counter()
-    pso.init()
-    its = 0
-    while time.perf_counter() - t0 < budget_s and (iters_cap is None or its < iters_cap):
-        pso.step(1)
-        its += 1
-    dt = time.perf_counter() - t0
-    units = c["M"] * c["days"] * (its + 1)
-    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{c['M']} particles x {c['days']} days, init + {its} PSO iterations "
-                      f"({dt:.1f} s, single thread, FP64)"}
-
-
-def run_reference(args, rank: int, world: int) -> dict | None:
-    if rank != 0:
-        return None
-    c, ser, y, lb, ub = workload(args.workload)
-    per_step = []
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the workload."""
     import oracle as O
 
     O.build()
+    t0 = time.perf_counter()
+    units = 0
+    if name == "c3":
+        c, wins, lb, ub = c3_windows(0)
+        zlb, zub = np.log(lb), np.log(ub)
+        done = 0
+        for w in wins:
+            if time.perf_counter() - t0 >= budget_s or (iters_cap is not None and done >= iters_cap):
+                break
+            pb = O.Problem(yD=w["yD"], N=w["N"], R0=w["R0"], K=c["K"], spd=c["spd"])
+            O.PSO(pb, w["particles"], zlb, zub, logdim=[1] * len(lb), seed=w["seed"], stream=w["stream_id"],
+                  store_f32=True).init().step(1)
+            units += w["particles"] * w["L"] * 2
+            done += 1
+        sample = f"{done} windows x (init + 1 PSO iteration), full swarms"
+    else:
+        c, ser, y, lb, ub = single_window(name)
+        logd = [1] * len(lb) if c["log"] else [0] * len(lb)
+        zlb = np.log(lb) if c["log"] else np.array(lb, float)
+        zub = np.log(ub) if c["log"] else np.array(ub, float)
+        pso = O.PSO(O.Problem(yD=y, N=ser["N"], K=c["K"], spd=c["spd"]), c["M"], zlb, zub, logdim=logd,
+                    seed=c["seed"], store_f32=c["precision"] == 32).init()
+        its = 0
+        while time.perf_counter() - t0 < budget_s and (iters_cap is None or its < iters_cap):
+            pso.step(1)
+            its += 1
+        units = c["M"] * c["days"] * (its + 1)
+        sample = f"{c['M']} particles x {c['days']} days, init + {its} PSO iterations"
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample}, single thread, FP64 ({dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    per_step = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        cb = cpu_baseline(args.workload, budget_s=0.0, iters_cap=args.ref_iters)
+        cb = cpu_baseline(args.workload, budget_s=1e9, iters_cap=args.ref_units)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             per_step.append((cb, dt))
-    units = sum(c["M"] * c["days"] * (args.ref_iters + 1) for _ in per_step)
-    secs = sum(dt for _, dt in per_step)
-    value = units / secs
+    value = statistics.mean(cb["value"] for cb, _ in per_step)
+    ms = statistics.mean(dt for _, dt in per_step) * 1e3
     return {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / len(per_step) * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": describe(c), "name": c["name"],
-                   "sample": f"each step: init + {args.ref_iters} PSO iterations of the full swarm"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{c['M']} particles x {c['days']} days x (init + {args.ref_iters} iterations) "
-                                   f"per step, single thread"},
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": describe(args.workload), "name": configs.CONFIGS[args.workload]["name"],
+                   "sample": per_step[0][0]["sample"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": per_step[0][0]["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -325,10 +452,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c1", "c2", "c5"], default="c2")
+    ap.add_argument("--workload", choices=["c3", "c2", "c1", "c5"], default="c3")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--ref-iters", type=int, default=4)
+    ap.add_argument("--ref-units", type=int, default=2,
+                    help="reference arm: windows (batched) or PSO iterations (single window) per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-s2c", action="store_true", help="skip the seconds-to-calibrate comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -339,10 +468,16 @@ def main():
         import torch
         import torch.distributed as dist
 
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        if args.impl == "ours":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
     try:
-        out = run_ours(args, rank, world) if args.impl == "ours" else run_reference(args, rank, world)
+        if args.impl == "reference":
+            out = run_reference(args, rank, world)
+        elif args.workload == "c3":
+            out = run_c3(args, rank, world)
+        else:
+            out = run_single(args, rank, world)
     finally:
         if world > 1:
             import torch.distributed as dist

@@ -285,6 +285,9 @@ sird_status sird_batch_calibrate(sird_batch_t b, sird_result* results);
 /* Threads per block and blocks per SM the batch runs with (autotuned or given); 0 if b is NULL. */
 int sird_batch_block_size(sird_batch_t b);
 int sird_batch_blocks_per_sm(sird_batch_t b);
+/* Measurement hook: every later sird_batch_calibrate records the two CUDA events (cudaEvent_t;
+ * NULL to stop) right before and right after the batch kernel.  Re-captures the graph. */
+sird_status sird_batch_set_timing(sird_batch_t b, void* event_begin, void* event_end);
 void sird_batch_destroy(sird_batch_t b);
 /* One-shot create + calibrate + destroy.  Errors of the batch calls: sird_last_error(NULL). */
 sird_status sird_pso_calibrate_batched(int W, const sird_problem* problems, const sird_pso_config* configs,

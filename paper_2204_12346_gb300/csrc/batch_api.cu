@@ -32,6 +32,7 @@ struct sird_batch {
     BatchOut* h_out = nullptr;  // pinned
     std::vector<double> ss_tot;
     cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // optional timing events around the batch kernel
     std::string msg;
 };
 
@@ -82,7 +83,7 @@ void tune_cache_put(const std::string& key, int block) {
     std::fclose(f);
 }
 
-cudaError_t run(sird_batch* b, int iters, int block, int per_sm, cudaStream_t s, bool reeval) {
+cudaError_t run(sird_batch* b, int iters, int block, int per_sm, cudaStream_t s, bool reeval, bool timed = false) {
     int per = batch_blocks_per_sm(b->mdl, block, b->n_max);
     if (per <= 0) return cudaErrorInvalidConfiguration;
     if (per_sm > 0 && per_sm < per) per = per_sm;
@@ -91,8 +92,15 @@ cudaError_t run(sird_batch* b, int iters, int block, int per_sm, cudaStream_t s,
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::min(b->W, per * nsm);
     b->grid = grid;
-    return launch_batch(b->wins, b->order, b->W, b->mdl, b->c, b->yf, b->invy, b->yd, b->swarm, b->queue, b->out,
-                        iters, b->n_max, block, grid, reeval, s);
+    cudaError_t e = cudaSuccess;
+    if (timed && b->ev_begin) e = cudaEventRecordWithFlags(b->ev_begin, s, cudaEventRecordExternal);
+    if (e == cudaSuccess)
+        e = launch_batch(b->wins, b->order, b->W, b->mdl, b->c, b->yf, b->invy, b->yd, b->swarm, b->queue, b->out,
+                         iters, b->n_max, block, grid, false, s);
+    if (e == cudaSuccess && timed && b->ev_end) e = cudaEventRecordWithFlags(b->ev_end, s, cudaEventRecordExternal);
+    if (e == cudaSuccess && reeval)
+        e = launch_batch_reeval(b->wins, b->W, b->mdl, b->c.logmask, b->yd, b->out, s);
+    return e;
 }
 
 // Times short trial runs (2 iterations) of each candidate (threads per block, blocks per SM)
@@ -297,6 +305,17 @@ extern "C" void sird_batch_destroy(sird_batch_t b) {
 
 extern "C" int sird_batch_block_size(sird_batch_t b) { return b ? b->block : 0; }
 
+extern "C" sird_status sird_batch_set_timing(sird_batch_t b, void* event_begin, void* event_end) {
+    if (!b) return berr(SIRD_ERR_ARG, "batch is NULL");
+    b->ev_begin = (cudaEvent_t)event_begin;
+    b->ev_end = (cudaEvent_t)event_end;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return SIRD_OK;
+}
+
 extern "C" int sird_batch_blocks_per_sm(sird_batch_t b) {
     if (!b) return 0;
     const int maxper = batch_blocks_per_sm(b->mdl, b->block, b->n_max);
@@ -311,7 +330,7 @@ extern "C" sird_status sird_batch_calibrate(sird_batch_t b, sird_result* results
         cudaGraph_t g = nullptr;
         if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e1 = run(b, b->iters, b->block, b->per_sm, b->cap, true);
+            cudaError_t e1 = run(b, b->iters, b->block, b->per_sm, b->cap, true, true);
             if (e1 == cudaSuccess)
                 e1 = cudaMemcpyAsync(b->h_out, b->out, sizeof(BatchOut) * b->W, cudaMemcpyDeviceToHost, b->cap);
             e = cudaStreamEndCapture(b->cap, &g);

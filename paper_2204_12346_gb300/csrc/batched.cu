@@ -191,11 +191,15 @@ cudaError_t launch_batch(const BatchWindow* wins, const int* order, int W, const
             kern<<<grid, block, sm, s>>>(wins, order, W, m, c, yf_all, invy_all, swarm, queue, out, iters, n_max);
     }));
     if (e == cudaSuccess) e = cudaGetLastError();
-    if (e == cudaSuccess && reeval) {
-        batch_reeval_kernel<<<(W + 63) / 64, 64, 0, s>>>(wins, W, m, c.logmask, yd_all, out);
-        e = cudaGetLastError();
-    }
+    if (e == cudaSuccess && reeval) e = launch_batch_reeval(wins, W, m, c.logmask, yd_all, out, s);
     return e;
+}
+
+cudaError_t launch_batch_reeval(const BatchWindow* wins, int W, const ModelDev& m, uint32_t logmask,
+                                const double* yd_all, BatchOut* out, cudaStream_t s) {
+    (void)cudaGetLastError();
+    batch_reeval_kernel<<<(W + 63) / 64, 64, 0, s>>>(wins, W, m, logmask, yd_all, out);
+    return cudaGetLastError();
 }
 
 }  // namespace sird

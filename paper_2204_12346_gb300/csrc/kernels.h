@@ -135,6 +135,8 @@ cudaError_t launch_batch(const BatchWindow* wins, const int* order, int W, const
                          const float* yf_all, const float* invy_all, const double* yd_all, float* swarm,
                          unsigned* queue, BatchOut* out, int iters, int n_max, int block, int grid, bool reeval,
                          cudaStream_t s);
+cudaError_t launch_batch_reeval(const BatchWindow* wins, int W, const ModelDev& m, uint32_t logmask,
+                                const double* yd_all, BatchOut* out, cudaStream_t s);
 
 // Message returned by sird_last_error(NULL) on this thread.
 void set_global_error(const char* msg);

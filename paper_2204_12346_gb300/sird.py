@@ -30,7 +30,7 @@ EXPORTS = [
     "sird_pso_result", "sird_pso_sync", "sird_pso_get_state", "sird_pso_set_state", "sird_loss_grad",
     "sird_forecast", "sird_pso_calibrate_batched", "sird_pso_set_observations", "sird_pso_set_timing", "sird_pso_launch_mode",
     "sird_pso_step_f32_noalloc", "sird_pso_topk", "sird_pso_polish", "sird_batch_create", "sird_batch_calibrate",
-    "sird_batch_block_size", "sird_batch_blocks_per_sm", "sird_batch_destroy",
+    "sird_batch_block_size", "sird_batch_blocks_per_sm", "sird_batch_destroy", "sird_batch_set_timing",
 ]
 
 
@@ -110,6 +110,7 @@ def lib():
         L.sird_batch_calibrate.argtypes = [vp, C.POINTER(Result)]
         L.sird_batch_block_size.argtypes = [vp]
         L.sird_batch_blocks_per_sm.argtypes = [vp]
+        L.sird_batch_set_timing.argtypes = [vp, vp, vp]
         L.sird_batch_destroy.argtypes = [vp]
         L.sird_batch_destroy.restype = None
         L.sird_pso_polish.argtypes = [vp, ip, ip, C.c_double, ip, C.POINTER(Result)]
@@ -350,6 +351,25 @@ except ImportError:  # the binding still loads for CPU-only tooling
     SirdLoss = None
 
 
+def _batch_structs(windows, K, spd, cost, beta_form, fit_I0, iters, lb, ub, log_scale, w, c1, c2, particles, seed,
+                   block_size):
+    W = len(windows)
+    keep = []
+    pbs = (Problem * W)()
+    cfgs = (Config * W)()
+    for i, win in enumerate(windows):
+        pb, k1 = make_problem(win["yD"], win["N"], K, spd, win.get("R0", 0.0), win.get("I0", 0.0), fit_I0,
+                              beta_form, cost)
+        cfg, k2 = make_config(int(win.get("particles", particles)), iters, lb, ub, log_scale, w, c1, c2, 32,
+                              int(win.get("seed", seed)), int(win.get("stream_id", i)), 0,
+                              block_size if i == 0 else 0, 0)
+        keep += k1 + k2
+        pbs[i] = pb
+        cfgs[i] = cfg
+    keep += [pbs, cfgs]
+    return pbs, cfgs, keep
+
+
 class Batch:
     """Many calibration windows in one persistent launch (wraps a sird_batch_t).
 
@@ -362,19 +382,8 @@ class Batch:
                  stream=None):
         self._lib = lib()
         W = len(windows)
-        self._keep = []
-        pbs = (Problem * W)()
-        cfgs = (Config * W)()
-        for i, win in enumerate(windows):
-            pb, k1 = make_problem(win["yD"], win["N"], K, spd, win.get("R0", 0.0), win.get("I0", 0.0), fit_I0,
-                                  beta_form, cost)
-            cfg, k2 = make_config(int(win.get("particles", particles)), iters, lb, ub, log_scale, w, c1, c2, 32,
-                                  int(win.get("seed", seed)), int(win.get("stream_id", i)), 0,
-                                  block_size if i == 0 else 0, 0)
-            self._keep += k1 + k2
-            pbs[i] = pb
-            cfgs[i] = cfg
-        self._keep += [pbs, cfgs]
+        pbs, cfgs, self._keep = _batch_structs(windows, K, spd, cost, beta_form, fit_I0, iters, lb, ub, log_scale,
+                                               w, c1, c2, particles, seed, block_size)
         h = C.c_void_p()
         st = self._lib.sird_batch_create(W, pbs, cfgs, C.c_void_p(current_stream_handle(stream)), C.byref(h))
         if st != OK:
@@ -383,6 +392,14 @@ class Batch:
         self.W = W
         self.block_size = self._lib.sird_batch_block_size(h)
         self.blocks_per_sm = self._lib.sird_batch_blocks_per_sm(h)
+
+    def set_timing(self, ev_begin=None, ev_end=None):
+        """torch.cuda.Event pair recorded around the batch kernel of every calibrate."""
+        b = C.c_void_p(ev_begin.cuda_event) if ev_begin is not None else None
+        e = C.c_void_p(ev_end.cuda_event) if ev_end is not None else None
+        st = self._lib.sird_batch_set_timing(self.h, b, e)
+        if st != OK:
+            raise SirdError(st, self._lib.sird_last_error(None).decode())
 
     def calibrate(self):
         res = (Result * self.W)()
@@ -401,6 +418,21 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def calibrate_batched(windows, *, K=1, spd=10, cost=COST_MSE, beta_form=BETA_PWC, fit_I0=True, iters=100, lb=None,
+                      ub=None, log_scale=None, w=0.5, c1=0.5, c2=0.5, particles=256, seed=0, block_size=0,
+                      stream=None):
+    """One-shot batched calibration (sird_pso_calibrate_batched): host inputs in, results out."""
+    L = lib()
+    W = len(windows)
+    pbs, cfgs, keep = _batch_structs(windows, K, spd, cost, beta_form, fit_I0, iters, lb, ub, log_scale, w, c1, c2,
+                                     particles, seed, block_size)
+    res = (Result * W)()
+    st = L.sird_pso_calibrate_batched(W, pbs, cfgs, C.c_void_p(current_stream_handle(stream)), res)
+    if st != OK:
+        raise SirdError(st, L.sird_last_error(None).decode())
+    return [r.as_dict() for r in res]
 
 
 def forecast(yD, N, theta, horizon, *, K=1, spd=10, R0=0.0, I0=0.0, fit_I0=True, beta_form=BETA_PWC,
