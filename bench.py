@@ -48,8 +48,8 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 # DRAM bytes per launch of the dominant kernel from committed ncu captures, valid only for the
 # kernel sources they were taken on (sha256[:16] of the files listed).
 PROFILED = {
-    "c3": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": None,
-           "traffic_bytes": None, "profile": "profiles/pso_batch_f32_c3.md"},
+    "c3": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "64aa7529fa253ee8",
+           "traffic_bytes": 13113856, "profile": "profiles/pso_batch_f32_c3.md"},
     "c2": {"files": ["pso_persistent.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"],
            "sha": "ea40821fd8e456d2", "traffic_bytes": 727296, "profile": "profiles/pso_f32_persistent_c2.md"},
 }
@@ -263,7 +263,7 @@ def run_c3(args, rank, world):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         batch = sird.Batch(wins, K=c["K"], spd=c["spd"], iters=c["iters"], lb=lb, ub=ub, log_scale=[1] * len(lb),
-                           stream=stream)
+                           block_size=args.block, stream=stream)
         ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
         ev[0].record(stream)  # torch reads only events it has seen recorded; the graph re-records them
         ev[1].record(stream)
@@ -297,7 +297,8 @@ def run_c3(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": describe("c3"), "name": c["name"], "windows": len(wins),
                    "particle_days_per_iteration": pdays, "iterations": c["iters"], "steps_per_day": c["spd"],
-                   "params": len(lb), "block": f"{batch.block_size} threads x {batch.blocks_per_sm} per SM (autotuned)",
+                   "params": len(lb), "block": f"{batch.block_size} threads x {batch.blocks_per_sm} per SM "
+                                               + ("(autotuned)" if args.block == 0 else "(given)"),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"independent batches x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -458,6 +459,7 @@ def main():
                     help="reference arm: windows (batched) or PSO iterations (single window) per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-s2c", action="store_true", help="skip the seconds-to-calibrate comparison")
+    ap.add_argument("--block", type=int, default=0, help="batched: threads per block (0 = autotune)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -123,7 +123,8 @@ cudaError_t autotune(sird_batch* b, long long work) {
     for (int block : {128, 256, 512, 1024}) {
         const int maxper = batch_blocks_per_sm(b->mdl, block, b->n_max);
         for (int per : {1, 2, maxper}) {
-            if (maxper <= 0 || per > maxper || (per == maxper && per <= 2 && per != maxper)) continue;
+            // each distinct (block, blocks per SM) that fits, once
+            if (maxper <= 0 || per > maxper || (per == maxper && maxper <= 2)) continue;
             float ms = 0.f;
             for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // first run warms up
                 e = cudaEventRecord(e0, b->stream);
