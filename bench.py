@@ -76,6 +76,11 @@ def algorithmic_flops_per_particle_day(spd: int) -> int:
     return 8 * spd + 3
 
 
+# FP64 gradient: 8 flops forward, 8 to recompute the stretch from its checkpoint, 20 in the
+# reverse step (lambda_S, lambda_I and the three parameter sums, FMA counted as 2).
+GRAD_FLOPS_PER_STEP = 36
+
+
 def single_window(name: str):
     c = dict(configs.CONFIGS[name])
     ser = synth.load_series(c["series"])
@@ -105,7 +110,10 @@ def describe(name: str) -> str:
         "c2": ("single window FP32 + Kahan loss: 60 days, beta piecewise constant over 4 segments (7 params), "
                "log-uniform PSO box, 4096 particles, 1000 iterations, dt=0.1, FP64 re-evaluation of the 32 best"),
         "c1": "plain method FP64: constant beta, gamma, mu + I0, 30 days, 64 particles, 200 iterations, dt=0.1",
-        "c5": "large FP32: 2^20 particles, 10 segments, 120 days, dt=0.05, 100 iterations",
+        "c4": ("gradient FP64: loss + exact gradient (discrete adjoint, checkpoints every 16 steps) of the 4096 "
+               "personal bests of a calibrated swarm, 90 days, 4 beta segments (7 params), dt=0.05"),
+        "c5": ("large FP32: 2^20 particles, 10 segments (13 params), 120 days, dt=0.05, 100 iterations, FP64 "
+               "re-evaluation of the 32 best, then the 1024 best personal bests forecast 14 held-out days (FP64)"),
     }[name]
 
 
@@ -179,14 +187,15 @@ def _max_over_ranks(x: float, world: int) -> float:
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
-def timed_steps(args, world, stream, step_fn, kernel_events):
+def timed_steps(args, world, stream, step_fn, kernel_events=None):
     """Runs args.steps steps with an L2 flush before each, timed by CUDA events on `stream`.
-    Returns (total ms max over ranks, per-step kernel ms from kernel_events, clocks, last result)."""
+    Returns (total ms max over ranks, per-step kernel ms from kernel_events -- the step's own
+    events when None --, clocks, last result)."""
     import torch
 
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
@@ -204,7 +213,8 @@ def timed_steps(args, world, stream, step_fn, kernel_events):
             res = step_fn()
             ends[i].record(stream)
             torch.cuda.synchronize()
-            kern_ms.append(kernel_events[0].elapsed_time(kernel_events[1]))
+            kev = kernel_events or (starts[i], ends[i])
+            kern_ms.append(kev[0].elapsed_time(kev[1]))
     torch.cuda.synchronize()
     _barrier(world)
     total = _max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world)
@@ -320,6 +330,18 @@ def run_c3(args, rank, world):
     return out
 
 
+def topk_launches(M: int, k: int, chunk: int = 4096) -> int:
+    """Launches of the selection kernel for the k best of M (chunks of 4096, then the k best of
+    every chunk, until one chunk is left)."""
+    n, launches = M, 0
+    while True:
+        blocks = (n + chunk - 1) // chunk
+        launches += 1
+        if blocks == 1:
+            return launches
+        n = blocks * k
+
+
 def run_single(args, rank, world):
     import torch
 
@@ -330,27 +352,39 @@ def run_single(args, rank, world):
     kw = dict(K=c["K"], spd=c["spd"], particles=c["M"], iters=c["iters"], lb=lb, ub=ub,
               log_scale=[1] * len(lb) if c["log"] else None, precision=c["precision"], seed=c["seed"],
               stream_id=rank, reeval_topk=c.get("reeval_topk", 0))
+    horizon, fk = c.get("horizon", 0), c.get("forecast_topk", 0)
+
     with torch.cuda.stream(stream):
         cal = sird.Calibrator(y, ser["N"], stream=stream, **kw)
         ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
         ev[0].record(stream)
         ev[1].record(stream)
         cal.set_timing(*ev)
+
+    def step():
+        r = cal.calibrate()
+        if not horizon:
+            return r, None
+        # the forecast leg (Sec. 4.2): the fk best personal bests continued `horizon` days
+        th, _ = cal.topk(fk)
+        return r, sird.forecast(y, ser["N"], th, horizon, K=c["K"], spd=c["spd"], precision=64, stream=stream)
+
+    with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            cal.calibrate()
-    total_ms, kern_ms, clocks, res = timed_steps(args, world, stream, cal.calibrate, ev)
+            step()
+    total_ms, kern_ms, clocks, (res, fc) = timed_steps(args, world, stream, step, ev)
     e2e = []
     y_host = np.asarray(y, dtype=np.float64)
     for _ in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cal.set_observations(y_host)
-        cal.calibrate()
+        step()
         e2e.append((time.perf_counter() - t0) * 1e3)
     e2e_total = _max_over_ranks(sum(e2e), world)
     if rank != 0:
         return None
-    L, spd = c["days"], c["spd"]
+    L, spd, P = c["days"], c["spd"], len(lb)
     units = c["M"] * L * c["iters"]
     persistent = cal.launch_mode == sird.LAUNCH_PERSISTENT
     iter_launches = 1 if persistent else c["iters"]
@@ -359,29 +393,108 @@ def run_single(args, rank, world):
     achieved = flops / (kms / 1e3) / 1e12
     fp64 = c["precision"] == 64
     peak = 1.25 if fp64 else FP32_PEAK_TFLOPS
+    rk = c.get("reeval_topk", 0)
+    launches = 1 + iter_launches + (topk_launches(c["M"], rk) + 1 if rk else 1)
+    h2d, d2h = (L + 1) * 16, 288
+    if horizon:
+        launches += topk_launches(c["M"], fk) + 1 + 1
+        h2d += fk * P * 8 + (L + 1) * 16
+        d2h += fk * (P + 1) * 8 + fk * horizon * 8
     out = {
         "metric": METRIC, "value": units * args.steps * world / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
         "config": {"workload": describe(args.workload), "name": c["name"], "particles": c["M"], "days": L,
-                   "iterations": c["iters"], "steps_per_day": spd, "params": len(lb),
-                   "l2": "flushed between timed steps (256 MiB write)",
+                   "iterations": c["iters"], "steps_per_day": spd, "params": P,
+                   "l2": "flushed between timed steps (256 MiB write)" + (
+                       "; swarm state larger than L2" if c["M"] * P * 16 > 129e6 else ""),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": profiled_traffic(args.workload) if persistent else None,
+                     "traffic": profiled_traffic(args.workload),
                      "kernel": "pso_f32_persistent" if persistent else ("pso_f64_kernel" if fp64 else "pso_f32_kernel"),
                      "avg_launch_us": kms * 1e3 / iter_launches, "us_per_iteration": kms * 1e3 / c["iters"],
                      "peak_basis": ("nominal FP64 1.25 TFLOP/s" if fp64
                                     else "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz")},
         "e2e": {"value": units * args.steps * world / (e2e_total / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": (L + 1) * 16, "d2h_bytes_per_step": 288, "ms_per_step": e2e_total / args.steps},
-        "gpu_launches": args.steps * (1 + iter_launches + (1 if c.get("reeval_topk", 0) else 0) + 1),
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_total / args.steps},
+        "gpu_launches": args.steps * launches,
         "clocks": clocks,
         "result": {"loss_fp64": res["loss"], "loss_search": res["loss_search"], "r2_D": res["r2_D"]},
     }
+    if horizon:
+        held = np.asarray(ser["yD"][L + 1:L + 1 + horizon])
+        rel = np.abs(fc - held[None, :]) / held[None, :]
+        inside = (fc.min(axis=0) <= held) & (held <= fc.max(axis=0))
+        out["result"].update({"forecast_days": f"{L + 1}..{L + horizon} (held out)", "forecast_topk": fk,
+                              "forecast_best_max_rel_err": float(rel[0].max()),
+                              "forecast_median_max_rel_err": float(np.median(rel.max(axis=1))),
+                              "held_out_inside_topk_range": float(inside.mean())})
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_budget)
     return out
+
+
+def run_c4(args, rank, world):
+    """Gradient workload: FP64 loss and exact gradient (discrete adjoint, checkpoints every 16
+    steps) of every personal best of a calibrated 4096-particle FP32 swarm on the 90-day window
+    at dt = 0.05 day.  One step = one gradient launch over all particles."""
+    import torch
+
+    from paper_2204_12346_gb300 import sird
+
+    c, ser, y, lb, ub = single_window("c4")
+    stream = torch.cuda.Stream()
+    P = len(lb)
+    with torch.cuda.stream(stream):
+        cal = sird.Calibrator(y, ser["N"], K=c["K"], spd=c["spd"], particles=c["M"], iters=c["iters"], lb=lb, ub=ub,
+                              log_scale=[1] * P, precision=32, seed=c["seed"], stream_id=rank,
+                              reeval_topk=c["reeval_topk"], stream=stream)
+        cal.calibrate()
+        st = cal.get_state()
+        theta = torch.from_numpy(np.exp(st["pbest"].astype(np.float64))).to("cuda").contiguous()
+        for _ in range(args.warmup):
+            cal.loss_grad(theta, ckpt_every=c["ckpt"])
+    total_ms, kern_ms, clocks, (loss, grad) = timed_steps(
+        args, world, stream, lambda: cal.loss_grad(theta, ckpt_every=c["ckpt"]))
+    e2e = []
+    th_host = torch.empty_like(theta, device="cpu").pin_memory()
+    th_host.copy_(theta)
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            th_dev = th_host.to("cuda", non_blocking=True)
+            lo, gr = cal.loss_grad(th_dev, ckpt_every=c["ckpt"])
+            lo_h, gr_h = lo.cpu(), gr.cpu()
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = _max_over_ranks(sum(e2e), world)
+    pol = cal.polish(k=c["polish_topk"], iters=50, first_step=1e-2, ckpt_every=c["ckpt"])
+    if rank != 0:
+        return None
+    L, spd, M = c["days"], c["spd"], c["M"]
+    units = M * L
+    kms = statistics.mean(kern_ms)
+    flops = M * L * spd * GRAD_FLOPS_PER_STEP
+    achieved = flops / (kms / 1e3) / 1e12
+    return {
+        "metric": METRIC, "value": units * args.steps * world / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": describe("c4"), "name": c["name"], "particles": M, "days": L, "steps_per_day": spd,
+                   "params": P, "checkpoint_every": c["ckpt"], "units": "particle-days of loss + gradient",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s", "frac": achieved / 1.25,
+                     "traffic": profiled_traffic("c4"), "kernel": "loss_grad_f64_kernel", "avg_launch_us": kms * 1e3,
+                     "flops_per_launch": flops, "peak_basis": "nominal FP64 1.25 TFLOP/s"},
+        "e2e": {"value": units * args.steps * world / (e2e_total / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": M * P * 8, "d2h_bytes_per_step": M * (P + 1) * 8,
+                "ms_per_step": e2e_total / args.steps},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "result": {"finite_fraction": float(torch.isfinite(grad).all(dim=0).double().mean()),
+                   "median_loss": float(loss.median()), "polish_50_iters_loss": pol["loss"]},
+    }
 
 
 # ------------------------------------------------------------------ oracle on the host cores
@@ -406,19 +519,31 @@ def cpu_baseline(name: str, budget_s: float = 15.0, iters_cap: int | None = None
             units += w["particles"] * w["L"] * 2
             done += 1
         sample = f"{done} windows x (init + 1 PSO iteration), full swarms"
+    elif name == "c4":
+        c, ser, y, lb, ub = single_window(name)
+        pb = O.Problem(yD=y, N=ser["N"], K=c["K"], spd=c["spd"])
+        rng = np.random.default_rng(c["seed"])
+        done = 0
+        while time.perf_counter() - t0 < budget_s and (iters_cap is None or done < iters_cap * 64):
+            for th in synth.box_sample(lb, ub, [1] * len(lb), 64, rng):
+                O.loss_grad(pb, th)
+            done += 64
+        units = done * c["days"]
+        sample = f"loss + gradient of {done} box-sampled parameter vectors (90 days, dt=0.05)"
     else:
         c, ser, y, lb, ub = single_window(name)
         logd = [1] * len(lb) if c["log"] else [0] * len(lb)
+        M = min(c["M"], 4096)  # bounded sample of the 2^20-particle swarm
         zlb = np.log(lb) if c["log"] else np.array(lb, float)
         zub = np.log(ub) if c["log"] else np.array(ub, float)
-        pso = O.PSO(O.Problem(yD=y, N=ser["N"], K=c["K"], spd=c["spd"]), c["M"], zlb, zub, logdim=logd,
+        pso = O.PSO(O.Problem(yD=y, N=ser["N"], K=c["K"], spd=c["spd"]), M, zlb, zub, logdim=logd,
                     seed=c["seed"], store_f32=c["precision"] == 32).init()
         its = 0
         while time.perf_counter() - t0 < budget_s and (iters_cap is None or its < iters_cap):
             pso.step(1)
             its += 1
-        units = c["M"] * c["days"] * (its + 1)
-        sample = f"{c['M']} particles x {c['days']} days, init + {its} PSO iterations"
+        units = M * c["days"] * (its + 1)
+        sample = f"{M} particles x {c['days']} days, init + {its} PSO iterations"
     dt = time.perf_counter() - t0
     return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{sample}, single thread, FP64 ({dt:.1f} s)"}
@@ -453,7 +578,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c3", "c2", "c1", "c5"], default="c3")
+    ap.add_argument("--workload", choices=["c3", "c2", "c1", "c4", "c5"], default="c3")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-units", type=int, default=2,
                     help="reference arm: windows (batched) or PSO iterations (single window) per step")
@@ -478,6 +603,8 @@ def main():
             out = run_reference(args, rank, world)
         elif args.workload == "c3":
             out = run_c3(args, rank, world)
+        elif args.workload == "c4":
+            out = run_c4(args, rank, world)
         else:
             out = run_single(args, rank, world)
     finally:
