@@ -230,24 +230,33 @@ sird_status sird_pso_topk(sird_pso_t h, int k, double* theta_out, double* loss_o
  * PSO is used because no gradient is available, Sec. 3.3 -- the discrete loss does have
  * one).  d_theta [P][ld], d_loss [M], d_grad [P][ld_grad] (dL/dtheta) and d_grad_u0
  * [4][ld_grad] (dL/d(S0, I0, R0, D0) with the four taken as independent; may be NULL)
- * are device memory of the handle's precision type.  Trajectories are recomputed from
- * checkpoints every ckpt_every steps (1..64).  Costs: MSE, MAE, MAPE, MXSE (sub-gradients
- * at kinks) on F_D.
+ * are device memory of the type `precision` names (32: float, 64: double), for a handle of
+ * either precision.  precision 64: the paper's operation order, equal to the plain FP64
+ * computation bit for bit; trajectories are recomputed from checkpoints every ckpt_every steps
+ * (1..64).  precision 32: the compensated FP32 trajectory (the loss equals sird_pso_eval's FP32
+ * loss bit for bit), checkpoints at every day start (ckpt_every is checked but not used),
+ * steps_per_day 10, 20 or at most 64 (else SIRD_ERR_UNSUPPORTED); its gradient is the exact
+ * adjoint of the discrete map evaluated in FP32 (relative error near 1e-5 of the summed terms).
+ * Costs: MSE, MAE, MAPE, MXSE (sub-gradients at kinks) on F_D.  Asynchronous on the handle's
+ * stream; the checkpoint scratch grows on demand (that call synchronises the stream).
  */
 sird_status sird_loss_grad(sird_pso_t h, const void* d_theta, int M, int ld, void* d_loss,
                            void* d_grad, int ld_grad, void* d_grad_u0, int precision, int ckpt_every);
 
 /*
  * Gradient polish of an FP32 swarm's k best personal bests (k <= min(1024, particles)): iters
- * L-BFGS iterations in FP64 on the search coordinates (dL/dz = theta dL/dtheta on log
- * dimensions; 8 stored pairs), each with one sird_loss_grad evaluation (checkpoints every
- * ckpt_every steps) and a line search that evaluates 16 step lengths 2^-q in one FP64 launch
- * and takes the longest one meeting the Armijo condition; positions are clamped to the box.
+ * L-BFGS iterations on the search coordinates (dL/dz = theta dL/dtheta on log dimensions;
+ * 8 stored pairs, algebra in FP64), each with one sird_loss_grad evaluation and a line search
+ * that evaluates 16 step lengths 2^-q in one launch and takes the longest one meeting the
+ * Armijo condition; positions are clamped to the box.  precision 64: trials and gradients in
+ * the paper's FP64 arithmetic (checkpoints every ckpt_every steps, 1..64); precision 32: the
+ * compensated FP32 evaluation and the FP32 adjoint (steps_per_day 10, 20 or <= 64).
  * first_step is the largest change of any search coordinate in the first (steepest-descent)
- * step.  The best point ever evaluated is reported in *out (FP64 loss; index = the
- * candidate's particle).  The swarm itself is not changed.  Blocks.
+ * step.  The best point ever evaluated is re-scored in FP64 and reported in *out (FP64 loss;
+ * index = the candidate's particle).  The swarm itself is not changed.  Blocks.
  */
-sird_status sird_pso_polish(sird_pso_t h, int k, int iters, double first_step, int ckpt_every, sird_result* out);
+sird_status sird_pso_polish(sird_pso_t h, int k, int iters, double first_step, int ckpt_every, int precision,
+                            sird_result* out);
 
 /* ---------------------------------------------------------------- forecast */
 

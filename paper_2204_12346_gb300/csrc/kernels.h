@@ -105,14 +105,22 @@ cudaError_t launch_loss_grad_f64(const WindowDev& w, const ModelDev& m, const Ob
                                  int M, double* loss, double* grad, int ldg, double* grad_u0, double* ckpt, int C,
                                  cudaStream_t s);
 
-// FP64 L-BFGS polish of the k candidates named by keys (FP32 swarm): iters iterations with a
-// parallel line search, best point kept, the best candidate's theta / loss / sse into *res.
-// scratch: polish_scratch_doubles(P, k) doubles.
+// The same in FP32 (compensated trajectory; loss identical to the FP32 evaluation), checkpoints
+// at every day start in ckpt (adjoint_ckpt_bytes_f32); steps per day 10, 20 or at most 64.
+size_t adjoint_ckpt_bytes_f32(const WindowDev& w, int M);
+cudaError_t launch_loss_grad_f32(const WindowDev& w, const ModelDev& m, const ObsDev& o, const float* theta, int ld,
+                                 int M, float* loss, float* grad, int ldg, float* grad_u0, float* ckpt,
+                                 cudaStream_t s);
+
+// L-BFGS polish of the k candidates named by keys (FP32 swarm): iters iterations with a
+// parallel line search, trials and gradient in FP32 (precision 32) or FP64 (64), best point kept,
+// the best candidate's theta / FP64 loss / sse into *res.  scratch: polish_scratch_doubles(P, k)
+// doubles; ckpt: adjoint_ckpt_bytes_f32(w, k) or adjoint_ckpt_bytes(w, m, k, ckpt_every) bytes.
 size_t polish_scratch_doubles(int P, int k);
 cudaError_t launch_polish(const WindowDev& w, const ModelDev& m, const ObsDev& o, const PsoCoeffs<double>& c,
                           const unsigned long long* keys, int k, const float* pb, const float* pbf, int ld, int iters,
-                          double first_step, double* scratch, double* ckpt, int ckpt_every, ResultDev* res,
-                          cudaStream_t s);
+                          double first_step, int precision, double* scratch, void* ckpt, int ckpt_every,
+                          ResultDev* res, cudaStream_t s);
 
 // ---------------------------------------------------------------- batched windows
 struct BatchWindow {

@@ -1,4 +1,4 @@
-// polish.cu -- FP64 L-BFGS polish of the best PSO candidates with a parallel line search.
+// polish.cu -- L-BFGS polish of the best PSO candidates with a parallel line search.
 //
 // PSO (Sec. 3.3) needs no gradient; near its optimum the swarm resolves the loss only as far
 // as its search does.  The discrete adjoint gives the exact gradient of the FP64 loss, so the
@@ -6,12 +6,15 @@
 // dimensions, where dL/dz = theta dL/dtheta), positions clamped to the box.  Each iteration:
 //   1. direction d = -H g by the two-loop recursion over the last kMem (s, y) pairs,
 //   2. kTrials trial points z + 2^-q d (q = 0..kTrials-1) for every candidate, evaluated in ONE
-//      FP64 launch -- on this GPU an FP64 evaluation is latency-bound, so 16 trials cost about
+//      launch -- an evaluation of a few candidates is latency-bound, so 16 trials cost about
 //      what one does,
 //   3. the largest step that satisfies the Armijo condition (else the best trial if it lowers
 //      the loss, else the candidate stops),
 //   4. the gradient at the accepted point (adjoint launch) and the history update.
-// The best point ever evaluated is reported.
+// The best point ever evaluated is re-scored in FP64 (the paper's operation order) and reported.
+// Precision 64 evaluates the trials and the gradient in FP64; precision 32 uses the compensated
+// FP32 evaluation and the FP32 adjoint (about 15x faster per iteration) while the L-BFGS
+// algebra stays in FP64.
 #include <cmath>
 
 #include "kernels.h"
@@ -26,8 +29,9 @@ constexpr int kTrials = 16;
 // Per-candidate state, structure of arrays with candidate j at [.. * k + j].
 struct PolishState {
     double *z, *g, *f, *d, *zt, *tht, *ft, *S, *Y, *rho, *best_f, *best_th, *gth, *lnew;
+    float *thf, *ftf, *gthf, *lnewf;  // FP32 mode: trial thetas, their losses, gradient, loss
     int *head, *count, *active, *cand;
-    int P, k;
+    int P, k, f32;
 };
 
 __device__ __forceinline__ double decode(double z, bool lg) { return lg ? exp(z) : z; }
@@ -45,7 +49,9 @@ __global__ void polish_init_kernel(PolishState s, const unsigned long long* __re
     for (int d = 0; d < s.P; ++d) {
         const double z = (double)pb[(size_t)d * ld + idx];
         s.z[(size_t)d * s.k + j] = z;
-        s.tht[(size_t)d * s.k * kTrials + j] = decode(z, (logmask >> d) & 1u);  // slot 0: gradient point
+        const double th = decode(z, (logmask >> d) & 1u);
+        s.tht[(size_t)d * s.k * kTrials + j] = th;  // slot 0: gradient point
+        if (s.f32) s.thf[(size_t)d * s.k * kTrials + j] = (float)th;
     }
 }
 
@@ -55,12 +61,13 @@ __global__ void polish_accept_kernel(PolishState s, uint32_t logmask, int first)
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= s.k) return;
     const int P = s.P, k = s.k, kt = k * kTrials;
-    const double fnew = s.lnew[j];
+    const double fnew = s.f32 ? (double)s.lnewf[j] : s.lnew[j];
     double sy = 0.0, yy = 0.0, ss = 0.0;
     for (int d = 0; d < P; ++d) {
         const bool lg = (logmask >> d) & 1u;
         const double th = s.tht[(size_t)d * kt + j];
-        const double gz = lg ? th * s.gth[(size_t)d * k + j] : s.gth[(size_t)d * k + j];
+        const double gr = s.f32 ? (double)s.gthf[(size_t)d * k + j] : s.gth[(size_t)d * k + j];
+        const double gz = lg ? th * gr : gr;
         if (!first) {
             const double sd = s.zt[(size_t)d * k + j] - s.z[(size_t)d * k + j];
             const double yd = gz - s.g[(size_t)d * k + j];
@@ -137,7 +144,9 @@ __global__ void polish_direction_kernel(PolishState s, PsoCoeffs<double> c, doub
         const double alpha = ldexp(1.0, -t);
         for (int d = 0; d < P; ++d) {
             const double zn = fmin(fmax(s.z[(size_t)d * k + j] + alpha * s.d[(size_t)d * k + j], c.zlb[d]), c.zub[d]);
-            s.tht[(size_t)d * kt + (size_t)t * k + j] = decode(zn, (c.logmask >> d) & 1u);
+            const double th = decode(zn, (c.logmask >> d) & 1u);
+            s.tht[(size_t)d * kt + (size_t)t * k + j] = th;
+            if (s.f32) s.thf[(size_t)d * kt + (size_t)t * k + j] = (float)th;
         }
     }
 }
@@ -154,7 +163,7 @@ __global__ void polish_select_kernel(PolishState s, PsoCoeffs<double> c) {
     double fbest = f0;
     int tbest = -1;
     for (int t = 0; t < kTrials; ++t) {
-        const double ft = s.ft[(size_t)t * k + j];
+        const double ft = s.f32 ? (double)s.ftf[(size_t)t * k + j] : s.ft[(size_t)t * k + j];
         if (pick < 0 && ft <= f0 + 1e-4 * ldexp(1.0, -t) * gd) pick = t;
         if (ft < fbest) {
             fbest = ft;
@@ -174,7 +183,9 @@ __global__ void polish_select_kernel(PolishState s, PsoCoeffs<double> c) {
             zn = s.z[(size_t)d * k + j];
         }
         s.zt[(size_t)d * k + j] = zn;
-        s.tht[(size_t)d * kt + j] = decode(zn, (c.logmask >> d) & 1u);
+        const double th = decode(zn, (c.logmask >> d) & 1u);
+        s.tht[(size_t)d * kt + j] = th;
+        if (s.f32) s.thf[(size_t)d * kt + j] = (float)th;
     }
 }
 
@@ -217,10 +228,11 @@ __global__ void polish_pick_kernel(WindowDev w, ModelDev m, ObsDev o, PolishStat
     }
 }
 
-PolishState carve(double* base, int P, int k) {
+PolishState carve(double* base, int P, int k, int f32) {
     PolishState s{};
     s.P = P;
     s.k = k;
+    s.f32 = f32;
     const size_t pk = (size_t)P * k;
     double* q = base;
     s.z = q; q += pk;
@@ -237,7 +249,12 @@ PolishState carve(double* base, int P, int k) {
     s.ft = q; q += (size_t)k * kTrials;
     s.best_f = q; q += k;
     s.lnew = q; q += k;
-    int* iq = (int*)q;
+    float* fq = (float*)q;
+    s.thf = fq; fq += pk * kTrials;
+    s.ftf = fq; fq += (size_t)k * kTrials;
+    s.gthf = fq; fq += pk;
+    s.lnewf = fq; fq += k;
+    int* iq = (int*)fq;
     s.head = iq; iq += k;
     s.count = iq; iq += k;
     s.active = iq; iq += k;
@@ -249,24 +266,31 @@ PolishState carve(double* base, int P, int k) {
 
 size_t polish_scratch_doubles(int P, int k) {
     const size_t pk = (size_t)P * k;
-    return pk * (6 + kTrials + 2 * kMem) + (size_t)k * (kMem + kTrials + 3) + 2 * (size_t)k + 8;
+    const size_t floats = pk * (kTrials + 1) + (size_t)k * (kTrials + 1);
+    return pk * (6 + kTrials + 2 * kMem) + (size_t)k * (kMem + kTrials + 3) + (floats + 1) / 2 + 2 * (size_t)k + 8;
 }
 
 int polish_trials() { return kTrials; }
 
 cudaError_t launch_polish(const WindowDev& w, const ModelDev& m, const ObsDev& o, const PsoCoeffs<double>& c,
                           const unsigned long long* keys, int k, const float* pb, const float* pbf, int ld, int iters,
-                          double first_step, double* scratch, double* ckpt, int ckpt_every, ResultDev* res,
-                          cudaStream_t st) {
+                          double first_step, int precision, double* scratch, void* ckpt, int ckpt_every,
+                          ResultDev* res, cudaStream_t st) {
     const int P = m.P;
-    PolishState s = carve(scratch, P, k);
+    const bool f32 = precision == 32;
+    PolishState s = carve(scratch, P, k, f32 ? 1 : 0);
     const unsigned grid = (unsigned)((k + 127) / 128);
     const int kt = k * kTrials;
+    auto grad_at_slot0 = [&]() {
+        return f32 ? launch_loss_grad_f32(w, m, o, s.thf, kt, k, s.lnewf, s.gthf, k, nullptr, (float*)ckpt, st)
+                   : launch_loss_grad_f64(w, m, o, s.tht, kt, k, s.lnew, s.gth, k, nullptr, (double*)ckpt,
+                                          ckpt_every, st);
+    };
     (void)cudaGetLastError();
     polish_init_kernel<<<grid, 128, 0, st>>>(s, keys, pb, ld, c.logmask);
     cudaError_t e = cudaGetLastError();
     // loss and gradient at the starting points (trial slot 0 holds their theta)
-    if (e == cudaSuccess) e = launch_loss_grad_f64(w, m, o, s.tht, kt, k, s.lnew, s.gth, k, nullptr, ckpt, ckpt_every, st);
+    if (e == cudaSuccess) e = grad_at_slot0();
     if (e == cudaSuccess) {
         polish_accept_kernel<<<grid, 128, 0, st>>>(s, c.logmask, 1);
         e = cudaGetLastError();
@@ -274,11 +298,13 @@ cudaError_t launch_polish(const WindowDev& w, const ModelDev& m, const ObsDev& o
     for (int it = 0; it < iters && e == cudaSuccess; ++it) {
         polish_direction_kernel<<<grid, 128, 0, st>>>(s, c, first_step);
         e = cudaGetLastError();
-        if (e == cudaSuccess) e = launch_eval_f64(w, m, o, s.tht, kt, kt, s.ft, 64, nullptr, st);
+        if (e == cudaSuccess)
+            e = f32 ? launch_eval_f32(w, m, o, s.thf, kt, kt, s.ftf, 128, nullptr, st)
+                    : launch_eval_f64(w, m, o, s.tht, kt, kt, s.ft, 64, nullptr, st);
         if (e != cudaSuccess) break;
         polish_select_kernel<<<grid, 128, 0, st>>>(s, c);
         e = cudaGetLastError();
-        if (e == cudaSuccess) e = launch_loss_grad_f64(w, m, o, s.tht, kt, k, s.lnew, s.gth, k, nullptr, ckpt, ckpt_every, st);
+        if (e == cudaSuccess) e = grad_at_slot0();
         if (e != cudaSuccess) break;
         polish_accept_kernel<<<grid, 128, 0, st>>>(s, c.logmask, 0);
         e = cudaGetLastError();

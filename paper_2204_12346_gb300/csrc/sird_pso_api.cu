@@ -617,7 +617,7 @@ extern "C" sird_status sird_pso_set_state(sird_pso_t h, const void* buf, size_t 
     return SIRD_OK;
 }
 
-// ---------------------------------------------------------------- not yet built
+// ---------------------------------------------------------------- gradient
 
 extern "C" sird_status sird_loss_grad(sird_pso_t h, const void* d_theta, int M, int ld, void* d_loss, void* d_grad,
                                       int ld_grad, void* d_grad_u0, int precision, int ckpt_every) {
@@ -626,9 +626,12 @@ extern "C" sird_status sird_loss_grad(sird_pso_t h, const void* d_theta, int M, 
     if (M < 0 || ld < M || ld_grad < M || (M > 0 && (!d_theta || !d_loss || !d_grad)))
         return h->fail(SIRD_ERR_ARG, "loss_grad: bad M/ld/pointers");
     if (ckpt_every < 1 || ckpt_every > 64) return h->fail(SIRD_ERR_ARG, "loss_grad: ckpt_every out of range [1, 64]");
-    if (precision != 64) return h->fail(SIRD_ERR_UNSUPPORTED, "loss_grad: FP64 only");
+    if (precision != 32 && precision != 64) return h->fail(SIRD_ERR_ARG, "loss_grad: precision must be 32 or 64");
+    if (precision == 32 && h->mdl.spd != 10 && h->mdl.spd != 20 && h->mdl.spd > 64)
+        return h->fail(SIRD_ERR_UNSUPPORTED, "loss_grad: FP32 needs steps_per_day <= 64");
     if (M == 0) return SIRD_OK;
-    const size_t need = adjoint_ckpt_bytes(h->win, h->mdl, M, ckpt_every);
+    const size_t need = precision == 64 ? adjoint_ckpt_bytes(h->win, h->mdl, M, ckpt_every)
+                                        : adjoint_ckpt_bytes_f32(h->win, M);
     if (need > h->ckpt_bytes) {
         sird_status s = h->cuda(cudaStreamSynchronize(h->stream), "sync");
         if (s) return s;
@@ -639,6 +642,10 @@ extern "C" sird_status sird_loss_grad(sird_pso_t h, const void* d_theta, int M, 
         if (s) return s;
         h->ckpt_bytes = need;
     }
+    if (precision == 32)
+        return h->cuda(launch_loss_grad_f32(h->win, h->mdl, h->obs, (const float*)d_theta, ld, M, (float*)d_loss,
+                                            (float*)d_grad, ld_grad, (float*)d_grad_u0, (float*)h->d_ckpt, h->stream),
+                       "loss_grad launch");
     return h->cuda(launch_loss_grad_f64(h->win, h->mdl, h->obs, (const double*)d_theta, ld, M, (double*)d_loss,
                                         (double*)d_grad, ld_grad, (double*)d_grad_u0, (double*)h->d_ckpt,
                                         ckpt_every, h->stream),
@@ -646,15 +653,18 @@ extern "C" sird_status sird_loss_grad(sird_pso_t h, const void* d_theta, int M, 
 }
 
 extern "C" sird_status sird_pso_polish(sird_pso_t h, int k, int iters, double first_step, int ckpt_every,
-                                       sird_result* out) {
+                                       int precision, sird_result* out) {
     if (!h || !out) return SIRD_ERR_ARG;
     if (h->sticky) return h->sticky;
     if (h->precision != 32) return h->fail(SIRD_ERR_UNSUPPORTED, "polish: FP32 swarms only");
-    if (k < 1 || k > 1024 || k > h->M || iters < 0 || !(first_step > 0) || ckpt_every < 1 || ckpt_every > 64)
-        return h->fail(SIRD_ERR_ARG, "polish: bad k/iters/first_step/ckpt_every");
+    if (k < 1 || k > 1024 || k > h->M || iters < 0 || !(first_step > 0) || ckpt_every < 1 || ckpt_every > 64 ||
+        (precision != 32 && precision != 64))
+        return h->fail(SIRD_ERR_ARG, "polish: bad k/iters/first_step/ckpt_every/precision");
+    if (precision == 32 && h->mdl.spd != 10 && h->mdl.spd != 20 && h->mdl.spd > 64)
+        return h->fail(SIRD_ERR_UNSUPPORTED, "polish: FP32 needs steps_per_day <= 64");
     if (h->iter < 0) return h->fail(SIRD_ERR_STATE, "polish before init");
     const size_t nk = topk_scratch_keys(h->M, k);
-    const size_t ck = adjoint_ckpt_bytes(h->win, h->mdl, k, ckpt_every);
+    const size_t ck = precision == 32 ? adjoint_ckpt_bytes_f32(h->win, k) : adjoint_ckpt_bytes(h->win, h->mdl, k, ckpt_every);
     const size_t bytes = 2 * nk * sizeof(unsigned long long) + polish_scratch_doubles(h->P, k) * sizeof(double) + ck;
     void* dmem = nullptr;
     sird_status st = h->cuda(cudaMalloc(&dmem, bytes), "polish scratch");
@@ -662,12 +672,12 @@ extern "C" sird_status sird_pso_polish(sird_pso_t h, int k, int iters, double fi
     unsigned long long* a = (unsigned long long*)dmem;
     unsigned long long* b = a + nk;
     double* scratch = (double*)(b + nk);
-    double* ckpt = scratch + polish_scratch_doubles(h->P, k);
+    void* ckpt = scratch + polish_scratch_doubles(h->P, k);
     unsigned long long* keys = nullptr;
     cudaError_t e = launch_topk_f32((const float*)h->pbf, h->M, k, a, b, &keys, h->stream);
     if (e == cudaSuccess)
         e = launch_polish(h->win, h->mdl, h->obs, h->c64, keys, k, (const float*)h->pb, (const float*)h->pbf, h->ld,
-                          iters, first_step, scratch, ckpt, ckpt_every, h->d_res, h->stream);
+                          iters, first_step, precision, scratch, ckpt, ckpt_every, h->d_res, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_res, h->d_res, sizeof(ResultDev), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(dmem);

@@ -113,7 +113,7 @@ def lib():
         L.sird_batch_set_timing.argtypes = [vp, vp, vp]
         L.sird_batch_destroy.argtypes = [vp]
         L.sird_batch_destroy.restype = None
-        L.sird_pso_polish.argtypes = [vp, ip, ip, C.c_double, ip, C.POINTER(Result)]
+        L.sird_pso_polish.argtypes = [vp, ip, ip, C.c_double, ip, ip, C.POINTER(Result)]
         L.sird_pso_step_f32_noalloc.argtypes = [C.POINTER(Problem), C.POINTER(Config)] + [vp] * 6 + [ip, ip, vp, vp]
         _lib = L
     return _lib
@@ -245,21 +245,24 @@ class Calibrator:
         self._check(self._lib.sird_pso_set_timing(self.h, b, e))
 
     def loss_grad(self, theta, ckpt_every=16, grad_u0=False):
-        """FP64 loss and exact gradient (discrete adjoint) of each column of theta ([P, M] CUDA
-        float64).  Returns (loss [M], grad [P, M]) or (loss, grad, grad_u0 [4, M])."""
+        """Loss and exact gradient (discrete adjoint) of each column of theta ([P, M] CUDA
+        tensor; float64: the paper's FP64 arithmetic, float32: the compensated FP32 path).
+        Returns (loss [M], grad [P, M]) or (loss, grad, grad_u0 [4, M]) in theta's dtype."""
         import torch
 
-        if theta.dtype != torch.float64 or not theta.is_cuda or theta.dim() != 2 or theta.shape[0] != self.P:
-            raise ValueError("theta must be a CUDA float64 tensor [P, M]")
+        if theta.dtype not in (torch.float32, torch.float64) or not theta.is_cuda or theta.dim() != 2 \
+                or theta.shape[0] != self.P:
+            raise ValueError("theta must be a CUDA float32/float64 tensor [P, M]")
         if theta.stride(1) != 1:
             raise ValueError("theta rows must be contiguous")
+        prec = 64 if theta.dtype == torch.float64 else 32
         M = theta.shape[1]
-        loss = torch.empty(M, dtype=torch.float64, device=theta.device)
-        grad = torch.empty(self.P, M, dtype=torch.float64, device=theta.device)
-        gu = torch.empty(4, M, dtype=torch.float64, device=theta.device) if grad_u0 else None
+        loss = torch.empty(M, dtype=theta.dtype, device=theta.device)
+        grad = torch.empty(self.P, M, dtype=theta.dtype, device=theta.device)
+        gu = torch.empty(4, M, dtype=theta.dtype, device=theta.device) if grad_u0 else None
         self._check(self._lib.sird_loss_grad(self.h, C.c_void_p(theta.data_ptr()), M, theta.stride(0),
                                              C.c_void_p(loss.data_ptr()), C.c_void_p(grad.data_ptr()), M,
-                                             C.c_void_p(gu.data_ptr()) if gu is not None else None, 64,
+                                             C.c_void_p(gu.data_ptr()) if gu is not None else None, prec,
                                              int(ckpt_every)))
         return (loss, grad, gu) if grad_u0 else (loss, grad)
 
@@ -284,11 +287,12 @@ class Calibrator:
         self._check(self._lib.sird_pso_result(self.h, C.byref(r)))
         return r.as_dict()
 
-    def polish(self, k=32, iters=50, first_step=1e-2, ckpt_every=16) -> dict:
-        """FP64 L-BFGS polish of the k best personal bests (discrete-adjoint gradient)."""
+    def polish(self, k=32, iters=50, first_step=1e-2, ckpt_every=16, precision=64) -> dict:
+        """L-BFGS polish of the k best personal bests (discrete-adjoint gradient); trials and
+        gradients in FP64 (precision=64) or FP32 (32); the reported loss is FP64."""
         r = Result()
         self._check(self._lib.sird_pso_polish(self.h, int(k), int(iters), float(first_step), int(ckpt_every),
-                                              C.byref(r)))
+                                              int(precision), C.byref(r)))
         return r.as_dict()
 
     def topk(self, k: int):
