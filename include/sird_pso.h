@@ -291,6 +291,16 @@ sird_status sird_batch_create(int W, const sird_problem* problems, const sird_ps
                               sird_batch_t* out);
 /* Runs the batch (captured once into a CUDA graph, replayed after); results[W] on the host.  Blocks. */
 sird_status sird_batch_calibrate(sird_batch_t b, sird_result* results);
+/*
+ * New observations for every window of the batch, e.g. the next day's data on the same rolling
+ * windows.  y_all (host) holds each window's n_obs values (the counts given at create), window
+ * after window: n_total = sum of n_obs.  Each window's D0 becomes its new first observation; N,
+ * I0, R0 and the PSO settings stay.  The values are packed into pinned staging and copied on
+ * the batch's stream, ordered before the next sird_batch_calibrate; y_all may be reused on
+ * return.  *h2d_bytes (may be NULL) receives the bytes copied.  SIRD_ERR_ARG on NULL, a wrong
+ * n_total or a non-finite value.
+ */
+sird_status sird_batch_set_observations(sird_batch_t b, const double* y_all, long long n_total, size_t* h2d_bytes);
 /* Threads per block and blocks per SM the batch runs with (autotuned or given); 0 if b is NULL. */
 int sird_batch_block_size(sird_batch_t b);
 int sird_batch_blocks_per_sm(sird_batch_t b);

@@ -34,6 +34,14 @@ struct sird_batch {
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;  // optional timing events around the batch kernel
     std::string msg;
+    // for sird_batch_set_observations: the windows' settings, their device images and a pinned
+    // staging copy of [windows | observations] laid out like the device memory
+    std::vector<sird_problem> probs;
+    std::vector<BatchWindow> h_wins;
+    std::vector<int> obs_off;
+    size_t nobs = 0, wins_bytes = 0, obs_bytes = 0;
+    unsigned char* h_stage = nullptr;
+    cudaEvent_t ev_upload = nullptr;
 };
 
 namespace {
@@ -284,6 +292,13 @@ extern "C" sird_status sird_batch_create(int W, const sird_problem* problems, co
     if (e != cudaSuccess) return bail(e, "uploading the batch");
     e = cudaMallocHost((void**)&b->h_out, sizeof(BatchOut) * W);
     if (e != cudaSuccess) return bail(e, "allocating pinned results");
+    b->probs.assign(problems, problems + W);
+    for (auto& pr : b->probs) pr.y_D = nullptr;
+    b->h_wins = wins;
+    b->obs_off = obs_off;
+    b->nobs = nobs;
+    b->wins_bytes = sizeof(BatchWindow) * W;
+    b->obs_bytes = (size_t)((unsigned char*)(b->yd + nobs) - (unsigned char*)b->yf);
     if (c0.block_size) {
         b->block = c0.block_size;
     } else {
@@ -301,6 +316,8 @@ extern "C" void sird_batch_destroy(sird_batch_t b) {
     if (b->cap) cudaStreamDestroy(b->cap);
     cudaFree(b->d_mem);
     if (b->h_out) cudaFreeHost(b->h_out);
+    if (b->h_stage) cudaFreeHost(b->h_stage);
+    if (b->ev_upload) cudaEventDestroy(b->ev_upload);
     delete b;
 }
 
@@ -361,6 +378,66 @@ extern "C" sird_status sird_batch_calibrate(sird_batch_t b, sird_result* results
         r.index = b->h_out[i].index;
         r.iters_done = b->iters;
     }
+    return SIRD_OK;
+}
+
+extern "C" sird_status sird_batch_set_observations(sird_batch_t b, const double* y_all, long long n_total,
+                                                   size_t* h2d_bytes) {
+    if (!b || !y_all) return berr(SIRD_ERR_ARG, "batch or y_all is NULL");
+    long long need = 0;
+    for (const auto& pr : b->probs) need += pr.n_obs;
+    if (n_total != need) return berr(SIRD_ERR_ARG, "y_all must hold sum(n_obs) = " + std::to_string(need) + " values");
+    for (long long i = 0; i < n_total; ++i)
+        if (!std::isfinite(y_all[i])) return berr(SIRD_ERR_ARG, "non-finite observation in y_all");
+    cudaError_t e = cudaSuccess;
+    if (!b->h_stage) {
+        e = cudaMallocHost((void**)&b->h_stage, b->wins_bytes + b->obs_bytes);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_upload, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return berr(SIRD_ERR_NOMEM, std::string("pinned staging: ") + cudaGetErrorString(e));
+        }
+    } else {
+        e = cudaEventSynchronize(b->ev_upload);  // the previous upload has left the staging buffer
+        if (e != cudaSuccess) return berr(SIRD_ERR_CUDA, std::string("upload wait: ") + cudaGetErrorString(e));
+    }
+    BatchWindow* hw = (BatchWindow*)b->h_stage;
+    unsigned char* ob = b->h_stage + b->wins_bytes;
+    float* yf = (float*)ob;
+    float* invy = (float*)(ob + ((unsigned char*)b->invy - (unsigned char*)b->yf));
+    double* yd = (double*)(ob + ((unsigned char*)b->yd - (unsigned char*)b->yf));
+    std::memset(ob, 0, b->obs_bytes);
+    const double* y = y_all;
+    for (int i = 0; i < b->W; ++i) {
+        sird_problem pr = b->probs[i];
+        pr.y_D = y;
+        ModelDev m{};
+        BatchWindow bw = b->h_wins[i];
+        sird_fill_window(&pr, bw.w, m);  // D0 = the new first observation
+        b->h_wins[i] = bw;
+        hw[i] = bw;
+        double mean = 0.0;
+        for (int j = 0; j < pr.n_obs; ++j) {
+            const int o = b->obs_off[i] + j;
+            yf[o] = (float)y[j];
+            invy[o] = y[j] != 0.0 ? (float)(1.0 / y[j]) : 0.f;
+            yd[o] = y[j];
+            mean += y[j];
+        }
+        mean /= pr.n_obs;
+        double ss = 0.0;
+        for (int j = 0; j < pr.n_obs; ++j) ss += (y[j] - mean) * (y[j] - mean);
+        b->ss_tot[i] = ss;
+        y += pr.n_obs;
+    }
+    e = cudaMemcpyAsync(b->wins, hw, b->wins_bytes, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->yf, ob, b->obs_bytes, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_upload, b->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return berr(SIRD_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    }
+    if (h2d_bytes) *h2d_bytes = b->wins_bytes + b->obs_bytes;
     return SIRD_OK;
 }
 

@@ -29,7 +29,7 @@ EXPORTS = [
     "sird_pso_num_params", "sird_pso_eval", "sird_pso_init", "sird_pso_step", "sird_pso_calibrate",
     "sird_pso_result", "sird_pso_sync", "sird_pso_get_state", "sird_pso_set_state", "sird_loss_grad",
     "sird_forecast", "sird_pso_calibrate_batched", "sird_pso_set_observations", "sird_pso_set_timing", "sird_pso_launch_mode",
-    "sird_pso_step_f32_noalloc", "sird_pso_topk", "sird_pso_polish", "sird_batch_create", "sird_batch_calibrate",
+    "sird_pso_step_f32_noalloc", "sird_pso_topk", "sird_pso_polish", "sird_batch_create", "sird_batch_calibrate", "sird_batch_set_observations",
     "sird_batch_block_size", "sird_batch_blocks_per_sm", "sird_batch_destroy", "sird_batch_set_timing",
 ]
 
@@ -111,6 +111,7 @@ def lib():
         L.sird_batch_block_size.argtypes = [vp]
         L.sird_batch_blocks_per_sm.argtypes = [vp]
         L.sird_batch_set_timing.argtypes = [vp, vp, vp]
+        L.sird_batch_set_observations.argtypes = [vp, C.POINTER(C.c_double), C.c_longlong, C.POINTER(C.c_size_t)]
         L.sird_batch_destroy.argtypes = [vp]
         L.sird_batch_destroy.restype = None
         L.sird_pso_polish.argtypes = [vp, ip, ip, C.c_double, ip, ip, C.POINTER(Result)]
@@ -404,6 +405,16 @@ class Batch:
         st = self._lib.sird_batch_set_timing(self.h, b, e)
         if st != OK:
             raise SirdError(st, self._lib.sird_last_error(None).decode())
+
+    def set_observations(self, y_all) -> int:
+        """New observations for every window (concatenated, each window's original length); the
+        copy is ordered before the next calibrate.  Returns the bytes copied to the device."""
+        y = _f64(y_all)
+        nb = C.c_size_t(0)
+        st = self._lib.sird_batch_set_observations(self.h, _dptr(y), len(y), C.byref(nb))
+        if st != OK:
+            raise SirdError(st, self._lib.sird_last_error(None).decode())
+        return int(nb.value)
 
     def calibrate(self):
         res = (Result * self.W)()

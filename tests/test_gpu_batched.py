@@ -44,6 +44,27 @@ def test_batch_windows_match_single_window_calibrations():
         assert res[i]["r2_D"] == pytest.approx(r["r2_D"], rel=1e-12)
 
 
+def test_batch_set_observations_equals_a_fresh_batch():
+    # the next day's data on the same windows (each window shifted by one day, same lengths)
+    ser = synth.load_series("c3")
+    lay = small_layout()
+    wins = synth.rolling_window_problems(ser, lay)
+    nxt = synth.rolling_window_problems(ser, dict(lay, T=lay["T"] + 1))
+    kw = shared()
+    batch = sird.Batch(wins, iters=6, block_size=128, **kw)
+    batch.calibrate()
+    nb = batch.set_observations(np.concatenate([w["yD"] for w in nxt]))
+    assert nb >= 16 * sum(len(w["yD"]) for w in nxt) + 128 * len(nxt)
+    got = batch.calibrate()
+    # R0 stays that of the first layout: the fresh batch gets the same R0
+    fresh = sird.Batch([dict(w, R0=o["R0"]) for w, o in zip(nxt, wins)], iters=6, block_size=128, **kw).calibrate()
+    for a, b in zip(got, fresh):
+        assert a["index"] == b["index"] and a["loss"] == b["loss"] and a["loss_search"] == b["loss_search"]
+        assert np.array_equal(a["theta"], b["theta"]) and a["r2_D"] == b["r2_D"]
+    with pytest.raises(sird.SirdError):
+        batch.set_observations(np.ones(3))
+
+
 def test_batch_block_sizes_agree():
     ser = synth.load_series("c3")
     wins = synth.rolling_window_problems(ser, small_layout())
