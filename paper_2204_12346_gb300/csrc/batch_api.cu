@@ -128,7 +128,7 @@ cudaError_t autotune(sird_batch* b, long long work) {
     if (e != cudaSuccess) return e;
     float best = 1e30f;
     int best_block = 128, best_per = 0;
-    for (int block : {128, 256, 512, 1024}) {
+    for (int block : {128, 256, 512, 768, 1024}) {
         const int maxper = batch_blocks_per_sm(b->mdl, block, b->n_max);
         for (int per : {1, 2, maxper}) {
             // each distinct (block, blocks per SM) that fits, once

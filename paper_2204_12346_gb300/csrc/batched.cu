@@ -5,8 +5,9 @@
 // window from an atomic queue (windows sorted longest first, so the tail of the run is made of
 // short ones), runs that window's whole PSO -- initialisation and every iteration -- and takes
 // the next.  A window's swarm never leaves its block, so the synchronous global best is a
-// block-level minimum and no block ever waits for another.  Threads loop over the window's
-// particles (particle j = thread + q * blockDim).
+// block-level minimum and no block ever waits for another.  Thread t takes particles t,
+// t + 2 blockDim, ... and, where they exist, their partners t + blockDim, t + 3 blockDim, ...;
+// a pair's trajectories are integrated together in packed f32x2 arithmetic.
 //
 // Every window uses the same Philox counters, arithmetic and order of updates as a
 // single-window calibration, so its result equals that of sird_pso_calibrate with the same
@@ -30,11 +31,11 @@ __global__ void __launch_bounds__(1024) pso_batch_f32(const BatchWindow* __restr
     extern __shared__ float smem[];
     __shared__ unsigned long long wk[32];
     __shared__ int s_win;
-    const int B = blockDim.x, tid = threadIdx.x, P = m.P;
+    const int B = blockDim.x, B2 = 2 * B, tid = threadIdx.x, P = m.P;
     float* ys = smem;
     float* invys = (COST == COST_MAPE) ? ys + pad4(n_max) : ys;
-    float* th_s = smem + pad4(n_max) * (COST == COST_MAPE ? 2 : 1);
-    float* g_s = th_s + P * B;
+    float* th_s = smem + pad4(n_max) * (COST == COST_MAPE ? 2 : 1);  // [P][2B]
+    float* g_s = th_s + P * B2;
     float* lb_s = g_s + kMaxParams;
     float* ub_s = lb_s + kMaxParams;
     if (tid < P) {
@@ -64,7 +65,8 @@ __global__ void __launch_bounds__(1024) pso_batch_f32(const BatchWindow* __restr
         unsigned long long gkey = ~0ull;
         for (int it = 0; it <= iters; ++it) {
             unsigned long long key = ~0ull;
-            for (int j = tid; j < M; j += B) {
+            // particle j's update (initialisation at it == 0), theta decoded into th_s column col
+            auto update = [&](int j, int col) {
                 uint4 rnd = make_uint4(0, 0, 0, 0);
                 for (int d = 0; d < P; ++d) {
                     if ((d & 1) == 0)
@@ -87,9 +89,10 @@ __global__ void __launch_bounds__(1024) pso_batch_f32(const BatchWindow* __restr
                     }
                     X[off] = xn;
                     V[off] = vn;
-                    th_s[d * B + tid] = ((c.logmask >> d) & 1u) ? expf(xn) : xn;
+                    th_s[d * B2 + col] = ((c.logmask >> d) & 1u) ? expf(xn) : xn;
                 }
-                float f = fitness_f32<SPD, COST>(w, m, ys, invys, th_s + tid, B);
+            };
+            auto settle = [&](int j, float f) {  // personal best and the running block minimum
                 if (f != f) f = INFINITY;
                 float best = f;
                 if (it == 0 || f < PBF[j]) {
@@ -100,6 +103,22 @@ __global__ void __launch_bounds__(1024) pso_batch_f32(const BatchWindow* __restr
                 }
                 const unsigned long long kj = argmin_key(best, (uint32_t)j);
                 key = kj < key ? kj : key;
+            };
+            // a thread takes particle j0 and, when the window has more particles than the block
+            // has threads, also j0 + B; a pair is integrated together in packed form (one
+            // instruction stream for both), so a window of up to 2B particles takes one pass
+            for (int j0 = tid; j0 < M; j0 += B2) {
+                const int j1 = j0 + B;
+                update(j0, tid);
+                if (j1 < M) {
+                    update(j1, B + tid);
+                    float fa, fb;
+                    fitness_f32x2<SPD, COST>(w, m, ys, invys, th_s + tid, th_s + B + tid, B2, fa, fb);
+                    settle(j0, fa);
+                    settle(j1, fb);
+                } else {
+                    settle(j0, fitness_f32<SPD, COST>(w, m, ys, invys, th_s + tid, B2));
+                }
             }
             key = warp_min_key(key);
             if ((tid & 31) == 0) wk[tid >> 5] = key;
@@ -144,7 +163,7 @@ __global__ void batch_reeval_kernel(const BatchWindow* __restrict__ wins, int W,
 }  // namespace
 
 size_t batch_smem_bytes(const ModelDev& m, int block, int n_max) {
-    return ((size_t)pad4(n_max) * (m.cost == COST_MAPE ? 2 : 1) + (size_t)m.P * block + 3 * kMaxParams) *
+    return ((size_t)pad4(n_max) * (m.cost == COST_MAPE ? 2 : 1) + (size_t)m.P * 2 * block + 3 * kMaxParams) *
            sizeof(float);
 }
 

@@ -45,11 +45,79 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// ---------------------------------------------------------------- packed pairs (f32x2)
+// Two independent FP32 lanes in one 64-bit register: lane 0 in the low word.  Every operation
+// is the IEEE round-to-nearest operation of each lane (the .f32x2 forms of add / sub / mul /
+// fma), so a pair computes exactly what two scalar evaluations compute, with one instruction
+// issued per operation instead of two.
+struct F2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ F2 f2(float a, float b) {
+    return F2{((unsigned long long)__float_as_uint(b) << 32) | (unsigned long long)__float_as_uint(a)};
+}
+__device__ __forceinline__ F2 f2(float a) { return f2(a, a); }
+__device__ __forceinline__ float f2lo(F2 x) { return __uint_as_float((uint32_t)x.v); }
+__device__ __forceinline__ float f2hi(F2 x) { return __uint_as_float((uint32_t)(x.v >> 32)); }
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {
+    F2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return d;
+}
+__device__ __forceinline__ F2 add2(F2 a, F2 b) {
+    F2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 sub2(F2 a, F2 b) {
+    F2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) {
+    F2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 abs2(F2 a) { return F2{a.v & 0x7FFFFFFF7FFFFFFFull}; }
+
+__device__ __forceinline__ void two_sum2(F2 a, F2 b, F2& s, F2& e) {
+    s = add2(a, b);
+    const F2 bb = sub2(s, a);
+    e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+
+struct Kahan2 {
+    F2 sum{0ull}, comp{0ull};
+    __device__ __forceinline__ void add(F2 x) {
+        const F2 y = sub2(x, comp);
+        const F2 t = add2(sum, y);
+        comp = sub2(sub2(t, sum), y);
+        sum = t;
+    }
+    // adds the exact product a*b (the compensation is taken off before the single rounding);
+    // products enter the sum only this way, so no product is rounded on its own and no
+    // optimiser can fuse one into the subtraction in one form but not in the other
+    __device__ __forceinline__ void add_prod(F2 a, F2 b) {
+        const F2 y = fma2(a, b, F2{comp.v ^ 0x8000000080000000ull});
+        const F2 t = add2(sum, y);
+        comp = sub2(sub2(t, sum), y);
+        sum = t;
+    }
+};
+
 // Kahan summation step.
 struct Kahan {
     float sum = 0.f, comp = 0.f;
     __device__ __forceinline__ void add(float x) {
         const float y = __fsub_rn(x, comp);
+        const float t = __fadd_rn(sum, y);
+        comp = __fsub_rn(__fsub_rn(t, sum), y);
+        sum = t;
+    }
+    // adds the exact product a*b: y = fl(a*b - comp) in one rounding
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float y = __fmaf_rn(a, b, -comp);
         const float t = __fadd_rn(sum, y);
         comp = __fsub_rn(__fsub_rn(t, sum), y);
         sum = t;

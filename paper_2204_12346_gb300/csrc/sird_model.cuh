@@ -13,7 +13,8 @@
 //       (I - r is exact) and summed into a low part that is folded back once a day;
 //     - C and D: the day's increments are summed apart from the totals and folded in once a
 //       day, C with an exact TwoSum into a (hi, lo) pair;
-//     - the loss is a Kahan sum.
+//     - the loss is a Kahan sum whose terms e^2 (|e|/y for MAPE) enter unrounded, the
+//       compensation subtracted within the product's FMA.
 //   Nine FP32 instructions per step; the dependence chain through I is one FMA per step.
 //
 //  FP64 (fitness_f64): S, I, D in double precision in the paper's own operation order, with
@@ -61,9 +62,9 @@ struct LossF32 {
     Kahan sum;
     float mx = 0.f;
     __device__ __forceinline__ void add(float e, float invy) {
-        if (COST == COST_MSE) sum.add(__fmul_rn(e, e));
+        if (COST == COST_MSE) sum.add_prod(e, e);
         else if (COST == COST_MAE) sum.add(fabsf(e));
-        else if (COST == COST_MAPE) sum.add(__fmul_rn(fabsf(e), invy));
+        else if (COST == COST_MAPE) sum.add_prod(fabsf(e), invy);
         else mx = fmaxf(mx, __fmul_rn(e, e));
     }
     __device__ __forceinline__ float result(int n, int n_kept) const {
@@ -193,6 +194,144 @@ __device__ float fitness_f32(const WindowDev& w, const ModelDev& m, const float*
         }
     }
     return loss.result(w.n_obs, w.n_kept);
+}
+
+// ---------------------------------------------------------------- FP32, two particles per thread
+// The same arithmetic for two parameter vectors of one window at once in packed f32x2 form:
+// every lane performs exactly fitness_f32's operations in the same order, so each loss equals
+// fitness_f32's bit for bit, while one instruction advances both trajectories.
+
+__device__ __forceinline__ void euler_f32x2(F2 cb, F2 na, F2 dm, F2 Sday, F2& cday, F2& dday, F2& I, F2& Il) {
+    const F2 S = sub2(Sday, cday);
+    const F2 g = fma2(cb, S, na);
+    const F2 t = mul2(cb, I);
+    cday = fma2(t, S, cday);
+    dday = fma2(dm, I, dday);
+    const F2 r = fma2(g, I, I);
+    Il = fma2(g, I, add2(Il, sub2(I, r)));
+    I = r;
+}
+
+struct DayStateF32x2 {
+    F2 Ch, Cl, Sday, Dh, Nh, Nl;
+    __device__ __forceinline__ void init(const WindowDev& w, float I0a, float I0b, float y0) {
+        float ha, la, hb, lb;
+        two_sum(I0a, w.RD0h, ha, la);
+        two_sum(I0b, w.RD0h, hb, lb);
+        Ch = f2(ha, hb);
+        Cl = add2(f2(la, lb), f2(w.RD0l));
+        Nh = f2(w.Nh);
+        Nl = f2(w.Nl);
+        Sday = add2(sub2(Nh, Ch), sub2(Nl, Cl));
+        Dh = f2(y0);
+    }
+    __device__ __forceinline__ F2 close_day(F2 cday, F2 dday, float y, F2& I, F2& Il) {
+        const F2 si = add2(I, Il);
+        Il = sub2(Il, sub2(si, I));
+        I = si;
+        F2 s, e;
+        two_sum2(Ch, cday, s, e);
+        Ch = s;
+        Cl = add2(Cl, e);
+        Sday = add2(sub2(Nh, Ch), sub2(Nl, Cl));
+        Dh = add2(Dh, dday);
+        return sub2(f2(y), Dh);
+    }
+};
+
+template <int COST>
+struct LossF32x2 {
+    Kahan2 sum;
+    float mxa = 0.f, mxb = 0.f;
+    __device__ __forceinline__ void add(F2 e, float invy) {
+        if (COST == COST_MSE) sum.add_prod(e, e);
+        else if (COST == COST_MAE) sum.add(abs2(e));
+        else if (COST == COST_MAPE) sum.add_prod(abs2(e), f2(invy));
+        else {
+            const F2 e2 = mul2(e, e);
+            mxa = fmaxf(mxa, f2lo(e2));
+            mxb = fmaxf(mxb, f2hi(e2));
+        }
+    }
+    __device__ __forceinline__ void result(int n, int n_kept, float& fa, float& fb) const {
+        if (COST == COST_MXSE) {
+            fa = mxa;
+            fb = mxb;
+            return;
+        }
+        LossF32<COST> la, lb;
+        la.sum.sum = f2lo(sum.sum);
+        lb.sum.sum = f2hi(sum.sum);
+        fa = la.result(n, n_kept);
+        fb = lb.result(n, n_kept);
+    }
+};
+
+// Losses of two parameter vectors (theta_d at tha[d*stride], thb[d*stride]); the ramp form
+// evaluates them one after the other with fitness_f32.
+template <int SPD, int COST>
+__device__ void fitness_f32x2(const WindowDev& w, const ModelDev& m, const float* __restrict__ ys,
+                              const float* __restrict__ invys, const float* tha, const float* thb, int stride,
+                              float& fa, float& fb) {
+    if (m.beta_form == BETA_RAMP) {
+        fa = fitness_f32<SPD, COST>(w, m, ys, invys, tha, stride);
+        fb = fitness_f32<SPD, COST>(w, m, ys, invys, thb, stride);
+        return;
+    }
+    const int spd = SPD > 0 ? SPD : m.spd;
+    const int L = w.n_obs - 1;
+    const int steps = L * spd;
+    const int K = m.K;
+    const F2 gam = f2(tha[K * stride], thb[K * stride]), mu = f2(tha[(K + 1) * stride], thb[(K + 1) * stride]);
+    F2 I = m.fit_I0 ? f2(tha[(K + 2) * stride], thb[(K + 2) * stride]) : f2(w.I0f);
+    F2 Il = f2(0.f);
+    const F2 gm = add2(gam, mu);
+    const F2 dth = f2(w.dt_h), dtl = f2(w.dt_l);
+    const F2 a = fma2(gm, dth, mul2(gm, dtl));
+    const F2 na = F2{a.v ^ 0x8000000080000000ull};  // -a, exact
+    const F2 dm = fma2(mu, dth, mul2(mu, dtl));
+    const F2 cbnh = f2(w.cbn_h), cbnl = f2(w.cbn_l);
+    DayStateF32x2 ds;
+    ds.init(w, f2lo(I), f2hi(I), ys[0]);
+    LossF32x2<COST> loss;
+
+    int k = 0, day = 0, in_day = 0;
+    F2 cday = f2(0.f), dday = f2(0.f);
+    for (int seg = 0; seg < K; ++seg) {
+        const F2 b = f2(tha[seg * stride], thb[seg * stride]);
+        const F2 cb = fma2(b, cbnh, mul2(b, cbnl));
+        const int kend = segment_start(seg + 1, steps, K);
+        while (in_day != 0 && k < kend) {
+            euler_f32x2(cb, na, dm, ds.Sday, cday, dday, I, Il);
+            ++k;
+            if (++in_day == spd) {
+                ++day;
+                in_day = 0;
+                loss.add(ds.close_day(cday, dday, ys[day], I, Il), COST == COST_MAPE ? invys[day] : 0.f);
+                cday = f2(0.f);
+                dday = f2(0.f);
+            }
+        }
+        while (k + spd <= kend) {
+            if (SPD > 0) {
+#pragma unroll
+                for (int s = 0; s < (SPD > 0 ? SPD : 1); ++s) euler_f32x2(cb, na, dm, ds.Sday, cday, dday, I, Il);
+            } else {
+                for (int s = 0; s < spd; ++s) euler_f32x2(cb, na, dm, ds.Sday, cday, dday, I, Il);
+            }
+            k += spd;
+            ++day;
+            loss.add(ds.close_day(cday, dday, ys[day], I, Il), COST == COST_MAPE ? invys[day] : 0.f);
+            cday = f2(0.f);
+            dday = f2(0.f);
+        }
+        while (k < kend) {
+            euler_f32x2(cb, na, dm, ds.Sday, cday, dday, I, Il);
+            ++k;
+            ++in_day;
+        }
+    }
+    loss.result(w.n_obs, w.n_kept, fa, fb);
 }
 
 // ---------------------------------------------------------------- FP64
