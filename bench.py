@@ -49,10 +49,14 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 # DRAM bytes per launch of the dominant kernel from committed ncu captures, valid only for the
 # kernel sources they were taken on (sha256[:16] of the files listed).
 PROFILED = {
-    "c3": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "64aa7529fa253ee8",
-           "traffic_bytes": 13113856, "profile": "profiles/pso_batch_f32_c3.md"},
+    "c3": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "3101a04715ddb40a",
+           "traffic_bytes": 13456128, "profile": "profiles/pso_batch_f32_c3.md"},
     "c2": {"files": ["pso_persistent.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"],
            "sha": "ea40821fd8e456d2", "traffic_bytes": 727296, "profile": "profiles/pso_f32_persistent_c2.md"},
+    "c4": {"files": ["adjoint_f32.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "ebec4e291f32b671",
+           "traffic_bytes": 159232, "profile": "profiles/loss_grad_f32_c4.md"},
+    "c5": {"files": ["pso_kernels.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "f3e448c66ebdd01d",
+           "traffic_bytes": 282807040, "profile": "profiles/pso_f32_kernel_c5.md"},
 }
 
 
@@ -417,6 +421,7 @@ def run_single(args, rank, world):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": profiled_traffic(args.workload),
+                     "traffic_source": PROFILED.get(args.workload, {}).get("profile"),
                      "kernel": "pso_f32_persistent" if persistent else ("pso_f64_kernel" if fp64 else "pso_f32_kernel"),
                      "avg_launch_us": kms * 1e3 / iter_launches, "us_per_iteration": kms * 1e3 / c["iters"],
                      "peak_basis": ("nominal FP64 1.25 TFLOP/s" if fp64
@@ -502,6 +507,7 @@ def run_c4(args, rank, world):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic("c4"),
+                     "traffic_source": PROFILED["c4"]["profile"],
                      "kernel": "loss_grad_f32_kernel", "avg_launch_us": kms * 1e3, "flops_per_launch": flops,
                      "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
         "e2e": {"value": units * args.steps * world / (e2e_total / 1e3), "unit": UNIT,
