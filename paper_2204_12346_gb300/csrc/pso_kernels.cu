@@ -36,6 +36,8 @@ __device__ __forceinline__ float* after_obs_f32(float* smem, const WindowDev& w)
 
 // ------------------------------------------------------------------ FP32 eval
 
+// A thread evaluates two parameter vectors, p0 = block * 2B + thread and p1 = p0 + B, together
+// in packed f32x2 form (each loss equal to the one-at-a-time evaluation bit for bit).
 template <int SPD, int COST>
 __global__ void __launch_bounds__(1024) eval_f32_kernel(WindowDev w, ModelDev m, ObsDev o,
                                                          const float* __restrict__ theta, int ld, int M,
@@ -43,13 +45,22 @@ __global__ void __launch_bounds__(1024) eval_f32_kernel(WindowDev w, ModelDev m,
     extern __shared__ float smem[];
     float* ys = smem;
     float* invys = stage_obs_f32<COST>(smem, w, o);
-    float* th_s = after_obs_f32<COST>(smem, w);
-    const int B = blockDim.x, tid = threadIdx.x;
-    const int p = blockIdx.x * B + tid;
-    if (p < M)
-        for (int d = 0; d < m.P; ++d) th_s[d * B + tid] = theta[(size_t)d * ld + p];
+    float* th_s = after_obs_f32<COST>(smem, w);  // [P][2B]
+    const int B = blockDim.x, B2 = 2 * B, tid = threadIdx.x;
+    const int p0 = blockIdx.x * B2 + tid, p1 = p0 + B;
+    for (int d = 0; d < m.P; ++d) {
+        if (p0 < M) th_s[d * B2 + tid] = theta[(size_t)d * ld + p0];
+        if (p1 < M) th_s[d * B2 + B + tid] = theta[(size_t)d * ld + p1];
+    }
     __syncthreads();
-    if (p < M) loss[p] = fitness_f32<SPD, COST>(w, m, ys, invys, th_s + tid, B);
+    if (p1 < M) {
+        float fa, fb;
+        fitness_f32x2<SPD, COST>(w, m, ys, invys, th_s + tid, th_s + B + tid, B2, fa, fb);
+        loss[p0] = fa;
+        loss[p1] = fb;
+    } else if (p0 < M) {
+        loss[p0] = fitness_f32<SPD, COST>(w, m, ys, invys, th_s + tid, B2);
+    }
 }
 
 // ------------------------------------------------------------------ FP32 PSO iteration
@@ -60,11 +71,11 @@ __global__ void __launch_bounds__(1024) pso_f32_kernel(WindowDev w, ModelDev m, 
     extern __shared__ float smem[];
     __shared__ unsigned long long wk[32];
     __shared__ int last;
-    const int B = blockDim.x, tid = threadIdx.x, P = m.P;
+    const int B = blockDim.x, B2 = 2 * B, tid = threadIdx.x, P = m.P;
     float* ys = smem;
     float* invys = stage_obs_f32<COST>(smem, w, o);
-    float* th_s = after_obs_f32<COST>(smem, w);
-    float* g_s = th_s + P * B;
+    float* th_s = after_obs_f32<COST>(smem, w);  // [P][2B]
+    float* g_s = th_s + P * B2;
     float* lb_s = g_s + kMaxParams;
     float* ub_s = lb_s + kMaxParams;
     if (tid < P) {
@@ -74,9 +85,11 @@ __global__ void __launch_bounds__(1024) pso_f32_kernel(WindowDev w, ModelDev m, 
     }
     __syncthreads();
 
-    const int p = blockIdx.x * B + tid;
+    // particles p0 = block * 2B + thread and p1 = p0 + B; a pair is integrated together in
+    // packed f32x2 form
+    const int p0 = blockIdx.x * B2 + tid, p1 = p0 + B;
     unsigned long long key = ~0ull;
-    if (p < sw.M) {
+    auto update = [&](int p, int col) {
         uint4 rnd = make_uint4(0, 0, 0, 0);
         for (int d = 0; d < P; ++d) {
             // one Philox call per (particle, iteration, dimension pair)
@@ -101,9 +114,10 @@ __global__ void __launch_bounds__(1024) pso_f32_kernel(WindowDev w, ModelDev m, 
             }
             sw.x[off] = xn;
             sw.v[off] = vn;
-            th_s[d * B + tid] = ((c.logmask >> d) & 1u) ? expf(xn) : xn;
+            th_s[d * B2 + col] = ((c.logmask >> d) & 1u) ? expf(xn) : xn;
         }
-        float f = fitness_f32<SPD, COST>(w, m, ys, invys, th_s + tid, B);
+    };
+    auto settle = [&](int p, float f) {
         if (f != f) f = INFINITY;
         float best = f;
         const bool improve = (iter == 0) || (f < sw.pbf[p]);
@@ -113,7 +127,20 @@ __global__ void __launch_bounds__(1024) pso_f32_kernel(WindowDev w, ModelDev m, 
         } else {
             best = sw.pbf[p];
         }
-        key = argmin_key(best, (uint32_t)p);
+        const unsigned long long kp = argmin_key(best, (uint32_t)p);
+        key = kp < key ? kp : key;
+    };
+    if (p0 < sw.M) {
+        update(p0, tid);
+        if (p1 < sw.M) {
+            update(p1, B + tid);
+            float fa, fb;
+            fitness_f32x2<SPD, COST>(w, m, ys, invys, th_s + tid, th_s + B + tid, B2, fa, fb);
+            settle(p0, fa);
+            settle(p1, fb);
+        } else {
+            settle(p0, fitness_f32<SPD, COST>(w, m, ys, invys, th_s + tid, B2));
+        }
     }
 
     // block minimum -> one atomicMin per block -> the last block publishes the global best
@@ -388,11 +415,14 @@ unsigned grid_for(int M, int block) {
     return (unsigned)((M + block - 1) / block);
 }
 
+// FP32 eval / iteration kernels: two particles per thread
+unsigned grid_for_pairs(int M, int block) { return grid_for(M, 2 * block); }
+
 }  // namespace
 
 size_t smem_bytes_f32(const WindowDev& w, const ModelDev& m, int block, bool with_theta) {
     size_t n = (size_t)pad4(w.n_obs) * (m.cost == COST_MAPE ? 2 : 1);
-    if (with_theta) n += (size_t)m.P * block + 3 * kMaxParams;
+    if (with_theta) n += (size_t)m.P * 2 * block + 3 * kMaxParams;  // theta of two particles per thread
     return n * sizeof(float);
 }
 
@@ -423,7 +453,7 @@ cudaError_t launch_eval_f32(const WindowDev& w, const ModelDev& m, const ObsDev&
     SIRD_DISPATCH_SPD(m.spd, SIRD_DISPATCH_COST(m.cost, {
         auto kern = eval_f32_kernel<S_, C_>;
         e = set_smem(kern, sm);
-        if (e == cudaSuccess) kern<<<grid_for(M, block), block, sm, s>>>(w, m, o, theta, ld, M, loss);
+        if (e == cudaSuccess) kern<<<grid_for_pairs(M, block), block, sm, s>>>(w, m, o, theta, ld, M, loss);
     }));
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -448,7 +478,7 @@ cudaError_t launch_pso_f32(const WindowDev& w, const ModelDev& m, const ObsDev& 
     SIRD_DISPATCH_SPD(m.spd, SIRD_DISPATCH_COST(m.cost, {
         auto kern = pso_f32_kernel<S_, C_>;
         e = set_smem(kern, sm);
-        if (e == cudaSuccess) kern<<<grid_for(sw.M, block), block, sm, s>>>(w, m, o, c, sw, r, iter);
+        if (e == cudaSuccess) kern<<<grid_for_pairs(sw.M, block), block, sm, s>>>(w, m, o, c, sw, r, iter);
     }));
     return e != cudaSuccess ? e : cudaGetLastError();
 }

@@ -294,6 +294,11 @@ extern "C" sird_status sird_pso_create(const sird_problem* pb, const sird_pso_co
     h->c32.key1 = h->c64.key1 = (uint32_t)(cfg->seed >> 32);
     h->c32.stream_id = h->c64.stream_id = cfg->stream_id;
 
+    if (h->precision == 32 && smem_bytes_f32(h->win, h->mdl, h->block, true) > 227 * 1024) {
+        g_create_error = "block_size too large for this many parameters (shared memory)";
+        sird_pso_destroy(h);
+        return SIRD_ERR_ARG;
+    }
     auto bail = [&](cudaError_t e, const char* what) {
         g_create_error = std::string(what) + ": " + cudaGetErrorString(e);
         sird_pso_destroy(h);
