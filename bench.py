@@ -75,10 +75,11 @@ def profiled_traffic(workload: str):
     return p["traffic_bytes"]
 
 
-def algorithmic_flops_per_particle_day(spd: int) -> int:
+def algorithmic_flops_per_particle_day(spd: int, ramp: bool = False) -> int:
     """8 flops per Euler step (S = N - C, inf = cb*S*I, C += inf, I += inf - a*I, D += dm*I with
-    FMA counted as 2) times steps per day, plus 3 for the day's error and its square-sum."""
-    return 8 * spd + 3
+    FMA counted as 2) times steps per day, plus 3 for the day's error and its square-sum; the
+    ramp form of eq. (beta) adds 5 per step (t = k dt, beta on the ramp, cb = beta dt/N)."""
+    return (13 if ramp else 8) * spd + 3
 
 
 # Bytes of one window's result record copied back by a batched calibration.
@@ -97,17 +98,27 @@ def single_window(name: str):
     return c, ser, y, lb, ub
 
 
-def c3_windows(seed_offset: int = 0):
-    c = dict(configs.CONFIGS["c3"])
-    ser = synth.load_series("c3")
+BATCHED = ("c3", "paper")
+
+
+def batch_windows(name: str, seed_offset: int = 0):
+    """(config, windows, lb, ub, model keywords) of a batched workload; rank r's windows use the
+    Philox stream words r*W .. r*W + W - 1."""
+    c = dict(configs.CONFIGS[name])
+    ser = synth.load_series(c["series"])
     lay = synth.rolling_windows(W=c["W"], L_min=c["L_min"], L_max=c["L_max"], M_min=c["M_min"], M_max=c["M_max"],
                                 delta=c["delta"], seed=c["seed"])
     wins = synth.rolling_window_problems(ser, lay)
     for i, w in enumerate(wins):
         w["seed"] = c["seed"]
         w["stream_id"] = seed_offset * c["W"] + i
-    lb, ub = configs.bounds(c["K"], c["log"])
-    return c, wins, lb, ub
+    if c.get("beta_form") == "ramp":
+        lb, ub = configs.bounds_ramp()
+        model = dict(K=1, beta_form=1, log_scale=None)
+    else:
+        lb, ub = configs.bounds(c["K"], c["log"])
+        model = dict(K=c["K"], beta_form=0, log_scale=[1] * len(lb) if c["log"] else None)
+    return c, wins, lb, ub, model
 
 
 def describe(name: str) -> str:
@@ -118,6 +129,9 @@ def describe(name: str) -> str:
         "c2": ("single window FP32 + Kahan loss: 60 days, beta piecewise constant over 4 segments (7 params), "
                "log-uniform PSO box, 4096 particles, 1000 iterations, dt=0.1, FP64 re-evaluation of the 32 best"),
         "c1": "plain method FP64: constant beta, gamma, mu + I0, 30 days, 64 particles, 200 iterations, dt=0.1",
+        "paper": ("the paper's setting, batched FP32: ramp beta(t) (beta1, beta2, t1, t2, gamma, mu, I0), 139 "
+                  "rolling windows of 35 days shifted by 3 days over a 450-day series, 10000 particles per window, "
+                  "linear PSO box, 100 iterations, dt=0.1, one persistent launch, FP64 re-evaluation per window"),
         "c4": ("gradient FP32: loss + exact gradient (discrete adjoint of the compensated FP32 trajectory, "
                "day-start checkpoints) of the 4096 personal bests of a calibrated swarm, 90 days, 4 beta segments "
                "(7 params), dt=0.05"),
@@ -273,16 +287,18 @@ def s_to_calibrate() -> dict:
 
 # ------------------------------------------------------------------ our arm
 
-def run_c3(args, rank, world):
+def run_batched(args, rank, world):
     import torch
 
     from paper_2204_12346_gb300 import sird
 
-    c, wins, lb, ub = c3_windows(rank)
+    name = args.workload
+    c, wins, lb, ub, model = batch_windows(name, rank)
+    ramp = model["beta_form"] == 1
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        batch = sird.Batch(wins, K=c["K"], spd=c["spd"], iters=c["iters"], lb=lb, ub=ub, log_scale=[1] * len(lb),
-                           block_size=args.block, stream=stream)
+        batch = sird.Batch(wins, spd=c["spd"], iters=c["iters"], lb=lb, ub=ub, block_size=args.block, stream=stream,
+                           **model)
         ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
         ev[0].record(stream)  # torch reads only events it has seen recorded; the graph re-records them
         ev[1].record(stream)
@@ -307,7 +323,7 @@ def run_c3(args, rank, world):
         return None
     pdays = sum(w["particles"] * w["L"] for w in wins)
     units = pdays * c["iters"]
-    flops = pdays * algorithmic_flops_per_particle_day(c["spd"]) * (c["iters"] + 1)
+    flops = pdays * algorithmic_flops_per_particle_day(c["spd"], ramp) * (c["iters"] + 1)
     kms = statistics.mean(kern_ms)
     achieved = flops / (kms / 1e3) / 1e12
     d2h = len(wins) * BATCH_OUT_BYTES
@@ -315,15 +331,15 @@ def run_c3(args, rank, world):
         "metric": METRIC, "value": units * args.steps * world / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": describe("c3"), "name": c["name"], "windows": len(wins),
+        "config": {"workload": describe(name), "name": c["name"], "windows": len(wins),
                    "particle_days_per_iteration": pdays, "iterations": c["iters"], "steps_per_day": c["spd"],
                    "params": len(lb), "block": f"{batch.block_size} threads x {batch.blocks_per_sm} per SM "
                                                + ("(autotuned)" if args.block == 0 else "(given)"),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"independent batches x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic("c3"),
-                     "traffic_source": PROFILED["c3"]["profile"], "kernel": "pso_batch_f32",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic(name),
+                     "traffic_source": PROFILED.get(name, {}).get("profile"), "kernel": "pso_batch_f32",
                      "avg_launch_us": kms * 1e3, "flops_per_launch": flops,
                      "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
         "e2e": {"value": units * args.steps * world / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -331,12 +347,13 @@ def run_c3(args, rank, world):
         "gpu_launches": args.steps * 2,
         "clocks": clocks,
         "result": {"windows": len(res), "median_r2_D": float(np.median([r["r2_D"] for r in res])),
+                   "min_r2_D": float(np.min([r["r2_D"] for r in res])),
                    "window0_loss_fp64": res[0]["loss"]},
     }
-    if not args.no_s2c:
+    if not args.no_s2c and name == "c3":
         out["s_to_calibrate"] = s_to_calibrate()
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline("c3", budget_s=args.cpu_budget)
+        out["cpu_baseline"] = cpu_baseline(name, budget_s=args.cpu_budget)
     return out
 
 
@@ -531,15 +548,18 @@ def cpu_baseline(name: str, budget_s: float = 15.0, iters_cap: int | None = None
     O.build()
     t0 = time.perf_counter()
     units = 0
-    if name == "c3":
-        c, wins, lb, ub = c3_windows(0)
-        zlb, zub = np.log(lb), np.log(ub)
+    if name in BATCHED:
+        c, wins, lb, ub, model = batch_windows(name, 0)
+        logd = [1] * len(lb) if model["log_scale"] else [0] * len(lb)
+        zlb = np.where(logd, np.log(np.maximum(lb, 1e-300)), lb)
+        zub = np.where(logd, np.log(np.maximum(ub, 1e-300)), ub)
         done = 0
         for w in wins:
             if time.perf_counter() - t0 >= budget_s or (iters_cap is not None and done >= iters_cap):
                 break
-            pb = O.Problem(yD=w["yD"], N=w["N"], R0=w["R0"], K=c["K"], spd=c["spd"])
-            O.PSO(pb, w["particles"], zlb, zub, logdim=[1] * len(lb), seed=w["seed"], stream=w["stream_id"],
+            pb = O.Problem(yD=w["yD"], N=w["N"], R0=w["R0"], K=model["K"], spd=c["spd"],
+                           beta_form=O.BETA_RAMP if model["beta_form"] == 1 else O.BETA_PWC)
+            O.PSO(pb, w["particles"], zlb, zub, logdim=logd, seed=w["seed"], stream=w["stream_id"],
                   store_f32=True).init().step(1)
             units += w["particles"] * w["L"] * 2
             done += 1
@@ -603,7 +623,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c3", "c2", "c1", "c4", "c5"], default="c3")
+    ap.add_argument("--workload", choices=["c3", "c2", "c1", "c4", "c5", "paper"], default="c3")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-units", type=int, default=2,
                     help="reference arm: windows (batched) or PSO iterations (single window) per step")
@@ -626,8 +646,8 @@ def main():
     try:
         if args.impl == "reference":
             out = run_reference(args, rank, world)
-        elif args.workload == "c3":
-            out = run_c3(args, rank, world)
+        elif args.workload in BATCHED:
+            out = run_batched(args, rank, world)
         elif args.workload == "c4":
             out = run_c4(args, rank, world)
         else:

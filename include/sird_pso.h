@@ -280,7 +280,7 @@ sird_status sird_forecast(const sird_problem* problem, const double* theta, int 
  *
  * problems[W], configs[W] are host arrays.  Every window must share beta_form, K,
  * steps_per_day, cost, objective, fit_I0, precision (32), w, c1, c2, iters, the bounds and
- * log_scale; n_obs, observations, N, I0, R0, particles (1..2048), seed and stream_id may
+ * log_scale; n_obs, observations, N, I0, R0, particles (1..2^20), seed and stream_id may
  * differ.  configs[0].block_size = 0 lets the library pick the threads per block and the blocks
  * per SM by timing short trial runs of each candidate (cached in the file named by the
  * environment variable SIRD_TUNE_CACHE when it is set); otherwise a multiple of 32 in 32..1024

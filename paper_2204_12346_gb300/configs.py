@@ -23,6 +23,13 @@ def bounds(K: int, log: bool):
     return lb, ub
 
 
+def bounds_ramp(t_max: float = 28.0):
+    """Linear box of the paper's ramp form (beta1, beta2, t1, t2, gamma, mu, I0): the second,
+    narrowed box of Sec. 3.2 (beta in [0, 2], gamma in [0, 1], mu in [0, 0.1]) with the ramp's
+    end at most t_max = 28 days after the window start; I0 in [0, 1e6]."""
+    return [0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0], [2.0, 2.0, t_max, t_max, 1.0, 0.1, 1e6]
+
+
 CONFIGS = {
     # Plain method in FP64: constant rates (K = 1) plus I0, 30 days, dt = 0.1 day.
     "c1": dict(name="c1-plain-fp64", series="c1", K=1, days=30, spd=10, M=64, iters=200,
@@ -36,6 +43,10 @@ CONFIGS = {
     # Adjoint gradient over a 90-day window at dt = 0.05 day, checkpoints every 16 steps.
     "c4": dict(name="c4-adjoint-90d", series="c4", K=4, days=90, spd=20, M=4096, iters=200,
                precision=32, log=True, seed=0, ckpt=16, polish_topk=32, reeval_topk=32),
+    # The paper's own setting (Sec. 3.1-3.3): ramp beta(t), 139 rolling windows of tau = 35 days
+    # shifted by delta = 3 days over the 450-day series, 10000 particles, 100 iterations.
+    "paper": dict(name="paper-ramp-139-windows", series="c3", beta_form="ramp", W=139, iters=100, spd=10,
+                  precision=32, log=False, seed=0, L_min=35, L_max=35, M_min=10000, M_max=10000, delta=3),
     # 2^20 particles, 10 segments, 120 days at dt = 0.05 day, then a 14-day forecast.
     "c5": dict(name="c5-large-2^20", series="c5", K=10, days=120, spd=20, M=1 << 20, iters=100,
                precision=32, log=True, seed=0, horizon=14, forecast_topk=1024, reeval_topk=32),

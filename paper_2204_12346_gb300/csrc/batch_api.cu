@@ -178,7 +178,8 @@ extern "C" sird_status sird_batch_create(int W, const sird_problem* problems, co
             p.objective != p0.objective || p.fit_I0 != p0.fit_I0)
             return berr(SIRD_ERR_ARG, "window " + std::to_string(i) + ": model settings differ from window 0");
         if (c.precision != 32) return berr(SIRD_ERR_UNSUPPORTED, "batched calibration is FP32 only");
-        if (c.particles < 1 || c.particles > 2048) return berr(SIRD_ERR_ARG, "particles per window out of range [1, 2048]");
+        if (c.particles < 1 || c.particles > (1 << 20))
+            return berr(SIRD_ERR_ARG, "particles per window out of range [1, 2^20]");
         if (c.iters != c0.iters || c.w != c0.w || c.c1 != c0.c1 || c.c2 != c0.c2 || c.iters < 0)
             return berr(SIRD_ERR_ARG, "window " + std::to_string(i) + ": PSO coefficients or iterations differ");
         if (!c.lb || !c.ub) return berr(SIRD_ERR_ARG, "lb/ub is NULL");

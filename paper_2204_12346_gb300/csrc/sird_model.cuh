@@ -267,18 +267,60 @@ struct LossF32x2 {
     }
 };
 
-// Losses of two parameter vectors (theta_d at tha[d*stride], thb[d*stride]); the ramp form
-// evaluates them one after the other with fitness_f32.
+// eq. (beta) for one particle at step k, and its cb = dt beta / N, as fitness_f32 computes them.
+struct RampCoefF32 {
+    float b1, b2, t1, t2, slope;
+    __device__ __forceinline__ void init(const float* th, int stride) {
+        b1 = th[0];
+        b2 = th[stride];
+        const float ta = th[2 * stride], tb = th[3 * stride];
+        t1 = fminf(ta, tb);
+        t2 = fmaxf(ta, tb);
+        slope = (t2 > t1) ? __fdiv_rn(__fsub_rn(b2, b1), __fsub_rn(t2, t1)) : 0.f;
+    }
+    __device__ __forceinline__ float cb(float t, const WindowDev& w) const {
+        const float beta = (t < t1) ? b1 : ((t < t2) ? __fmaf_rn(slope, __fsub_rn(t, t1), b1) : b2);
+        return __fmaf_rn(beta, w.cbn_h, __fmul_rn(beta, w.cbn_l));
+    }
+};
+
+// Losses of two parameter vectors (theta_d at tha[d*stride], thb[d*stride]).
 template <int SPD, int COST>
 __device__ void fitness_f32x2(const WindowDev& w, const ModelDev& m, const float* __restrict__ ys,
                               const float* __restrict__ invys, const float* tha, const float* thb, int stride,
                               float& fa, float& fb) {
+    const int spd = SPD > 0 ? SPD : m.spd;
     if (m.beta_form == BETA_RAMP) {
-        fa = fitness_f32<SPD, COST>(w, m, ys, invys, tha, stride);
-        fb = fitness_f32<SPD, COST>(w, m, ys, invys, thb, stride);
+        // the ramp changes beta every step: each lane's cb is formed as in fitness_f32, the
+        // step itself is packed
+        const int L = w.n_obs - 1;
+        const F2 gam = f2(tha[4 * stride], thb[4 * stride]), mu = f2(tha[5 * stride], thb[5 * stride]);
+        F2 I = m.fit_I0 ? f2(tha[6 * stride], thb[6 * stride]) : f2(w.I0f);
+        F2 Il = f2(0.f);
+        const F2 gm = add2(gam, mu);
+        const F2 dth = f2(w.dt_h), dtl = f2(w.dt_l);
+        const F2 a = fma2(gm, dth, mul2(gm, dtl));
+        const F2 na = F2{a.v ^ 0x8000000080000000ull};
+        const F2 dm = fma2(mu, dth, mul2(mu, dtl));
+        RampCoefF32 ra, rb;
+        ra.init(tha, stride);
+        rb.init(thb, stride);
+        const float dtf = __fadd_rn(w.dt_h, w.dt_l);
+        DayStateF32x2 ds;
+        ds.init(w, f2lo(I), f2hi(I), ys[0]);
+        LossF32x2<COST> loss;
+        int k = 0;
+        for (int day = 1; day <= L; ++day) {
+            F2 cday = f2(0.f), dday = f2(0.f);
+            for (int s = 0; s < spd; ++s, ++k) {
+                const float t = __fmul_rn((float)k, dtf);
+                euler_f32x2(f2(ra.cb(t, w), rb.cb(t, w)), na, dm, ds.Sday, cday, dday, I, Il);
+            }
+            loss.add(ds.close_day(cday, dday, ys[day], I, Il), COST == COST_MAPE ? invys[day] : 0.f);
+        }
+        loss.result(w.n_obs, w.n_kept, fa, fb);
         return;
     }
-    const int spd = SPD > 0 ? SPD : m.spd;
     const int L = w.n_obs - 1;
     const int steps = L * spd;
     const int K = m.K;

@@ -5,7 +5,7 @@ import torch
 
 import oracle as O
 from paper_2204_12346_gb300 import configs, sird, synth
-from util import f32, rel_err
+from util import f32, fp32_loss_tol, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -96,3 +96,55 @@ def test_full_512_window_layout_against_the_oracle_at_initialisation():
         s = np.sort(pso.pbest_f)
         if s[1] - s[0] > 3e-5 * s[0]:
             assert res[i]["index"] == pso.gbest_idx
+
+
+def ramp_shared():
+    lb, ub = configs.bounds_ramp()
+    return dict(K=1, spd=10, beta_form=sird.BETA_RAMP, lb=lb, ub=ub, log_scale=None, seed=5)
+
+
+def test_batch_ramp_windows_match_single_window_calibrations():
+    # the paper's ramp form on a linear box; swarms beyond 2 x block size (several passes per
+    # thread, packed pairs and single particles)
+    ser = synth.load_series("c3")
+    lay = {"L": np.array([35, 35, 20, 35]), "M": np.array([3000, 700, 129, 2500]), "T": np.array([0, 90, 200, 414])}
+    wins = synth.rolling_window_problems(ser, lay)
+    kw = ramp_shared()
+    res = sird.Batch(wins, iters=5, block_size=256, **kw).calibrate()
+    for i, w in enumerate(wins):
+        cal = sird.Calibrator(w["yD"], w["N"], R0=w["R0"], particles=w["particles"], iters=5, precision=32,
+                              stream_id=i, reeval_topk=0, **kw)
+        r = cal.calibrate()
+        assert res[i]["index"] == r["index"], i
+        assert res[i]["loss_search"] == r["loss_search"], i
+        assert res[i]["loss"] == r["loss"], i
+        assert np.array_equal(res[i]["theta"], r["theta"]), i
+
+
+def test_paper_layout_against_the_oracle_at_initialisation():
+    # the paper's setting: 139 windows of 35 days shifted by 3 days, 10000 particles, ramp beta(t)
+    c = configs.CONFIGS["paper"]
+    ser = synth.load_series(c["series"])
+    lay = synth.rolling_windows(W=c["W"], L_min=c["L_min"], L_max=c["L_max"], M_min=c["M_min"], M_max=c["M_max"],
+                                delta=c["delta"], seed=c["seed"])
+    wins = synth.rolling_window_problems(ser, lay)
+    assert len(wins) == 139 and all(w["particles"] == 10000 and w["L"] == 35 for w in wins)
+    assert [w["T"] for w in wins[:3]] == [0, 3, 6] and wins[-1]["T"] == 414
+    kw = ramp_shared()
+    res = sird.Batch(wins, iters=0, **kw).calibrate()
+    assert len(res) == 139 and all(np.isfinite(r["loss"]) for r in res)
+    lb, ub = configs.bounds_ramp()
+    zlb, zub = f32(lb), f32(ub)
+    for i in (0, 70, 138):
+        w = wins[i]
+        pb = O.Problem(yD=w["yD"], N=w["N"], R0=w["R0"], beta_form=O.BETA_RAMP, spd=10)
+        pso = O.PSO(pb, w["particles"], zlb, zub, logdim=[0] * 7, seed=kw["seed"], stream=i, store_f32=True).init()
+        # the best of 10000 is a good fit, where FP32 resolves the loss only to fp32_loss_tol
+        th_best = np.array(pso.pbest[pso.gbest_idx])  # linear box: theta = z
+        tol = fp32_loss_tol(O, pb, th_best)
+        assert rel_err(res[i]["loss_search"], pso.gbest_f) <= tol, (i, tol)
+        s = np.sort(pso.pbest_f)
+        if s[1] - s[0] > 2 * tol * s[0]:
+            assert res[i]["index"] == pso.gbest_idx
+        # the reported loss is the FP64 loss of the reported theta, bit for bit
+        assert res[i]["loss"] == O.loss(pb, res[i]["theta"])

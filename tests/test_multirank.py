@@ -52,7 +52,7 @@ def test_max_over_ranks_gloo():
 def test_window_shards_are_disjoint_streams():
     import bench
 
-    shards = [bench.c3_windows(r)[1] for r in range(4)]
+    shards = [bench.batch_windows("c3", r)[1] for r in range(4)]
     ids = [{w["stream_id"] for w in sh} for sh in shards]
     for a in range(4):
         assert len(ids[a]) == len(shards[a])
