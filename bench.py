@@ -75,11 +75,13 @@ def profiled_traffic(workload: str):
     return p["traffic_bytes"]
 
 
-def algorithmic_flops_per_particle_day(spd: int, ramp: bool = False) -> int:
+def algorithmic_flops_per_particle_day(spd: int, ramp: bool = False, ird: bool = False) -> int:
     """8 flops per Euler step (S = N - C, inf = cb*S*I, C += inf, I += inf - a*I, D += dm*I with
     FMA counted as 2) times steps per day, plus 3 for the day's error and its square-sum; the
-    ramp form of eq. (beta) adds 5 per step (t = k dt, beta on the ramp, cb = beta dt/N)."""
-    return (13 if ramp else 8) * spd + 3
+    ramp form of eq. (beta) adds 5 per step (t = k dt, beta on the ramp, cb = beta dt/N), the
+    F_IRD objective 2 per step (R += dr*I) and the I and R errors each day."""
+    per_step = 8 + (5 if ramp else 0) + (2 if ird else 0)
+    return per_step * spd + (9 if ird else 3)
 
 
 # Bytes of one window's result record copied back by a batched calibration.
@@ -98,7 +100,11 @@ def single_window(name: str):
     return c, ser, y, lb, ub
 
 
-BATCHED = ("c3", "paper")
+BATCHED = ("c3", "paper", "paper_ird")
+
+# The paper's own timing (context only: other hardware, real data, time per PSO iteration of one
+# window with 10000 particles on F_IRD^MXSE): 2.176 s on a TITAN V, 55.655 s on a Xeon E5-2650 v4.
+PAPER_GPU_S_PER_ITERATION = 2.176
 
 
 def batch_windows(name: str, seed_offset: int = 0):
@@ -106,6 +112,8 @@ def batch_windows(name: str, seed_offset: int = 0):
     Philox stream words r*W .. r*W + W - 1."""
     c = dict(configs.CONFIGS[name])
     ser = synth.load_series(c["series"])
+    if c.get("objective") == "ird":
+        ser = synth.reported_IR(ser, c["seed"])
     lay = synth.rolling_windows(W=c["W"], L_min=c["L_min"], L_max=c["L_max"], M_min=c["M_min"], M_max=c["M_max"],
                                 delta=c["delta"], seed=c["seed"])
     wins = synth.rolling_window_problems(ser, lay)
@@ -118,6 +126,8 @@ def batch_windows(name: str, seed_offset: int = 0):
     else:
         lb, ub = configs.bounds(c["K"], c["log"])
         model = dict(K=c["K"], beta_form=0, log_scale=[1] * len(lb) if c["log"] else None)
+    model["objective"] = 1 if c.get("objective") == "ird" else 0
+    model["cost"] = {"mse": 0, "mxse": 1, "mae": 2, "mape": 3}[c.get("cost", "mse")]
     return c, wins, lb, ub, model
 
 
@@ -132,6 +142,9 @@ def describe(name: str) -> str:
         "paper": ("the paper's setting, batched FP32: ramp beta(t) (beta1, beta2, t1, t2, gamma, mu, I0), 139 "
                   "rolling windows of 35 days shifted by 3 days over a 450-day series, 10000 particles per window, "
                   "linear PSO box, 100 iterations, dt=0.1, one persistent launch, FP64 re-evaluation per window"),
+        "paper_ird": ("the paper's setting on its representative objective F_IRD^MXSE, batched FP32: ramp beta(t), "
+                      "139 rolling 35-day windows shifted by 3 days, reported I, R, D, 10000 particles per window, "
+                      "linear PSO box, 100 iterations, dt=0.1, one persistent launch, FP64 re-evaluation per window"),
         "c4": ("gradient FP32: loss + exact gradient (discrete adjoint of the compensated FP32 trajectory, "
                "day-start checkpoints) of the 4096 personal bests of a calibrated swarm, 90 days, 4 beta segments "
                "(7 params), dt=0.05"),
@@ -323,7 +336,7 @@ def run_batched(args, rank, world):
         return None
     pdays = sum(w["particles"] * w["L"] for w in wins)
     units = pdays * c["iters"]
-    flops = pdays * algorithmic_flops_per_particle_day(c["spd"], ramp) * (c["iters"] + 1)
+    flops = pdays * algorithmic_flops_per_particle_day(c["spd"], ramp, model["objective"] == 1) * (c["iters"] + 1)
     kms = statistics.mean(kern_ms)
     achieved = flops / (kms / 1e3) / 1e12
     d2h = len(wins) * BATCH_OUT_BYTES
@@ -350,6 +363,13 @@ def run_batched(args, rank, world):
                    "min_r2_D": float(np.min([r["r2_D"] for r in res])),
                    "window0_loss_fp64": res[0]["loss"]},
     }
+    if name.startswith("paper"):
+        per_it = (total_ms / args.steps / 1e3) / (len(wins) * (c["iters"] + 1))
+        out["result"]["paper_context"] = {
+            "s_per_pso_iteration_per_window": per_it,
+            "paper_gpu_s_per_pso_iteration": PAPER_GPU_S_PER_ITERATION,
+            "note": "the paper's figure is one window's PSO iteration (10000 particles, F_IRD^MXSE, real data) on a "
+                    "TITAN V with the cost on the CPU; ours is the batch's wall time spread over its window-iterations"}
     if not args.no_s2c and name == "c3":
         out["s_to_calibrate"] = s_to_calibrate()
     if not args.no_cpu_baseline:
@@ -558,7 +578,8 @@ def cpu_baseline(name: str, budget_s: float = 15.0, iters_cap: int | None = None
             if time.perf_counter() - t0 >= budget_s or (iters_cap is not None and done >= iters_cap):
                 break
             pb = O.Problem(yD=w["yD"], N=w["N"], R0=w["R0"], K=model["K"], spd=c["spd"],
-                           beta_form=O.BETA_RAMP if model["beta_form"] == 1 else O.BETA_PWC)
+                           beta_form=O.BETA_RAMP if model["beta_form"] == 1 else O.BETA_PWC, cost=model["cost"],
+                           objective=model["objective"], yI=w.get("yI"), yR=w.get("yR"))
             O.PSO(pb, w["particles"], zlb, zub, logdim=logd, seed=w["seed"], stream=w["stream_id"],
                   store_f32=True).init().step(1)
             units += w["particles"] * w["L"] * 2
@@ -623,7 +644,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c3", "c2", "c1", "c4", "c5", "paper"], default="c3")
+    ap.add_argument("--workload", choices=["c3", "c2", "c1", "c4", "c5", "paper", "paper_ird"], default="c3")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-units", type=int, default=2,
                     help="reference arm: windows (batched) or PSO iterations (single window) per step")

@@ -80,7 +80,11 @@ typedef enum sird_objective { SIRD_FIT_D = 0, SIRD_FIT_IRD = 1 } sird_objective;
  *   beta_form      SIRD_BETA_PWC or SIRD_BETA_RAMP
  *   K              number of segments for SIRD_BETA_PWC (1..SIRD_MAX_PARAMS-3)
  *   steps_per_day  Euler steps per day; dt = 1/steps_per_day day
- *   cost, objective  see the enums
+ *   cost, objective  see the enums.  SIRD_FIT_IRD: the cost of each of I, R, D against y_I,
+ *                  y_R, y_D, errors divided by the series' range max - min (1 for a flat
+ *                  series; MAPE unnormalised), the loss the largest of the three.  Every
+ *                  evaluation, PSO, re-evaluation and batched call takes it; the gradient,
+ *                  polish and set_observations calls answer SIRD_ERR_UNSUPPORTED.
  *
  * theta layout (P entries):
  *   PWC : beta_1..beta_K, gamma, mu [, I0]          segment j covers steps

@@ -47,6 +47,11 @@ CONFIGS = {
     # shifted by delta = 3 days over the 450-day series, 10000 particles, 100 iterations.
     "paper": dict(name="paper-ramp-139-windows", series="c3", beta_form="ramp", W=139, iters=100, spd=10,
                   precision=32, log=False, seed=0, L_min=35, L_max=35, M_min=10000, M_max=10000, delta=3),
+    # The same with the paper's representative objective F_IRD^MXSE (Sec. 3.1, the cost its
+    # timings are quoted on): reported I and R series alongside D.
+    "paper_ird": dict(name="paper-ramp-139-windows-F_IRD-MXSE", series="c3", beta_form="ramp", objective="ird",
+                      cost="mxse", W=139, iters=100, spd=10, precision=32, log=False, seed=0, L_min=35, L_max=35,
+                      M_min=10000, M_max=10000, delta=3),
     # 2^20 particles, 10 segments, 120 days at dt = 0.05 day, then a 14-day forecast.
     "c5": dict(name="c5-large-2^20", series="c5", K=10, days=120, spd=20, M=1 << 20, iters=100,
                precision=32, log=True, seed=0, horizon=14, forecast_topk=1024, reeval_topk=32),

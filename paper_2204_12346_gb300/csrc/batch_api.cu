@@ -208,7 +208,8 @@ extern "C" sird_status sird_batch_create(int W, const sird_problem* problems, co
         ModelDev m{};
         sird_fill_window(&problems[i], wins[i].w, m);
         if (i == 0) b->mdl = m;
-        obs_off[i + 1] = obs_off[i] + ((problems[i].n_obs + 3) & ~3);
+        // the window's series stacked D | I | R (F_IRD) with stride obs_stride(n_obs)
+        obs_off[i + 1] = obs_off[i] + (p0.objective == SIRD_FIT_IRD ? 3 : 1) * obs_stride(problems[i].n_obs);
         wins[i].obs_off = obs_off[i];
         wins[i].M = configs[i].particles;
         wins[i].ld = (configs[i].particles + 31) & ~31;
@@ -250,6 +251,16 @@ extern "C" sird_status sird_batch_create(int W, const sird_problem* problems, co
             yf[obs_off[i] + j] = (float)p.y_D[j];
             invy[obs_off[i] + j] = p.y_D[j] != 0.0 ? (float)(1.0 / p.y_D[j]) : 0.f;
             yd[obs_off[i] + j] = p.y_D[j];
+            if (p.objective == SIRD_FIT_IRD) {
+                const int ps = obs_stride(p.n_obs);
+                const double* ir[2] = {p.y_I, p.y_R};
+                for (int k = 0; k < 2; ++k) {
+                    const int o = obs_off[i] + (k + 1) * ps + j;
+                    yf[o] = (float)ir[k][j];
+                    invy[o] = ir[k][j] != 0.0 ? (float)(1.0 / ir[k][j]) : 0.f;
+                    yd[o] = ir[k][j];
+                }
+            }
             mean += p.y_D[j];
         }
         mean /= p.n_obs;
@@ -385,6 +396,7 @@ extern "C" sird_status sird_batch_calibrate(sird_batch_t b, sird_result* results
 extern "C" sird_status sird_batch_set_observations(sird_batch_t b, const double* y_all, long long n_total,
                                                    size_t* h2d_bytes) {
     if (!b || !y_all) return berr(SIRD_ERR_ARG, "batch or y_all is NULL");
+    if (b->mdl.ird) return berr(SIRD_ERR_UNSUPPORTED, "set_observations: F_D batches only");
     long long need = 0;
     for (const auto& pr : b->probs) need += pr.n_obs;
     if (n_total != need) return berr(SIRD_ERR_ARG, "y_all must hold sum(n_obs) = " + std::to_string(need) + " values");

@@ -33,8 +33,9 @@ __global__ void __launch_bounds__(1024) pso_batch_f32(const BatchWindow* __restr
     __shared__ int s_win;
     const int B = blockDim.x, B2 = 2 * B, tid = threadIdx.x, P = m.P;
     float* ys = smem;
-    float* invys = (COST == COST_MAPE) ? ys + pad4(n_max) : ys;
-    float* th_s = smem + pad4(n_max) * (COST == COST_MAPE ? 2 : 1);  // [P][2B]
+    const int obs_region = pad4(n_max) * (m.ird ? 3 : 1);  // the stacked series of the longest window
+    float* invys = (COST == COST_MAPE) ? ys + obs_region : ys;
+    float* th_s = smem + obs_region * (COST == COST_MAPE ? 2 : 1);  // [P][2B]
     float* g_s = th_s + P * B2;
     float* lb_s = g_s + kMaxParams;
     float* ub_s = lb_s + kMaxParams;
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(1024) pso_batch_f32(const BatchWindow* __restr
         if (wi < 0) break;
         const BatchWindow bw = wins[wi];
         const WindowDev& w = bw.w;
-        for (int i = tid; i < w.n_obs; i += B) {
+        for (int i = tid, span = obs_span(w, m); i < span; i += B) {
             ys[i] = yf_all[bw.obs_off + i];
             if (COST == COST_MAPE) invys[i] = invy_all[bw.obs_off + i];
         }
@@ -163,7 +164,8 @@ __global__ void batch_reeval_kernel(const BatchWindow* __restrict__ wins, int W,
 }  // namespace
 
 size_t batch_smem_bytes(const ModelDev& m, int block, int n_max) {
-    return ((size_t)pad4(n_max) * (m.cost == COST_MAPE ? 2 : 1) + (size_t)m.P * 2 * block + 3 * kMaxParams) *
+    return ((size_t)pad4(n_max) * (m.ird ? 3 : 1) * (m.cost == COST_MAPE ? 2 : 1) + (size_t)m.P * 2 * block +
+            3 * kMaxParams) *
            sizeof(float);
 }
 

@@ -196,7 +196,7 @@ __global__ void polish_pick_kernel(WindowDev w, ModelDev m, ObsDev o, PolishStat
     __shared__ double wf[32];
     __shared__ int wi[32];
     const int tid = threadIdx.x, B = blockDim.x, k = s.k;
-    for (int i = tid; i < w.n_obs; i += B) dsm[i] = o.yd[i];
+    for (int i = tid, span = obs_span(w, m); i < span; i += B) dsm[i] = o.yd[i];
     double f = tid < k ? s.best_f[tid] : INFINITY;
     int j = tid < k ? tid : INT_MAX;
     warp_min_pair(f, j);
@@ -311,7 +311,7 @@ cudaError_t launch_polish(const WindowDev& w, const ModelDev& m, const ObsDev& o
     }
     if (e != cudaSuccess) return e;
     const int block = ((k + 31) / 32) * 32;
-    polish_pick_kernel<<<1, block, (size_t)w.n_obs * sizeof(double), st>>>(w, m, o, s, pbf, res);
+    polish_pick_kernel<<<1, block, (size_t)obs_span(w, m) * sizeof(double), st>>>(w, m, o, s, pbf, res);
     return cudaGetLastError();
 }
 

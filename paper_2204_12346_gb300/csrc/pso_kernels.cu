@@ -17,12 +17,14 @@ constexpr int kTopkChunk = 4096;
 
 __host__ __device__ __forceinline__ int pad4(int n) { return (n + 3) & ~3; }
 
-// Copies the observations into shared memory; returns the reciprocal table (or ys).
+// Copies the observations (all stacked series) into shared memory; returns the reciprocal table
+// (or ys).
 template <int COST>
-__device__ __forceinline__ float* stage_obs_f32(float* smem, const WindowDev& w, const ObsDev& o) {
+__device__ __forceinline__ float* stage_obs_f32(float* smem, const WindowDev& w, const ModelDev& m, const ObsDev& o) {
     float* ys = smem;
-    float* invys = (COST == COST_MAPE) ? ys + pad4(w.n_obs) : ys;
-    for (int i = threadIdx.x; i < w.n_obs; i += blockDim.x) {
+    float* invys = (COST == COST_MAPE) ? ys + obs_span_pad(w, m) : ys;
+    const int span = obs_span(w, m);
+    for (int i = threadIdx.x; i < span; i += blockDim.x) {
         ys[i] = o.yf[i];
         if (COST == COST_MAPE) invys[i] = o.invyf[i];
     }
@@ -30,8 +32,8 @@ __device__ __forceinline__ float* stage_obs_f32(float* smem, const WindowDev& w,
 }
 
 template <int COST>
-__device__ __forceinline__ float* after_obs_f32(float* smem, const WindowDev& w) {
-    return smem + pad4(w.n_obs) * (COST == COST_MAPE ? 2 : 1);
+__device__ __forceinline__ float* after_obs_f32(float* smem, const WindowDev& w, const ModelDev& m) {
+    return smem + obs_span_pad(w, m) * (COST == COST_MAPE ? 2 : 1);
 }
 
 // ------------------------------------------------------------------ FP32 eval
@@ -44,8 +46,8 @@ __global__ void __launch_bounds__(1024) eval_f32_kernel(WindowDev w, ModelDev m,
                                                          float* __restrict__ loss) {
     extern __shared__ float smem[];
     float* ys = smem;
-    float* invys = stage_obs_f32<COST>(smem, w, o);
-    float* th_s = after_obs_f32<COST>(smem, w);  // [P][2B]
+    float* invys = stage_obs_f32<COST>(smem, w, m, o);
+    float* th_s = after_obs_f32<COST>(smem, w, m);  // [P][2B]
     const int B = blockDim.x, B2 = 2 * B, tid = threadIdx.x;
     const int p0 = blockIdx.x * B2 + tid, p1 = p0 + B;
     for (int d = 0; d < m.P; ++d) {
@@ -73,8 +75,8 @@ __global__ void __launch_bounds__(1024) pso_f32_kernel(WindowDev w, ModelDev m, 
     __shared__ int last;
     const int B = blockDim.x, B2 = 2 * B, tid = threadIdx.x, P = m.P;
     float* ys = smem;
-    float* invys = stage_obs_f32<COST>(smem, w, o);
-    float* th_s = after_obs_f32<COST>(smem, w);  // [P][2B]
+    float* invys = stage_obs_f32<COST>(smem, w, m, o);
+    float* th_s = after_obs_f32<COST>(smem, w, m);  // [P][2B]
     float* g_s = th_s + P * B2;
     float* lb_s = g_s + kMaxParams;
     float* ub_s = lb_s + kMaxParams;
@@ -179,9 +181,9 @@ __global__ void __launch_bounds__(256) eval_f64_kernel(WindowDev w, ModelDev m, 
                                                         double* __restrict__ loss) {
     extern __shared__ double dsm[];
     double* ys = dsm;
-    double* th_s = dsm + w.n_obs;
+    double* th_s = dsm + obs_span(w, m);
     const int B = blockDim.x, tid = threadIdx.x;
-    for (int i = tid; i < w.n_obs; i += B) ys[i] = o.yd[i];
+    for (int i = tid, span = obs_span(w, m); i < span; i += B) ys[i] = o.yd[i];
     const int p = blockIdx.x * B + tid;
     if (p < M)
         for (int d = 0; d < m.P; ++d) th_s[d * B + tid] = theta[(size_t)d * ld + p];
@@ -198,9 +200,9 @@ __global__ void __launch_bounds__(256) pso_f64_kernel(WindowDev w, ModelDev m, O
     __shared__ int last;
     const int B = blockDim.x, tid = threadIdx.x, P = m.P;
     double* ys = dsm;
-    double* th_s = dsm + w.n_obs;
+    double* th_s = dsm + obs_span(w, m);
     double* g_s = th_s + P * B;
-    for (int i = tid; i < w.n_obs; i += B) ys[i] = o.yd[i];
+    for (int i = tid, span = obs_span(w, m); i < span; i += B) ys[i] = o.yd[i];
     if (tid < P) g_s[tid] = sw.gbest[tid];
     __syncthreads();
 
@@ -344,9 +346,9 @@ __global__ void __launch_bounds__(1024) reeval_kernel(WindowDev w, ModelDev m, O
     __shared__ double wf[32];
     __shared__ int wi[32];
     double* ys = dsm;
-    double* th_s = dsm + w.n_obs;
+    double* th_s = dsm + obs_span(w, m);
     const int B = blockDim.x, tid = threadIdx.x, P = m.P;
-    for (int i = tid; i < w.n_obs; i += B) ys[i] = o.yd[i];
+    for (int i = tid, span = obs_span(w, m); i < span; i += B) ys[i] = o.yd[i];
     int idx = INT_MAX;
     if (tid < k) {
         idx = keys ? (int)(keys[tid] & 0xFFFFFFFFu) : *gbest_idx;
@@ -421,13 +423,13 @@ unsigned grid_for_pairs(int M, int block) { return grid_for(M, 2 * block); }
 }  // namespace
 
 size_t smem_bytes_f32(const WindowDev& w, const ModelDev& m, int block, bool with_theta) {
-    size_t n = (size_t)pad4(w.n_obs) * (m.cost == COST_MAPE ? 2 : 1);
+    size_t n = (size_t)obs_span_pad(w, m) * (m.cost == COST_MAPE ? 2 : 1);
     if (with_theta) n += (size_t)m.P * 2 * block + 3 * kMaxParams;  // theta of two particles per thread
     return n * sizeof(float);
 }
 
 static size_t smem_bytes_f64(const WindowDev& w, const ModelDev& m, int block, bool with_g) {
-    return ((size_t)w.n_obs + (size_t)m.P * block + (with_g ? kMaxParams : 0)) * sizeof(double);
+    return ((size_t)obs_span(w, m) + (size_t)m.P * block + (with_g ? kMaxParams : 0)) * sizeof(double);
 }
 
 #define SIRD_DISPATCH_COST(COSTV, ...)                          \

@@ -49,8 +49,8 @@ __global__ void __launch_bounds__(1024) pso_f32_persistent(WindowDev w, ModelDev
     const int B = blockDim.x, tid = threadIdx.x, P = m.P, G = gridDim.x;
     const int npairs = (P + 1) >> 1;
     float* ys = smem;
-    float* invys = (COST == COST_MAPE) ? ys + pad4(w.n_obs) : ys;
-    float* th_s = smem + pad4(w.n_obs) * (COST == COST_MAPE ? 2 : 1);
+    float* invys = (COST == COST_MAPE) ? ys + obs_span_pad(w, m) : ys;
+    float* th_s = smem + obs_span_pad(w, m) * (COST == COST_MAPE ? 2 : 1);
     float* xs = th_s + P * B;
     float* vs = xs + P * B;
     float* pbs = vs + P * B;
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(1024) pso_f32_persistent(WindowDev w, ModelDev
     float* slot_pos = ub_s + kMaxParams;                          // [G][P] positions read from the slots
     uint4* rnd = (uint4*)(slot_pos + pad4(G * P));                 // [npairs][B] Philox words
 
-    for (int i = tid; i < w.n_obs; i += B) {
+    for (int i = tid, span = obs_span(w, m); i < span; i += B) {
         ys[i] = o.yf[i];
         if (COST == COST_MAPE) invys[i] = o.invyf[i];
     }
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(1024) pso_f32_persistent(WindowDev w, ModelDev
 }  // namespace
 
 size_t smem_bytes_persistent(const WindowDev& w, const ModelDev& m, int block, int grid) {
-    const size_t floats = (size_t)pad4(w.n_obs) * (m.cost == COST_MAPE ? 2 : 1) + 4 * (size_t)m.P * block + block +
+    const size_t floats = (size_t)obs_span_pad(w, m) * (m.cost == COST_MAPE ? 2 : 1) + 4 * (size_t)m.P * block + block +
                           3 * kMaxParams + pad4(grid * m.P);
     return floats * sizeof(float) + (size_t)((m.P + 1) / 2) * block * sizeof(uint4);
 }

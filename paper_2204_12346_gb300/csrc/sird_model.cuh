@@ -44,11 +44,30 @@ struct WindowDev {
     float I0f;
     float cbn_h, cbn_l; // dt/N = cbn_h + cbn_l
     float dt_h, dt_l;   // dt = dt_h + dt_l
+    // F_IRD (Sec. 3.1): the reported I and R series' ranges max - min (1 for a flat series) used by
+    // the min-max normalisation, their reciprocals, their counts of nonzero values, R0 split
+    double rng_I, rng_R, rng_D;
+    float inv_rng_I, inv_rng_R, inv_rng_D;
+    int n_kept_I, n_kept_R;
+    float R0h, R0l;
 };
 
 struct ModelDev {
     int P, K, spd, beta_form, fit_I0, cost;
+    int ird;  // objective F_IRD (else F_D)
 };
+
+// Observation layout: the series are stacked D | I | R (I and R only for F_IRD), each padded to
+// obs_stride(n_obs) entries, in every float and double copy.
+__host__ __device__ __forceinline__ int obs_stride(int n_obs) { return (n_obs + 3) & ~3; }
+// Entries of one staged copy of the observations: n (F_D) or the three stacked series (F_IRD);
+// obs_span_pad rounds the F_D case up to obs_stride.
+__host__ __device__ __forceinline__ int obs_span(const WindowDev& w, const ModelDev& m) {
+    return m.ird ? 3 * obs_stride(w.n_obs) : w.n_obs;
+}
+__host__ __device__ __forceinline__ int obs_span_pad(const WindowDev& w, const ModelDev& m) {
+    return (m.ird ? 3 : 1) * obs_stride(w.n_obs);
+}
 
 // First step of PWC segment j: ceil(j*steps/K).
 __device__ __forceinline__ int segment_start(int j, int steps, int K) {
@@ -113,11 +132,92 @@ struct DayStateF32 {
     }
 };
 
+// F_IRD^C (Sec. 3.1): the cost of each of I, R, D against its reported series, errors divided by
+// the series' range (min-max normalisation; MAPE unnormalised), and the largest of the three.
+// R is carried as a compensated (hi, lo) pair with its day increments summed apart, like C.
+// Both beta forms, any steps per day; cb is formed per step as in fitness_f32.
+template <int COST>
+__device__ float fitness_f32_ird(const WindowDev& w, const ModelDev& m, const float* __restrict__ ys,
+                                 const float* __restrict__ invys, const float* th, int stride) {
+    const int spd = m.spd, n = w.n_obs, L = n - 1, steps = L * spd, ps = obs_stride(n);
+    const float *yI = ys + ps, *yR = ys + 2 * ps, *iyI = invys + ps, *iyR = invys + 2 * ps;
+    const bool ramp = m.beta_form == BETA_RAMP;
+    const int gi = ramp ? 4 : m.K, K = ramp ? 1 : m.K;
+    const float gam = th[gi * stride], mu = th[(gi + 1) * stride];
+    float I = m.fit_I0 ? th[(gi + 2) * stride] : w.I0f;
+    float Il = 0.f;
+    const float gm = __fadd_rn(gam, mu);
+    const float a = __fmaf_rn(gm, w.dt_h, __fmul_rn(gm, w.dt_l));
+    const float dm = __fmaf_rn(mu, w.dt_h, __fmul_rn(mu, w.dt_l));
+    const float dr = __fmaf_rn(gam, w.dt_h, __fmul_rn(gam, w.dt_l));
+    float rb1 = 0.f, rb2 = 0.f, rt1 = 0.f, rt2 = 0.f, slope = 0.f;
+    if (ramp) {
+        rb1 = th[0];
+        rb2 = th[stride];
+        const float ta = th[2 * stride], tb = th[3 * stride];
+        rt1 = fminf(ta, tb);
+        rt2 = fmaxf(ta, tb);
+        slope = (rt2 > rt1) ? __fdiv_rn(__fsub_rn(rb2, rb1), __fsub_rn(rt2, rt1)) : 0.f;
+    }
+    const float dtf = __fadd_rn(w.dt_h, w.dt_l);
+    DayStateF32 ds;
+    ds.init(w, I, ys[0]);
+    float Rh = w.R0h, Rl = w.R0l;
+    LossF32<COST> lI, lR, lD;
+    auto observe = [&](int day, float eD) {
+        const float eI = __fsub_rn(yI[day], I);
+        const float eR = __fsub_rn(__fsub_rn(yR[day], Rh), Rl);
+        if (COST == COST_MAPE) {
+            lI.add(eI, iyI[day]);
+            lR.add(eR, iyR[day]);
+            lD.add(eD, invys[day]);
+        } else {
+            lI.add(__fmul_rn(eI, w.inv_rng_I), 0.f);
+            lR.add(__fmul_rn(eR, w.inv_rng_R), 0.f);
+            lD.add(__fmul_rn(eD, w.inv_rng_D), 0.f);
+        }
+    };
+    observe(0, 0.f);  // e_D(0) = 0: D0 is the first observation
+    int seg = 0, next_b = (!ramp && K > 1) ? segment_start(1, steps, K) : INT_MAX;
+    float cb = ramp ? 0.f : __fmaf_rn(th[0], w.cbn_h, __fmul_rn(th[0], w.cbn_l));
+    int k = 0;
+    for (int day = 1; day <= L; ++day) {
+        float cday = 0.f, dday = 0.f, rday = 0.f;
+        for (int s = 0; s < spd; ++s, ++k) {
+            if (ramp) {
+                const float t = __fmul_rn((float)k, dtf);
+                const float beta = (t < rt1) ? rb1 : ((t < rt2) ? __fmaf_rn(slope, __fsub_rn(t, rt1), rb1) : rb2);
+                cb = __fmaf_rn(beta, w.cbn_h, __fmul_rn(beta, w.cbn_l));
+            } else {
+                while (k == next_b) {
+                    ++seg;
+                    cb = __fmaf_rn(th[seg * stride], w.cbn_h, __fmul_rn(th[seg * stride], w.cbn_l));
+                    next_b = (seg + 1 < K) ? segment_start(seg + 1, steps, K) : INT_MAX;
+                }
+            }
+            rday = __fmaf_rn(dr, I, rday);  // R' = gamma I, from the state at the start of the step
+            euler_f32(cb, a, dm, ds.Sday, cday, dday, I, Il);
+        }
+        const float eD = ds.close_day(w, cday, dday, ys[day], I, Il);
+        float sr, er;
+        two_sum(Rh, rday, sr, er);
+        Rh = sr;
+        Rl = __fadd_rn(Rl, er);
+        observe(day, eD);
+    }
+    const float cI = lI.result(n, w.n_kept_I), cR = lR.result(n, w.n_kept_R), cD = lD.result(n, w.n_kept);
+    float c = cI;
+    if (cR > c) c = cR;
+    if (cD > c) c = cD;
+    return c;
+}
+
 // Loss of one parameter vector, theta_d at th[d*stride].  ys / invys: observations and their
 // reciprocals (0 where y == 0) in shared memory.  SPD > 0 fixes steps per day at compile time.
 template <int SPD, int COST>
 __device__ float fitness_f32(const WindowDev& w, const ModelDev& m, const float* __restrict__ ys,
                              const float* __restrict__ invys, const float* th, int stride) {
+    if (m.ird) return fitness_f32_ird<COST>(w, m, ys, invys, th, stride);
     const int spd = SPD > 0 ? SPD : m.spd;
     const int L = w.n_obs - 1;
     const int steps = L * spd;
@@ -289,6 +389,11 @@ template <int SPD, int COST>
 __device__ void fitness_f32x2(const WindowDev& w, const ModelDev& m, const float* __restrict__ ys,
                               const float* __restrict__ invys, const float* tha, const float* thb, int stride,
                               float& fa, float& fb) {
+    if (m.ird) {
+        fa = fitness_f32_ird<COST>(w, m, ys, invys, tha, stride);
+        fb = fitness_f32_ird<COST>(w, m, ys, invys, thb, stride);
+        return;
+    }
     const int spd = SPD > 0 ? SPD : m.spd;
     if (m.beta_form == BETA_RAMP) {
         // the ramp changes beta every step: each lane's cb is formed as in fitness_f32, the
@@ -397,11 +502,107 @@ struct LossF64 {
     }
 };
 
+// One series' cost in FP64 (Sec. 3.1) with errors e = (y - yhat) / scale, accumulated in day
+// order: MSE and MAE over n, MXSE the largest e^2, MAPE 100 |y - yhat| / |y| over the nonzero y.
+template <int COST>
+struct SeriesCostF64 {
+    double acc = 0.0;
+    int kept = 0;
+    __device__ __forceinline__ void add(double y, double yhat, double scale) {
+        const double e = __ddiv_rn(__dsub_rn(y, yhat), scale);
+        if (COST == COST_MSE) acc = __dadd_rn(acc, __dmul_rn(e, e));
+        else if (COST == COST_MXSE) { if (__dmul_rn(e, e) > acc) acc = __dmul_rn(e, e); }
+        else if (COST == COST_MAE) acc = __dadd_rn(acc, fabs(e));
+        else if (y != 0.0) {
+            acc = __dadd_rn(acc, fabs(__ddiv_rn(__dsub_rn(y, yhat), y)));
+            ++kept;
+        }
+    }
+    __device__ __forceinline__ double result(int n) const {
+        if (COST == COST_MSE || COST == COST_MAE) return __ddiv_rn(acc, (double)n);
+        if (COST == COST_MAPE) return kept > 0 ? __ddiv_rn(__dmul_rn(100.0, acc), (double)kept) : 0.0;
+        return acc;
+    }
+};
+
+// F_IRD^C in FP64, the paper's operation order (R' = gamma I added after D'), no contraction.
+template <int COST>
+__device__ double fitness_f64_ird(const WindowDev& w, const ModelDev& m, const double* __restrict__ ys,
+                                  const double* th, int stride, double* sse_out) {
+    const int spd = m.spd, n = w.n_obs, L = n - 1, steps = L * spd, ps = obs_stride(n);
+    const double *yI = ys + ps, *yR = ys + 2 * ps;
+    const bool ramp = (m.beta_form == BETA_RAMP);
+    const int gi = ramp ? 4 : m.K, K = ramp ? 1 : m.K;
+    const double gam = th[gi * stride], mu = th[(gi + 1) * stride];
+    const double I0 = m.fit_I0 ? th[(gi + 2) * stride] : w.I0;
+    const double gm = __dadd_rn(gam, mu);
+    const double dt = w.dt;
+    double S = __dsub_rn(__dsub_rn(__dsub_rn(w.N, I0), w.R0), w.D0);
+    double I = I0, R = w.R0, D = w.D0;
+    const bool mape = COST == COST_MAPE;
+    const double sI = mape ? 1.0 : w.rng_I, sR = mape ? 1.0 : w.rng_R, sD = mape ? 1.0 : w.rng_D;
+    SeriesCostF64<COST> cI, cR, cD;
+    double sse = 0.0;
+    auto observe = [&](int day) {
+        cI.add(yI[day], I, sI);
+        cR.add(yR[day], R, sR);
+        cD.add(ys[day], D, sD);
+        const double e = __dsub_rn(ys[day], D);
+        sse = __dadd_rn(sse, __dmul_rn(e, e));
+    };
+    observe(0);
+    double rb1 = 0, rb2 = 0, rt1 = 0, rt2 = 0;
+    if (ramp) {
+        rb1 = th[0];
+        rb2 = th[stride];
+        const double ta = th[2 * stride], tb = th[3 * stride];
+        rt1 = ta < tb ? ta : tb;
+        rt2 = ta < tb ? tb : ta;
+    }
+    int seg = 0, prev_seg = -1;
+    double bN = 0.0;
+    int next_b = (!ramp && K > 1) ? segment_start(1, steps, K) : INT_MAX;
+    for (int k = 0; k < steps; ++k) {
+        if (ramp) {
+            const double t = __ddiv_rn((double)k, (double)spd);
+            double beta;
+            if (t < rt1) beta = rb1;
+            else if (t < rt2) beta = __dadd_rn(rb1, __dmul_rn(__ddiv_rn(__dsub_rn(rb2, rb1), __dsub_rn(rt2, rt1)),
+                                                              __dsub_rn(t, rt1)));
+            else beta = rb2;
+            bN = __ddiv_rn(beta, w.N);
+        } else {
+            while (k == next_b) {
+                ++seg;
+                next_b = (seg + 1 < K) ? segment_start(seg + 1, steps, K) : INT_MAX;
+            }
+            if (k == 0 || seg != prev_seg) bN = __ddiv_rn(th[seg * stride], w.N);
+            prev_seg = seg;
+        }
+        const double fS = __dmul_rn(__dmul_rn(-bN, S), I);
+        const double fI = __dsub_rn(__dmul_rn(__dmul_rn(bN, I), S), __dmul_rn(gm, I));
+        const double fR = __dmul_rn(gam, I);
+        const double fD = __dmul_rn(mu, I);
+        S = __dadd_rn(S, __dmul_rn(dt, fS));
+        I = __dadd_rn(I, __dmul_rn(dt, fI));
+        R = __dadd_rn(R, __dmul_rn(dt, fR));
+        D = __dadd_rn(D, __dmul_rn(dt, fD));
+        if ((k + 1) % spd == 0) observe((k + 1) / spd);
+    }
+    if (sse_out) *sse_out = sse;
+    const double a = cI.result(n), b = cR.result(n), c = cD.result(n);
+    double r = a;
+    if (b > r) r = b;
+    if (c > r) r = c;
+    return r;
+}
+
 // Loss of one parameter vector in FP64 (theta_d at th[d*stride]); *sse_out gets sum e_i^2.
 // Observation i is compared after i*spd steps; the sum runs over days in order.
 template <int COST>
 __device__ double fitness_f64(const WindowDev& w, const ModelDev& m, const double* __restrict__ ys,
                               const double* th, int stride, double* sse_out) {
+    if (m.ird) return fitness_f64_ird<COST>(w, m, ys, th, stride, sse_out);
     const int spd = m.spd;
     const int L = w.n_obs - 1;
     const int steps = L * spd;

@@ -160,8 +160,13 @@ sird_status sird_check_problem(const sird_problem* pb, std::string& why) {
         return why = "K out of range [1, SIRD_MAX_PARAMS-3]", SIRD_ERR_ARG;
     if (pb->cost < SIRD_COST_MSE || pb->cost > SIRD_COST_MAPE) return why = "unknown cost", SIRD_ERR_ARG;
     if (pb->fit_I0 != 0 && pb->fit_I0 != 1) return why = "fit_I0 must be 0 or 1", SIRD_ERR_ARG;
-    if (pb->objective == SIRD_FIT_IRD) return why = "F_IRD objective is not implemented on the GPU yet", SIRD_ERR_UNSUPPORTED;
-    if (pb->objective != SIRD_FIT_D) return why = "unknown objective", SIRD_ERR_ARG;
+    if (pb->objective != SIRD_FIT_D && pb->objective != SIRD_FIT_IRD) return why = "unknown objective", SIRD_ERR_ARG;
+    if (pb->objective == SIRD_FIT_IRD) {
+        if (!pb->y_I || !pb->y_R) return why = "F_IRD needs y_I and y_R", SIRD_ERR_ARG;
+        for (int i = 0; i < pb->n_obs; ++i)
+            if (!std::isfinite(pb->y_I[i]) || !std::isfinite(pb->y_R[i]))
+                return why = "non-finite observation in y_I / y_R", SIRD_ERR_ARG;
+    }
     return SIRD_OK;
 }
 
@@ -188,6 +193,32 @@ void sird_fill_window(const sird_problem* pb, WindowDev& w, ModelDev& m) {
     s = split(w.dt);
     w.dt_h = s.h;
     w.dt_l = s.l;
+    s = split(pb->R0);
+    w.R0h = s.h;
+    w.R0l = s.l;
+    // F_IRD: ranges of the reported series for the min-max normalisation (a flat series: 1)
+    auto range = [n](const double* y) {
+        double lo = y[0], hi = y[0];
+        for (int i = 1; i < n; ++i) {
+            lo = y[i] < lo ? y[i] : lo;
+            hi = y[i] > hi ? y[i] : hi;
+        }
+        return hi > lo ? hi - lo : 1.0;
+    };
+    const bool ird = pb->objective == SIRD_FIT_IRD;
+    w.rng_D = ird ? range(pb->y_D) : 1.0;
+    w.rng_I = ird ? range(pb->y_I) : 1.0;
+    w.rng_R = ird ? range(pb->y_R) : 1.0;
+    w.inv_rng_D = (float)(1.0 / w.rng_D);
+    w.inv_rng_I = (float)(1.0 / w.rng_I);
+    w.inv_rng_R = (float)(1.0 / w.rng_R);
+    w.n_kept_I = w.n_kept_R = 0;
+    if (ird)
+        for (int i = 0; i < n; ++i) {
+            w.n_kept_I += (pb->y_I[i] != 0.0);
+            w.n_kept_R += (pb->y_R[i] != 0.0);
+        }
+    m.ird = ird ? 1 : 0;
     m.P = nparams_of(pb);
     m.K = pb->beta_form == SIRD_BETA_PWC ? pb->K : 1;
     m.spd = pb->steps_per_day;
@@ -196,22 +227,27 @@ void sird_fill_window(const sird_problem* pb, WindowDev& w, ModelDev& m) {
     m.cost = pb->cost;
 }
 
-// Observations to the device: float copy, float reciprocals (0 where y == 0), double copy.
+// Observations to the device: float copy, float reciprocals (0 where y == 0), double copy, each
+// holding the series stacked D | I | R (I, R for F_IRD only) with stride obs_stride(n).
 static cudaError_t upload_obs(const sird_problem* pb, void** mem, ObsDev& o, cudaStream_t s) {
     const int n = pb->n_obs;
-    const size_t nf = (size_t)((n + 3) & ~3);
-    const size_t bytes = nf * 2 * sizeof(float) + (size_t)n * sizeof(double);
+    const int nser = pb->objective == SIRD_FIT_IRD ? 3 : 1;
+    const size_t ps = (size_t)obs_stride(n), nf = ps * nser;
+    const size_t bytes = nf * 2 * sizeof(float) + nf * sizeof(double);
     cudaError_t e = cudaMalloc(mem, bytes);
     if (e != cudaSuccess) return e;
     std::vector<unsigned char> host(bytes, 0);
     float* yf = (float*)host.data();
     float* inv = yf + nf;
     double* yd = (double*)(inv + nf);
-    for (int i = 0; i < n; ++i) {
-        yf[i] = (float)pb->y_D[i];
-        inv[i] = pb->y_D[i] != 0.0 ? (float)(1.0 / pb->y_D[i]) : 0.f;
-        yd[i] = pb->y_D[i];
-    }
+    const double* series[3] = {pb->y_D, pb->y_I, pb->y_R};
+    for (int k = 0; k < nser; ++k)
+        for (int i = 0; i < n; ++i) {
+            const double y = series[k][i];
+            yf[k * ps + i] = (float)y;
+            inv[k * ps + i] = y != 0.0 ? (float)(1.0 / y) : 0.f;
+            yd[k * ps + i] = y;
+        }
     e = cudaMemcpyAsync(*mem, host.data(), bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     o.yf = (const float*)*mem;
@@ -465,6 +501,7 @@ extern "C" sird_status sird_pso_set_observations(sird_pso_t h, const double* y_D
     if (!h) return SIRD_ERR_ARG;
     if (h->sticky) return h->sticky;
     if (!y_D || n_obs != h->n_obs) return h->fail(SIRD_ERR_ARG, "set_observations: y_D NULL or n_obs differs");
+    if (h->mdl.ird) return h->fail(SIRD_ERR_UNSUPPORTED, "set_observations: F_D handles only");
     for (int i = 0; i < n_obs; ++i)
         if (!std::isfinite(y_D[i])) return h->fail(SIRD_ERR_ARG, "set_observations: non-finite observation");
     if (y_D[0] != h->win.D0) return h->fail(SIRD_ERR_ARG, "set_observations: y_D[0] (D0) must not change");
@@ -632,6 +669,7 @@ extern "C" sird_status sird_loss_grad(sird_pso_t h, const void* d_theta, int M, 
         return h->fail(SIRD_ERR_ARG, "loss_grad: bad M/ld/pointers");
     if (ckpt_every < 1 || ckpt_every > 64) return h->fail(SIRD_ERR_ARG, "loss_grad: ckpt_every out of range [1, 64]");
     if (precision != 32 && precision != 64) return h->fail(SIRD_ERR_ARG, "loss_grad: precision must be 32 or 64");
+    if (h->mdl.ird) return h->fail(SIRD_ERR_UNSUPPORTED, "loss_grad: the adjoint covers F_D only");
     if (precision == 32 && h->mdl.spd != 10 && h->mdl.spd != 20 && h->mdl.spd > 64)
         return h->fail(SIRD_ERR_UNSUPPORTED, "loss_grad: FP32 needs steps_per_day <= 64");
     if (M == 0) return SIRD_OK;
@@ -662,6 +700,7 @@ extern "C" sird_status sird_pso_polish(sird_pso_t h, int k, int iters, double fi
     if (!h || !out) return SIRD_ERR_ARG;
     if (h->sticky) return h->sticky;
     if (h->precision != 32) return h->fail(SIRD_ERR_UNSUPPORTED, "polish: FP32 swarms only");
+    if (h->mdl.ird) return h->fail(SIRD_ERR_UNSUPPORTED, "polish: the adjoint covers F_D only");
     if (k < 1 || k > 1024 || k > h->M || iters < 0 || !(first_step > 0) || ckpt_every < 1 || ckpt_every > 64 ||
         (precision != 32 && precision != 64))
         return h->fail(SIRD_ERR_ARG, "polish: bad k/iters/first_step/ckpt_every/precision");

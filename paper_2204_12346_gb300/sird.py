@@ -175,9 +175,10 @@ class Calibrator:
 
     def __init__(self, yD, N, *, K=1, spd=10, R0=0.0, I0=0.0, fit_I0=True, beta_form=BETA_PWC, cost=COST_MSE,
                  particles=64, iters=100, lb=None, ub=None, log_scale=None, w=0.5, c1=0.5, c2=0.5, precision=32,
-                 seed=0, stream_id=0, reeval_topk=0, block_size=0, launch_mode=0, stream=None):
+                 seed=0, stream_id=0, reeval_topk=0, block_size=0, launch_mode=0, stream=None, objective=FIT_D,
+                 yI=None, yR=None):
         self._lib = lib()
-        self.problem, k1 = make_problem(yD, N, K, spd, R0, I0, fit_I0, beta_form, cost)
+        self.problem, k1 = make_problem(yD, N, K, spd, R0, I0, fit_I0, beta_form, cost, objective, yI, yR)
         self.config, k2 = make_config(particles, iters, lb, ub, log_scale, w, c1, c2, precision, seed, stream_id,
                                       reeval_topk, block_size, launch_mode)
         self._keep = k1 + k2
@@ -357,14 +358,14 @@ except ImportError:  # the binding still loads for CPU-only tooling
 
 
 def _batch_structs(windows, K, spd, cost, beta_form, fit_I0, iters, lb, ub, log_scale, w, c1, c2, particles, seed,
-                   block_size):
+                   block_size, objective=FIT_D):
     W = len(windows)
     keep = []
     pbs = (Problem * W)()
     cfgs = (Config * W)()
     for i, win in enumerate(windows):
         pb, k1 = make_problem(win["yD"], win["N"], K, spd, win.get("R0", 0.0), win.get("I0", 0.0), fit_I0,
-                              beta_form, cost)
+                              beta_form, cost, objective, win.get("yI"), win.get("yR"))
         cfg, k2 = make_config(int(win.get("particles", particles)), iters, lb, ub, log_scale, w, c1, c2, 32,
                               int(win.get("seed", seed)), int(win.get("stream_id", i)), 0,
                               block_size if i == 0 else 0, 0)
@@ -384,11 +385,11 @@ class Batch:
 
     def __init__(self, windows, *, K=1, spd=10, cost=COST_MSE, beta_form=BETA_PWC, fit_I0=True, iters=100,
                  lb=None, ub=None, log_scale=None, w=0.5, c1=0.5, c2=0.5, particles=256, seed=0, block_size=0,
-                 stream=None):
+                 stream=None, objective=FIT_D):
         self._lib = lib()
         W = len(windows)
         pbs, cfgs, self._keep = _batch_structs(windows, K, spd, cost, beta_form, fit_I0, iters, lb, ub, log_scale,
-                                               w, c1, c2, particles, seed, block_size)
+                                               w, c1, c2, particles, seed, block_size, objective)
         h = C.c_void_p()
         st = self._lib.sird_batch_create(W, pbs, cfgs, C.c_void_p(current_stream_handle(stream)), C.byref(h))
         if st != OK:
@@ -437,12 +438,12 @@ class Batch:
 
 def calibrate_batched(windows, *, K=1, spd=10, cost=COST_MSE, beta_form=BETA_PWC, fit_I0=True, iters=100, lb=None,
                       ub=None, log_scale=None, w=0.5, c1=0.5, c2=0.5, particles=256, seed=0, block_size=0,
-                      stream=None):
+                      stream=None, objective=FIT_D):
     """One-shot batched calibration (sird_pso_calibrate_batched): host inputs in, results out."""
     L = lib()
     W = len(windows)
     pbs, cfgs, keep = _batch_structs(windows, K, spd, cost, beta_form, fit_I0, iters, lb, ub, log_scale, w, c1, c2,
-                                     particles, seed, block_size)
+                                     particles, seed, block_size, objective)
     res = (Result * W)()
     st = L.sird_pso_calibrate_batched(W, pbs, cfgs, C.c_void_p(current_stream_handle(stream)), res)
     if st != OK:

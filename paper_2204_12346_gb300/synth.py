@@ -37,7 +37,18 @@ def box_sample(lb, ub, log_mask, M: int, rng: np.random.Generator) -> np.ndarray
     zl = np.where(log_mask, np.log(np.where(log_mask, lb, 1.0)), lb)
     zu = np.where(log_mask, np.log(np.where(log_mask, ub, 1.0)), ub)
     z = zl + (zu - zl) * rng.random((M, lb.size))
-    return np.where(log_mask, np.exp(z), z)
+    return np.where(log_mask, np.exp(np.where(log_mask, z, 0.0)), z)
+
+
+def reported_IR(series: dict, seed: int = 0) -> dict:
+    """Reported infectious and recovered series for the F_IRD objective: I as Poisson counts
+    around the series' I, R as R[0] plus cumulative Poisson daily increments (as for D).
+    Returns a copy of the series with keys yI and yR added."""
+    rng = np.random.default_rng(seed)
+    out = dict(series)
+    out["yI"] = rng.poisson(np.clip(np.asarray(series["I_true"], dtype=np.float64), 0.0, None)).astype(np.float64)
+    out["yR"] = poisson_cumulative(np.asarray(series["R_true"], dtype=np.float64), rng)
+    return out
 
 
 def rolling_windows(W: int = 512, series_days: int = 450, L_min: int = 21, L_max: int = 90,
@@ -67,13 +78,19 @@ def load_series(name: str) -> dict:
 def rolling_window_problems(series: dict, layout: dict) -> list:
     """Cuts windows out of a long stored series: window w covers days T_w .. T_w + L_w; its
     observed deaths are the noisy cumulative counts on those days (the Euler scheme starts from
-    the first one), R0 is the series' recovered count on day T_w rounded, and its swarm size is
-    layout["M"][w]."""
+    the first one), R0 is the series' recovered count on day T_w rounded (the reported one when
+    the series carries reported I and R, which the window then carries too), and its swarm size
+    is layout["M"][w]."""
     y = series["yD"]
     R = series["R_true"]
     out = []
     for w, (L, M, T) in enumerate(zip(layout["L"], layout["M"], layout["T"])):
-        out.append({"yD": y[T:T + L + 1].copy(), "N": float(series["N"]), "R0": float(np.round(R[T])),
-                    "particles": int(M), "T": int(T), "L": int(L)})
+        win = {"yD": y[T:T + L + 1].copy(), "N": float(series["N"]), "R0": float(np.round(R[T])),
+               "particles": int(M), "T": int(T), "L": int(L)}
+        if "yI" in series:  # reported I and R (F_IRD); R0 is then the reported R on day T
+            win["yI"] = series["yI"][T:T + L + 1].copy()
+            win["yR"] = series["yR"][T:T + L + 1].copy()
+            win["R0"] = float(win["yR"][0])
+        out.append(win)
     return out
 

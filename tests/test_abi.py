@@ -54,7 +54,8 @@ def _create(L, **over):
     (dict(K=0), 1),
     (dict(K=40, lb=[0] * 43, ub=[1] * 43), 1),
     (dict(cost=9), 1),
-    (dict(objective=1), 7),
+    (dict(objective=1), 1),  # F_IRD without the I and R series
+    (dict(objective=5), 1),
     (dict(particles=0), 1),
     (dict(precision=16), 1),
     (dict(block_size=48), 1),

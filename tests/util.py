@@ -41,18 +41,31 @@ def fp32_loss_tol(O, pb, theta, cost="mse", base=1e-5, rho=RHO_F32):
     large counts) it is what FP32 can resolve.  O is the oracle module."""
     y = np.asarray(pb.yD, dtype=np.float64)
     n = y.size
-    D = O.simulate(pb, theta)["D"][:n]
-    e = y - D
-    dD = rho * np.abs(D)
-    if cost == "mse":
-        L, dL = np.mean(e * e), (2.0 / n) * np.sum(np.abs(e) * dD)
-    elif cost == "mxse":
-        i = int(np.argmax(e * e))
-        L, dL = e[i] ** 2, 2.0 * abs(e[i]) * dD[i]
-    elif cost == "mae":
-        L, dL = np.mean(np.abs(e)), np.sum(dD) / n
+    traj = O.simulate(pb, theta)
+
+    def cost_and_bound(yx, xhat, scale):
+        e = (yx - xhat) / scale
+        dx = rho * np.abs(xhat) / scale
+        if cost == "mse":
+            return np.mean(e * e), (2.0 / n) * np.sum(np.abs(e) * dx)
+        if cost == "mxse":
+            i = int(np.argmax(e * e))
+            return e[i] ** 2, 2.0 * abs(e[i]) * dx[i]
+        if cost == "mae":
+            return np.mean(np.abs(e)), np.sum(dx) / n
+        keep = yx != 0
+        return (100.0 * np.mean(np.abs((yx[keep] - xhat[keep]) / yx[keep])),
+                100.0 * np.sum(rho * np.abs(xhat[keep]) / np.abs(yx[keep])) / max(int(keep.sum()), 1))
+
+    if getattr(pb, "objective", 0) == 1:  # F_IRD: the largest of the three normalised costs
+        parts = []
+        for key, yx in (("I", pb.yI), ("R", pb.yR), ("D", pb.yD)):
+            yx = np.asarray(yx, dtype=np.float64)
+            rng = yx.max() - yx.min()
+            scale = 1.0 if cost == "mape" or not rng > 0 else rng
+            parts.append(cost_and_bound(yx, traj[key][:n], scale))
+        L = max(c for c, _ in parts)
+        dL = max(b for _, b in parts)
     else:
-        keep = y != 0
-        L = 100.0 * np.mean(np.abs(e[keep] / y[keep]))
-        dL = 100.0 * np.sum(dD[keep] / np.abs(y[keep])) / max(int(keep.sum()), 1)
+        L, dL = cost_and_bound(y, traj["D"][:n], 1.0)
     return base + dL / max(L, 1e-300)
