@@ -323,7 +323,8 @@ def run_batched(args, rank, world):
     # end to end through the public API with host buffers: every step uploads all windows'
     # observations (and the windows' settings that depend on them) from host memory, calibrates
     # and copies every window's result back (the daily re-calibration of a serving loop)
-    y_host = np.concatenate([np.asarray(w["yD"], dtype=np.float64) for w in wins])
+    y_host = np.concatenate([np.concatenate([w["yD"], w["yI"], w["yR"]]) if model["objective"] == 1
+                             else np.asarray(w["yD"], dtype=np.float64) for w in wins])
     e2e, h2d = [], 0
     for _ in range(args.steps):
         torch.cuda.synchronize()

@@ -84,7 +84,7 @@ typedef enum sird_objective { SIRD_FIT_D = 0, SIRD_FIT_IRD = 1 } sird_objective;
  *                  y_R, y_D, errors divided by the series' range max - min (1 for a flat
  *                  series; MAPE unnormalised), the loss the largest of the three.  Every
  *                  evaluation, PSO, re-evaluation and batched call takes it; the gradient,
- *                  polish and set_observations calls answer SIRD_ERR_UNSUPPORTED.
+ *                  polish and sird_pso_set_observations calls answer SIRD_ERR_UNSUPPORTED.
  *
  * theta layout (P entries):
  *   PWC : beta_1..beta_K, gamma, mu [, I0]          segment j covers steps
@@ -297,8 +297,9 @@ sird_status sird_batch_create(int W, const sird_problem* problems, const sird_ps
 sird_status sird_batch_calibrate(sird_batch_t b, sird_result* results);
 /*
  * New observations for every window of the batch, e.g. the next day's data on the same rolling
- * windows.  y_all (host) holds each window's n_obs values (the counts given at create), window
- * after window: n_total = sum of n_obs.  Each window's D0 becomes its new first observation; N,
+ * windows.  y_all (host) holds each window's n_obs values of y_D (the counts given at create) —
+ * for an F_IRD batch its y_D, y_I and y_R, n_obs values each — window after window: n_total =
+ * sum of n_obs (three times that for F_IRD).  Each window's D0 becomes its new first observation; N,
  * I0, R0 and the PSO settings stay.  The values are packed into pinned staging and copied on
  * the batch's stream, ordered before the next sird_batch_calibrate; y_all may be reused on
  * return.  *h2d_bytes (may be NULL) receives the bytes copied.  SIRD_ERR_ARG on NULL, a wrong

@@ -396,10 +396,11 @@ extern "C" sird_status sird_batch_calibrate(sird_batch_t b, sird_result* results
 extern "C" sird_status sird_batch_set_observations(sird_batch_t b, const double* y_all, long long n_total,
                                                    size_t* h2d_bytes) {
     if (!b || !y_all) return berr(SIRD_ERR_ARG, "batch or y_all is NULL");
-    if (b->mdl.ird) return berr(SIRD_ERR_UNSUPPORTED, "set_observations: F_D batches only");
+    const int nser = b->mdl.ird ? 3 : 1;  // F_IRD: each window's D, I, R series
     long long need = 0;
-    for (const auto& pr : b->probs) need += pr.n_obs;
-    if (n_total != need) return berr(SIRD_ERR_ARG, "y_all must hold sum(n_obs) = " + std::to_string(need) + " values");
+    for (const auto& pr : b->probs) need += (long long)nser * pr.n_obs;
+    if (n_total != need)
+        return berr(SIRD_ERR_ARG, "y_all must hold " + std::to_string(need) + " values (the series of every window)");
     for (long long i = 0; i < n_total; ++i)
         if (!std::isfinite(y_all[i])) return berr(SIRD_ERR_ARG, "non-finite observation in y_all");
     cudaError_t e = cudaSuccess;
@@ -424,24 +425,31 @@ extern "C" sird_status sird_batch_set_observations(sird_batch_t b, const double*
     for (int i = 0; i < b->W; ++i) {
         sird_problem pr = b->probs[i];
         pr.y_D = y;
+        if (nser == 3) {
+            pr.y_I = y + pr.n_obs;
+            pr.y_R = y + 2 * pr.n_obs;
+        }
         ModelDev m{};
         BatchWindow bw = b->h_wins[i];
-        sird_fill_window(&pr, bw.w, m);  // D0 = the new first observation
+        sird_fill_window(&pr, bw.w, m);  // D0 = the new first observation; F_IRD ranges
         b->h_wins[i] = bw;
         hw[i] = bw;
+        const int ps = obs_stride(pr.n_obs);
+        for (int k = 0; k < nser; ++k)
+            for (int j = 0; j < pr.n_obs; ++j) {
+                const int o = b->obs_off[i] + k * ps + j;
+                const double v = y[k * pr.n_obs + j];
+                yf[o] = (float)v;
+                invy[o] = v != 0.0 ? (float)(1.0 / v) : 0.f;
+                yd[o] = v;
+            }
         double mean = 0.0;
-        for (int j = 0; j < pr.n_obs; ++j) {
-            const int o = b->obs_off[i] + j;
-            yf[o] = (float)y[j];
-            invy[o] = y[j] != 0.0 ? (float)(1.0 / y[j]) : 0.f;
-            yd[o] = y[j];
-            mean += y[j];
-        }
+        for (int j = 0; j < pr.n_obs; ++j) mean += y[j];
         mean /= pr.n_obs;
         double ss = 0.0;
         for (int j = 0; j < pr.n_obs; ++j) ss += (y[j] - mean) * (y[j] - mean);
         b->ss_tot[i] = ss;
-        y += pr.n_obs;
+        y += (long long)nser * pr.n_obs;
     }
     e = cudaMemcpyAsync(b->wins, hw, b->wins_bytes, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->yf, ob, b->obs_bytes, cudaMemcpyHostToDevice, b->stream);

@@ -408,8 +408,9 @@ class Batch:
             raise SirdError(st, self._lib.sird_last_error(None).decode())
 
     def set_observations(self, y_all) -> int:
-        """New observations for every window (concatenated, each window's original length); the
-        copy is ordered before the next calibrate.  Returns the bytes copied to the device."""
+        """New observations for every window (concatenated, each window's original length; for an
+        F_IRD batch each window's yD, yI, yR in turn); the copy is ordered before the next
+        calibrate.  Returns the bytes copied to the device."""
         y = _f64(y_all)
         nb = C.c_size_t(0)
         st = self._lib.sird_batch_set_observations(self.h, _dptr(y), len(y), C.byref(nb))

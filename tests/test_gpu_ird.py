@@ -105,3 +105,20 @@ def test_ird_rejects_the_gradient_calls():
     cal.calibrate()
     with pytest.raises(sird.SirdError):
         cal.loss_grad(torch.ones(4, 8, dtype=torch.float64, device="cuda"))
+
+
+def test_ird_batch_set_observations_equals_a_fresh_batch():
+    ser = synth.reported_IR(synth.load_series("c3"), 4)
+    lay = {"L": np.array([25, 40]), "M": np.array([200, 450]), "T": np.array([30, 200])}
+    wins = synth.rolling_window_problems(ser, lay)
+    nxt = synth.rolling_window_problems(ser, dict(lay, T=lay["T"] + 2))
+    lb, ub = configs.bounds(2, log=True)
+    kw = dict(K=2, spd=10, lb=lb, ub=ub, log_scale=[1] * 5, seed=9, objective=sird.FIT_IRD, cost=sird.COST_MSE,
+              block_size=128)
+    batch = sird.Batch(wins, iters=4, **kw)
+    batch.calibrate()
+    batch.set_observations(np.concatenate([np.concatenate([w["yD"], w["yI"], w["yR"]]) for w in nxt]))
+    got = batch.calibrate()
+    fresh = sird.Batch([dict(w, R0=o["R0"]) for w, o in zip(nxt, wins)], iters=4, **kw).calibrate()
+    for a, b in zip(got, fresh):
+        assert a["index"] == b["index"] and a["loss"] == b["loss"] and np.array_equal(a["theta"], b["theta"])
