@@ -273,6 +273,21 @@ sird_status sird_pso_polish(sird_pso_t h, int k, int iters, double first_step, i
 sird_status sird_forecast(const sird_problem* problem, const double* theta, int k, int horizon,
                           double* out_D, int precision, void* cuda_stream);
 
+/*
+ * Ensemble bands of repeated calibrations (Sec. 4.2): for k parameter vectors (host, row-major
+ * [k][P], e.g. the results of k calibrations of one window with different stream_id), each
+ * integrated over the window and `horizon` more days with the last transmission rate, gamma
+ * and mu (FP64, the paper's operation order), per day d = 0 .. n_obs+horizon-1 and per quantity
+ * q = beta(t), R0(t) = beta(t)/(gamma+mu), S, I, R, D (beta and R0 at the day's first step;
+ * the compartments after d days): the median of the k values (the mean of the two middle ones
+ * for even k) and, for each fractions[b] in (0, 1], the central band holding that fraction:
+ * the sorted values at floor(k (1 - f) / 2) from either end.
+ *   out (host) [6][n_obs + horizon][1 + 2 n_bands]: median, low_0, high_0, low_1, high_1, ...
+ * k in 1..4096, n_bands in 0..16, horizon >= 0.  Blocks until out is written.
+ */
+sird_status sird_ensemble_bands(const sird_problem* problem, const double* theta, int k, int horizon,
+                                const double* fractions, int n_bands, double* out, void* cuda_stream);
+
 /* ---------------------------------------------------------------- batched */
 
 /*

@@ -248,6 +248,37 @@ def forecast(pb: Problem, theta, horizon: int) -> np.ndarray:
     return out
 
 
+def ensemble_bands(pb: Problem, thetas, horizon: int, fractions=(0.95, 0.9, 0.5)) -> dict:
+    """Per-day summaries of an ensemble of parameter vectors (Sec. 4.2): each member simulated
+    over the window and `horizon` more days; per day the values of beta(t) (at the day's first
+    step), R0(t) = beta(t) / (gamma + mu), S, I, R, D sorted over the members, the median (mean
+    of the two middle values for an even count) and, for each fraction f, the central band that
+    leaves floor(k (1 - f) / 2) sorted values out at either end.  Returns {quantity: [n_days,
+    1 + 2 len(fractions)]} with columns median, low_0, high_0, ..."""
+    th = np.atleast_2d(_f64(thetas))
+    k = th.shape[0]
+    n_days = pb.days + 1 + int(horizon)
+    gi = 4 if pb.beta_form == BETA_RAMP else pb.K
+    vals = {q: np.zeros((n_days, k)) for q in ("beta", "R0", "S", "I", "R", "D")}
+    for j in range(k):
+        tr = simulate(pb, th[j], n_days - 1)
+        beta = np.array([beta_at(pb, th[j], d * pb.spd) for d in range(n_days)])
+        vals["beta"][:, j] = beta
+        vals["R0"][:, j] = beta / (th[j, gi] + th[j, gi + 1])
+        for q in "SIRD":
+            vals[q][:, j] = tr[q]
+    drops = [int(np.floor(k * (1.0 - f) / 2.0 + 1e-9)) for f in fractions]
+    out = {}
+    for q, v in vals.items():
+        v = np.sort(v, axis=1)
+        med = v[:, k // 2] if k % 2 else (v[:, k // 2 - 1] + v[:, k // 2]) * 0.5
+        cols = [med]
+        for dr in drops:
+            cols += [v[:, dr], v[:, k - 1 - dr]]
+        out[q] = np.stack(cols, axis=1)
+    return out
+
+
 class PSO:
     """Synchronous PSO of Sec. 3.3 with particle-major FP64 state arrays."""
 

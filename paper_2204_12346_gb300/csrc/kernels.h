@@ -112,6 +112,16 @@ cudaError_t launch_loss_grad_f32(const WindowDev& w, const ModelDev& m, const Ob
                                  int M, float* loss, float* grad, int ldg, float* grad_u0, float* ckpt,
                                  cudaStream_t s);
 
+// Ensemble statistics (bands.cu): k <= kMaxEnsemble parameter vectors ([P][k] device), their
+// FP64 trajectories over n_days days (window + extension) into traj (ensemble_traj_bytes), then
+// per day and quantity (beta, R0, S, I, R, D) the median and n_bands central bands, each
+// dropping drop[b] sorted values at either end, into out [6][n_days][1 + 2 n_bands].
+constexpr int kMaxEnsemble = 4096;
+constexpr int kBandQuantities = 6;
+size_t ensemble_traj_bytes(int k, int n_days);
+cudaError_t launch_ensemble_bands(const WindowDev& w, const ModelDev& m, const double* theta, int k, int n_days,
+                                  const int* drop, int n_bands, double* traj, double* out, cudaStream_t s);
+
 // L-BFGS polish of the k candidates named by keys (FP32 swarm): iters iterations with a
 // parallel line search, trials and gradient in FP32 (precision 32) or FP64 (64), best point kept,
 // the best candidate's theta / FP64 loss / sse into *res.  scratch: polish_scratch_doubles(P, k)

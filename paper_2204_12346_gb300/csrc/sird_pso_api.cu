@@ -770,6 +770,54 @@ extern "C" sird_status sird_forecast(const sird_problem* pb, const double* theta
     return SIRD_OK;
 }
 
+extern "C" sird_status sird_ensemble_bands(const sird_problem* pb, const double* theta, int k, int horizon,
+                                           const double* fractions, int n_bands, double* out, void* cuda_stream) {
+    std::string why;
+    sird_status st = sird_check_problem(pb, why);
+    if (st != SIRD_OK) return g_create_error = why, st;
+    if (!theta || !out || k < 1 || k > kMaxEnsemble || horizon < 0 || horizon > 100000 || n_bands < 0 ||
+        n_bands > 16 || (n_bands > 0 && !fractions))
+        return g_create_error = "ensemble_bands: bad theta/out/k/horizon/bands", SIRD_ERR_ARG;
+    std::vector<int> drop(n_bands > 0 ? n_bands : 1, 0);
+    for (int b = 0; b < n_bands; ++b) {
+        const double f = fractions[b];
+        if (!(f > 0.0 && f <= 1.0)) return g_create_error = "ensemble_bands: fractions must be in (0, 1]", SIRD_ERR_ARG;
+        // a central band holding the fraction f of the sorted values: floor(k (1 - f) / 2) left out at
+        // each end (the small offset keeps e.g. k = 1000, f = 0.9 at exactly 50)
+        drop[b] = (int)std::floor((double)k * (1.0 - f) / 2.0 + 1e-9);
+    }
+    WindowDev w{};
+    ModelDev m{};
+    sird_fill_window(pb, w, m);
+    const int P = m.P, n_days = pb->n_obs + horizon, nq = 1 + 2 * n_bands;
+    for (size_t i = 0; i < (size_t)k * P; ++i)
+        if (!std::isfinite(theta[i])) return g_create_error = "ensemble_bands: non-finite theta", SIRD_ERR_ARG;
+    const size_t th_bytes = (size_t)P * k * sizeof(double), drop_bytes = 256;
+    const size_t traj_bytes = ensemble_traj_bytes(k, n_days);
+    const size_t out_count = (size_t)kBandQuantities * n_days * nq;
+    std::vector<double> hth((size_t)P * k);
+    for (int j = 0; j < k; ++j)
+        for (int d = 0; d < P; ++d) hth[(size_t)d * k + j] = theta[(size_t)j * P + d];
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    unsigned char* dmem = nullptr;
+    cudaError_t e = cudaMalloc((void**)&dmem, th_bytes + drop_bytes + traj_bytes + out_count * sizeof(double));
+    double* dth = (double*)dmem;
+    int* ddrop = (int*)(dmem + th_bytes);
+    double* dtraj = (double*)(dmem + th_bytes + drop_bytes);
+    double* dout = (double*)(dmem + th_bytes + drop_bytes + traj_bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dth, hth.data(), th_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ddrop, drop.data(), sizeof(int) * drop.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_ensemble_bands(w, m, dth, k, n_days, ddrop, n_bands, dtraj, dout, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, out_count * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dmem);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return g_create_error = std::string("ensemble_bands: ") + cudaGetErrorString(e), SIRD_ERR_CUDA;
+    }
+    return SIRD_OK;
+}
+
 extern "C" sird_status sird_pso_topk(sird_pso_t h, int k, double* theta_out, double* loss_out) {
     if (!h) return SIRD_ERR_ARG;
     if (h->sticky) return h->sticky;

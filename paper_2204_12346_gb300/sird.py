@@ -29,7 +29,7 @@ EXPORTS = [
     "sird_pso_num_params", "sird_pso_eval", "sird_pso_init", "sird_pso_step", "sird_pso_calibrate",
     "sird_pso_result", "sird_pso_sync", "sird_pso_get_state", "sird_pso_set_state", "sird_loss_grad",
     "sird_forecast", "sird_pso_calibrate_batched", "sird_pso_set_observations", "sird_pso_set_timing", "sird_pso_launch_mode",
-    "sird_pso_step_f32_noalloc", "sird_pso_topk", "sird_pso_polish", "sird_batch_create", "sird_batch_calibrate", "sird_batch_set_observations",
+    "sird_pso_step_f32_noalloc", "sird_pso_topk", "sird_ensemble_bands", "sird_pso_polish", "sird_batch_create", "sird_batch_calibrate", "sird_batch_set_observations",
     "sird_batch_block_size", "sird_batch_blocks_per_sm", "sird_batch_destroy", "sird_batch_set_timing",
 ]
 
@@ -101,6 +101,7 @@ def lib():
         L.sird_pso_set_state.argtypes = [vp, vp, C.c_size_t]
         L.sird_loss_grad.argtypes = [vp, vp, ip, ip, vp, vp, ip, vp, ip, ip]
         L.sird_forecast.argtypes = [C.POINTER(Problem), dp, ip, ip, dp, ip, vp]
+        L.sird_ensemble_bands.argtypes = [C.POINTER(Problem), dp, ip, ip, dp, ip, dp, vp]
         L.sird_pso_calibrate_batched.argtypes = [ip, C.POINTER(Problem), C.POINTER(Config), vp, C.POINTER(Result)]
         L.sird_pso_set_observations.argtypes = [vp, dp, ip]
         L.sird_pso_set_timing.argtypes = [vp, vp, vp]
@@ -464,6 +465,28 @@ def forecast(yD, N, theta, horizon, *, K=1, spd=10, R0=0.0, I0=0.0, fit_I0=True,
     if st != OK:
         raise SirdError(st, L.sird_last_error(None).decode())
     return out
+
+
+BAND_QUANTITIES = ("beta", "R0", "S", "I", "R", "D")
+
+
+def ensemble_bands(yD, N, theta, horizon, fractions=(0.95, 0.9, 0.5), *, K=1, spd=10, R0=0.0, I0=0.0, fit_I0=True,
+                   beta_form=BETA_PWC, stream=None) -> dict:
+    """Median and central bands over an ensemble of parameter vectors ([k, P]) per day of the
+    window and `horizon` more days: {quantity: [n_days, 1 + 2 len(fractions)]} with columns
+    median, low_0, high_0, low_1, high_1, ..."""
+    L = lib()
+    pb, keep = make_problem(yD, N, K, spd, R0, I0, fit_I0, beta_form)
+    th = _f64(np.atleast_2d(theta))
+    fr = _f64(fractions)
+    n_days = len(_f64(yD)) + int(horizon)
+    nq = 1 + 2 * len(fr)
+    out = np.zeros((len(BAND_QUANTITIES), n_days, nq))
+    st = L.sird_ensemble_bands(C.byref(pb), _dptr(th), th.shape[0], int(horizon), _dptr(fr), len(fr), _dptr(out),
+                               C.c_void_p(current_stream_handle(stream)))
+    if st != OK:
+        raise SirdError(st, L.sird_last_error(None).decode())
+    return {q: out[i] for i, q in enumerate(BAND_QUANTITIES)}
 
 
 def step_f32_noalloc(yD, N, obs, x, v, pbest, pbest_f, gbest, iteration, *, gbest_index=None, stream=None,

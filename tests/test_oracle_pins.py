@@ -444,3 +444,44 @@ def test_forecast(orc):
     # the window's second segment already has beta = 0, so the decay law holds from its start too
     Ik = I_end * (1 - (0.1 + 0.003) / pb.spd) ** k
     assert np.allclose(fc0, st["D"][-1] + 0.003 / 0.103 * (I_end - Ik), rtol=1e-12)
+
+
+# ---------------------------------------------------------------- ensemble bands (Sec. 4.2)
+
+def test_ensemble_bands_of_identical_members_collapse_to_the_trajectory(orc):
+    s = synth.load_series("c2")
+    pb = orc.Problem(yD=s["yD"], N=s["N"], K=4, spd=10)
+    th = np.asarray(s["theta_true"])
+    b = orc.ensemble_bands(pb, np.tile(th, (6, 1)), 14)
+    tr = orc.simulate(pb, th, pb.days + 14)
+    for q in "SIRD":
+        assert np.all(b[q] == tr[q][:, None])
+
+
+def test_ensemble_bands_order_statistics_and_nesting(orc):
+    # members differing only in mu: deaths increase with mu on every day after the first, so the
+    # sorted members are the mu-sorted ones and the median is the middle member's trajectory
+    s = synth.load_series("c2")
+    pb = orc.Problem(yD=s["yD"], N=s["N"], K=4, spd=10)
+    th = np.tile(np.asarray(s["theta_true"]), (9, 1))
+    th[:, 5] = np.linspace(1e-3, 3e-3, 9)
+    b = orc.ensemble_bands(pb, th[::-1], 10, fractions=(0.95, 0.5))
+    D = np.stack([orc.simulate(pb, t, pb.days + 10)["D"] for t in th], axis=1)
+    assert np.array_equal(b["D"][1:, 0], D[1:, 4])
+    # drop = floor(9 * 0.05 / 2) = 0 and floor(9 * 0.5 / 2) = 2
+    assert np.array_equal(b["D"][1:, 1], D[1:, 0]) and np.array_equal(b["D"][1:, 2], D[1:, 8])
+    assert np.array_equal(b["D"][1:, 3], D[1:, 2]) and np.array_equal(b["D"][1:, 4], D[1:, 6])
+    for q in b:
+        assert np.all(b[q][:, 1] <= b[q][:, 3]) and np.all(b[q][:, 3] <= b[q][:, 0])
+        assert np.all(b[q][:, 0] <= b[q][:, 4]) and np.all(b[q][:, 4] <= b[q][:, 2])
+
+
+def test_ensemble_bands_reproduction_number_closed_form(orc):
+    # constant beta: R0(t) = beta / (gamma + mu) on every day, inside the window and past it
+    s = synth.load_series("c1")
+    pb = orc.Problem(yD=s["yD"], N=s["N"], K=1, spd=10)
+    th = np.array([[0.3, 0.1, 0.002, 1e4], [0.2, 0.12, 0.004, 2e4]])
+    b = orc.ensemble_bands(pb, th, 21, fractions=())
+    r = np.sort(th[:, 0] / (th[:, 1] + th[:, 2]))
+    assert np.all(b["R0"][:, 0] == (r[0] + r[1]) * 0.5)
+    assert b["R0"].shape == (31 + 21, 1)
