@@ -145,6 +145,10 @@ def describe(name: str) -> str:
         "paper_ird": ("the paper's setting on its representative objective F_IRD^MXSE, batched FP32: ramp beta(t), "
                       "139 rolling 35-day windows shifted by 3 days, reported I, R, D, 10000 particles per window, "
                       "linear PSO box, 100 iterations, dt=0.1, one persistent launch, FP64 re-evaluation per window"),
+        "stability": ("the paper's stability test (Sec. 4.2): 2 windows of 35 days each calibrated 1000 times "
+                      "(independent Philox streams, 10000 particles, ramp beta(t), F_IRD^MXSE, 100 iterations) in "
+                      "one batched launch, then per day the median and 95/90/50% bands of beta, R0, S, I, R, D over "
+                      "the window and a 21-day extension (FP64 ensemble integration, on-device sort)"),
         "c4": ("gradient FP32: loss + exact gradient (discrete adjoint of the compensated FP32 trajectory, "
                "day-start checkpoints) of the 4096 personal bests of a calibrated swarm, 90 days, 4 beta segments "
                "(7 params), dt=0.05"),
@@ -378,6 +382,107 @@ def run_batched(args, rank, world):
     return out
 
 
+def stability_windows(rank: int = 0):
+    """The stability configuration: reps copies of each chosen window (Philox stream words
+    distinct per copy and per rank), with reported I and R."""
+    c = dict(configs.CONFIGS["stability"])
+    ser = synth.reported_IR(synth.load_series(c["series"]), c["seed"])
+    T = np.repeat(np.asarray(c["windows_T"]), c["reps"])
+    lay = {"L": np.full(T.size, c["L"]), "M": np.full(T.size, c["M"]), "T": T}
+    wins = synth.rolling_window_problems(ser, lay)
+    for i, w in enumerate(wins):
+        w["seed"] = c["seed"]
+        w["stream_id"] = rank * len(wins) + i
+    return c, ser, wins
+
+
+def run_stability(args, rank, world):
+    import torch
+
+    from paper_2204_12346_gb300 import sird
+
+    c, ser, wins = stability_windows(rank)
+    lb, ub = configs.bounds_ramp()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch = sird.Batch(wins, K=1, beta_form=sird.BETA_RAMP, spd=c["spd"], iters=c["iters"], lb=lb, ub=ub,
+                           cost=sird.COST_MXSE, objective=sird.FIT_IRD, block_size=args.block, stream=stream)
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record(stream)
+        ev[1].record(stream)
+        batch.set_timing(*ev)
+    reps = c["reps"]
+
+    def step():
+        res = batch.calibrate()
+        bands = []
+        for t in range(len(c["windows_T"])):
+            th = np.array([r["theta"] for r in res[t * reps:(t + 1) * reps]])
+            w = wins[t * reps]
+            bands.append(sird.ensemble_bands(w["yD"], w["N"], th, c["horizon"], c["fractions"], K=1,
+                                             beta_form=sird.BETA_RAMP, R0=w["R0"], spd=c["spd"], stream=stream))
+        return res, bands
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    total_ms, kern_ms, clocks, (res, bands) = timed_steps(args, world, stream, step, ev)
+    # end to end: every step also uploads all windows' D, I, R series from host memory
+    y_host = np.concatenate([np.concatenate([w["yD"], w["yI"], w["yR"]]) for w in wins])
+    e2e, h2d = [], 0
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2d = batch.set_observations(y_host)
+        step()
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = _max_over_ranks(sum(e2e), world)
+    if rank != 0:
+        return None
+    pdays = sum(w["particles"] * w["L"] for w in wins)
+    units = pdays * c["iters"]
+    kms = statistics.mean(kern_ms)
+    flops = pdays * algorithmic_flops_per_particle_day(c["spd"], True, True) * (c["iters"] + 1)
+    achieved = flops / (kms / 1e3) / 1e12
+    held = {}
+    for t, T in enumerate(c["windows_T"]):
+        L, h = c["L"], c["horizon"]
+        days = slice(L + 1, L + 1 + h)
+        cover = {}
+        for q, key in (("I", "yI"), ("R", "yR"), ("D", "yD")):
+            rep_ = np.asarray(ser[key][T + L + 1:T + L + 1 + h])
+            b = bands[t][q][days]
+            cover[q] = {"inside_95": float(np.mean((b[:, 1] <= rep_) & (rep_ <= b[:, 2]))),
+                        "median_max_rel_err": float(np.max(np.abs(b[:, 0] - rep_) / np.abs(rep_)))}
+        th = np.array([r["theta"] for r in res[t * reps:(t + 1) * reps]])
+        held[f"window_day_{T}"] = {"extension_vs_reported": cover,
+                                   "theta_median": np.median(th, axis=0).tolist(),
+                                   "beta_R0_last_day_median": [float(bands[t]["beta"][L, 0]),
+                                                               float(bands[t]["R0"][L, 0])]}
+    return {
+        "metric": METRIC, "value": units * args.steps * world / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": describe("stability"), "name": c["name"], "windows": len(wins),
+                   "repetitions_per_window": reps, "particles": c["M"], "days": c["L"], "iterations": c["iters"],
+                   "block": f"{batch.block_size} threads x {batch.blocks_per_sm} per SM",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"independent batches x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "pso_batch_f32",
+                     "avg_launch_us": kms * 1e3, "flops_per_launch": flops,
+                     "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+        "e2e": {"value": units * args.steps * world / (e2e_total / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d + 2 * reps * 7 * 8,
+                "d2h_bytes_per_step": len(wins) * BATCH_OUT_BYTES + 2 * 6 * (c["L"] + 1 + c["horizon"]) * 7 * 8,
+                "ms_per_step": e2e_total / args.steps},
+        "gpu_launches": args.steps * (2 + 2 * 2),
+        "clocks": clocks,
+        "result": held,
+        **({} if args.no_cpu_baseline else {"cpu_baseline": cpu_baseline("stability", budget_s=args.cpu_budget)}),
+    }
+
+
 def topk_launches(M: int, k: int, chunk: int = 4096) -> int:
     """Launches of the selection kernel for the k best of M (chunks of 4096, then the k best of
     every chunk, until one chunk is left)."""
@@ -586,6 +691,20 @@ def cpu_baseline(name: str, budget_s: float = 15.0, iters_cap: int | None = None
             units += w["particles"] * w["L"] * 2
             done += 1
         sample = f"{done} windows x (init + 1 PSO iteration), full swarms"
+    elif name == "stability":
+        c, ser, wins = stability_windows(0)
+        lb, ub = configs.bounds_ramp()
+        done = 0
+        for w in wins:
+            if time.perf_counter() - t0 >= budget_s or (iters_cap is not None and done >= iters_cap):
+                break
+            pb = O.Problem(yD=w["yD"], N=w["N"], R0=w["R0"], beta_form=O.BETA_RAMP, spd=c["spd"], cost=O.MXSE,
+                           objective=O.FIT_IRD, yI=w["yI"], yR=w["yR"])
+            O.PSO(pb, w["particles"], lb, ub, logdim=[0] * len(lb), seed=w["seed"], stream=w["stream_id"],
+                  store_f32=True).init().step(1)
+            units += w["particles"] * w["L"] * 2
+            done += 1
+        sample = f"{done} repetitions x (init + 1 PSO iteration), 10000 particles each"
     elif name == "c4":
         c, ser, y, lb, ub = single_window(name)
         pb = O.Problem(yD=y, N=ser["N"], K=c["K"], spd=c["spd"])
@@ -645,7 +764,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c3", "c2", "c1", "c4", "c5", "paper", "paper_ird"], default="c3")
+    ap.add_argument("--workload", choices=["c3", "c2", "c1", "c4", "c5", "paper", "paper_ird", "stability"],
+                    default="c3")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-units", type=int, default=2,
                     help="reference arm: windows (batched) or PSO iterations (single window) per step")
@@ -672,6 +792,8 @@ def main():
             out = run_batched(args, rank, world)
         elif args.workload == "c4":
             out = run_c4(args, rank, world)
+        elif args.workload == "stability":
+            out = run_stability(args, rank, world)
         else:
             out = run_single(args, rank, world)
     finally:

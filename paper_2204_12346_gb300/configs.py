@@ -52,6 +52,13 @@ CONFIGS = {
     "paper_ird": dict(name="paper-ramp-139-windows-F_IRD-MXSE", series="c3", beta_form="ramp", objective="ird",
                       cost="mxse", W=139, iters=100, spd=10, precision=32, log=False, seed=0, L_min=35, L_max=35,
                       M_min=10000, M_max=10000, delta=3),
+    # The stability test of Sec. 4.2: two windows (tau = 35 days) each calibrated 1000 times with
+    # independent random streams (10000 particles, ramp beta(t), F_IRD^MXSE) in one batched
+    # launch, then per day the median and 95/90/50% bands of beta, R0, S, I, R, D over the
+    # window and a 21-day extension.
+    "stability": dict(name="stability-2x1000-repetitions", series="c3", beta_form="ramp", objective="ird",
+                      cost="mxse", windows_T=(120, 330), L=35, reps=1000, M=10000, iters=100, spd=10,
+                      precision=32, log=False, seed=0, horizon=21, fractions=(0.95, 0.9, 0.5)),
     # 2^20 particles, 10 segments, 120 days at dt = 0.05 day, then a 14-day forecast.
     "c5": dict(name="c5-large-2^20", series="c5", K=10, days=120, spd=20, M=1 << 20, iters=100,
                precision=32, log=True, seed=0, horizon=14, forecast_topk=1024, reeval_topk=32),
