@@ -153,7 +153,8 @@ def describe(name: str) -> str:
                "day-start checkpoints) of the 4096 personal bests of a calibrated swarm, 90 days, 4 beta segments "
                "(7 params), dt=0.05"),
         "c5": ("large FP32: 2^20 particles, 10 segments (13 params), 120 days, dt=0.05, 100 iterations, FP64 "
-               "re-evaluation of the 32 best, then the 1024 best personal bests forecast 14 held-out days (FP64)"),
+               "re-evaluation of the 32 best, 20 FP32 L-BFGS iterations (adjoint gradient) on the 32 best, then the "
+               "1024 best personal bests forecast 14 held-out days (FP64)"),
     }[name]
 
 
@@ -379,6 +380,7 @@ def run_batched(args, rank, world):
         out["s_to_calibrate"] = s_to_calibrate()
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(name, budget_s=args.cpu_budget)
+        out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(name)
     return out
 
 
@@ -514,8 +516,12 @@ def run_single(args, rank, world):
         ev[1].record(stream)
         cal.set_timing(*ev)
 
+    polish = c.get("polish_iters", 0)
+
     def step():
         r = cal.calibrate()
+        if polish:  # FP32 L-BFGS polish of the best personal bests (adjoint gradient)
+            r = dict(r, polished=cal.polish(k=c["polish_topk"], iters=polish, first_step=1e-2, precision=32))
         if not horizon:
             return r, None
         # the forecast leg (Sec. 4.2): the fk best personal bests continued `horizon` days
@@ -549,6 +555,8 @@ def run_single(args, rank, world):
     rk = c.get("reeval_topk", 0)
     launches = 1 + iter_launches + (topk_launches(c["M"], rk) + 1 if rk else 1)
     h2d, d2h = (L + 1) * 16, 288
+    if polish:  # selection, init + gradient + accept, 5 per iteration, the final FP64 pick
+        launches += topk_launches(c["M"], c["polish_topk"]) + 3 + 5 * polish + 1
     if horizon:
         launches += topk_launches(c["M"], fk) + 1 + 1
         h2d += fk * P * 8 + (L + 1) * 16
@@ -575,6 +583,9 @@ def run_single(args, rank, world):
         "clocks": clocks,
         "result": {"loss_fp64": res["loss"], "loss_search": res["loss_search"], "r2_D": res["r2_D"]},
     }
+    if polish:
+        out["result"].update({"polish": f"top {c['polish_topk']}, {polish} FP32 L-BFGS iterations",
+                              "loss_fp64_polished": res["polished"]["loss"]})
     if horizon:
         held = np.asarray(ser["yD"][L + 1:L + 1 + horizon])
         rel = np.abs(fc - held[None, :]) / held[None, :]
@@ -667,6 +678,66 @@ def run_c4(args, rank, world):
 
 # ------------------------------------------------------------------ oracle on the host cores
 
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+_WORKER_WINDOWS = {}
+
+
+def _oracle_windows_worker(args):
+    """One worker of the all-cores baseline: the oracle's initialisation and one PSO iteration on
+    the given windows of the batched workload; returns particle-days processed."""
+    name, idx = args
+    import oracle as O
+
+    if name not in _WORKER_WINDOWS:  # built once per worker, before the timed call
+        _WORKER_WINDOWS[name] = batch_windows(name, 0)
+    c, wins, lb, ub, model = _WORKER_WINDOWS[name]
+    logd = [1] * len(lb) if model["log_scale"] else [0] * len(lb)
+    zlb = np.where(logd, np.log(np.maximum(lb, 1e-300)), lb)
+    zub = np.where(logd, np.log(np.maximum(ub, 1e-300)), ub)
+    units = 0
+    for i in idx:
+        w = wins[i]
+        pb = O.Problem(yD=w["yD"], N=w["N"], R0=w["R0"], K=model["K"], spd=c["spd"],
+                       beta_form=O.BETA_RAMP if model["beta_form"] == 1 else O.BETA_PWC, cost=model["cost"],
+                       objective=model["objective"], yI=w.get("yI"), yR=w.get("yR"))
+        O.PSO(pb, w["particles"], zlb, zub, logdim=logd, seed=w["seed"], stream=w["stream_id"],
+              store_f32=True).init().step(1)
+        units += w["particles"] * w["L"] * 2
+    return units
+
+
+def cpu_baseline_all_cores(name: str, windows_per_core: int = 16) -> dict:
+    """The same oracle on every host core: one process per core (spawned, not forked, since the
+    parent has used the GPU), each running whole windows of the batched workload."""
+    import multiprocessing as mp
+
+    import oracle as O
+
+    O.build()
+    cores = os.cpu_count() or 1
+    c, wins, _, _, _ = batch_windows(name, 0)
+    n = min(len(wins), cores * windows_per_core)
+    jobs = [(name, list(range(r, n, cores))) for r in range(cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_windows_worker, [(name, [0])] * cores)  # start-up and imports, not timed
+        t0 = time.perf_counter()
+        units = sum(pool.map(_oracle_windows_worker, jobs))
+        dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+            "sample": f"{n} windows x (init + 1 PSO iteration), one process per core, FP64 ({dt:.1f} s)"}
+
+
 def cpu_baseline(name: str, budget_s: float = 15.0, iters_cap: int | None = None) -> dict:
     """The FP64 oracle as it stands, single-threaded, on a bounded sample of the workload."""
     import oracle as O
@@ -731,7 +802,7 @@ def cpu_baseline(name: str, budget_s: float = 15.0, iters_cap: int | None = None
         units = M * c["days"] * (its + 1)
         sample = f"{M} particles x {c['days']} days, init + {its} PSO iterations"
     dt = time.perf_counter() - t0
-    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": cpu_model(),
             "sample": f"{sample}, single thread, FP64 ({dt:.1f} s)"}
 
 

@@ -61,5 +61,6 @@ CONFIGS = {
                       precision=32, log=False, seed=0, horizon=21, fractions=(0.95, 0.9, 0.5)),
     # 2^20 particles, 10 segments, 120 days at dt = 0.05 day, then a 14-day forecast.
     "c5": dict(name="c5-large-2^20", series="c5", K=10, days=120, spd=20, M=1 << 20, iters=100,
-               precision=32, log=True, seed=0, horizon=14, forecast_topk=1024, reeval_topk=32),
+               precision=32, log=True, seed=0, horizon=14, forecast_topk=1024, reeval_topk=32, polish_topk=32,
+               polish_iters=20),
 }
