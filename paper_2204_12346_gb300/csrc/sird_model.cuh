@@ -384,14 +384,101 @@ struct RampCoefF32 {
     }
 };
 
+// F_IRD^C for two parameter vectors in packed form: each lane performs fitness_f32_ird's
+// operations in the same order.
+template <int COST>
+__device__ void fitness_f32x2_ird(const WindowDev& w, const ModelDev& m, const float* __restrict__ ys,
+                                  const float* __restrict__ invys, const float* tha, const float* thb, int stride,
+                                  float& fa, float& fb) {
+    const int spd = m.spd, n = w.n_obs, L = n - 1, steps = L * spd, ps = obs_stride(n);
+    const float *yI = ys + ps, *yR = ys + 2 * ps, *iyI = invys + ps, *iyR = invys + 2 * ps;
+    const bool ramp = m.beta_form == BETA_RAMP;
+    const int gi = ramp ? 4 : m.K, K = ramp ? 1 : m.K;
+    const F2 gam = f2(tha[gi * stride], thb[gi * stride]), mu = f2(tha[(gi + 1) * stride], thb[(gi + 1) * stride]);
+    F2 I = m.fit_I0 ? f2(tha[(gi + 2) * stride], thb[(gi + 2) * stride]) : f2(w.I0f);
+    F2 Il = f2(0.f);
+    const F2 gm = add2(gam, mu);
+    const F2 dth = f2(w.dt_h), dtl = f2(w.dt_l);
+    const F2 a = fma2(gm, dth, mul2(gm, dtl));
+    const F2 na = F2{a.v ^ 0x8000000080000000ull};
+    const F2 dm = fma2(mu, dth, mul2(mu, dtl));
+    const F2 dr = fma2(gam, dth, mul2(gam, dtl));
+    const F2 cbnh = f2(w.cbn_h), cbnl = f2(w.cbn_l);
+    RampCoefF32 ra{}, rb{};
+    if (ramp) {
+        ra.init(tha, stride);
+        rb.init(thb, stride);
+    }
+    const float dtf = __fadd_rn(w.dt_h, w.dt_l);
+    DayStateF32x2 ds;
+    ds.init(w, f2lo(I), f2hi(I), ys[0]);
+    F2 Rh = f2(w.R0h), Rl = f2(w.R0l);
+    LossF32x2<COST> lI, lR, lD;
+    const F2 sI = f2(w.inv_rng_I), sR = f2(w.inv_rng_R), sD = f2(w.inv_rng_D);
+    auto observe = [&](int day, F2 eD) {
+        const F2 eI = sub2(f2(yI[day]), I);
+        const F2 eR = sub2(sub2(f2(yR[day]), Rh), Rl);
+        if (COST == COST_MAPE) {
+            lI.add(eI, iyI[day]);
+            lR.add(eR, iyR[day]);
+            lD.add(eD, invys[day]);
+        } else {
+            lI.add(mul2(eI, sI), 0.f);
+            lR.add(mul2(eR, sR), 0.f);
+            lD.add(mul2(eD, sD), 0.f);
+        }
+    };
+    observe(0, f2(0.f));
+    int seg = 0, next_b = (!ramp && K > 1) ? segment_start(1, steps, K) : INT_MAX;
+    F2 cb = f2(0.f);
+    if (!ramp) {
+        const F2 b = f2(tha[0], thb[0]);
+        cb = fma2(b, cbnh, mul2(b, cbnl));
+    }
+    int k = 0;
+    for (int day = 1; day <= L; ++day) {
+        F2 cday = f2(0.f), dday = f2(0.f), rday = f2(0.f);
+        for (int s = 0; s < spd; ++s, ++k) {
+            if (ramp) {
+                const float t = __fmul_rn((float)k, dtf);
+                cb = f2(ra.cb(t, w), rb.cb(t, w));
+            } else {
+                while (k == next_b) {
+                    ++seg;
+                    const F2 b = f2(tha[seg * stride], thb[seg * stride]);
+                    cb = fma2(b, cbnh, mul2(b, cbnl));
+                    next_b = (seg + 1 < K) ? segment_start(seg + 1, steps, K) : INT_MAX;
+                }
+            }
+            rday = fma2(dr, I, rday);
+            euler_f32x2(cb, na, dm, ds.Sday, cday, dday, I, Il);
+        }
+        const F2 eD = ds.close_day(cday, dday, ys[day], I, Il);
+        F2 sr, er;
+        two_sum2(Rh, rday, sr, er);
+        Rh = sr;
+        Rl = add2(Rl, er);
+        observe(day, eD);
+    }
+    float cIa, cIb, cRa, cRb, cDa, cDb;
+    lI.result(n, w.n_kept_I, cIa, cIb);
+    lR.result(n, w.n_kept_R, cRa, cRb);
+    lD.result(n, w.n_kept, cDa, cDb);
+    fa = cIa;
+    if (cRa > fa) fa = cRa;
+    if (cDa > fa) fa = cDa;
+    fb = cIb;
+    if (cRb > fb) fb = cRb;
+    if (cDb > fb) fb = cDb;
+}
+
 // Losses of two parameter vectors (theta_d at tha[d*stride], thb[d*stride]).
 template <int SPD, int COST>
 __device__ void fitness_f32x2(const WindowDev& w, const ModelDev& m, const float* __restrict__ ys,
                               const float* __restrict__ invys, const float* tha, const float* thb, int stride,
                               float& fa, float& fb) {
     if (m.ird) {
-        fa = fitness_f32_ird<COST>(w, m, ys, invys, tha, stride);
-        fb = fitness_f32_ird<COST>(w, m, ys, invys, thb, stride);
+        fitness_f32x2_ird<COST>(w, m, ys, invys, tha, thb, stride, fa, fb);
         return;
     }
     const int spd = SPD > 0 ? SPD : m.spd;
