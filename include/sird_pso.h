@@ -61,7 +61,14 @@ typedef enum sird_cost { SIRD_COST_MSE = 0, SIRD_COST_MXSE = 1, SIRD_COST_MAE = 
 typedef enum sird_beta_form { SIRD_BETA_PWC = 0, SIRD_BETA_RAMP = 1 } sird_beta_form;
 
 /* How the swarm iterations are launched (results are identical). */
-typedef enum sird_launch_mode { SIRD_LAUNCH_AUTO = 0, SIRD_LAUNCH_PER_ITER = 1, SIRD_LAUNCH_PERSISTENT = 2 } sird_launch_mode;
+typedef enum sird_launch_mode {
+    SIRD_LAUNCH_AUTO = 0,
+    SIRD_LAUNCH_PER_ITER = 1,
+    SIRD_LAUNCH_PERSISTENT = 2,
+    /* batches (configs[0].launch_mode, with configs[0].block_size given): */
+    SIRD_LAUNCH_WINDOW_PER_BLOCK = 3, /* a block runs one window at a time (the default) */
+    SIRD_LAUNCH_FLAT = 4              /* every window's swarm spread over the whole grid */
+} sird_launch_mode;
 
 /* Main objective: F_D^C (deaths only) or F_IRD^C (max over I, R, D), Sec. 3.1. */
 typedef enum sird_objective { SIRD_FIT_D = 0, SIRD_FIT_IRD = 1 } sird_objective;
@@ -300,10 +307,15 @@ sird_status sird_ensemble_bands(const sird_problem* problem, const double* theta
  * problems[W], configs[W] are host arrays.  Every window must share beta_form, K,
  * steps_per_day, cost, objective, fit_I0, precision (32), w, c1, c2, iters, the bounds and
  * log_scale; n_obs, observations, N, I0, R0, particles (1..2^20), seed and stream_id may
- * differ.  configs[0].block_size = 0 lets the library pick the threads per block and the blocks
- * per SM by timing short trial runs of each candidate (cached in the file named by the
- * environment variable SIRD_TUNE_CACHE when it is set); otherwise a multiple of 32 in 32..1024
- * with as many blocks per SM as fit.
+ * differ.  Two forms run a batch: one window per block (a block takes the next window from a
+ * queue, longest first), or flat (every window's particle pairs spread over all threads of a
+ * co-resident grid, one bounded grid barrier per iteration, the last item of a window to
+ * finish an iteration publishing its global best; SIRD_ERR_TIMEOUT if a barrier wait runs
+ * out).  Both give the same results.  configs[0].block_size = 0 lets the library pick the form,
+ * the threads per block and the blocks per SM by timing short trial runs of each candidate
+ * (cached in the file named by the environment variable SIRD_TUNE_CACHE when it is set);
+ * otherwise a multiple of 32 in 32..1024 with as many blocks per SM as fit, in the form
+ * configs[0].launch_mode names (SIRD_LAUNCH_FLAT, else one window per block).
  */
 typedef struct sird_batch* sird_batch_t;
 sird_status sird_batch_create(int W, const sird_problem* problems, const sird_pso_config* configs, void* cuda_stream,
@@ -324,6 +336,8 @@ sird_status sird_batch_set_observations(sird_batch_t b, const double* y_all, lon
 /* Threads per block and blocks per SM the batch runs with (autotuned or given); 0 if b is NULL. */
 int sird_batch_block_size(sird_batch_t b);
 int sird_batch_blocks_per_sm(sird_batch_t b);
+/* The batch's form: SIRD_LAUNCH_FLAT or SIRD_LAUNCH_WINDOW_PER_BLOCK; 0 if b is NULL. */
+int sird_batch_launch_mode(sird_batch_t b);
 /* Measurement hook: every later sird_batch_calibrate records the two CUDA events (cudaEvent_t;
  * NULL to stop) right before and right after the batch kernel.  Re-captures the graph. */
 sird_status sird_batch_set_timing(sird_batch_t b, void* event_begin, void* event_end);

@@ -19,6 +19,11 @@ void sird_fill_window(const sird_problem* pb, WindowDev& w, ModelDev& m);
 
 struct sird_batch {
     int W = 0, P = 0, iters = 0, n_max = 0, block = 0, grid = 0, per_sm = 0;  // per_sm 0 = occupancy maximum
+    int flat = 0;  // 1: the flat form (every swarm spread over the grid, one grid barrier per iteration)
+    int n_items = 0;
+    int4* items = nullptr;   // flat form: (window, particle, partner or -1), windows longest first
+    int* n_items_w = nullptr;
+    FlatScratch fs{};
     ModelDev mdl{};
     PsoCoeffs<float> c{};
     cudaStream_t stream = nullptr, cap = nullptr;
@@ -91,20 +96,27 @@ void tune_cache_put(const std::string& key, int block) {
     std::fclose(f);
 }
 
-cudaError_t run(sird_batch* b, int iters, int block, int per_sm, cudaStream_t s, bool reeval, bool timed = false) {
-    int per = batch_blocks_per_sm(b->mdl, block, b->n_max);
+cudaError_t run(sird_batch* b, int iters, int block, int per_sm, int flat, cudaStream_t s, bool reeval,
+                bool timed = false) {
+    int per = flat ? flat_blocks_per_sm(b->mdl, block) : batch_blocks_per_sm(b->mdl, block, b->n_max);
     if (per <= 0) return cudaErrorInvalidConfiguration;
     if (per_sm > 0 && per_sm < per) per = per_sm;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = std::min(b->W, per * nsm);
+    // the flat form needs every block resident at once (it waits at a grid barrier)
+    const int grid = flat ? per * nsm : std::min(b->W, per * nsm);
     b->grid = grid;
     cudaError_t e = cudaSuccess;
     if (timed && b->ev_begin) e = cudaEventRecordWithFlags(b->ev_begin, s, cudaEventRecordExternal);
-    if (e == cudaSuccess)
-        e = launch_batch(b->wins, b->order, b->W, b->mdl, b->c, b->yf, b->invy, b->yd, b->swarm, b->queue, b->out,
-                         iters, b->n_max, block, grid, false, s);
+    if (e == cudaSuccess) {
+        if (flat)
+            e = launch_flat(b->wins, b->n_items_w, b->items, b->n_items, b->W, b->mdl, b->c, b->yf, b->invy,
+                            b->swarm, b->fs, b->out, iters, block, grid, s);
+        else
+            e = launch_batch(b->wins, b->order, b->W, b->mdl, b->c, b->yf, b->invy, b->yd, b->swarm, b->queue,
+                             b->out, iters, b->n_max, block, grid, false, s);
+    }
     if (e == cudaSuccess && timed && b->ev_end) e = cudaEventRecordWithFlags(b->ev_end, s, cudaEventRecordExternal);
     if (e == cudaSuccess && reeval)
         e = launch_batch_reeval(b->wins, b->W, b->mdl, b->c.logmask, b->yd, b->out, s);
@@ -119,7 +131,8 @@ cudaError_t autotune(sird_batch* b, long long work) {
     const int cached = tune_cache_get(key);
     if (cached) {
         b->block = cached & 0xFFFF;
-        b->per_sm = cached >> 16;
+        b->per_sm = (cached >> 16) & 0xFF;
+        b->flat = (cached >> 24) & 1;
         return cudaSuccess;
     }
     cudaEvent_t e0, e1;
@@ -127,35 +140,39 @@ cudaError_t autotune(sird_batch* b, long long work) {
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e != cudaSuccess) return e;
     float best = 1e30f;
-    int best_block = 128, best_per = 0;
-    for (int block : {128, 256, 512, 768, 1024}) {
-        const int maxper = batch_blocks_per_sm(b->mdl, block, b->n_max);
-        for (int per : {1, 2, maxper}) {
-            // each distinct (block, blocks per SM) that fits, once
-            if (maxper <= 0 || per > maxper || (per == maxper && maxper <= 2)) continue;
-            float ms = 0.f;
-            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // first run warms up
-                e = cudaEventRecord(e0, b->stream);
-                if (e == cudaSuccess) e = run(b, 2, block, per, b->stream, false);
-                if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    int best_block = 128, best_per = 0, best_flat = 0;
+    for (int flat = 0; flat < 2 && e == cudaSuccess; ++flat) {
+        for (int block : {128, 256, 512, 768, 1024}) {
+            const int maxper = flat ? flat_blocks_per_sm(b->mdl, block) : batch_blocks_per_sm(b->mdl, block, b->n_max);
+            for (int per : {1, 2, maxper}) {
+                // each distinct (block, blocks per SM) that fits, once
+                if (maxper <= 0 || per > maxper || (per == maxper && maxper <= 2)) continue;
+                float ms = 0.f;
+                for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // first run warms up
+                    e = cudaEventRecord(e0, b->stream);
+                    if (e == cudaSuccess) e = run(b, 2, block, per, flat, b->stream, false);
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                }
+                if (e != cudaSuccess) break;
+                if (ms < best) {
+                    best = ms;
+                    best_block = block;
+                    best_per = per;
+                    best_flat = flat;
+                }
             }
             if (e != cudaSuccess) break;
-            if (ms < best) {
-                best = ms;
-                best_block = block;
-                best_per = per;
-            }
         }
-        if (e != cudaSuccess) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return e;
     b->block = best_block;
     b->per_sm = best_per;
-    tune_cache_put(key, best_block | (best_per << 16));
+    b->flat = best_flat;
+    tune_cache_put(key, best_block | (best_per << 16) | (best_flat << 24));
     return cudaSuccess;
 }
 
@@ -268,10 +285,25 @@ extern "C" sird_status sird_batch_create(int W, const sird_problem* problems, co
         for (int j = 0; j < p.n_obs; ++j) ss += (p.y_D[j] - mean) * (p.y_D[j] - mean);
         b->ss_tot[i] = ss;
     }
+    // flat form: particle pairs of every window, windows longest first (the items a thread owns,
+    // i, i + T, ..., then fall on windows of similar length), pairs (2q, 2q + 1), a last single
+    std::vector<int> by_len(W);
+    std::iota(by_len.begin(), by_len.end(), 0);
+    std::stable_sort(by_len.begin(), by_len.end(), [&](int a, int c) { return wins[a].w.n_obs > wins[c].w.n_obs; });
+    std::vector<int4> items;
+    std::vector<int> n_items_w(W, 0);
+    for (int wi : by_len) {
+        const int M = wins[wi].M;
+        for (int q = 0; 2 * q < M; ++q) items.push_back(make_int4(wi, 2 * q, 2 * q + 1 < M ? 2 * q + 1 : -1, 0));
+        n_items_w[wi] = (M + 1) / 2;
+    }
+    b->n_items = (int)items.size();
     auto r256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
     const size_t bytes = r256(sizeof(BatchWindow) * W) + r256(sizeof(int) * W) + 2 * r256(nobs * sizeof(float)) +
                          r256(nobs * sizeof(double)) + r256(256) + r256(sizeof(BatchOut) * W) +
-                         r256((size_t)sw_total * sizeof(float));
+                         r256((size_t)sw_total * sizeof(float)) + r256(sizeof(int4) * items.size()) +
+                         r256(sizeof(int) * W) + r256(sizeof(unsigned long long) * W) + r256(sizeof(unsigned) * W) +
+                         r256(sizeof(float) * kMaxParams * W) + r256(256);
     cudaError_t e = cudaMalloc(&b->d_mem, bytes);
     auto bail = [&](cudaError_t err, const char* what) {
         std::string m = std::string(what) + ": " + cudaGetErrorString(err);
@@ -294,12 +326,27 @@ extern "C" sird_status sird_batch_create(int W, const sird_problem* problems, co
     b->queue = (unsigned*)take(256);
     b->out = (BatchOut*)take(sizeof(BatchOut) * W);
     b->swarm = (float*)take((size_t)sw_total * sizeof(float));
+    b->items = (int4*)take(sizeof(int4) * items.size());
+    b->n_items_w = (int*)take(sizeof(int) * W);
+    b->fs.gkey = (unsigned long long*)take(sizeof(unsigned long long) * W);
+    b->fs.done = (unsigned*)take(sizeof(unsigned) * W);
+    b->fs.gpos = (float*)take(sizeof(float) * kMaxParams * W);
+    unsigned* words = (unsigned*)take(256);
+    b->fs.bar_count = words;
+    b->fs.bar_gen = words + 1;
+    b->fs.err = words + 2;
+    b->fs.abort = words + 3;
     if ((size_t)(q - (unsigned char*)b->d_mem) > bytes) return bail(cudaErrorInvalidValue, "batch layout");
     e = cudaMemcpyAsync(b->wins, wins.data(), sizeof(BatchWindow) * W, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->order, order.data(), sizeof(int) * W, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->yf, yf.data(), nobs * sizeof(float), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->invy, invy.data(), nobs * sizeof(float), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->yd, yd.data(), nobs * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->n_items_w, n_items_w.data(), sizeof(int) * W, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(words, 0, 256, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bail(e, "uploading the batch");
     e = cudaMallocHost((void**)&b->h_out, sizeof(BatchOut) * W);
@@ -313,6 +360,11 @@ extern "C" sird_status sird_batch_create(int W, const sird_problem* problems, co
     b->obs_bytes = (size_t)((unsigned char*)(b->yd + nobs) - (unsigned char*)b->yf);
     if (c0.block_size) {
         b->block = c0.block_size;
+        b->flat = c0.launch_mode == SIRD_LAUNCH_FLAT ? 1 : 0;
+        if (b->flat && flat_blocks_per_sm(b->mdl, b->block) <= 0) {
+            sird_batch_destroy(b);
+            return berr(SIRD_ERR_ARG, "block_size does not fit the flat form");
+        }
     } else {
         e = autotune(b, work);
         if (e != cudaSuccess) return bail(e, "autotuning");
@@ -346,9 +398,13 @@ extern "C" sird_status sird_batch_set_timing(sird_batch_t b, void* event_begin, 
     return SIRD_OK;
 }
 
+extern "C" int sird_batch_launch_mode(sird_batch_t b) {
+    return b ? (b->flat ? SIRD_LAUNCH_FLAT : SIRD_LAUNCH_WINDOW_PER_BLOCK) : 0;
+}
+
 extern "C" int sird_batch_blocks_per_sm(sird_batch_t b) {
     if (!b) return 0;
-    const int maxper = batch_blocks_per_sm(b->mdl, b->block, b->n_max);
+    const int maxper = b->flat ? flat_blocks_per_sm(b->mdl, b->block) : batch_blocks_per_sm(b->mdl, b->block, b->n_max);
     return (b->per_sm > 0 && b->per_sm < maxper) ? b->per_sm : maxper;
 }
 
@@ -360,7 +416,7 @@ extern "C" sird_status sird_batch_calibrate(sird_batch_t b, sird_result* results
         cudaGraph_t g = nullptr;
         if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e1 = run(b, b->iters, b->block, b->per_sm, b->cap, true, true);
+            cudaError_t e1 = run(b, b->iters, b->block, b->per_sm, b->flat, b->cap, true, true);
             if (e1 == cudaSuccess)
                 e1 = cudaMemcpyAsync(b->h_out, b->out, sizeof(BatchOut) * b->W, cudaMemcpyDeviceToHost, b->cap);
             e = cudaStreamEndCapture(b->cap, &g);
@@ -378,6 +434,12 @@ extern "C" sird_status sird_batch_calibrate(sird_batch_t b, sird_result* results
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return berr(SIRD_ERR_CUDA, std::string("batch run: ") + cudaGetErrorString(e));
+    }
+    if (b->flat) {
+        unsigned err = 0;
+        e = cudaMemcpy(&err, b->fs.err, sizeof(err), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return berr(SIRD_ERR_CUDA, std::string("reading the error word: ") + cudaGetErrorString(e));
+        if (err & kErrTimeout) return berr(SIRD_ERR_TIMEOUT, "a grid barrier wait ran out");
     }
     for (int i = 0; i < b->W; ++i) {
         sird_result& r = results[i];

@@ -157,6 +157,14 @@ __device__ __forceinline__ unsigned long long warp_min_key(unsigned long long ke
     return ((unsigned long long)mhi << 32) | lo;
 }
 
+// The same over the lanes in `mask` (every lane of the mask calls it with the same mask).
+__device__ __forceinline__ unsigned long long masked_min_key(unsigned mask, unsigned long long key) {
+    const uint32_t hi = (uint32_t)(key >> 32);
+    const uint32_t mhi = __reduce_min_sync(mask, hi);
+    const uint32_t lo = __reduce_min_sync(mask, hi == mhi ? (uint32_t)key : 0xFFFFFFFFu);
+    return ((unsigned long long)mhi << 32) | lo;
+}
+
 // FP64 (value, index) pair with NaN as +inf and lowest index on ties.
 struct MinPair64 {
     double f;

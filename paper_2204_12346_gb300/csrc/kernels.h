@@ -147,6 +147,24 @@ struct BatchOut {
     float loss;                 // FP32 global-best loss
     int index;
 };
+// Flat form of the batch: every thread of a co-resident grid owns the particle pairs
+// (w, j0, j1) with item index thread + r * threads; one bounded grid barrier per iteration; the
+// last item of a window to finish an iteration publishes the window's global best.
+struct FlatScratch {
+    unsigned long long* gkey;  // [W] packed (loss, index) minimum of the running iteration
+    unsigned* done;            // [W] items finished in the running iteration
+    float* gpos;               // [W][kMaxParams] global-best position of the last iteration
+    unsigned* bar_count;       // grid barrier arrivals
+    unsigned* bar_gen;         // grid barrier generation
+    unsigned* err;             // error bits (kErrTimeout)
+    unsigned* abort;           // set by a block that gave up waiting
+};
+size_t flat_smem_bytes(const ModelDev& m, int block);
+int flat_blocks_per_sm(const ModelDev& m, int block);
+cudaError_t launch_flat(const BatchWindow* wins, const int* n_items_w, const int4* items, int n_items, int W,
+                        const ModelDev& m, const PsoCoeffs<float>& c, const float* yf_all, const float* invy_all,
+                        float* swarm, const FlatScratch& fs, BatchOut* out, int iters, int block, int grid,
+                        cudaStream_t s);
 size_t batch_smem_bytes(const ModelDev& m, int block, int n_max);
 int batch_blocks_per_sm(const ModelDev& m, int block, int n_max);
 cudaError_t launch_batch(const BatchWindow* wins, const int* order, int W, const ModelDev& m, const PsoCoeffs<float>& c,

@@ -21,7 +21,7 @@ COST_MSE, COST_MXSE, COST_MAE, COST_MAPE = 0, 1, 2, 3
 COSTS = {"mse": COST_MSE, "mxse": COST_MXSE, "mae": COST_MAE, "mape": COST_MAPE}
 BETA_PWC, BETA_RAMP = 0, 1
 FIT_D, FIT_IRD = 0, 1
-LAUNCH_AUTO, LAUNCH_PER_ITER, LAUNCH_PERSISTENT = 0, 1, 2
+LAUNCH_AUTO, LAUNCH_PER_ITER, LAUNCH_PERSISTENT, LAUNCH_WINDOW_PER_BLOCK, LAUNCH_FLAT = 0, 1, 2, 3, 4
 
 # Symbols the header declares (checked by the ABI test).
 EXPORTS = [
@@ -29,7 +29,7 @@ EXPORTS = [
     "sird_pso_num_params", "sird_pso_eval", "sird_pso_init", "sird_pso_step", "sird_pso_calibrate",
     "sird_pso_result", "sird_pso_sync", "sird_pso_get_state", "sird_pso_set_state", "sird_loss_grad",
     "sird_forecast", "sird_pso_calibrate_batched", "sird_pso_set_observations", "sird_pso_set_timing", "sird_pso_launch_mode",
-    "sird_pso_step_f32_noalloc", "sird_pso_topk", "sird_ensemble_bands", "sird_pso_polish", "sird_batch_create", "sird_batch_calibrate", "sird_batch_set_observations",
+    "sird_pso_step_f32_noalloc", "sird_pso_topk", "sird_ensemble_bands", "sird_pso_polish", "sird_batch_create", "sird_batch_calibrate", "sird_batch_set_observations", "sird_batch_launch_mode",
     "sird_batch_block_size", "sird_batch_blocks_per_sm", "sird_batch_destroy", "sird_batch_set_timing",
 ]
 
@@ -111,6 +111,7 @@ def lib():
         L.sird_batch_calibrate.argtypes = [vp, C.POINTER(Result)]
         L.sird_batch_block_size.argtypes = [vp]
         L.sird_batch_blocks_per_sm.argtypes = [vp]
+        L.sird_batch_launch_mode.argtypes = [vp]
         L.sird_batch_set_timing.argtypes = [vp, vp, vp]
         L.sird_batch_set_observations.argtypes = [vp, C.POINTER(C.c_double), C.c_longlong, C.POINTER(C.c_size_t)]
         L.sird_batch_destroy.argtypes = [vp]
@@ -359,7 +360,7 @@ except ImportError:  # the binding still loads for CPU-only tooling
 
 
 def _batch_structs(windows, K, spd, cost, beta_form, fit_I0, iters, lb, ub, log_scale, w, c1, c2, particles, seed,
-                   block_size, objective=FIT_D):
+                   block_size, objective=FIT_D, launch_mode=0):
     W = len(windows)
     keep = []
     pbs = (Problem * W)()
@@ -369,7 +370,7 @@ def _batch_structs(windows, K, spd, cost, beta_form, fit_I0, iters, lb, ub, log_
                               beta_form, cost, objective, win.get("yI"), win.get("yR"))
         cfg, k2 = make_config(int(win.get("particles", particles)), iters, lb, ub, log_scale, w, c1, c2, 32,
                               int(win.get("seed", seed)), int(win.get("stream_id", i)), 0,
-                              block_size if i == 0 else 0, 0)
+                              block_size if i == 0 else 0, launch_mode if i == 0 else 0)
         keep += k1 + k2
         pbs[i] = pb
         cfgs[i] = cfg
@@ -386,11 +387,11 @@ class Batch:
 
     def __init__(self, windows, *, K=1, spd=10, cost=COST_MSE, beta_form=BETA_PWC, fit_I0=True, iters=100,
                  lb=None, ub=None, log_scale=None, w=0.5, c1=0.5, c2=0.5, particles=256, seed=0, block_size=0,
-                 stream=None, objective=FIT_D):
+                 stream=None, objective=FIT_D, launch_mode=0):
         self._lib = lib()
         W = len(windows)
         pbs, cfgs, self._keep = _batch_structs(windows, K, spd, cost, beta_form, fit_I0, iters, lb, ub, log_scale,
-                                               w, c1, c2, particles, seed, block_size, objective)
+                                               w, c1, c2, particles, seed, block_size, objective, launch_mode)
         h = C.c_void_p()
         st = self._lib.sird_batch_create(W, pbs, cfgs, C.c_void_p(current_stream_handle(stream)), C.byref(h))
         if st != OK:
@@ -399,6 +400,7 @@ class Batch:
         self.W = W
         self.block_size = self._lib.sird_batch_block_size(h)
         self.blocks_per_sm = self._lib.sird_batch_blocks_per_sm(h)
+        self.launch_mode = self._lib.sird_batch_launch_mode(h)
 
     def set_timing(self, ev_begin=None, ev_end=None):
         """torch.cuda.Event pair recorded around the batch kernel of every calibrate."""

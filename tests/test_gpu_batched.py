@@ -148,3 +148,33 @@ def test_paper_layout_against_the_oracle_at_initialisation():
             assert res[i]["index"] == pso.gbest_idx
         # the reported loss is the FP64 loss of the reported theta, bit for bit
         assert res[i]["loss"] == O.loss(pb, res[i]["theta"])
+
+
+@pytest.mark.parametrize("block", [128, 256, 768])
+def test_flat_form_equals_one_window_per_block(block):
+    # every window's swarm spread over the grid (one grid barrier per iteration) gives the same
+    # swarms as one window per block: same Philox counters and arithmetic per particle
+    ser = synth.load_series("c3")
+    wins = synth.rolling_window_problems(ser, small_layout())
+    kw = shared()
+    a = sird.Batch(wins, iters=9, block_size=256, **kw).calibrate()
+    fb = sird.Batch(wins, iters=9, block_size=block, launch_mode=sird.LAUNCH_FLAT, **kw)
+    assert fb.launch_mode == sird.LAUNCH_FLAT
+    b = fb.calibrate()
+    b2 = fb.calibrate()  # replayed graph: the barrier and reduction words start fresh
+    for x, y, z in zip(a, b, b2):
+        assert x["index"] == y["index"] == z["index"] and x["loss_search"] == y["loss_search"] == z["loss_search"]
+        assert x["loss"] == y["loss"] and np.array_equal(x["theta"], y["theta"])
+
+
+def test_flat_form_ramp_ird_and_mape():
+    ser = synth.reported_IR(synth.load_series("c3"), 3)
+    lay = {"L": np.array([35, 35, 20, 35]), "M": np.array([3000, 700, 129, 2500]), "T": np.array([0, 90, 200, 414])}
+    wins = synth.rolling_window_problems(ser, lay)
+    lb, ub = configs.bounds_ramp()
+    for obj, cost in ((sird.FIT_D, sird.COST_MAPE), (sird.FIT_IRD, sird.COST_MXSE)):
+        kw = dict(K=1, spd=10, beta_form=sird.BETA_RAMP, lb=lb, ub=ub, seed=4, objective=obj, cost=cost)
+        a = sird.Batch(wins, iters=4, block_size=256, **kw).calibrate()
+        b = sird.Batch(wins, iters=4, block_size=512, launch_mode=sird.LAUNCH_FLAT, **kw).calibrate()
+        for x, y in zip(a, b):
+            assert x["index"] == y["index"] and x["loss"] == y["loss"] and x["loss_search"] == y["loss_search"]
