@@ -142,7 +142,7 @@ cudaError_t autotune(sird_batch* b, long long work) {
     float best = 1e30f;
     int best_block = 128, best_per = 0, best_flat = 0;
     for (int flat = 0; flat < 2 && e == cudaSuccess; ++flat) {
-        for (int block : {128, 256, 512, 768, 1024}) {
+        for (int block : {128, 256, 512, 640, 768, 1024}) {
             const int maxper = flat ? flat_blocks_per_sm(b->mdl, block) : batch_blocks_per_sm(b->mdl, block, b->n_max);
             for (int per : {1, 2, maxper}) {
                 // each distinct (block, blocks per SM) that fits, once

@@ -23,7 +23,7 @@ namespace {
 __host__ __device__ __forceinline__ int pad4(int n) { return (n + 3) & ~3; }
 
 template <int SPD, int COST>
-__global__ void __launch_bounds__(1024) pso_batch_f32(const BatchWindow* __restrict__ wins, const int* __restrict__ order,
+__global__ void __launch_bounds__(768) pso_batch_f32(const BatchWindow* __restrict__ wins, const int* __restrict__ order,
                                                      int W, ModelDev m, PsoCoeffs<float> c, const float* __restrict__ yf_all,
                                                      const float* __restrict__ invy_all, float* __restrict__ swarm,
                                                      unsigned* __restrict__ queue, BatchOut* __restrict__ out, int iters,

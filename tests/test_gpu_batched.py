@@ -72,7 +72,7 @@ def test_batch_block_sizes_agree():
     for a, b in zip(*out):
         assert a["index"] == b["index"] and a["loss"] == b["loss"]
     auto = sird.Batch(wins, iters=8, **shared())
-    assert auto.block_size in (128, 256, 512, 768, 1024) and auto.blocks_per_sm >= 1
+    assert auto.block_size in (128, 256, 512, 640, 768, 1024) and auto.blocks_per_sm >= 1
 
 
 def test_full_512_window_layout_against_the_oracle_at_initialisation():
