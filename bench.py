@@ -352,8 +352,10 @@ def run_batched(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": describe(name), "name": c["name"], "windows": len(wins),
                    "particle_days_per_iteration": pdays, "iterations": c["iters"], "steps_per_day": c["spd"],
-                   "params": len(lb), "block": f"{batch.block_size} threads x {batch.blocks_per_sm} per SM "
-                                               + ("(autotuned)" if args.block == 0 else "(given)"),
+                   "params": len(lb), "block": f"{batch.block_size} threads x {batch.blocks_per_sm} per SM, "
+                                               + ("flat" if batch.launch_mode == sird.LAUNCH_FLAT
+                                                  else "one window per block")
+                                               + (" (autotuned)" if args.block == 0 else " (given)"),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"independent batches x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",

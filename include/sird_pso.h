@@ -313,7 +313,8 @@ sird_status sird_ensemble_bands(const sird_problem* problem, const double* theta
  * finish an iteration publishing its global best; SIRD_ERR_TIMEOUT if a barrier wait runs
  * out).  Both give the same results.  configs[0].block_size = 0 lets the library pick the form,
  * the threads per block and the blocks per SM by timing short trial runs of each candidate
- * (cached in the file named by the environment variable SIRD_TUNE_CACHE when it is set);
+ * (cached in the file named by the environment variable SIRD_TUNE_CACHE when it is set; with
+ * SIRD_TUNE_VERBOSE=1 every candidate's time goes to stderr);
  * otherwise a multiple of 32 in 32..1024 with as many blocks per SM as fit, in the form
  * configs[0].launch_mode names (SIRD_LAUNCH_FLAT, else one window per block).
  */

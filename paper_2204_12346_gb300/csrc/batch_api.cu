@@ -123,8 +123,8 @@ cudaError_t run(sird_batch* b, int iters, int block, int per_sm, int flat, cudaS
     return e;
 }
 
-// Times short trial runs (2 iterations) of each candidate (threads per block, blocks per SM)
-// and keeps the fastest.  One block per SM gives a long window a whole SM; more blocks per SM
+// Times short trial runs (up to 8 iterations) of each candidate (form, threads per block, blocks
+// per SM) and keeps the fastest.  One block per SM gives a long window a whole SM; more blocks per SM
 // hide latency better when windows are short.
 cudaError_t autotune(sird_batch* b, long long work) {
     const std::string key = tune_key(b, work);
@@ -141,21 +141,30 @@ cudaError_t autotune(sird_batch* b, long long work) {
     if (e != cudaSuccess) return e;
     float best = 1e30f;
     int best_block = 128, best_per = 0, best_flat = 0;
+    // long enough that the balance of windows over blocks and the per-iteration costs weigh as
+    // in the full run (two iterations favoured shapes that lose over a hundred)
+    const int trial_iters = std::min(b->iters, 8);
+    const char* vv = std::getenv("SIRD_TUNE_VERBOSE");  // candidate timings to stderr when set
+    const bool verbose = vv && *vv && *vv != '0';
     for (int flat = 0; flat < 2 && e == cudaSuccess; ++flat) {
         for (int block : {128, 256, 512, 640, 768, 1024}) {
             const int maxper = flat ? flat_blocks_per_sm(b->mdl, block) : batch_blocks_per_sm(b->mdl, block, b->n_max);
-            for (int per : {1, 2, maxper}) {
-                // each distinct (block, blocks per SM) that fits, once
-                if (maxper <= 0 || per > maxper || (per == maxper && maxper <= 2)) continue;
+            for (int ci = 0; ci < 3; ++ci) {
+                // each distinct (block, blocks per SM) that fits, once: 1, 2 and the maximum
+                const int per = ci == 0 ? 1 : (ci == 1 ? 2 : maxper);
+                if (maxper <= 0 || per > maxper || (ci == 2 && maxper <= 2)) continue;
                 float ms = 0.f;
                 for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // first run warms up
                     e = cudaEventRecord(e0, b->stream);
-                    if (e == cudaSuccess) e = run(b, 2, block, per, flat, b->stream, false);
+                    if (e == cudaSuccess) e = run(b, trial_iters, block, per, flat, b->stream, false);
                     if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
                     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
                 }
                 if (e != cudaSuccess) break;
+                if (verbose)
+                    std::fprintf(stderr, "sird batch autotune: %s, %d threads x %d per SM: %.3f ms\n",
+                                 flat ? "flat" : "one window per block", block, per, ms);
                 if (ms < best) {
                     best = ms;
                     best_block = block;
