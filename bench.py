@@ -49,14 +49,15 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 # DRAM bytes per launch of the dominant kernel from committed ncu captures, valid only for the
 # kernel sources they were taken on (sha256[:16] of the files listed).
 PROFILED = {
-    "c3": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "3101a04715ddb40a",
-           "traffic_bytes": 13456128, "profile": "profiles/pso_batch_f32_c3.md"},
+    "c3": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "9379b46a831ff993",
+           "traffic_bytes": 14515712, "fma_pipe": 0.6545, "profile": "profiles/pso_batch_f32_c3.md"},
     "c2": {"files": ["pso_persistent.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "ea40821fd8e456d2", "traffic_bytes": 727296, "profile": "profiles/pso_f32_persistent_c2.md"},
-    "c4": {"files": ["adjoint_f32.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "ebec4e291f32b671",
-           "traffic_bytes": 159232, "profile": "profiles/loss_grad_f32_c4.md"},
-    "c5": {"files": ["pso_kernels.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "f3e448c66ebdd01d",
-           "traffic_bytes": 282807040, "profile": "profiles/pso_f32_kernel_c5.md"},
+           "sha": "dae14ee208fa0341", "traffic_bytes": 447232, "fma_pipe": 0.3734,
+           "profile": "profiles/pso_f32_persistent_c2.md"},
+    "c4": {"files": ["adjoint_f32.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "67f2c8704b68013a",
+           "traffic_bytes": 159744, "fma_pipe": 0.1220, "profile": "profiles/loss_grad_f32_c4.md"},
+    "c5": {"files": ["pso_kernels.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "1f090857e67f2ef5",
+           "traffic_bytes": 276251648, "fma_pipe": 0.7472, "profile": "profiles/pso_f32_kernel_c5.md"},
 }
 
 
@@ -68,11 +69,13 @@ def kernel_sources_sha(files) -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
+def profiled_traffic(workload: str, key: str = "traffic_bytes"):
+    """A figure of the committed ncu capture of the workload's dominant kernel (DRAM bytes per
+    launch, or the FMA pipe's active fraction), or None once the kernel sources have changed."""
     p = PROFILED.get(workload)
     if not p or p["sha"] is None or kernel_sources_sha(p["files"]) != p["sha"]:
         return None
-    return p["traffic_bytes"]
+    return p[key]
 
 
 def algorithmic_flops_per_particle_day(spd: int, ramp: bool = False, ird: bool = False) -> int:
@@ -361,6 +364,7 @@ def run_batched(args, rank, world):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic(name),
                      "traffic_source": PROFILED.get(name, {}).get("profile"), "kernel": "pso_batch_f32",
+                     "ncu_fma_pipe_active": profiled_traffic(name, "fma_pipe"),
                      "avg_launch_us": kms * 1e3, "flops_per_launch": flops,
                      "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
         "e2e": {"value": units * args.steps * world / (e2e_total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -575,6 +579,7 @@ def run_single(args, rank, world):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": profiled_traffic(args.workload),
                      "traffic_source": PROFILED.get(args.workload, {}).get("profile"),
+                     "ncu_fma_pipe_active": profiled_traffic(args.workload, "fma_pipe"),
                      "kernel": "pso_f32_persistent" if persistent else ("pso_f64_kernel" if fp64 else "pso_f32_kernel"),
                      "avg_launch_us": kms * 1e3 / iter_launches, "us_per_iteration": kms * 1e3 / c["iters"],
                      "peak_basis": ("nominal FP64 1.25 TFLOP/s" if fp64
@@ -664,6 +669,7 @@ def run_c4(args, rank, world):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic("c4"),
                      "traffic_source": PROFILED["c4"]["profile"],
+                     "ncu_fma_pipe_active": profiled_traffic("c4", "fma_pipe"),
                      "kernel": "loss_grad_f32_kernel", "avg_launch_us": kms * 1e3, "flops_per_launch": flops,
                      "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
         "e2e": {"value": units * args.steps * world / (e2e_total / 1e3), "unit": UNIT,
