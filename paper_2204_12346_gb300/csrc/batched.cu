@@ -151,7 +151,7 @@ constexpr unsigned kFlatSpinLimit = 1u << 22;  // polls of >= 32 ns: a few secon
 
 // Bounded grid barrier; returns false (and raises the abort flag) if a wait ran out or another
 // block gave up.
-__device__ __forceinline__ bool flat_grid_sync(const FlatScratch& fs, int* s_ok) {
+__device__ __forceinline__ bool flat_grid_sync(const FlatScratch& fs, unsigned spin_limit, int* s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
@@ -163,7 +163,7 @@ __device__ __forceinline__ bool flat_grid_sync(const FlatScratch& fs, int* s_ok)
             atomicAdd(fs.bar_gen, 1u);
         } else {
             ok = 0;
-            for (unsigned spin = 0; spin < kFlatSpinLimit; ++spin) {
+            for (unsigned spin = 0; spin < spin_limit; ++spin) {
                 if (__ldcg(fs.bar_gen) != gen) {
                     ok = 1;
                     break;
@@ -189,7 +189,8 @@ __global__ void __launch_bounds__(768) pso_flat_f32(const BatchWindow* __restric
                                                     const int4* __restrict__ items, int n_items, ModelDev m,
                                                     PsoCoeffs<float> c, const float* __restrict__ yf_all,
                                                     const float* __restrict__ invy_all, float* __restrict__ swarm,
-                                                    FlatScratch fs, BatchOut* __restrict__ out, int iters) {
+                                                    FlatScratch fs, BatchOut* __restrict__ out, int iters,
+                                                    unsigned spin_limit) {
     extern __shared__ float smem[];
     __shared__ int s_ok;
     const int B = blockDim.x, B2 = 2 * B, tid = threadIdx.x, P = m.P;
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(768) pso_flat_f32(const BatchWindow* __restric
                 }
             }
         }
-        if (it < iters && !flat_grid_sync(fs, &s_ok)) return;
+        if (it < iters && !flat_grid_sync(fs, spin_limit, &s_ok)) return;
     }
 }
 
@@ -423,7 +424,7 @@ cudaError_t launch_flat(const BatchWindow* wins, const int* n_items_w, const int
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             e = cudaLaunchKernelEx(&cfg, kern, wins, n_items_w, items, n_items, m, c, yf_all, invy_all, swarm, fs,
-                                   out, iters);
+                                   out, iters, bounded_wait_limit(kFlatSpinLimit));
         }
     }));
     return e != cudaSuccess ? e : cudaGetLastError();

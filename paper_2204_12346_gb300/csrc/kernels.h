@@ -147,6 +147,11 @@ struct BatchOut {
     float loss;                 // FP32 global-best loss
     int index;
 };
+// Poll limit of a device-side bounded wait: dflt, or the positive value of the environment
+// variable SIRD_WAIT_LIMIT (read at each launch; a small value makes the waits run out, which
+// is how the timeout path is tested).
+unsigned bounded_wait_limit(unsigned dflt);
+
 // Flat form of the batch: every thread of a co-resident grid owns the particle pairs
 // (w, j0, j1) with item index thread + r * threads; one bounded grid barrier per iteration; the
 // last item of a window to finish an iteration publishes the window's global best.

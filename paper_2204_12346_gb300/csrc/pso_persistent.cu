@@ -41,7 +41,8 @@ __device__ __forceinline__ unsigned long long tagged(unsigned tag, uint32_t v) {
 template <int SPD, int COST>
 __global__ void __launch_bounds__(1024) pso_f32_persistent(WindowDev w, ModelDev m, ObsDev o, PsoCoeffs<float> c,
                                                             SwarmDev<float> sw, ReduceScratch r,
-                                                            ExchangeSlot* __restrict__ slots, int iter0, int n_iters) {
+                                                            ExchangeSlot* __restrict__ slots, int iter0, int n_iters,
+                                                            unsigned spin_limit) {
     extern __shared__ float smem[];
     __shared__ unsigned long long wk[32];
     __shared__ int s_flag;
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(1024) pso_f32_persistent(WindowDev w, ModelDev
             unsigned long long best = ~0ull;
             int bblk = 0;
             bool ok = false;
-            for (unsigned spin = 0; spin < kSpinLimit; ++spin) {
+            for (unsigned spin = 0; spin < spin_limit; ++spin) {
                 bool ready = true;
                 for (int b = tid; b < G; b += 32) {
                     const ExchangeSlot* sl = row + b;
@@ -292,7 +293,8 @@ cudaError_t launch_pso_f32_persistent(const WindowDev& w, const ModelDev& m, con
             attr[0].val.cooperative = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            e = cudaLaunchKernelEx(&cfg, kern, w, m, o, c, sw, r, slots, iter0, n_iters);
+            e = cudaLaunchKernelEx(&cfg, kern, w, m, o, c, sw, r, slots, iter0, n_iters,
+                                   bounded_wait_limit(kSpinLimit));
         }
     }));
     return e;

@@ -1,5 +1,6 @@
 // sird_pso_api.cu -- the C ABI (include/sird_pso.h): validation, device memory, graphs.
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -142,6 +143,13 @@ struct sird_pso {
         out->iters_done = iter;
     }
 };
+
+unsigned sird::bounded_wait_limit(unsigned dflt) {
+    const char* v = std::getenv("SIRD_WAIT_LIMIT");
+    if (!v || !*v) return dflt;
+    const long long x = std::atoll(v);
+    return x > 0 && x < (1LL << 31) ? (unsigned)x : dflt;
+}
 
 // ---------------------------------------------------------------- validation
 
