@@ -14,7 +14,7 @@ single 60-day window: the plain FP64 swarm (4096 particles, 1000 iterations) set
 L_ref; the FP32 swarm followed by the L-BFGS polish (FP32 trials and adjoint gradient, FP64
 re-scoring of the result) must reach (1 + 1e-6) L_ref.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c3|c2|c1|c5]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload batch512|window60|plain64|gradient90|swarm2p20|paper|paper_ird|stability]
 
 With --gpus N > 1 (one process per GPU under torchrun) every rank calibrates its own batch of
 windows (its own Philox stream words); there is no data-path collective, and value = all ranks'
@@ -49,15 +49,15 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 # DRAM bytes per launch of the dominant kernel from committed ncu captures, valid only for the
 # kernel sources they were taken on (sha256[:16] of the files listed).
 PROFILED = {
-    "c3": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "9379b46a831ff993",
-           "traffic_bytes": 14515712, "fma_pipe": 0.6545, "profile": "profiles/pso_batch_f32_c3.md"},
-    "c2": {"files": ["pso_persistent.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"],
+    "batch512": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "9379b46a831ff993",
+           "traffic_bytes": 14515712, "fma_pipe": 0.6545, "profile": "profiles/pso_batch_f32_batch512.md"},
+    "window60": {"files": ["pso_persistent.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"],
            "sha": "dae14ee208fa0341", "traffic_bytes": 447232, "fma_pipe": 0.3734,
-           "profile": "profiles/pso_f32_persistent_c2.md"},
-    "c4": {"files": ["adjoint_f32.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "67f2c8704b68013a",
-           "traffic_bytes": 159744, "fma_pipe": 0.1220, "profile": "profiles/loss_grad_f32_c4.md"},
-    "c5": {"files": ["pso_kernels.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "1f090857e67f2ef5",
-           "traffic_bytes": 276251648, "fma_pipe": 0.7472, "profile": "profiles/pso_f32_kernel_c5.md"},
+           "profile": "profiles/pso_f32_persistent_window60.md"},
+    "gradient90": {"files": ["adjoint_f32.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "67f2c8704b68013a",
+           "traffic_bytes": 159744, "fma_pipe": 0.1220, "profile": "profiles/loss_grad_f32_gradient90.md"},
+    "swarm2p20": {"files": ["pso_kernels.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "1f090857e67f2ef5",
+           "traffic_bytes": 276251648, "fma_pipe": 0.7472, "profile": "profiles/pso_f32_kernel_swarm2p20.md"},
 }
 
 
@@ -103,7 +103,7 @@ def single_window(name: str):
     return c, ser, y, lb, ub
 
 
-BATCHED = ("c3", "paper", "paper_ird")
+BATCHED = ("batch512", "paper", "paper_ird")
 
 # The paper's own timing (context only: other hardware, real data, time per PSO iteration of one
 # window with 10000 particles on F_IRD^MXSE): 2.176 s on a TITAN V, 55.655 s on a Xeon E5-2650 v4.
@@ -136,12 +136,12 @@ def batch_windows(name: str, seed_offset: int = 0):
 
 def describe(name: str) -> str:
     return {
-        "c3": ("batched FP32: 512 rolling windows of 21..90 days cut from a 450-day series, 256..2048 particles "
+        "batch512": ("batched FP32: 512 rolling windows of 21..90 days cut from a 450-day series, 256..2048 particles "
                "per window, beta piecewise constant over 6 segments (9 params), log-uniform PSO box, 100 iterations, "
                "dt=0.1, one persistent launch in a CUDA graph, autotuned block shape, FP64 re-evaluation per window"),
-        "c2": ("single window FP32 + Kahan loss: 60 days, beta piecewise constant over 4 segments (7 params), "
+        "window60": ("single window FP32 + Kahan loss: 60 days, beta piecewise constant over 4 segments (7 params), "
                "log-uniform PSO box, 4096 particles, 1000 iterations, dt=0.1, FP64 re-evaluation of the 32 best"),
-        "c1": "plain method FP64: constant beta, gamma, mu + I0, 30 days, 64 particles, 200 iterations, dt=0.1",
+        "plain64": "plain method FP64: constant beta, gamma, mu + I0, 30 days, 64 particles, 200 iterations, dt=0.1",
         "paper": ("the paper's setting, batched FP32: ramp beta(t) (beta1, beta2, t1, t2, gamma, mu, I0), 139 "
                   "rolling windows of 35 days shifted by 3 days over a 450-day series, 10000 particles per window, "
                   "linear PSO box, 100 iterations, dt=0.1, one persistent launch, FP64 re-evaluation per window"),
@@ -152,10 +152,10 @@ def describe(name: str) -> str:
                       "(independent Philox streams, 10000 particles, ramp beta(t), F_IRD^MXSE, 100 iterations) in "
                       "one batched launch, then per day the median and 95/90/50% bands of beta, R0, S, I, R, D over "
                       "the window and a 21-day extension (FP64 ensemble integration, on-device sort)"),
-        "c4": ("gradient FP32: loss + exact gradient (discrete adjoint of the compensated FP32 trajectory, "
+        "gradient90": ("gradient FP32: loss + exact gradient (discrete adjoint of the compensated FP32 trajectory, "
                "day-start checkpoints) of the 4096 personal bests of a calibrated swarm, 90 days, 4 beta segments "
                "(7 params), dt=0.05"),
-        "c5": ("large FP32: 2^20 particles, 10 segments (13 params), 120 days, dt=0.05, 100 iterations, FP64 "
+        "swarm2p20": ("large FP32: 2^20 particles, 10 segments (13 params), 120 days, dt=0.05, 100 iterations, FP64 "
                "re-evaluation of the 32 best, 20 FP32 L-BFGS iterations (adjoint gradient) on the 32 best, then the "
                "1024 best personal bests forecast 14 held-out days (FP64)"),
     }[name]
@@ -274,7 +274,7 @@ def s_to_calibrate() -> dict:
 
     from paper_2204_12346_gb300 import sird
 
-    c, ser, y, lb, ub = single_window("c2")
+    c, ser, y, lb, ub = single_window("60d")
     kw = dict(K=c["K"], spd=c["spd"], particles=c["M"], iters=c["iters"], lb=lb, ub=ub,
               log_scale=[1] * len(lb), seed=c["seed"])
     c64 = sird.Calibrator(y, ser["N"], precision=64, **kw)
@@ -382,7 +382,7 @@ def run_batched(args, rank, world):
             "paper_gpu_s_per_pso_iteration": PAPER_GPU_S_PER_ITERATION,
             "note": "the paper's figure is one window's PSO iteration (10000 particles, F_IRD^MXSE, real data) on a "
                     "TITAN V with the cost on the CPU; ours is the batch's wall time spread over its window-iterations"}
-    if not args.no_s2c and name == "c3":
+    if not args.no_s2c and name == "batch512":
         out["s_to_calibrate"] = s_to_calibrate()
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(name, budget_s=args.cpu_budget)
@@ -606,7 +606,7 @@ def run_single(args, rank, world):
     return out
 
 
-def run_c4(args, rank, world):
+def run_gradient(args, rank, world):
     """Gradient workload: loss and exact gradient (discrete adjoint, FP32 compensated trajectory,
     day-start checkpoints) of every personal best of a calibrated 4096-particle FP32 swarm on the
     90-day window at dt = 0.05 day.  One step = one gradient launch over all particles.  The FP64
@@ -615,7 +615,7 @@ def run_c4(args, rank, world):
 
     from paper_2204_12346_gb300 import sird
 
-    c, ser, y, lb, ub = single_window("c4")
+    c, ser, y, lb, ub = single_window("90d")
     stream = torch.cuda.Stream()
     P = len(lb)
     with torch.cuda.stream(stream):
@@ -662,14 +662,14 @@ def run_c4(args, rank, world):
         "metric": METRIC, "value": units * args.steps * world / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": describe("c4"), "name": c["name"], "particles": M, "days": L, "steps_per_day": spd,
+        "config": {"workload": describe("gradient90"), "name": c["name"], "particles": M, "days": L, "steps_per_day": spd,
                    "params": P, "checkpoints": "every day start", "units": "particle-days of loss + gradient",
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic("c4"),
-                     "traffic_source": PROFILED["c4"]["profile"],
-                     "ncu_fma_pipe_active": profiled_traffic("c4", "fma_pipe"),
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic("gradient90"),
+                     "traffic_source": PROFILED["gradient90"]["profile"],
+                     "ncu_fma_pipe_active": profiled_traffic("gradient90", "fma_pipe"),
                      "kernel": "loss_grad_f32_kernel", "avg_launch_us": kms * 1e3, "flops_per_launch": flops,
                      "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
         "e2e": {"value": units * args.steps * world / (e2e_total / 1e3), "unit": UNIT,
@@ -784,7 +784,7 @@ def cpu_baseline(name: str, budget_s: float = 15.0, iters_cap: int | None = None
             units += w["particles"] * w["L"] * 2
             done += 1
         sample = f"{done} repetitions x (init + 1 PSO iteration), 10000 particles each"
-    elif name == "c4":
+    elif name == "gradient90":
         c, ser, y, lb, ub = single_window(name)
         pb = O.Problem(yD=y, N=ser["N"], K=c["K"], spd=c["spd"])
         rng = np.random.default_rng(c["seed"])
@@ -843,8 +843,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c3", "c2", "c1", "c4", "c5", "paper", "paper_ird", "stability"],
-                    default="c3")
+    ap.add_argument("--workload", choices=["batch512", "window60", "plain64", "gradient90", "swarm2p20", "paper", "paper_ird", "stability"],
+                    default="batch512")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-units", type=int, default=2,
                     help="reference arm: windows (batched) or PSO iterations (single window) per step")
@@ -869,8 +869,8 @@ def main():
             out = run_reference(args, rank, world)
         elif args.workload in BATCHED:
             out = run_batched(args, rank, world)
-        elif args.workload == "c4":
-            out = run_c4(args, rank, world)
+        elif args.workload == "gradient90":
+            out = run_gradient(args, rank, world)
         elif args.workload == "stability":
             out = run_stability(args, rank, world)
         else:

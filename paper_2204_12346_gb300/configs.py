@@ -32,35 +32,35 @@ def bounds_ramp(t_max: float = 28.0):
 
 CONFIGS = {
     # Plain method in FP64: constant rates (K = 1) plus I0, 30 days, dt = 0.1 day.
-    "c1": dict(name="c1-plain-fp64", series="c1", K=1, days=30, spd=10, M=64, iters=200,
+    "plain64": dict(name="plain-fp64-30d-64-particles", series="30d", K=1, days=30, spd=10, M=64, iters=200,
                precision=64, log=False, seed=0, reeval_topk=0),
     # One window in FP32 with compensated loss; 4 beta segments (7 params); log-uniform box.
-    "c2": dict(name="c2-single-window-fp32", series="c2", K=4, days=60, spd=10, M=4096, iters=1000,
+    "window60": dict(name="single-window-60d-4096-particles-fp32", series="60d", K=4, days=60, spd=10, M=4096, iters=1000,
                precision=32, log=True, seed=0, reeval_topk=32),
     # 512 rolling windows of uneven length and swarm size, 6 beta segments (9 params).
-    "c3": dict(name="c3-batched-512-windows-fp32", series="c3", K=6, spd=10, W=512, iters=100,
+    "batch512": dict(name="batched-512-windows-fp32", series="450d", K=6, spd=10, W=512, iters=100,
                precision=32, log=True, seed=0, L_min=21, L_max=90, M_min=256, M_max=2048, delta=3),
     # Adjoint gradient over a 90-day window at dt = 0.05 day, checkpoints every 16 steps.
-    "c4": dict(name="c4-adjoint-90d", series="c4", K=4, days=90, spd=20, M=4096, iters=200,
+    "gradient90": dict(name="gradient-90d-4096-points", series="90d", K=4, days=90, spd=20, M=4096, iters=200,
                precision=32, log=True, seed=0, ckpt=16, polish_topk=32, reeval_topk=32),
     # The paper's own setting (Sec. 3.1-3.3): ramp beta(t), 139 rolling windows of tau = 35 days
     # shifted by delta = 3 days over the 450-day series, 10000 particles, 100 iterations.
-    "paper": dict(name="paper-ramp-139-windows", series="c3", beta_form="ramp", W=139, iters=100, spd=10,
+    "paper": dict(name="paper-ramp-139-windows", series="450d", beta_form="ramp", W=139, iters=100, spd=10,
                   precision=32, log=False, seed=0, L_min=35, L_max=35, M_min=10000, M_max=10000, delta=3),
     # The same with the paper's representative objective F_IRD^MXSE (Sec. 3.1, the cost its
     # timings are quoted on): reported I and R series alongside D.
-    "paper_ird": dict(name="paper-ramp-139-windows-F_IRD-MXSE", series="c3", beta_form="ramp", objective="ird",
+    "paper_ird": dict(name="paper-ramp-139-windows-F_IRD-MXSE", series="450d", beta_form="ramp", objective="ird",
                       cost="mxse", W=139, iters=100, spd=10, precision=32, log=False, seed=0, L_min=35, L_max=35,
                       M_min=10000, M_max=10000, delta=3),
     # The stability test of Sec. 4.2: two windows (tau = 35 days) each calibrated 1000 times with
     # independent random streams (10000 particles, ramp beta(t), F_IRD^MXSE) in one batched
     # launch, then per day the median and 95/90/50% bands of beta, R0, S, I, R, D over the
     # window and a 21-day extension.
-    "stability": dict(name="stability-2x1000-repetitions", series="c3", beta_form="ramp", objective="ird",
+    "stability": dict(name="stability-2x1000-repetitions", series="450d", beta_form="ramp", objective="ird",
                       cost="mxse", windows_T=(120, 330), L=35, reps=1000, M=10000, iters=100, spd=10,
                       precision=32, log=False, seed=0, horizon=21, fractions=(0.95, 0.9, 0.5)),
     # 2^20 particles, 10 segments, 120 days at dt = 0.05 day, then a 14-day forecast.
-    "c5": dict(name="c5-large-2^20", series="c5", K=10, days=120, spd=20, M=1 << 20, iters=100,
+    "swarm2p20": dict(name="swarm-2^20-particles-120d", series="134d", K=10, days=120, spd=20, M=1 << 20, iters=100,
                precision=32, log=True, seed=0, horizon=14, forecast_topk=1024, reeval_topk=32, polish_topk=32,
                polish_iters=20),
 }

@@ -36,8 +36,8 @@ def gpu_loss_grad(cal, th, ckpt=16):
 @pytest.mark.parametrize("ckpt", [1, 7, 16, 64])
 def test_adjoint_f64_bit_exact_c4_window(cost, ckpt):
     # the differentiation configuration: 90 days at dt = 0.05 (1800 steps), 4 segments + gamma, mu, I0
-    y, N, _, _ = window("c4")
-    th = np.concatenate([near_truth("c4", 4, 40, 1), box_thetas(4, 24, 2)])
+    y, N, _, _ = window("90d")
+    th = np.concatenate([near_truth("90d", 4, 40, 1), box_thetas(4, 24, 2)])
     cal = sird.Calibrator(y, N, K=4, spd=20, cost=sird.COSTS[cost], particles=32, iters=1, lb=[1e-3] * 7,
                           ub=[1e6] * 7, precision=64)
     L, G, GU = gpu_loss_grad(cal, th, ckpt)
@@ -50,7 +50,7 @@ def test_adjoint_f64_bit_exact_c4_window(cost, ckpt):
 
 
 def test_adjoint_f64_ramp_form_bit_exact():
-    y, N, _, _ = window("c2", 40)
+    y, N, _, _ = window("60d", 40)
     rng = np.random.default_rng(6)
     M = 64
     th = np.column_stack([rng.uniform(0.1, 0.4, M), rng.uniform(0.1, 0.4, M), rng.uniform(1, 39, M),
@@ -67,8 +67,8 @@ def test_adjoint_f64_ramp_form_bit_exact():
 
 def test_adjoint_matches_central_differences_of_gpu_loss():
     # central differences (h = 1e-6 relative) of the GPU's own FP64 loss
-    y, N, _, _ = window("c4")
-    th = near_truth("c4", 4, 8, 3)
+    y, N, _, _ = window("90d")
+    th = near_truth("90d", 4, 8, 3)
     cal = sird.Calibrator(y, N, K=4, spd=20, particles=32, iters=1, lb=[1e-3] * 7, ub=[1e6] * 7, precision=64)
     _, G, _ = gpu_loss_grad(cal, th, 16)
     P = th.shape[1]
@@ -87,8 +87,8 @@ def test_adjoint_matches_central_differences_of_gpu_loss():
 
 
 def test_autograd_function_wraps_the_adjoint():
-    y, N, _, _ = window("c2")
-    th = near_truth("c2", 4, 5, 4)
+    y, N, _, _ = window("60d")
+    th = near_truth("60d", 4, 5, 4)
     cal = sird.Calibrator(y, N, K=4, spd=10, particles=32, iters=1, lb=[1e-3] * 7, ub=[1e6] * 7, precision=64)
     T = torch.from_numpy(np.ascontiguousarray(th.T)).cuda().requires_grad_(True)
     loss = sird.SirdLoss.apply(cal, T)
@@ -99,7 +99,7 @@ def test_autograd_function_wraps_the_adjoint():
 
 
 def test_polish_never_worsens_and_reports_its_own_fp64_loss():
-    y, N, _, _ = window("c2")
+    y, N, _, _ = window("60d")
     lb, ub = [1e-3] * 4 + [1e-3, 1e-5, 1.0], [2.0] * 4 + [1.0, 0.1, 1e6]
     cal = sird.Calibrator(y, N, K=4, spd=10, particles=512, iters=40, lb=lb, ub=ub, log_scale=[1] * 7,
                           precision=32, reeval_topk=8, seed=2)
@@ -171,8 +171,8 @@ def check_f32_gradient(pb, th, L, G, E, cost="mse"):
 
 @pytest.mark.parametrize("cost", ["mse", "mxse", "mae", "mape"])
 def test_adjoint_f32_c4_window(cost):
-    y, N, _, _ = window("c4")
-    th = f32(np.concatenate([near_truth("c4", 4, 40, 1), box_thetas(4, 24, 2)]))
+    y, N, _, _ = window("90d")
+    th = f32(np.concatenate([near_truth("90d", 4, 40, 1), box_thetas(4, 24, 2)]))
     cal = sird.Calibrator(y, N, K=4, spd=20, cost=sird.COSTS[cost], particles=32, iters=1, lb=[1e-3] * 7,
                           ub=[1e6] * 7, precision=32)
     L, G, GU, E = f32_loss_grad(cal, th)
@@ -183,8 +183,8 @@ def test_adjoint_f32_c4_window(cost):
 @pytest.mark.parametrize("spd,K,days", [(10, 4, 60), (7, 3, 31), (1, 2, 45)])
 def test_adjoint_f32_other_step_counts(spd, K, days):
     # spd 10 (unrolled day), 7 and 1 (generic day loop); K segments not aligned with days
-    y, N, _, _ = window("c2", days)
-    th = f32(np.concatenate([near_truth("c2", K, 16, 5), box_thetas(K, 16, 6)]))
+    y, N, _, _ = window("60d", days)
+    th = f32(np.concatenate([near_truth("60d", K, 16, 5), box_thetas(K, 16, 6)]))
     cal = sird.Calibrator(y, N, K=K, spd=spd, particles=32, iters=1, lb=[1e-3] * (K + 3), ub=[1e6] * (K + 3),
                           precision=32)
     L, G, _, E = f32_loss_grad(cal, th)
@@ -192,7 +192,7 @@ def test_adjoint_f32_other_step_counts(spd, K, days):
 
 
 def test_adjoint_f32_ramp_form():
-    y, N, _, _ = window("c2", 40)
+    y, N, _, _ = window("60d", 40)
     rng = np.random.default_rng(7)
     M = 48
     th = f32(np.column_stack([rng.uniform(0.1, 0.4, M), rng.uniform(0.1, 0.4, M), rng.uniform(1, 39, M),
@@ -206,7 +206,7 @@ def test_adjoint_f32_ramp_form():
 
 def test_adjoint_f32_ragged_particle_count_and_leading_dimension():
     # M not a multiple of the block, theta rows padded (ld > M)
-    y, N, _, _ = window("c4")
+    y, N, _, _ = window("90d")
     th = f32(box_thetas(4, 131, 9))
     cal = sird.Calibrator(y, N, K=4, spd=20, particles=32, iters=1, lb=[1e-3] * 7, ub=[1e6] * 7, precision=32)
     T = torch.zeros(7, 160, dtype=torch.float32, device="cuda")
@@ -218,7 +218,7 @@ def test_adjoint_f32_ragged_particle_count_and_leading_dimension():
 
 
 def test_polish_f32_improves_and_reports_fp64_loss():
-    y, N, _, _ = window("c2")
+    y, N, _, _ = window("60d")
     lb, ub = [1e-3] * 4 + [1e-3, 1e-5, 1.0], [2.0] * 4 + [1.0, 0.1, 1e6]
     cal = sird.Calibrator(y, N, K=4, spd=10, particles=512, iters=40, lb=lb, ub=ub, log_scale=[1] * 7,
                           precision=32, reeval_topk=8, seed=2)

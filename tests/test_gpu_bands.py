@@ -21,7 +21,7 @@ def near(th, M, seed, spread=0.08):
 
 @pytest.mark.parametrize("k", [1, 2, 7, 1000, 4096])
 def test_bands_bit_exact_pwc(k):
-    s = synth.load_series("c2")
+    s = synth.load_series("60d")
     th = near(np.asarray(s["theta_true"]), k, k)
     got = sird.ensemble_bands(s["yD"], s["N"], th, 21, K=4, spd=10)
     want = O.ensemble_bands(O.Problem(yD=s["yD"], N=s["N"], K=4, spd=10), th, 21)
@@ -30,7 +30,7 @@ def test_bands_bit_exact_pwc(k):
 
 
 def test_bands_bit_exact_ramp_with_fixed_I0_and_R0():
-    s = synth.load_series("c2")
+    s = synth.load_series("60d")
     y = s["yD"][:36]
     rng = np.random.default_rng(3)
     M = 300
@@ -47,7 +47,7 @@ def test_bands_bit_exact_ramp_with_fixed_I0_and_R0():
 def test_repeated_calibrations_of_one_window_as_one_batch():
     # the stability test of Sec. 4.2: one window calibrated many times (distinct Philox streams)
     # in one batched launch, then the ensemble's bands with a 21-day extension
-    s = synth.load_series("c3")
+    s = synth.load_series("450d")
     T, L, reps = 120, 35, 64
     lay = {"L": np.full(reps, L), "M": np.full(reps, 512), "T": np.full(reps, T)}
     wins = synth.rolling_window_problems(s, lay)

@@ -28,7 +28,7 @@ def shared(K=6):
 
 
 def test_batch_windows_match_single_window_calibrations():
-    ser = synth.load_series("c3")
+    ser = synth.load_series("450d")
     wins = synth.rolling_window_problems(ser, small_layout())
     kw = shared()
     batch = sird.Batch(wins, iters=15, **kw)
@@ -46,7 +46,7 @@ def test_batch_windows_match_single_window_calibrations():
 
 def test_batch_set_observations_equals_a_fresh_batch():
     # the next day's data on the same windows (each window shifted by one day, same lengths)
-    ser = synth.load_series("c3")
+    ser = synth.load_series("450d")
     lay = small_layout()
     wins = synth.rolling_window_problems(ser, lay)
     nxt = synth.rolling_window_problems(ser, dict(lay, T=lay["T"] + 1))
@@ -66,7 +66,7 @@ def test_batch_set_observations_equals_a_fresh_batch():
 
 
 def test_batch_block_sizes_agree():
-    ser = synth.load_series("c3")
+    ser = synth.load_series("450d")
     wins = synth.rolling_window_problems(ser, small_layout())
     out = [sird.Batch(wins, iters=8, block_size=b, **shared()).calibrate() for b in (64, 256)]
     for a, b in zip(*out):
@@ -77,8 +77,8 @@ def test_batch_block_sizes_agree():
 
 def test_full_512_window_layout_against_the_oracle_at_initialisation():
     # the batched configuration's layout: 512 windows, 21..90 days, 256..2048 particles, 6 segments
-    c = configs.CONFIGS["c3"]
-    ser = synth.load_series("c3")
+    c = configs.CONFIGS["batch512"]
+    ser = synth.load_series("450d")
     lay = synth.rolling_windows(W=c["W"], L_min=c["L_min"], L_max=c["L_max"], M_min=c["M_min"], M_max=c["M_max"],
                                 delta=c["delta"], seed=c["seed"])
     wins = synth.rolling_window_problems(ser, lay)
@@ -106,7 +106,7 @@ def ramp_shared():
 def test_batch_ramp_windows_match_single_window_calibrations():
     # the paper's ramp form on a linear box; swarms beyond 2 x block size (several passes per
     # thread, packed pairs and single particles)
-    ser = synth.load_series("c3")
+    ser = synth.load_series("450d")
     lay = {"L": np.array([35, 35, 20, 35]), "M": np.array([3000, 700, 129, 2500]), "T": np.array([0, 90, 200, 414])}
     wins = synth.rolling_window_problems(ser, lay)
     kw = ramp_shared()
@@ -154,7 +154,7 @@ def test_paper_layout_against_the_oracle_at_initialisation():
 def test_flat_form_equals_one_window_per_block(block):
     # every window's swarm spread over the grid (one grid barrier per iteration) gives the same
     # swarms as one window per block: same Philox counters and arithmetic per particle
-    ser = synth.load_series("c3")
+    ser = synth.load_series("450d")
     wins = synth.rolling_window_problems(ser, small_layout())
     kw = shared()
     a = sird.Batch(wins, iters=9, block_size=256, **kw).calibrate()
@@ -168,7 +168,7 @@ def test_flat_form_equals_one_window_per_block(block):
 
 
 def test_flat_form_ramp_ird_and_mape():
-    ser = synth.reported_IR(synth.load_series("c3"), 3)
+    ser = synth.reported_IR(synth.load_series("450d"), 3)
     lay = {"L": np.array([35, 35, 20, 35]), "M": np.array([3000, 700, 129, 2500]), "T": np.array([0, 90, 200, 414])}
     wins = synth.rolling_window_problems(ser, lay)
     lb, ub = configs.bounds_ramp()

@@ -19,7 +19,7 @@ def _dev():
 @pytest.mark.parametrize("precision", [64, 32])
 def test_forecast_pwc_matches_oracle(precision):
     # the largest configuration's window: 120 days, 10 segments, dt = 0.05, 14 days ahead
-    y, N, _, _ = window("c5", 120)
+    y, N, _, _ = window("134d", 120)
     th = box_thetas(10, 257, 77)
     th[:, :10] = np.clip(th[:, :10], 0.05, 0.6)  # keep trajectories from running out of susceptibles
     got = sird.forecast(y, N, th, 14, K=10, spd=20, precision=precision)
@@ -33,7 +33,7 @@ def test_forecast_pwc_matches_oracle(precision):
 
 @pytest.mark.parametrize("precision", [64, 32])
 def test_forecast_ramp_and_fixed_I0(precision):
-    y, N, _, _ = window("c2", 35)
+    y, N, _, _ = window("60d", 35)
     rng = np.random.default_rng(4)
     M = 100
     th = f32(np.column_stack([rng.uniform(0.05, 0.5, M), rng.uniform(0.05, 0.5, M), rng.uniform(0, 35, M),
@@ -48,7 +48,7 @@ def test_forecast_ramp_and_fixed_I0(precision):
 
 
 def test_topk_export_orders_personal_bests():
-    y, N, _, _ = window("c2")
+    y, N, _, _ = window("60d")
     lb, ub = log_box(4)
     zlb, zub = f32(np.log(lb)), f32(np.log(ub))
     M = 3000

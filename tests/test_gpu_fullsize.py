@@ -41,8 +41,8 @@ def check_swarm(cal, pb, logd, n_sample, seed):
 
 
 def test_single_window_4096_particles_1000_iterations():
-    c = configs.CONFIGS["c2"]
-    s = synth.load_series("c2")
+    c = configs.CONFIGS["window60"]
+    s = synth.load_series("60d")
     y = s["yD"][: c["days"] + 1]
     lb, ub = configs.bounds(c["K"], True)
     cal = sird.Calibrator(y, s["N"], K=c["K"], spd=c["spd"], particles=c["M"], iters=c["iters"], lb=lb, ub=ub,
@@ -58,8 +58,8 @@ def test_single_window_4096_particles_1000_iterations():
 
 
 def test_batched_512_windows_100_iterations():
-    c = configs.CONFIGS["c3"]
-    ser = synth.load_series("c3")
+    c = configs.CONFIGS["batch512"]
+    ser = synth.load_series("450d")
     lay = synth.rolling_windows(W=c["W"], L_min=c["L_min"], L_max=c["L_max"], M_min=c["M_min"], M_max=c["M_max"],
                                 delta=c["delta"], seed=c["seed"])
     wins = synth.rolling_window_problems(ser, lay)
@@ -77,8 +77,8 @@ def test_batched_512_windows_100_iterations():
 
 
 def test_gradient_4096_personal_bests():
-    c = configs.CONFIGS["c4"]
-    s = synth.load_series("c4")
+    c = configs.CONFIGS["gradient90"]
+    s = synth.load_series("90d")
     y = s["yD"][: c["days"] + 1]
     lb, ub = configs.bounds(c["K"], True)
     cal = sird.Calibrator(y, s["N"], K=c["K"], spd=c["spd"], particles=c["M"], iters=c["iters"], lb=lb, ub=ub,
@@ -100,8 +100,8 @@ def test_gradient_4096_personal_bests():
 
 
 def test_large_swarm_and_forecast():
-    c = configs.CONFIGS["c5"]
-    s = synth.load_series("c5")
+    c = configs.CONFIGS["swarm2p20"]
+    s = synth.load_series("134d")
     y = s["yD"][: c["days"] + 1]
     lb, ub = configs.bounds(c["K"], True)
     cal = sird.Calibrator(y, s["N"], K=c["K"], spd=c["spd"], particles=c["M"], iters=c["iters"], lb=lb, ub=ub,

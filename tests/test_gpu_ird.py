@@ -31,7 +31,7 @@ def ramp_thetas(M, seed, days):
 
 
 def setup(cost, form, days=60, spd=10):
-    yD, yI, yR, N = ird_series("c2", days)
+    yD, yI, yR, N = ird_series("60d", days)
     if form == "pwc":
         K, bf, th = 4, sird.BETA_PWC, np.concatenate([box_thetas(4, 96, 3), f32(synth.box_sample(
             [0.1] * 4 + [0.05, 1e-3, 5e3], [0.3] * 4 + [0.15, 3e-3, 2e4], [0] * 7, 64, np.random.default_rng(4)))])
@@ -68,7 +68,7 @@ def test_ird_fp32_within_tolerance(cost, form):
 
 def test_ird_fp64_calibration_matches_the_oracle_swarm():
     # the plain method in FP64 on F_IRD^MXSE (the paper's representative objective)
-    yD, yI, yR, N = ird_series("c1")
+    yD, yI, yR, N = ird_series("30d")
     lb, ub = configs.bounds(1, log=False)
     cal = sird.Calibrator(yD, N, R0=float(yR[0]), objective=sird.FIT_IRD, yI=yI, yR=yR, cost=sird.COST_MXSE,
                           particles=64, iters=30, lb=lb, ub=ub, precision=64, seed=3)
@@ -81,7 +81,7 @@ def test_ird_fp64_calibration_matches_the_oracle_swarm():
 
 
 def test_ird_fp32_calibration_reports_its_fp64_loss_and_batches_agree():
-    ser = synth.reported_IR(synth.load_series("c3"), 2)
+    ser = synth.reported_IR(synth.load_series("450d"), 2)
     lay = {"L": np.array([30, 45, 21]), "M": np.array([300, 700, 90]), "T": np.array([10, 150, 300])}
     wins = synth.rolling_window_problems(ser, lay)
     lb, ub = configs.bounds(3, log=True)
@@ -98,7 +98,7 @@ def test_ird_fp32_calibration_reports_its_fp64_loss_and_batches_agree():
 
 
 def test_ird_rejects_the_gradient_calls():
-    yD, yI, yR, N = ird_series("c2", 30)
+    yD, yI, yR, N = ird_series("60d", 30)
     lb, ub = configs.bounds(1, log=True)
     cal = sird.Calibrator(yD, N, R0=float(yR[0]), objective=sird.FIT_IRD, yI=yI, yR=yR, particles=64, iters=2,
                           lb=lb, ub=ub, log_scale=[1] * 4, precision=32)
@@ -108,7 +108,7 @@ def test_ird_rejects_the_gradient_calls():
 
 
 def test_ird_batch_set_observations_equals_a_fresh_batch():
-    ser = synth.reported_IR(synth.load_series("c3"), 4)
+    ser = synth.reported_IR(synth.load_series("450d"), 4)
     lay = {"L": np.array([25, 40]), "M": np.array([200, 450]), "T": np.array([30, 200])}
     wins = synth.rolling_window_problems(ser, lay)
     nxt = synth.rolling_window_problems(ser, dict(lay, T=lay["T"] + 2))

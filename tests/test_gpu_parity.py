@@ -49,12 +49,12 @@ def orc_problem(y, N, K, spd, cost=O.MSE, beta_form=O.BETA_PWC):
 
 CASES = [
     # series, days, K, spd
-    ("c2", None, 4, 10),     # 60 days, 4 segments, unrolled 10-step days
-    ("c4", None, 4, 20),     # 90 days at dt = 0.05
-    ("c5", 120, 10, 20),     # 120 days, 10 segments
-    ("c2", 22, 6, 10),       # ragged: segment starts inside a day
-    ("c2", 17, 5, 7),        # steps per day not specialised
-    ("c1", 3, 6, 1),         # segments shorter than a day, one step per day
+    ("window60", None, 4, 10),     # 60 days, 4 segments, unrolled 10-step days
+    ("gradient90", None, 4, 20),     # 90 days at dt = 0.05
+    ("swarm2p20", 120, 10, 20),     # 120 days, 10 segments
+    ("window60", 22, 6, 10),       # ragged: segment starts inside a day
+    ("window60", 17, 5, 7),        # steps per day not specialised
+    ("plain64", 3, 6, 1),         # segments shorter than a day, one step per day
 ]
 
 
@@ -87,7 +87,7 @@ def test_eval_f64_bit_exact(case, cost):
 
 
 def test_eval_ramp_form():
-    y, N, _, _ = window("c2", 36)
+    y, N, _, _ = window("60d", 36)
     rng = np.random.default_rng(3)
     M = 500
     th = np.column_stack([rng.uniform(0.05, 0.6, M), rng.uniform(0.05, 0.6, M), rng.uniform(0, 36, M),
@@ -103,7 +103,7 @@ def test_eval_ramp_form():
 
 
 def test_eval_fixed_I0_and_nonzero_R0():
-    y, N, _, _ = window("c2", 30)
+    y, N, _, _ = window("60d", 30)
     y = y + 500.0
     thetas = box_thetas(4, 300, 11)[:, :6]
     cal = sird.Calibrator(y, N, K=4, spd=10, R0=2.5e4, I0=7.7e3, fit_I0=False, particles=32, iters=1,
@@ -115,7 +115,7 @@ def test_eval_fixed_I0_and_nonzero_R0():
 
 def test_eval_f32_full_size_sampled():
     # the largest configuration: 2^20 parameter vectors, 120 days at dt = 0.05, K = 10
-    y, N, _, _ = window("c5", 120)
+    y, N, _, _ = window("134d", 120)
     M = 1 << 20
     thetas = box_thetas(10, M, 5)
     cal = cal_for(y, N, 10, 20, 32)
@@ -129,7 +129,7 @@ def test_eval_f32_full_size_sampled():
 # ------------------------------------------------------------------ swarm
 
 def c1_setup(M=100):
-    ser = synth.load_series("c1")
+    ser = synth.load_series("30d")
     lb, ub = configs.bounds(1, log=False)
     return ser["yD"], ser["N"], lb, ub
 
@@ -154,7 +154,7 @@ def test_pso_f64_bit_exact_with_oracle():
 def test_calibrate_f64_plain_method_matches_oracle():
     # configuration c1: FP64, K = 1 plus I0, 30 days, 64 particles, 200 iterations, seed 0
     y, N, lb, ub = c1_setup()
-    c = configs.CONFIGS["c1"]
+    c = configs.CONFIGS["plain64"]
     cal = sird.Calibrator(y, N, K=1, spd=10, particles=c["M"], iters=c["iters"], lb=lb, ub=ub, precision=64, seed=0)
     res = cal.calibrate()
     pso = O.PSO(O.Problem(yD=y, N=N, K=1, spd=10), c["M"], lb, ub, seed=0).init().step(c["iters"])
@@ -168,7 +168,7 @@ def test_calibrate_f64_plain_method_matches_oracle():
 
 
 def _f32_state_from_oracle(K, M, seed):
-    y, N, _, _ = window("c2")
+    y, N, _, _ = window("60d")
     lb, ub = log_box(K)
     zlb, zub = f32(np.log(lb)), f32(np.log(ub))
     pb = O.Problem(yD=y, N=N, K=K, spd=10)
@@ -205,7 +205,7 @@ def test_pso_f32_single_step_matches_oracle():
 
 
 def test_state_save_restore_is_bit_identical():
-    y, N, _, _ = window("c2")
+    y, N, _, _ = window("60d")
     lb, ub = log_box(4)
     kw = dict(K=4, spd=10, particles=300, iters=10, lb=lb, ub=ub, log_scale=[1] * 7, precision=32, seed=9)
     a = sird.Calibrator(y, N, **kw).init().step(8)
@@ -253,7 +253,7 @@ def test_one_day_window():
 
 @pytest.mark.parametrize("M,block", [(4096, 128), (1000, 64), (77, 32)])
 def test_persistent_and_per_iteration_launches_agree_bit_for_bit(M, block):
-    y, N, _, _ = window("c2")
+    y, N, _, _ = window("60d")
     lb, ub = log_box(4)
     kw = dict(K=4, spd=10, particles=M, iters=25, lb=lb, ub=ub, log_scale=[1] * 7, precision=32, seed=5,
               reeval_topk=8, block_size=block)

@@ -21,7 +21,7 @@ def _dev():
 
 
 def windows():
-    ser = synth.load_series("c3")
+    ser = synth.load_series("450d")
     lay = {"L": np.array([30, 40, 25]), "M": np.array([600, 900, 300]), "T": np.array([0, 100, 200])}
     return synth.rolling_window_problems(ser, lay)
 
@@ -42,7 +42,7 @@ def test_flat_batch_barrier_wait_runs_out(monkeypatch):
 
 
 def test_persistent_exchange_wait_runs_out(monkeypatch):
-    s = synth.load_series("c2")
+    s = synth.load_series("60d")
     lb, ub = configs.bounds(4, log=True)
     kw = dict(K=4, spd=10, particles=4096, iters=30, lb=lb, ub=ub, log_scale=[1] * 7, precision=32,
               launch_mode=sird.LAUNCH_PERSISTENT, seed=2)

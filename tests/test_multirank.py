@@ -52,7 +52,7 @@ def test_max_over_ranks_gloo():
 def test_window_shards_are_disjoint_streams():
     import bench
 
-    shards = [bench.batch_windows("c3", r)[1] for r in range(4)]
+    shards = [bench.batch_windows("batch512", r)[1] for r in range(4)]
     ids = [{w["stream_id"] for w in sh} for sh in shards]
     for a in range(4):
         assert len(ids[a]) == len(shards[a])
@@ -76,7 +76,7 @@ def test_reference_arm_two_ranks_prints_one_line():
     port = _free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
-           "--workload", "c1", "--steps", "1", "--warmup", "3", "--ref-units", "1"]
+           "--workload", "plain64", "--steps", "1", "--warmup", "3", "--ref-units", "1"]
     env = dict(os.environ, OMP_NUM_THREADS="1")
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=540, env=env)
     assert r.returncode == 0, r.stderr[-2000:]

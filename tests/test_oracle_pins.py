@@ -252,7 +252,7 @@ def _fd(orc, pb, th, j, h_rel=1e-6):
 @pytest.mark.parametrize("form,cost", [("pwc", "mse"), ("pwc", "mae"), ("pwc", "mxse"), ("pwc", "mape"),
                                        ("ramp", "mse")])
 def test_adjoint_matches_central_fd(orc, form, cost):
-    ser = synth.load_series("c2")
+    ser = synth.load_series("60d")
     y = ser["yD"][:41]
     if form == "pwc":
         pb = mkpb(orc, days=40, K=4, yD=y, cost=orc.COSTS[cost])
@@ -268,7 +268,7 @@ def test_adjoint_matches_central_fd(orc, form, cost):
 
 
 def test_adjoint_initial_state_gradient(orc):
-    ser = synth.load_series("c2")
+    ser = synth.load_series("60d")
     th = [0.21, 0.2, 0.15, 0.13, 0.1, 0.002, 1e4]
     y = ser["yD"][:31]
 
@@ -381,7 +381,7 @@ def test_store_f32_rounds_state(orc):
 
 
 def test_reeval_topk_is_best_of_k(orc):
-    ser = synth.load_series("c1")
+    ser = synth.load_series("30d")
     pb = mkpb(orc, days=30, yD=ser["yD"])
     lb, ub = [1e-3, 1e-3, 1e-5, 1.0], [2.0, 1.0, 0.1, 1e6]
     pso = orc.PSO(pb, 48, np.log(lb), np.log(ub), logdim=[1, 1, 1, 1], seed=4, store_f32=True).init().step(5)
@@ -414,7 +414,7 @@ def test_noise_free_recovery(orc):
 
 
 def test_brute_force_grid_contains_pso_optimum(orc):
-    ser = synth.load_series("c1")
+    ser = synth.load_series("30d")
     pb = mkpb(orc, days=30, yD=ser["yD"], fit_I0=False, I0=1e4)
     # two free parameters (beta, mu); gamma pinned by equal bounds
     lb, ub = [0.1, 0.1, 0.0005], [0.4, 0.1, 0.005]
@@ -449,7 +449,7 @@ def test_forecast(orc):
 # ---------------------------------------------------------------- ensemble bands (Sec. 4.2)
 
 def test_ensemble_bands_of_identical_members_collapse_to_the_trajectory(orc):
-    s = synth.load_series("c2")
+    s = synth.load_series("60d")
     pb = orc.Problem(yD=s["yD"], N=s["N"], K=4, spd=10)
     th = np.asarray(s["theta_true"])
     b = orc.ensemble_bands(pb, np.tile(th, (6, 1)), 14)
@@ -461,7 +461,7 @@ def test_ensemble_bands_of_identical_members_collapse_to_the_trajectory(orc):
 def test_ensemble_bands_order_statistics_and_nesting(orc):
     # members differing only in mu: deaths increase with mu on every day after the first, so the
     # sorted members are the mu-sorted ones and the median is the middle member's trajectory
-    s = synth.load_series("c2")
+    s = synth.load_series("60d")
     pb = orc.Problem(yD=s["yD"], N=s["N"], K=4, spd=10)
     th = np.tile(np.asarray(s["theta_true"]), (9, 1))
     th[:, 5] = np.linspace(1e-3, 3e-3, 9)
@@ -478,7 +478,7 @@ def test_ensemble_bands_order_statistics_and_nesting(orc):
 
 def test_ensemble_bands_reproduction_number_closed_form(orc):
     # constant beta: R0(t) = beta / (gamma + mu) on every day, inside the window and past it
-    s = synth.load_series("c1")
+    s = synth.load_series("30d")
     pb = orc.Problem(yD=s["yD"], N=s["N"], K=1, spd=10)
     th = np.array([[0.3, 0.1, 0.002, 1e4], [0.2, 0.12, 0.004, 2e4]])
     b = orc.ensemble_bands(pb, th, 21, fractions=())

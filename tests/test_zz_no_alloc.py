@@ -21,7 +21,7 @@ TOL32 = 1e-5
 @pytest.mark.parametrize("cost", [sird.COST_MSE, sird.COST_MAPE])
 def test_noalloc_step_matches_handle_step(cost):
     torch.cuda.set_device(0)
-    ser = synth.load_series("c2")
+    ser = synth.load_series("60d")
     y = ser["yD"]
     lb, ub = configs.bounds(4, log=True)
     M = 1000
