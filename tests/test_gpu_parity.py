@@ -49,12 +49,12 @@ def orc_problem(y, N, K, spd, cost=O.MSE, beta_form=O.BETA_PWC):
 
 CASES = [
     # series, days, K, spd
-    ("window60", None, 4, 10),     # 60 days, 4 segments, unrolled 10-step days
-    ("gradient90", None, 4, 20),     # 90 days at dt = 0.05
-    ("swarm2p20", 120, 10, 20),     # 120 days, 10 segments
-    ("window60", 22, 6, 10),       # ragged: segment starts inside a day
-    ("window60", 17, 5, 7),        # steps per day not specialised
-    ("plain64", 3, 6, 1),         # segments shorter than a day, one step per day
+    ("60d", None, 4, 10),     # 60 days, 4 segments, unrolled 10-step days
+    ("90d", None, 4, 20),     # 90 days at dt = 0.05
+    ("134d", 120, 10, 20),     # 120 days, 10 segments
+    ("60d", 22, 6, 10),       # ragged: segment starts inside a day
+    ("60d", 17, 5, 7),        # steps per day not specialised
+    ("30d", 3, 6, 1),         # segments shorter than a day, one step per day
 ]
 
 
