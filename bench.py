@@ -49,15 +49,15 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 # DRAM bytes per launch of the dominant kernel from committed ncu captures, valid only for the
 # kernel sources they were taken on (sha256[:16] of the files listed).
 PROFILED = {
-    "batch512": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "9379b46a831ff993",
-           "traffic_bytes": 14515712, "fma_pipe": 0.6545, "profile": "profiles/pso_batch_f32_batch512.md"},
+    "batch512": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "6b9e9b7c79328125",
+           "traffic_bytes": 14521856, "fma_pipe": 0.6546, "profile": "profiles/pso_batch_f32_batch512.md"},
     "window60": {"files": ["pso_persistent.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "dae14ee208fa0341", "traffic_bytes": 447232, "fma_pipe": 0.3734,
+           "sha": "838214511d57ce23", "traffic_bytes": 448000, "fma_pipe": 0.3726,
            "profile": "profiles/pso_f32_persistent_window60.md"},
-    "gradient90": {"files": ["adjoint_f32.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "67f2c8704b68013a",
-           "traffic_bytes": 159744, "fma_pipe": 0.1220, "profile": "profiles/loss_grad_f32_gradient90.md"},
-    "swarm2p20": {"files": ["pso_kernels.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "1f090857e67f2ef5",
-           "traffic_bytes": 276251648, "fma_pipe": 0.7472, "profile": "profiles/pso_f32_kernel_swarm2p20.md"},
+    "gradient90": {"files": ["adjoint_f32.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "53c9d1039132dcf9",
+           "traffic_bytes": 159232, "fma_pipe": 0.1222, "profile": "profiles/loss_grad_f32_gradient90.md"},
+    "swarm2p20": {"files": ["pso_kernels.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "6875c43733950da4",
+           "traffic_bytes": 276303616, "fma_pipe": 0.7505, "profile": "profiles/pso_f32_kernel_swarm2p20.md"},
 }
 
 
@@ -274,7 +274,7 @@ def s_to_calibrate() -> dict:
 
     from paper_2204_12346_gb300 import sird
 
-    c, ser, y, lb, ub = single_window("60d")
+    c, ser, y, lb, ub = single_window("window60")
     kw = dict(K=c["K"], spd=c["spd"], particles=c["M"], iters=c["iters"], lb=lb, ub=ub,
               log_scale=[1] * len(lb), seed=c["seed"])
     c64 = sird.Calibrator(y, ser["N"], precision=64, **kw)
@@ -615,7 +615,7 @@ def run_gradient(args, rank, world):
 
     from paper_2204_12346_gb300 import sird
 
-    c, ser, y, lb, ub = single_window("90d")
+    c, ser, y, lb, ub = single_window("gradient90")
     stream = torch.cuda.Stream()
     P = len(lb)
     with torch.cuda.stream(stream):
