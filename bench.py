@@ -658,7 +658,7 @@ def run_gradient(args, rank, world):
     kms = statistics.mean(kern_ms)
     flops = M * L * spd * GRAD_FLOPS_PER_STEP
     achieved = flops / (kms / 1e3) / 1e12
-    return {
+    out = {
         "metric": METRIC, "value": units * args.steps * world / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -682,6 +682,9 @@ def run_gradient(args, rank, world):
                    "fp64_adjoint_particle_days_per_s": units / (statistics.mean(f64_ms) / 1e3),
                    "polish_fp32_50_iters_loss_fp64": pol["loss"]},
     }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline("gradient90", budget_s=args.cpu_budget)
+    return out
 
 
 # ------------------------------------------------------------------ oracle on the host cores
