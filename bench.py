@@ -54,7 +54,7 @@ PROFILED = {
     "window60": {"files": ["pso_persistent.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"],
            "sha": "838214511d57ce23", "traffic_bytes": 448000, "fma_pipe": 0.3726,
            "profile": "profiles/pso_f32_persistent_window60.md"},
-    "gradient90": {"files": ["adjoint_f32.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "53c9d1039132dcf9",
+    "gradient90": {"files": ["adjoint_f32.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": None,
            "traffic_bytes": 159232, "fma_pipe": 0.1222, "profile": "profiles/loss_grad_f32_gradient90.md"},
     "swarm2p20": {"files": ["pso_kernels.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "6875c43733950da4",
            "traffic_bytes": 276303616, "fma_pipe": 0.7505, "profile": "profiles/pso_f32_kernel_swarm2p20.md"},
@@ -561,8 +561,8 @@ def run_single(args, rank, world):
     rk = c.get("reeval_topk", 0)
     launches = 1 + iter_launches + (topk_launches(c["M"], rk) + 1 if rk else 1)
     h2d, d2h = (L + 1) * 16, 288
-    if polish:  # selection, init + gradient + accept, 5 per iteration, the final FP64 pick
-        launches += topk_launches(c["M"], c["polish_topk"]) + 3 + 5 * polish + 1
+    if polish:  # selection, init + gradient + accept, 6 per iteration, the final FP64 pick
+        launches += topk_launches(c["M"], c["polish_topk"]) + 3 + 6 * polish + 1
     if horizon:
         launches += topk_launches(c["M"], fk) + 1 + 1
         h2d += fk * P * 8 + (L + 1) * 16
@@ -670,7 +670,7 @@ def run_gradient(args, rank, world):
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic("gradient90"),
                      "traffic_source": PROFILED["gradient90"]["profile"],
                      "ncu_fma_pipe_active": profiled_traffic("gradient90", "fma_pipe"),
-                     "kernel": "loss_grad_f32_kernel", "avg_launch_us": kms * 1e3, "flops_per_launch": flops,
+                     "kernel": "loss_grad_f32_ws_kernel", "avg_launch_us": kms * 1e3, "flops_per_launch": flops,
                      "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
         "e2e": {"value": units * args.steps * world / (e2e_total / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": M * P * 4, "d2h_bytes_per_step": M * (P + 1) * 4,

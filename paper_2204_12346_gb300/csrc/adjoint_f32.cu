@@ -125,6 +125,199 @@ __device__ __forceinline__ void day_steps(int day, int spd, int steps, int K, co
     }
 }
 
+// Loss, gradient and the state shared by the kernels below: theta of one vector at th[d * B].
+struct CoefF32 {
+    float a, dm, I0;
+    RampF32 rp;
+};
+
+template <bool RAMP>
+__device__ __forceinline__ CoefF32 coef_f32(const WindowDev& w, const ModelDev& m, const float* th, int B) {
+    CoefF32 c{};
+    const int gi = RAMP ? 4 : m.K;
+    const float gam = th[gi * B], mu = th[(gi + 1) * B];
+    c.I0 = m.fit_I0 ? th[(gi + 2) * B] : w.I0f;
+    const float gm = __fadd_rn(gam, mu);
+    c.a = __fmaf_rn(gm, w.dt_h, __fmul_rn(gm, w.dt_l));
+    c.dm = __fmaf_rn(mu, w.dt_h, __fmul_rn(mu, w.dt_l));
+    if (RAMP) {
+        RampF32& rp = c.rp;
+        rp.b1 = th[0];
+        rp.b2 = th[B];
+        const float ta = th[2 * B], tb = th[3 * B];
+        rp.swapped = ta > tb;
+        rp.t1 = fminf(ta, tb);
+        rp.t2 = fmaxf(ta, tb);
+        rp.slope = (rp.t2 > rp.t1) ? __fdiv_rn(__fsub_rn(rp.b2, rp.b1), __fsub_rn(rp.t2, rp.t1)) : 0.f;
+        rp.inv_len = (rp.t2 > rp.t1) ? __fdiv_rn(1.f, __fsub_rn(rp.t2, rp.t1)) : 0.f;
+        rp.dtf = __fadd_rn(w.dt_h, w.dt_l);
+    }
+    return c;
+}
+
+__device__ __forceinline__ float cb_of_f32(const WindowDev& w, float beta) {
+    return __fmaf_rn(beta, w.cbn_h, __fmul_rn(beta, w.cbn_l));
+}
+
+// Forward pass: the FP32 evaluation's arithmetic, plus the day-start checkpoints (Sday, I, Il,
+// e_day) at ck[(day * 4 + q) * cs].  Returns the loss; e_last = e_L, imax = the MXSE day.
+template <int SPD, int COST, bool RAMP>
+__device__ __forceinline__ float forward_checkpointed(const WindowDev& w, const ModelDev& m, const float* ys,
+                                                      const float* invys, const float* th, int B, const CoefF32& cf,
+                                                      float* ck, size_t cs, float& e_last, int& imax) {
+    const int n = w.n_obs, L = n - 1, spd = SPD > 0 ? SPD : m.spd, steps = L * spd, K = m.K;
+    float I = cf.I0, Il = 0.f;
+    DayStateF32 ds;
+    ds.init(w, I, ys[0]);
+    LossF32<COST> lossacc;
+    float emax = 0.f, e_prev = 0.f;  // e_0 = y_0 - D_0 = 0
+    imax = 0;
+    int seg = 0, next_b = (!RAMP && K > 1) ? segment_start(1, steps, K) : INT_MAX;
+    float cb = RAMP ? 0.f : cb_of_f32(w, th[0]);
+    for (int day = 0; day < L; ++day) {
+        float* c = ck + (size_t)day * 4 * cs;
+        c[0] = ds.Sday;
+        c[cs] = I;
+        c[2 * cs] = Il;
+        c[3 * cs] = e_prev;
+        float cday = 0.f, dday = 0.f;
+        day_steps<SPD, RAMP, false>(day, spd, steps, K, th, B, cf.rp, cf.a, cf.dm, w, ds.Sday, cday, dday, I, Il, seg,
+                                    next_b, cb, nullptr, nullptr, nullptr);
+        const float e = ds.close_day(w, cday, dday, ys[day + 1], I, Il);
+        lossacc.add(e, COST == COST_MAPE ? invys[day + 1] : 0.f);
+        if (COST == COST_MXSE) {
+            const float e2 = __fmul_rn(e, e);
+            if (e2 > emax) {
+                emax = e2;
+                imax = day + 1;
+            }
+        }
+        e_prev = e;
+    }
+    e_last = e_prev;
+    return lossacc.result(n, w.n_kept);
+}
+
+// Re-integrates one day from its checkpoint (ck as above), staging each step's S, I and cb at
+// stS/stI/stC[s * B].
+template <int SPD, bool RAMP>
+__device__ __forceinline__ void restage_day(const WindowDev& w, const ModelDev& m, const float* th, int B,
+                                            const CoefF32& cf, const float* ck, size_t cs, int day, float* stS,
+                                            float* stI, float* stC) {
+    const int spd = SPD > 0 ? SPD : m.spd, steps = (w.n_obs - 1) * spd, K = m.K;
+    const float* c = ck + (size_t)day * 4 * cs;
+    const float Sday = c[0];
+    float Ir = c[cs], Ilr = c[2 * cs];
+    int sg = RAMP ? 0 : seg_of_step(day * spd, steps, K);
+    int nb = (!RAMP && sg + 1 < K) ? segment_start(sg + 1, steps, K) : INT_MAX;
+    float cb = RAMP ? 0.f : cb_of_f32(w, th[sg * B]);
+    float cday = 0.f, dday = 0.f;
+    day_steps<SPD, RAMP, true>(day, spd, steps, K, th, B, cf.rp, cf.a, cf.dm, w, Sday, cday, dday, Ir, Ilr, sg, nb, cb,
+                               stS, stI, stC);
+}
+
+// Adjoint state of one vector through the reverse sweep: lambda_S, lambda_I with their low parts,
+// lambda_D, the segment being swept and the gradient sums.  Kept as separate scalars so that
+// they stay in registers (the sums are indexed by segment and live in local memory).
+struct RevF32 {
+    float lS, lI, lSl, lIl, lD;
+    int cur, seg_lo;
+};
+
+template <int COST, bool RAMP>
+__device__ __forceinline__ void rev_begin(RevF32& r, double* gacc, const WindowDev& w, const ModelDev& m,
+                                          const float* invys, int steps, float e_last, int imax) {
+    const int n = w.n_obs, L = n - 1;
+    for (int d = 0; d < m.P; ++d) gacc[d] = 0.0;
+    r.lS = r.lI = r.lSl = r.lIl = 0.f;
+    r.lD = grad_D<COST>(e_last, invys[L], n, w.n_kept, imax == L);
+    r.cur = RAMP ? 0 : seg_of_step(steps - 1, steps, m.K);
+    r.seg_lo = RAMP ? 0 : segment_start(r.cur, steps, m.K);
+}
+
+// The reverse sweep of one staged day (steps spd-1 .. 0), then the day's folds and dL/dDhat_day.
+template <int SPD, int COST, bool RAMP>
+__device__ __forceinline__ void rev_day(RevF32& r, double* gacc, const WindowDev& w, const ModelDev& m, const float* invys,
+                                        const CoefF32& cf, int day, int steps, const float* stS, const float* stI,
+                                        const float* stC, int B, float e_d, int imax) {
+    const int spd = SPD > 0 ? SPD : m.spd, K = m.K, n = w.n_obs, gi = RAMP ? 4 : K;
+    const float a = cf.a;
+    float pb = 0.f, pg = 0.f, pm = 0.f, pr[4] = {0.f, 0.f, 0.f, 0.f};
+    const float dmlD = __fmul_rn(cf.dm, r.lD);  // lambda_D is constant within the day
+#pragma unroll 4
+    for (int s = spd - 1; s >= 0; --s) {
+        const int k = day * spd + s;
+        const float S = stS[s * B], Iv = stI[s * B], c = stC[s * B];
+        if (!RAMP && k < r.seg_lo) {  // entering the previous segment (uniform across the warp)
+            gacc[r.cur] += (double)pb;
+            pb = 0.f;
+            r.cur = seg_of_step(k, steps, K);
+            r.seg_lo = segment_start(r.cur, steps, K);
+        }
+        const float q = __fsub_rn(r.lI, r.lS);
+        const float SI = __fmul_rn(S, Iv);
+        if (RAMP) {
+            float db[4];
+            cf.rp.dbeta(k, db);
+            const float rr = __fmul_rn(SI, q);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) pr[j] = __fmaf_rn(rr, db[j], pr[j]);
+        } else {
+            pb = __fmaf_rn(SI, q, pb);
+        }
+        pg = __fmaf_rn(Iv, r.lI, pg);
+        pm = __fmaf_rn(Iv, __fsub_rn(r.lD, r.lI), pm);
+        // lambda_S and lambda_I change by small increments per step; as for I in the forward
+        // pass, each sum's rounding error is kept (Fast2Sum) and folded in once a day
+        const float dS = __fmul_rn(__fmul_rn(c, Iv), q);
+        const float dI = __fmaf_rn(__fmul_rn(c, S), q, __fmaf_rn(-a, r.lI, dmlD));
+        const float rS = __fadd_rn(r.lS, dS), rI = __fadd_rn(r.lI, dI);
+        r.lSl = __fadd_rn(r.lSl, __fsub_rn(dS, __fsub_rn(rS, r.lS)));
+        r.lIl = __fadd_rn(r.lIl, __fsub_rn(dI, __fsub_rn(rI, r.lI)));
+        r.lS = rS;
+        r.lI = rI;
+    }
+    {
+        const float fs = __fadd_rn(r.lS, r.lSl), fi = __fadd_rn(r.lI, r.lIl);
+        r.lSl = __fsub_rn(r.lSl, __fsub_rn(fs, r.lS));
+        r.lIl = __fsub_rn(r.lIl, __fsub_rn(fi, r.lI));
+        r.lS = fs;
+        r.lI = fi;
+    }
+    r.lD = __fadd_rn(r.lD, grad_D<COST>(e_d, invys[day], n, w.n_kept, COST == COST_MXSE && imax == day));
+    if (RAMP) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) gacc[j] += (double)pr[j];
+    } else {
+        gacc[r.cur] += (double)pb;
+    }
+    gacc[gi] += (double)pg;
+    gacc[gi + 1] += (double)pm;
+}
+
+template <bool RAMP>
+__device__ __forceinline__ void rev_write(const RevF32& r, const double* gacc, const WindowDev& w, const ModelDev& m, int p, float Lval,
+                                          float* loss, float* grad, int ldg, float* grad_u0) {
+    const int K = m.K, gi = RAMP ? 4 : K;
+    const double dtN = w.dt / w.N;
+    const int nbeta = RAMP ? 4 : K;
+    for (int d = 0; d < nbeta; ++d) grad[(size_t)d * ldg + p] = (float)(gacc[d] * dtN);
+    grad[(size_t)gi * ldg + p] = (float)(-w.dt * gacc[gi]);
+    grad[(size_t)(gi + 1) * ldg + p] = (float)(w.dt * gacc[gi + 1]);
+    const float lS = __fadd_rn(r.lS, r.lSl);
+    const float lI = __fadd_rn(r.lI, r.lIl);
+    if (m.fit_I0) grad[(size_t)(gi + 2) * ldg + p] = __fsub_rn(lI, lS);
+    loss[p] = Lval;
+    if (grad_u0) {
+        grad_u0[p] = lS;
+        grad_u0[(size_t)ldg + p] = lI;
+        grad_u0[2 * (size_t)ldg + p] = 0.f;
+        grad_u0[3 * (size_t)ldg + p] = r.lD;
+    }
+}
+
+// One thread per parameter vector: forward pass, then per day (last to first) re-integration
+// into shared memory and the reverse sweep.  Any form and steps per day.
 template <int SPD, int COST, bool RAMP>
 __global__ void __launch_bounds__(64) loss_grad_f32_kernel(WindowDev w, ModelDev m, ObsDev o,
                                                             const float* __restrict__ theta, int ld, int M,
@@ -152,161 +345,101 @@ __global__ void __launch_bounds__(64) loss_grad_f32_kernel(WindowDev w, ModelDev
     __syncthreads();
     if (!active) return;
     const float* th = th_all + tid;
-
-    const int L = n - 1, steps = L * spd, K = m.K;
-    const int gi = RAMP ? 4 : K;
-    const float gam = th[gi * B], mu = th[(gi + 1) * B];
-    float I = m.fit_I0 ? th[(gi + 2) * B] : w.I0f;
-    float Il = 0.f;
-    const float gm = __fadd_rn(gam, mu);
-    const float a = __fmaf_rn(gm, w.dt_h, __fmul_rn(gm, w.dt_l));
-    const float dm = __fmaf_rn(mu, w.dt_h, __fmul_rn(mu, w.dt_l));
-    RampF32 rp{};
-    if (RAMP) {
-        rp.b1 = th[0];
-        rp.b2 = th[B];
-        const float ta = th[2 * B], tb = th[3 * B];
-        rp.swapped = ta > tb;
-        rp.t1 = fminf(ta, tb);
-        rp.t2 = fmaxf(ta, tb);
-        rp.slope = (rp.t2 > rp.t1) ? __fdiv_rn(__fsub_rn(rp.b2, rp.b1), __fsub_rn(rp.t2, rp.t1)) : 0.f;
-        rp.inv_len = (rp.t2 > rp.t1) ? __fdiv_rn(1.f, __fsub_rn(rp.t2, rp.t1)) : 0.f;
-        rp.dtf = __fadd_rn(w.dt_h, w.dt_l);
-    }
-    auto cb_of = [&](float beta) { return __fmaf_rn(beta, w.cbn_h, __fmul_rn(beta, w.cbn_l)); };
-
-    // ---- forward: the FP32 evaluation's arithmetic, plus the day-start checkpoints
-    DayStateF32 ds;
-    ds.init(w, I, ys[0]);
-    LossF32<COST> lossacc;
-    float emax = 0.f, e_prev = 0.f;  // e_0 = y_0 - D_0 = 0
-    int imax = 0;
-    int seg = 0, next_b = (!RAMP && K > 1) ? segment_start(1, steps, K) : INT_MAX;
-    float cb = RAMP ? 0.f : cb_of(th[0]);
-    for (int day = 0; day < L; ++day) {
-        const size_t base = (size_t)day * 4 * M + p;
-        ckpt[base] = ds.Sday;
-        ckpt[base + M] = I;
-        ckpt[base + 2 * (size_t)M] = Il;
-        ckpt[base + 3 * (size_t)M] = e_prev;
-        float cday = 0.f, dday = 0.f;
-        day_steps<SPD, RAMP, false>(day, spd, steps, K, th, B, rp, a, dm, w, ds.Sday, cday, dday, I, Il, seg, next_b,
-                                    cb, nullptr, nullptr, nullptr);
-        const float e = ds.close_day(w, cday, dday, ys[day + 1], I, Il);
-        lossacc.add(e, COST == COST_MAPE ? invys[day + 1] : 0.f);
-        if (COST == COST_MXSE) {
-            const float e2 = __fmul_rn(e, e);
-            if (e2 > emax) {
-                emax = e2;
-                imax = day + 1;
-            }
-        }
-        e_prev = e;
-    }
-    const float Lval = lossacc.result(n, w.n_kept);
-
-    // ---- reverse sweep, one day at a time
+    const int L = n - 1, steps = L * spd;
+    const CoefF32 cf = coef_f32<RAMP>(w, m, th, B);
+    float e_last;
+    int imax;
+    float* ck = ckpt + p;
+    const float Lval = forward_checkpointed<SPD, COST, RAMP>(w, m, ys, invys, th, B, cf, ck, (size_t)M, e_last, imax);
+    RevF32 r;
     double gacc[kMaxParams];
-    for (int d = 0; d < P; ++d) gacc[d] = 0.0;
-    float lS = 0.f, lI = 0.f, lSl = 0.f, lIl = 0.f;
-    float lD = grad_D<COST>(e_prev, invys[L], n, w.n_kept, imax == L);
-    int cur = RAMP ? 0 : seg_of_step(steps - 1, steps, K);
-    int seg_lo = RAMP ? 0 : segment_start(cur, steps, K);
-    // checkpoint of the day to re-integrate, loaded one day ahead
-    size_t base = (size_t)(L - 1) * 4 * M + p;
-    float nSday = ckpt[base], nI = ckpt[base + M], nIl = ckpt[base + 2 * (size_t)M], ne = ckpt[base + 3 * (size_t)M];
+    rev_begin<COST, RAMP>(r, gacc, w, m, invys, steps, e_last, imax);
     for (int day = L - 1; day >= 0; --day) {
-        const float Sday = nSday, e_d = ne;
-        float Ir = nI, Ilr = nIl;
-        if (day > 0) {
-            base = (size_t)(day - 1) * 4 * M + p;
-            nSday = ckpt[base];
-            nI = ckpt[base + M];
-            nIl = ckpt[base + 2 * (size_t)M];
-            ne = ckpt[base + 3 * (size_t)M];
-        }
-        // re-integrate the day (the forward pass's coefficients), staging each step's S, I, cb
-        {
-            int sg = RAMP ? 0 : seg_of_step(day * spd, steps, K);
-            int nb = (!RAMP && sg + 1 < K) ? segment_start(sg + 1, steps, K) : INT_MAX;
-            float c = RAMP ? 0.f : cb_of(th[sg * B]);
-            float cday = 0.f, dday = 0.f;
-            day_steps<SPD, RAMP, true>(day, spd, steps, K, th, B, rp, a, dm, w, Sday, cday, dday, Ir, Ilr, sg, nb, c,
-                                       stS, stI, stC);
-        }
-        float pb = 0.f, pg = 0.f, pm = 0.f, pr[4] = {0.f, 0.f, 0.f, 0.f};
-        const float dmlD = __fmul_rn(dm, lD);  // lambda_D is constant within the day
-#pragma unroll 4
-        for (int s = spd - 1; s >= 0; --s) {
-            const int k = day * spd + s;
-            const float S = stS[s * B], Iv = stI[s * B], c = stC[s * B];
-            if (!RAMP && k < seg_lo) {  // entering the previous segment (uniform across the warp)
-                gacc[cur] += (double)pb;
-                pb = 0.f;
-                cur = seg_of_step(k, steps, K);
-                seg_lo = segment_start(cur, steps, K);
-            }
-            const float q = __fsub_rn(lI, lS);
-            const float SI = __fmul_rn(S, Iv);
-            if (RAMP) {
-                float db[4];
-                rp.dbeta(k, db);
-                const float r = __fmul_rn(SI, q);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) pr[j] = __fmaf_rn(r, db[j], pr[j]);
-            } else {
-                pb = __fmaf_rn(SI, q, pb);
-            }
-            pg = __fmaf_rn(Iv, lI, pg);
-            pm = __fmaf_rn(Iv, __fsub_rn(lD, lI), pm);
-            // lambda_S and lambda_I change by small increments per step; as for I in the forward
-            // pass, each sum's rounding error is kept (Fast2Sum) and folded in once a day
-            const float dS = __fmul_rn(__fmul_rn(c, Iv), q);
-            const float dI = __fmaf_rn(__fmul_rn(c, S), q, __fmaf_rn(-a, lI, dmlD));
-            const float rS = __fadd_rn(lS, dS), rI = __fadd_rn(lI, dI);
-            lSl = __fadd_rn(lSl, __fsub_rn(dS, __fsub_rn(rS, lS)));
-            lIl = __fadd_rn(lIl, __fsub_rn(dI, __fsub_rn(rI, lI)));
-            lS = rS;
-            lI = rI;
-        }
-        {
-            const float fs = __fadd_rn(lS, lSl), fi = __fadd_rn(lI, lIl);
-            lSl = __fsub_rn(lSl, __fsub_rn(fs, lS));
-            lIl = __fsub_rn(lIl, __fsub_rn(fi, lI));
-            lS = fs;
-            lI = fi;
-        }
-        lD = __fadd_rn(lD, grad_D<COST>(e_d, invys[day], n, w.n_kept, COST == COST_MXSE && imax == day));
-        if (RAMP) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) gacc[j] += (double)pr[j];
+        restage_day<SPD, RAMP>(w, m, th, B, cf, ck, (size_t)M, day, stS, stI, stC);
+        rev_day<SPD, COST, RAMP>(r, gacc, w, m, invys, cf, day, steps, stS, stI, stC, B, ck[((size_t)day * 4 + 3) * M],
+                                 imax);
+    }
+    rev_write<RAMP>(r, gacc, w, m, p, Lval, loss, grad, ldg, grad_u0);
+}
+
+// Warp-specialised form (PWC, 10 or 20 steps per day): a block of two warps owns 32 parameter
+// vectors.  Warp 0 runs the forward pass and then re-integrates the days, last to first, into a
+// double-buffered stage in shared memory; warp 1 sweeps each staged day backwards while warp 0
+// re-integrates the day before it, one block barrier per day handing the buffers over.  The two
+// halves of the per-vector work run on two warp schedulers at once; each chain's arithmetic and
+// order are those of loss_grad_f32_kernel, so the results are identical.  A lane past the end of
+// the vectors integrates a copy of the last one and writes nothing but its own checkpoints.
+constexpr int kWsVectors = 32;
+
+template <int SPD, int COST>
+__global__ void __launch_bounds__(64) loss_grad_f32_ws_kernel(WindowDev w, ModelDev m, ObsDev o,
+                                                               const float* __restrict__ theta, int ld, int M,
+                                                               float* __restrict__ loss, float* __restrict__ grad,
+                                                               int ldg, float* __restrict__ grad_u0,
+                                                               float* __restrict__ ckpt, int Mpad) {
+    extern __shared__ float smem[];
+    constexpr int V = kWsVectors;
+    const int tid = threadIdx.x, lane = tid & 31, P = m.P, n = w.n_obs, L = n - 1, steps = L * SPD;
+    const bool fwd = tid < V;
+    float* ys = smem;
+    float* invys = ys + ((n + 3) & ~3);
+    float* th_all = invys + ((n + 3) & ~3);  // [P][V]
+    float* stage = th_all + P * V;           // [2 buffers][S, I, cb][SPD][V]
+    float* xch = stage + 6 * SPD * V;        // e_L, MXSE day and loss of each vector
+    for (int i = tid; i < n; i += 2 * V) {
+        ys[i] = o.yf[i];
+        invys[i] = o.invyf[i];
+    }
+    const int p = blockIdx.x * V + lane;
+    const bool active = p < M;
+    if (fwd) {
+        const int src = active ? p : M - 1;
+        for (int d = 0; d < P; ++d) th_all[d * V + lane] = theta[(size_t)d * ld + src];
+    }
+    __syncthreads();
+    const float* th = th_all + lane;
+    const CoefF32 cf = coef_f32<false>(w, m, th, V);
+    float* ck = ckpt + p;
+    const size_t cs = (size_t)Mpad;
+    auto buf = [&](int b, int q) { return stage + (size_t)(b * 3 + q) * SPD * V + lane; };
+    if (fwd) {
+        float e_last;
+        int imax;
+        const float Lval = forward_checkpointed<SPD, COST, false>(w, m, ys, invys, th, V, cf, ck, cs, e_last, imax);
+        xch[lane] = e_last;
+        xch[V + lane] = __int_as_float(imax);
+        xch[2 * V + lane] = Lval;
+        restage_day<SPD, false>(w, m, th, V, cf, ck, cs, L - 1, buf(0, 0), buf(0, 1), buf(0, 2));
+    }
+    __syncthreads();
+    RevF32 r{};
+    double gacc[kMaxParams];
+    int imax = 0;
+    float e_d = 0.f;
+    if (!fwd) {
+        imax = __float_as_int(xch[V + lane]);
+        rev_begin<COST, false>(r, gacc, w, m, invys, steps, xch[lane], imax);
+        e_d = ck[((size_t)(L - 1) * 4 + 3) * cs];
+    }
+    for (int day = L - 1; day >= 0; --day) {
+        const int b = (L - 1 - day) & 1;
+        if (fwd) {
+            if (day > 0) restage_day<SPD, false>(w, m, th, V, cf, ck, cs, day - 1, buf(b ^ 1, 0), buf(b ^ 1, 1), buf(b ^ 1, 2));
         } else {
-            gacc[cur] += (double)pb;
+            const float e_next = day > 0 ? ck[((size_t)(day - 1) * 4 + 3) * cs] : 0.f;
+            rev_day<SPD, COST, false>(r, gacc, w, m, invys, cf, day, steps, buf(b, 0), buf(b, 1), buf(b, 2), V, e_d, imax);
+            e_d = e_next;
         }
-        gacc[gi] += (double)pg;
-        gacc[gi + 1] += (double)pm;
+        __syncthreads();
     }
-    const double dtN = w.dt / w.N;
-    const int nbeta = RAMP ? 4 : K;
-    for (int d = 0; d < nbeta; ++d) grad[(size_t)d * ldg + p] = (float)(gacc[d] * dtN);
-    grad[(size_t)gi * ldg + p] = (float)(-w.dt * gacc[gi]);
-    grad[(size_t)(gi + 1) * ldg + p] = (float)(w.dt * gacc[gi + 1]);
-    lS = __fadd_rn(lS, lSl);
-    lI = __fadd_rn(lI, lIl);
-    if (m.fit_I0) grad[(size_t)(gi + 2) * ldg + p] = __fsub_rn(lI, lS);
-    loss[p] = Lval;
-    if (grad_u0) {
-        grad_u0[p] = lS;
-        grad_u0[(size_t)ldg + p] = lI;
-        grad_u0[2 * (size_t)ldg + p] = 0.f;
-        grad_u0[3 * (size_t)ldg + p] = lD;
-    }
+    if (!fwd && active) rev_write<false>(r, gacc, w, m, p, xch[2 * V + lane], loss, grad, ldg, grad_u0);
 }
 
 }  // namespace
 
 size_t adjoint_ckpt_bytes_f32(const WindowDev& w, int M) {
-    return (size_t)(w.n_obs - 1) * 4 * (size_t)M * sizeof(float);
+    const size_t Mpad = ((size_t)M + kWsVectors - 1) / kWsVectors * kWsVectors;
+    return (size_t)(w.n_obs - 1) * 4 * Mpad * sizeof(float);
 }
 
 cudaError_t launch_loss_grad_f32(const WindowDev& w, const ModelDev& m, const ObsDev& o, const float* theta, int ld,
@@ -314,12 +447,41 @@ cudaError_t launch_loss_grad_f32(const WindowDev& w, const ModelDev& m, const Ob
                                  cudaStream_t s) {
     if (M <= 0) return cudaSuccess;
     if (m.spd < 1 || m.spd > kMaxSpdGeneric) return cudaErrorInvalidValue;
+    (void)cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    const size_t obs = 2 * (size_t)((w.n_obs + 3) & ~3);
+    if (m.beta_form != BETA_RAMP && (m.spd == 10 || m.spd == 20)) {
+        // two warps per 32 vectors: the re-integration and the reverse sweep side by side
+        const int Mpad = (M + kWsVectors - 1) / kWsVectors * kWsVectors;
+        const size_t sm = (obs + (size_t)m.P * kWsVectors + 6 * (size_t)m.spd * kWsVectors + 3 * kWsVectors) * sizeof(float);
+#define SIRD_LGWS(SV, CV)                                                                                            \
+    {                                                                                                                \
+        auto kern = loss_grad_f32_ws_kernel<SV, CV>;                                                                 \
+        if (sm > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);   \
+        if (e == cudaSuccess)                                                                                        \
+            kern<<<Mpad / kWsVectors, 2 * kWsVectors, sm, s>>>(w, m, o, theta, ld, M, loss, grad, ldg, grad_u0, ckpt, \
+                                                             Mpad);                                                  \
+    }
+#define SIRD_LGWS_COST(SV)                                \
+    switch (m.cost) {                                     \
+        case COST_MSE: SIRD_LGWS(SV, COST_MSE) break;     \
+        case COST_MXSE: SIRD_LGWS(SV, COST_MXSE) break;   \
+        case COST_MAE: SIRD_LGWS(SV, COST_MAE) break;     \
+        default: SIRD_LGWS(SV, COST_MAPE) break;          \
+    }
+        if (m.spd == 10) {
+            SIRD_LGWS_COST(10)
+        } else {
+            SIRD_LGWS_COST(20)
+        }
+#undef SIRD_LGWS_COST
+#undef SIRD_LGWS
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
     // 64 threads per block: the work is one long serial chain per parameter vector, so a few
     // warps per SM on as many SMs as possible
     const int block = 64;
-    const size_t sm = (2 * (size_t)((w.n_obs + 3) & ~3) + (size_t)m.P * block + 3 * (size_t)m.spd * block) * sizeof(float);
-    (void)cudaGetLastError();
-    cudaError_t e = cudaSuccess;
+    const size_t sm = (obs + (size_t)m.P * block + 3 * (size_t)m.spd * block) * sizeof(float);
 #define SIRD_LG32(SV, CV, RV)                                                                                 \
     {                                                                                                         \
         auto kern = loss_grad_f32_kernel<SV, CV, RV>;                                                         \
@@ -337,11 +499,7 @@ cudaError_t launch_loss_grad_f32(const WindowDev& w, const ModelDev& m, const Ob
     if (m.beta_form == BETA_RAMP) {
         SIRD_LG32_COST(0, true)
     } else {
-        switch (m.spd) {
-            case 10: SIRD_LG32_COST(10, false) break;
-            case 20: SIRD_LG32_COST(20, false) break;
-            default: SIRD_LG32_COST(0, false) break;
-        }
+        SIRD_LG32_COST(0, false)
     }
 #undef SIRD_LG32_COST
 #undef SIRD_LG32

@@ -98,7 +98,7 @@ __global__ void polish_accept_kernel(PolishState s, uint32_t logmask, int first)
 __global__ void polish_direction_kernel(PolishState s, PsoCoeffs<double> c, double first_step) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= s.k) return;
-    const int P = s.P, k = s.k, kt = k * kTrials;
+    const int P = s.P, k = s.k;
     double q[kMaxParams], a[kMem];
     for (int d = 0; d < P; ++d) q[d] = s.g[(size_t)d * k + j];
     const int cnt = s.count[j];
@@ -140,22 +140,30 @@ __global__ void polish_direction_kernel(PolishState s, PsoCoeffs<double> c, doub
         for (int d = 0; d < P; ++d) s.d[(size_t)d * k + j] = -sc * s.g[(size_t)d * k + j];
         s.count[j] = 0;
     }
-    for (int t = 0; t < kTrials; ++t) {
-        const double alpha = ldexp(1.0, -t);
-        for (int d = 0; d < P; ++d) {
-            const double zn = fmin(fmax(s.z[(size_t)d * k + j] + alpha * s.d[(size_t)d * k + j], c.zlb[d]), c.zub[d]);
-            const double th = decode(zn, (c.logmask >> d) & 1u);
-            s.tht[(size_t)d * kt + (size_t)t * k + j] = th;
-            if (s.f32) s.thf[(size_t)d * kt + (size_t)t * k + j] = (float)th;
-        }
-    }
+}
+
+// The trial points z + 2^-t d, clamped to the box and decoded: one thread per (dimension, trial,
+// candidate), so that the decodes (an exp each on log dimensions) run side by side.
+__global__ void polish_trials_kernel(PolishState s, PsoCoeffs<double> c) {
+    const int k = s.k, kt = k * kTrials;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.P * kt) return;
+    const int j = i % k, t = (i / k) % kTrials, d = i / kt;
+    const double alpha = ldexp(1.0, -t);
+    const double zn = fmin(fmax(s.z[(size_t)d * k + j] + alpha * s.d[(size_t)d * k + j], c.zlb[d]), c.zub[d]);
+    const double th = decode(zn, (c.logmask >> d) & 1u);
+    s.tht[(size_t)d * kt + (size_t)t * k + j] = th;
+    if (s.f32) s.thf[(size_t)d * kt + (size_t)t * k + j] = (float)th;
 }
 
 // Armijo choice among the evaluated trials; the accepted theta goes to trial slot 0 and z to zt.
+// One thread per (dimension, candidate): each makes the candidate's (identical) choice and
+// decodes its own dimension; the dimension-0 thread records whether the candidate stops.
 __global__ void polish_select_kernel(PolishState s, PsoCoeffs<double> c) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= s.k) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.P * s.k) return;
     const int P = s.P, k = s.k, kt = k * kTrials;
+    const int j = i % k, dd = i / k;
     const double f0 = s.f[j];
     double gd = 0.0;
     for (int d = 0; d < P; ++d) gd += s.g[(size_t)d * k + j] * s.d[(size_t)d * k + j];
@@ -172,21 +180,22 @@ __global__ void polish_select_kernel(PolishState s, PsoCoeffs<double> c) {
     }
     if (pick < 0) pick = tbest;  // no Armijo step: take the lowest trial if it improves
     if (pick < 0 || !s.active[j]) {
-        s.active[j] = 0;
+        // a candidate stops for good; its other threads reach pick = -1 as well, whichever value
+        // of active[j] they read, since the trial choice above is the same in all of them
+        if (dd == 0) s.active[j] = 0;
         pick = -1;
     }
-    for (int d = 0; d < P; ++d) {
-        double zn;
-        if (pick >= 0) {
-            zn = fmin(fmax(s.z[(size_t)d * k + j] + ldexp(1.0, -pick) * s.d[(size_t)d * k + j], c.zlb[d]), c.zub[d]);
-        } else {
-            zn = s.z[(size_t)d * k + j];
-        }
-        s.zt[(size_t)d * k + j] = zn;
-        const double th = decode(zn, (c.logmask >> d) & 1u);
-        s.tht[(size_t)d * kt + j] = th;
-        if (s.f32) s.thf[(size_t)d * kt + j] = (float)th;
+    const int d = dd;
+    double zn;
+    if (pick >= 0) {
+        zn = fmin(fmax(s.z[(size_t)d * k + j] + ldexp(1.0, -pick) * s.d[(size_t)d * k + j], c.zlb[d]), c.zub[d]);
+    } else {
+        zn = s.z[(size_t)d * k + j];
     }
+    s.zt[(size_t)d * k + j] = zn;
+    const double th = decode(zn, (c.logmask >> d) & 1u);
+    s.tht[(size_t)d * kt + j] = th;
+    if (s.f32) s.thf[(size_t)d * kt + j] = (float)th;
 }
 
 // Best candidate: theta, FP64 loss and sum of squared errors (for R^2) into *res.
@@ -295,14 +304,19 @@ cudaError_t launch_polish(const WindowDev& w, const ModelDev& m, const ObsDev& o
         polish_accept_kernel<<<grid, 128, 0, st>>>(s, c.logmask, 1);
         e = cudaGetLastError();
     }
+    const unsigned grid_trials = (unsigned)((P * kt + 127) / 128), grid_dims = (unsigned)((P * k + 127) / 128);
     for (int it = 0; it < iters && e == cudaSuccess; ++it) {
         polish_direction_kernel<<<grid, 128, 0, st>>>(s, c, first_step);
         e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            polish_trials_kernel<<<grid_trials, 128, 0, st>>>(s, c);
+            e = cudaGetLastError();
+        }
         if (e == cudaSuccess)
             e = f32 ? launch_eval_f32(w, m, o, s.thf, kt, kt, s.ftf, 128, nullptr, st)
                     : launch_eval_f64(w, m, o, s.tht, kt, kt, s.ft, 64, nullptr, st);
         if (e != cudaSuccess) break;
-        polish_select_kernel<<<grid, 128, 0, st>>>(s, c);
+        polish_select_kernel<<<grid_dims, 128, 0, st>>>(s, c);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = grad_at_slot0();
         if (e != cudaSuccess) break;

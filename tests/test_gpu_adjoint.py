@@ -34,7 +34,7 @@ def gpu_loss_grad(cal, th, ckpt=16):
 
 @pytest.mark.parametrize("cost", ["mse", "mxse", "mae", "mape"])
 @pytest.mark.parametrize("ckpt", [1, 7, 16, 64])
-def test_adjoint_f64_bit_exact_c4_window(cost, ckpt):
+def test_adjoint_f64_bit_exact_90_day_window(cost, ckpt):
     # the differentiation configuration: 90 days at dt = 0.05 (1800 steps), 4 segments + gamma, mu, I0
     y, N, _, _ = window("90d")
     th = np.concatenate([near_truth("90d", 4, 40, 1), box_thetas(4, 24, 2)])
@@ -170,7 +170,7 @@ def check_f32_gradient(pb, th, L, G, E, cost="mse"):
 
 
 @pytest.mark.parametrize("cost", ["mse", "mxse", "mae", "mape"])
-def test_adjoint_f32_c4_window(cost):
+def test_adjoint_f32_90_day_window(cost):
     y, N, _, _ = window("90d")
     th = f32(np.concatenate([near_truth("90d", 4, 40, 1), box_thetas(4, 24, 2)]))
     cal = sird.Calibrator(y, N, K=4, spd=20, cost=sird.COSTS[cost], particles=32, iters=1, lb=[1e-3] * 7,

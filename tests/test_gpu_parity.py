@@ -128,14 +128,14 @@ def test_eval_f32_full_size_sampled():
 
 # ------------------------------------------------------------------ swarm
 
-def c1_setup(M=100):
+def plain64_setup(M=100):
     ser = synth.load_series("30d")
     lb, ub = configs.bounds(1, log=False)
     return ser["yD"], ser["N"], lb, ub
 
 
 def test_pso_f64_bit_exact_with_oracle():
-    y, N, lb, ub = c1_setup()
+    y, N, lb, ub = plain64_setup()
     M = 100
     cal = sird.Calibrator(y, N, K=1, spd=10, particles=M, iters=5, lb=lb, ub=ub, precision=64, seed=3)
     pso = O.PSO(O.Problem(yD=y, N=N, K=1, spd=10), M, lb, ub, seed=3).init()
@@ -152,8 +152,8 @@ def test_pso_f64_bit_exact_with_oracle():
 
 
 def test_calibrate_f64_plain_method_matches_oracle():
-    # configuration c1: FP64, K = 1 plus I0, 30 days, 64 particles, 200 iterations, seed 0
-    y, N, lb, ub = c1_setup()
+    # the plain64 configuration: FP64, K = 1 plus I0, 30 days, 64 particles, 200 iterations, seed 0
+    y, N, lb, ub = plain64_setup()
     c = configs.CONFIGS["plain64"]
     cal = sird.Calibrator(y, N, K=1, spd=10, particles=c["M"], iters=c["iters"], lb=lb, ub=ub, precision=64, seed=0)
     res = cal.calibrate()
@@ -236,7 +236,7 @@ def test_topk_reevaluation_matches_oracle(k):
 
 @pytest.mark.parametrize("M", [1, 31, 33, 129])
 def test_small_and_ragged_swarms(M):
-    y, N, lb, ub = c1_setup()
+    y, N, lb, ub = plain64_setup()
     cal = sird.Calibrator(y, N, K=1, spd=10, particles=M, iters=7, lb=lb, ub=ub, precision=64, seed=M)
     res = cal.calibrate()
     pso = O.PSO(O.Problem(yD=y, N=N, K=1, spd=10), M, lb, ub, seed=M).init().step(7)
