@@ -54,8 +54,12 @@ PROFILED = {
     "window60": {"files": ["pso_persistent.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"],
            "sha": "838214511d57ce23", "traffic_bytes": 448000, "fma_pipe": 0.3726,
            "profile": "profiles/pso_f32_persistent_window60.md"},
-    "gradient90": {"files": ["adjoint_f32.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": None,
-           "traffic_bytes": 159232, "fma_pipe": 0.1222, "profile": "profiles/loss_grad_f32_gradient90.md"},
+    "gradient90": {"files": ["adjoint_f32.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "86313126d365c9fb",
+           "traffic_bytes": 165888, "fma_pipe": 0.0737, "profile": "profiles/loss_grad_f32_gradient90.md"},
+    "paper": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "6b9e9b7c79328125",
+           "traffic_bytes": 24208924000, "fma_pipe": 0.4687, "profile": "profiles/pso_flat_f32_paper.md"},
+    "paper_ird": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "6b9e9b7c79328125",
+           "traffic_bytes": 24142548000, "fma_pipe": 0.4502, "profile": "profiles/pso_flat_f32_paper_ird.md"},
     "swarm2p20": {"files": ["pso_kernels.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "6875c43733950da4",
            "traffic_bytes": 276303616, "fma_pipe": 0.7505, "profile": "profiles/pso_f32_kernel_swarm2p20.md"},
 }
@@ -363,7 +367,8 @@ def run_batched(args, rank, world):
                    "parallelism": f"independent batches x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic(name),
-                     "traffic_source": PROFILED.get(name, {}).get("profile"), "kernel": "pso_batch_f32",
+                     "traffic_source": PROFILED.get(name, {}).get("profile"),
+                     "kernel": "pso_flat_f32" if batch.launch_mode == sird.LAUNCH_FLAT else "pso_batch_f32",
                      "ncu_fma_pipe_active": profiled_traffic(name, "fma_pipe"),
                      "avg_launch_us": kms * 1e3, "flops_per_launch": flops,
                      "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
@@ -477,7 +482,9 @@ def run_stability(args, rank, world):
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"independent batches x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "pso_batch_f32",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic("stability"),
+                     "traffic_source": PROFILED.get("stability", {}).get("profile"),
+                     "kernel": "pso_flat_f32" if batch.launch_mode == sird.LAUNCH_FLAT else "pso_batch_f32",
                      "avg_launch_us": kms * 1e3, "flops_per_launch": flops,
                      "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
         "e2e": {"value": units * args.steps * world / (e2e_total / 1e3), "unit": UNIT,
