@@ -48,7 +48,10 @@ typedef enum sird_status {
                                  non-finite observation, log scale with lb <= 0 */
     SIRD_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in sird_last_error) */
     SIRD_ERR_NUMERIC = 3,     /* no finite loss where one is needed (e.g. every particle NaN) */
-    SIRD_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out (the kernel returned early) */
+    SIRD_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out (the kernel returned early;
+                                 a wait polls 2^21 (single-window exchange) or 2^22 (flat-batch
+                                 barrier) times, a few seconds at most, or as many times as the
+                                 environment variable SIRD_WAIT_LIMIT gives, read at launch) */
     SIRD_ERR_STATE = 5,       /* call out of order, or a state blob that does not match the handle */
     SIRD_ERR_NOMEM = 6,       /* device or host allocation failed */
     SIRD_ERR_UNSUPPORTED = 7  /* option combination the library does not implement */
