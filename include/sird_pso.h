@@ -236,6 +236,34 @@ sird_status sird_pso_set_state(sird_pso_t h, const void* buf, size_t size);
  * loss_out (host, [k]) their stored FP32 losses.  Blocks.  The forecast ensemble of Sec. 4.2
  * is built from these. */
 sird_status sird_pso_topk(sird_pso_t h, int k, double* theta_out, double* loss_out);
+/* The same, with each one's particle index (host, [k]; global for a shard, see below). */
+sird_status sird_pso_topk_indexed(sird_pso_t h, int k, double* theta_out, double* loss_out, int* index_out);
+
+/* ---------------------------------------------------------------- one swarm over several ranks
+ *
+ * The particles of a swarm are evaluated independently (Sec. 3.3); the synchronous global best
+ * is their only coupling.  A swarm of `total` FP32 particles can therefore be split by particle:
+ * each rank creates a handle for its particles (config.particles of them, the same seed and
+ * stream word on every rank) and declares them particles offset .. offset + particles - 1 of the
+ * swarm.  Its random numbers and its argmin keys then use the global particle index, so after
+ *     sird_pso_init, then per iteration: sird_pso_shard_best on every rank, the argmin over the
+ *     ranks (lowest loss, lowest index on ties), sird_pso_set_gbest of that particle's position
+ *     on every rank, sird_pso_step(h, 1)
+ * the shards together hold exactly the personal bests of the unsharded swarm.  A shard runs one
+ * launch per iteration; sird_pso_calibrate, sird_pso_polish and the state blob calls refuse it;
+ * sird_pso_result re-evaluates the shard's own best (its index reported globally).
+ *
+ * set_shard: before sird_pso_init; FP32 handles only (SIRD_ERR_UNSUPPORTED otherwise);
+ *   SIRD_ERR_ARG unless 0 <= offset and offset + particles <= total <= SIRD_MAX_PARTICLES.
+ * shard_best: the best personal best among the handle's particles after the last init/step
+ *   (blocks): its FP32 loss, global index and position z (host, [P] floats, search
+ *   coordinates: ln theta on log-scaled dimensions).
+ * set_gbest: the swarm's global best for the next iteration (z host [P], inside the box; index
+ *   in 0 .. total - 1); blocks until the copy is on the device.
+ */
+sird_status sird_pso_set_shard(sird_pso_t h, int offset, int total);
+sird_status sird_pso_shard_best(sird_pso_t h, float* loss, int* index, float* z);
+sird_status sird_pso_set_gbest(sird_pso_t h, const float* z, float loss, int index);
 
 /* ---------------------------------------------------------------- gradient */
 

@@ -76,6 +76,7 @@ class _PsoCfg(C.Structure):
         ("stream", C.c_uint32),
         ("store_f32", C.c_int),
         ("objective_kind", C.c_int),
+        ("p_offset", C.c_uint32),
     ]
 
 
@@ -280,10 +281,13 @@ def ensemble_bands(pb: Problem, thetas, horizon: int, fractions=(0.95, 0.9, 0.5)
 
 
 class PSO:
-    """Synchronous PSO of Sec. 3.3 with particle-major FP64 state arrays."""
+    """Synchronous PSO of Sec. 3.3 with particle-major FP64 state arrays.  p_offset: the swarm
+    is particles p_offset .. p_offset + M - 1 of a larger one, numbered so in the random-number
+    counter (its gbest is then the caller's to set between steps)."""
 
     def __init__(self, pb: Problem | None, M: int, zlb, zub, logdim=None, w=0.5, c1=0.5, c2=0.5,
-                 seed: int = 0, stream: int = 0, store_f32: bool = False, objective_kind: int = OBJ_SIRD):
+                 seed: int = 0, stream: int = 0, store_f32: bool = False, objective_kind: int = OBJ_SIRD,
+                 p_offset: int = 0):
         self.pb = pb
         self.zlb = _f64(zlb)
         self.zub = _f64(zub)
@@ -291,7 +295,7 @@ class PSO:
         self.logdim = np.ascontiguousarray(np.zeros(P, np.int32) if logdim is None else np.asarray(logdim, np.int32))
         self.cfg = _PsoCfg(int(M), P, float(w), float(c1), float(c2), _dptr(self.zlb), _dptr(self.zub),
                            self.logdim.ctypes.data_as(C.POINTER(C.c_int)), int(seed) & (2**64 - 1),
-                           int(stream) & 0xFFFFFFFF, int(store_f32), int(objective_kind))
+                           int(stream) & 0xFFFFFFFF, int(store_f32), int(objective_kind), int(p_offset))
         self.M, self.P = int(M), P
         self.x = np.zeros((M, P))
         self.v = np.zeros((M, P))

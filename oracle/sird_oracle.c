@@ -406,7 +406,7 @@ static void set_gbest(const orc_pso_cfg* cfg, orc_pso_state* st) {
  * call gives four words; dimension d uses words 2*(d%2) and 2*(d%2)+1 as its (r1, r2)
  * (at iteration 0: the position and velocity draws). */
 static void draw(const orc_pso_cfg* cfg, int p, int d, int iter, double* u_a, double* u_b) {
-    uint32_t ctr[4] = {(uint32_t)p, (uint32_t)iter, (uint32_t)(d >> 1), cfg->stream};
+    uint32_t ctr[4] = {(uint32_t)p + cfg->p_offset, (uint32_t)iter, (uint32_t)(d >> 1), cfg->stream};
     uint32_t key[2] = {(uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32)};
     uint32_t r[4];
     orc_philox4x32_10(ctr, key, r);

@@ -124,6 +124,9 @@ typedef struct {
     uint32_t stream;       /* fourth Philox counter word (window / run id) */
     int store_f32;         /* 1: swarm state and decoded theta are stored as float32 values */
     int objective_kind;    /* ORC_OBJ_* */
+    uint32_t p_offset;     /* global index of particle 0: the swarm is particles p_offset ..
+                              p_offset + M - 1 of a larger one (Sec. 3.3: particles are
+                              independent), numbered so in the Philox counter; 0 otherwise */
 } orc_pso_cfg;
 
 /* Swarm state, particle-major: x[p*P + d]. */

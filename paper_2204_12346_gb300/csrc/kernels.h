@@ -45,6 +45,7 @@ struct PsoCoeffs {
     T zlb[kMaxParams], zub[kMaxParams];
     uint32_t logmask;
     uint32_t key0, key1, stream_id;
+    uint32_t p_off;  // global index of the swarm's particle 0 (a shard of a larger swarm; else 0)
 };
 
 // FP64 result of the re-evaluation of candidate personal bests.

@@ -94,9 +94,11 @@ __global__ void __launch_bounds__(1024) pso_f32_kernel(WindowDev w, ModelDev m, 
     auto update = [&](int p, int col) {
         uint4 rnd = make_uint4(0, 0, 0, 0);
         for (int d = 0; d < P; ++d) {
-            // one Philox call per (particle, iteration, dimension pair)
-            if ((d & 1) == 0) rnd = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)iter, (uint32_t)(d >> 1), c.stream_id),
-                                                 c.key0, c.key1);
+            // one Philox call per (particle, iteration, dimension pair); a shard counts its
+            // particles from its global offset
+            if ((d & 1) == 0)
+                rnd = philox4x32_10(make_uint4((uint32_t)p + c.p_off, (uint32_t)iter, (uint32_t)(d >> 1), c.stream_id),
+                                    c.key0, c.key1);
             const float ua = u01f((d & 1) ? rnd.z : rnd.x);
             const float ub = u01f((d & 1) ? rnd.w : rnd.y);
             const size_t off = (size_t)d * sw.ld + p;
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(1024) pso_f32_kernel(WindowDev w, ModelDev m, 
         } else {
             best = sw.pbf[p];
         }
-        const unsigned long long kp = argmin_key(best, (uint32_t)p);
+        const unsigned long long kp = argmin_key(best, (uint32_t)p + c.p_off);
         key = kp < key ? kp : key;
     };
     if (p0 < sw.M) {
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(1024) pso_f32_kernel(WindowDev w, ModelDev m, 
             wk[0] = g;
         }
         __syncthreads();
-        const int gi = (int)(wk[0] & 0xFFFFFFFFu);
+        const int gi = (int)((uint32_t)(wk[0] & 0xFFFFFFFFu) - c.p_off);  // local index of the best
         if (tid < P) sw.gbest[tid] = __ldcg(&sw.pb[(size_t)tid * sw.ld + gi]);
     }
 }

@@ -79,6 +79,7 @@ struct sird_pso {
     void* d_ckpt = nullptr;                             // adjoint checkpoints (grown on demand)
     size_t ckpt_bytes = 0;
     int n_obs = 0;
+    int shard_total = 0;  // > 0: the handle holds particles c32.p_off .. c32.p_off + M - 1 of a swarm this size
     // errors
     sird_status sticky = SIRD_OK;
     std::string msg;
@@ -118,11 +119,14 @@ struct sird_pso {
         return cudaSuccess;
     }
     cudaError_t enqueue_result(cudaStream_t s) {
-        if (precision == 32 && reeval_k > 0) {
+        // a shard's global-best index is global and may lie in another shard: it re-evaluates
+        // the best of its own particles, found by the top-k selection (local indices)
+        const int k = (precision == 32 && shard_total > 0 && reeval_k == 0) ? 1 : reeval_k;
+        if (precision == 32 && k > 0) {
             unsigned long long* keys = nullptr;
-            cudaError_t e = launch_topk_f32((const float*)pbf, M, reeval_k, tk_a, tk_b, &keys, s);
+            cudaError_t e = launch_topk_f32((const float*)pbf, M, k, tk_a, tk_b, &keys, s);
             if (e != cudaSuccess) return e;
-            e = launch_reeval(win, mdl, obs, &c32, nullptr, pb, pbf, ld, keys, reeval_k, nullptr, d_res, s);
+            e = launch_reeval(win, mdl, obs, &c32, nullptr, pb, pbf, ld, keys, k, nullptr, d_res, s);
             if (e != cudaSuccess) return e;
         } else {
             cudaError_t e = launch_reeval(win, mdl, obs, precision == 32 ? &c32 : nullptr,
@@ -139,7 +143,7 @@ struct sird_pso {
         out->loss = h_res->loss;
         out->loss_search = h_res->loss_search;
         out->r2_D = ss_tot > 0 ? 1.0 - h_res->sse / ss_tot : NAN;
-        out->index = h_res->index;
+        out->index = h_res->index + (int)c32.p_off;  // global particle index (a shard's offset added)
         out->iters_done = iter;
     }
 };
@@ -364,7 +368,9 @@ extern "C" sird_status sird_pso_create(const sird_problem* pb, const sird_pso_co
     h->gbest = base + 3 * plane + (size_t)h->ld * tsz;
 
     const size_t grid = (size_t)((h->M + h->block - 1) / h->block);
-    const size_t tk = h->reeval_k > 0 ? topk_scratch_keys(h->M, h->reeval_k) : 0;
+    // top-k keys for the FP32 re-evaluation (at least the best one: a shard's result uses them)
+    const int tk_k = h->precision == 32 ? (h->reeval_k > 1 ? h->reeval_k : 1) : h->reeval_k;
+    const size_t tk = tk_k > 0 ? topk_scratch_keys(h->M, tk_k) : 0;
     const size_t aux_bytes = 256 + grid * sizeof(MinPair64) + 2 * tk * sizeof(unsigned long long) + sizeof(ResultDev);
     e = cudaMalloc(&h->d_aux, aux_bytes);
     if (e != cudaSuccess) return bail(e, "allocating scratch");
@@ -568,6 +574,8 @@ extern "C" sird_status sird_pso_result(sird_pso_t h, sird_result* out) {
 extern "C" sird_status sird_pso_calibrate(sird_pso_t h, sird_result* out) {
     if (!h || !out) return SIRD_ERR_ARG;
     if (h->sticky) return h->sticky;
+    if (h->shard_total > 0)
+        return h->fail(SIRD_ERR_STATE, "calibrate: a shard steps with sird_pso_step, its global best set between steps");
     if (!h->calib) {
         // captured once on a private stream (the caller's may be the legacy default stream,
         // which cannot be captured), then launched on the caller's stream
@@ -604,6 +612,7 @@ extern "C" sird_status sird_pso_calibrate(sird_pso_t h, sird_result* out) {
 extern "C" sird_status sird_pso_get_state(sird_pso_t h, void* buf, size_t* size) {
     if (!h || !size) return SIRD_ERR_ARG;
     if (h->sticky) return h->sticky;
+    if (h->shard_total > 0) return h->fail(SIRD_ERR_UNSUPPORTED, "get_state: not for a shard of a swarm");
     const size_t tsz = h->precision == 32 ? 4 : 8;
     const size_t need = sizeof(StateHeader) + (3 * (size_t)h->P + 1) * h->M * tsz;
     if (!buf) {
@@ -635,6 +644,7 @@ extern "C" sird_status sird_pso_get_state(sird_pso_t h, void* buf, size_t* size)
 extern "C" sird_status sird_pso_set_state(sird_pso_t h, const void* buf, size_t size) {
     if (!h || !buf) return SIRD_ERR_ARG;
     if (h->sticky) return h->sticky;
+    if (h->shard_total > 0) return h->fail(SIRD_ERR_UNSUPPORTED, "set_state: not for a shard of a swarm");
     const size_t tsz = h->precision == 32 ? 4 : 8;
     const size_t need = sizeof(StateHeader) + (3 * (size_t)h->P + 1) * h->M * tsz;
     StateHeader hd;
@@ -707,6 +717,7 @@ extern "C" sird_status sird_pso_polish(sird_pso_t h, int k, int iters, double fi
                                        int precision, sird_result* out) {
     if (!h || !out) return SIRD_ERR_ARG;
     if (h->sticky) return h->sticky;
+    if (h->shard_total > 0) return h->fail(SIRD_ERR_STATE, "polish: not for a shard of a swarm");
     if (h->precision != 32) return h->fail(SIRD_ERR_UNSUPPORTED, "polish: FP32 swarms only");
     if (h->mdl.ird) return h->fail(SIRD_ERR_UNSUPPORTED, "polish: the adjoint covers F_D only");
     if (k < 1 || k > 1024 || k > h->M || iters < 0 || !(first_step > 0) || ckpt_every < 1 || ckpt_every > 64 ||
@@ -826,7 +837,19 @@ extern "C" sird_status sird_ensemble_bands(const sird_problem* pb, const double*
     return SIRD_OK;
 }
 
+static sird_status topk_impl(sird_pso_t h, int k, double* theta_out, double* loss_out, int* index_out);
+
 extern "C" sird_status sird_pso_topk(sird_pso_t h, int k, double* theta_out, double* loss_out) {
+    return topk_impl(h, k, theta_out, loss_out, nullptr);
+}
+
+extern "C" sird_status sird_pso_topk_indexed(sird_pso_t h, int k, double* theta_out, double* loss_out,
+                                             int* index_out) {
+    if (h && !h->sticky && !index_out) return h->fail(SIRD_ERR_ARG, "topk_indexed: index_out is NULL");
+    return topk_impl(h, k, theta_out, loss_out, index_out);
+}
+
+static sird_status topk_impl(sird_pso_t h, int k, double* theta_out, double* loss_out, int* index_out) {
     if (!h) return SIRD_ERR_ARG;
     if (h->sticky) return h->sticky;
     if (h->precision != 32) return h->fail(SIRD_ERR_UNSUPPORTED, "topk: FP32 swarms only");
@@ -848,8 +871,60 @@ extern "C" sird_status sird_pso_topk(sird_pso_t h, int k, double* theta_out, dou
                                dloss, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(theta_out, dth, (size_t)k * h->P * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(loss_out, dloss, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    std::vector<unsigned long long> hk(index_out ? (size_t)k : 0);
+    if (e == cudaSuccess && index_out)
+        e = cudaMemcpyAsync(hk.data(), keys, (size_t)k * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(dmem);
+    if (e == cudaSuccess && index_out)
+        for (int j = 0; j < k; ++j) index_out[j] = (int)((hk[j] & 0xFFFFFFFFu) + h->c32.p_off);
     return h->cuda(e, "topk");
+}
+
+// ---------------------------------------------------------------- sharded swarm
+
+extern "C" sird_status sird_pso_set_shard(sird_pso_t h, int offset, int total) {
+    if (!h) return SIRD_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if (h->precision != 32) return h->fail(SIRD_ERR_UNSUPPORTED, "set_shard: FP32 swarms only");
+    if (h->iter >= 0) return h->fail(SIRD_ERR_STATE, "set_shard: before init");
+    if (offset < 0 || total < 1 || total > SIRD_MAX_PARTICLES || (long long)offset + h->M > (long long)total)
+        return h->fail(SIRD_ERR_ARG, "set_shard: particles offset .. offset + M - 1 must lie in 0 .. total - 1");
+    h->c32.p_off = (uint32_t)offset;
+    h->shard_total = total;
+    h->persistent = false;  // one launch per iteration: the global best is exchanged between them
+    return SIRD_OK;
+}
+
+extern "C" sird_status sird_pso_shard_best(sird_pso_t h, float* loss, int* index, float* z) {
+    if (!h) return SIRD_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if (!loss || !index || !z) return h->fail(SIRD_ERR_ARG, "shard_best: NULL output");
+    if (h->precision != 32) return h->fail(SIRD_ERR_UNSUPPORTED, "shard_best: FP32 swarms only");
+    if (h->iter < 0) return h->fail(SIRD_ERR_STATE, "shard_best before init");
+    cudaError_t e = cudaMemcpyAsync(loss, h->red.gbest_f, sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(index, h->red.gbest_idx, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(z, h->gbest, (size_t)h->P * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return h->cuda(e, "shard_best");
+}
+
+extern "C" sird_status sird_pso_set_gbest(sird_pso_t h, const float* z, float loss, int index) {
+    if (!h) return SIRD_ERR_ARG;
+    if (h->sticky) return h->sticky;
+    if (!z) return h->fail(SIRD_ERR_ARG, "set_gbest: z is NULL");
+    if (h->precision != 32) return h->fail(SIRD_ERR_UNSUPPORTED, "set_gbest: FP32 swarms only");
+    if (h->iter < 0) return h->fail(SIRD_ERR_STATE, "set_gbest before init");
+    const int total = h->shard_total > 0 ? h->shard_total : h->M;
+    if (index < 0 || index >= total) return h->fail(SIRD_ERR_ARG, "set_gbest: index out of range");
+    for (int d = 0; d < h->P; ++d)
+        if (!(z[d] >= h->c32.zlb[d] && z[d] <= h->c32.zub[d]))
+            return h->fail(SIRD_ERR_ARG, "set_gbest: position outside the search box");
+    // host copies first, then the device; the stream orders them before the next iteration
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(h->gbest, z, (size_t)h->P * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->red.gbest_f, &loss, sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->red.gbest_idx, &index, sizeof(int), cudaMemcpyHostToDevice);
+    return h->cuda(e, "set_gbest");
 }
 

@@ -31,6 +31,7 @@ EXPORTS = [
     "sird_forecast", "sird_pso_calibrate_batched", "sird_pso_set_observations", "sird_pso_set_timing", "sird_pso_launch_mode",
     "sird_pso_step_f32_noalloc", "sird_pso_topk", "sird_ensemble_bands", "sird_pso_polish", "sird_batch_create", "sird_batch_calibrate", "sird_batch_set_observations", "sird_batch_launch_mode",
     "sird_batch_block_size", "sird_batch_blocks_per_sm", "sird_batch_destroy", "sird_batch_set_timing",
+    "sird_pso_topk_indexed", "sird_pso_set_shard", "sird_pso_shard_best", "sird_pso_set_gbest",
 ]
 
 
@@ -107,6 +108,10 @@ def lib():
         L.sird_pso_set_timing.argtypes = [vp, vp, vp]
         L.sird_pso_launch_mode.argtypes = [vp]
         L.sird_pso_topk.argtypes = [vp, ip, dp, dp]
+        L.sird_pso_topk_indexed.argtypes = [vp, ip, dp, dp, C.POINTER(C.c_int)]
+        L.sird_pso_set_shard.argtypes = [vp, ip, ip]
+        L.sird_pso_shard_best.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_int), C.POINTER(C.c_float)]
+        L.sird_pso_set_gbest.argtypes = [vp, C.POINTER(C.c_float), C.c_float, ip]
         L.sird_batch_create.argtypes = [ip, C.POINTER(Problem), C.POINTER(Config), vp, C.POINTER(vp)]
         L.sird_batch_calibrate.argtypes = [vp, C.POINTER(Result)]
         L.sird_batch_block_size.argtypes = [vp]
@@ -236,6 +241,16 @@ class Calibrator:
                                             C.c_void_p(out.data_ptr()), precision))
         return out
 
+    def eval64(self, thetas) -> np.ndarray:
+        """FP64 losses (the paper's arithmetic) of the rows of thetas ([k, P], host)."""
+        import torch
+
+        th = torch.from_numpy(np.ascontiguousarray(np.asarray(thetas, dtype=np.float64).T)).cuda()
+        torch.cuda.current_stream().synchronize()  # th is on the device before the handle's stream reads it
+        out = self.eval(th, precision=64)
+        self.sync()
+        return out.cpu().numpy()
+
     def set_observations(self, yD):
         """Uploads new observations (same length, same first value) for the next calibration."""
         y = _f64(yD)
@@ -299,12 +314,39 @@ class Calibrator:
                                               int(precision), C.byref(r)))
         return r.as_dict()
 
-    def topk(self, k: int):
-        """(theta [k, P], loss [k]) of the k best personal bests, best first."""
+    def topk(self, k: int, with_index: bool = False):
+        """(theta [k, P], loss [k]) of the k best personal bests, best first; with_index adds
+        their particle indices (global for a shard)."""
         th = np.zeros((k, self.P))
         lo = np.zeros(k)
-        self._check(self._lib.sird_pso_topk(self.h, int(k), _dptr(th), _dptr(lo)))
-        return th, lo
+        if not with_index:
+            self._check(self._lib.sird_pso_topk(self.h, int(k), _dptr(th), _dptr(lo)))
+            return th, lo
+        idx = np.zeros(k, dtype=np.int32)
+        self._check(self._lib.sird_pso_topk_indexed(self.h, int(k), _dptr(th), _dptr(lo),
+                                                    idx.ctypes.data_as(C.POINTER(C.c_int))))
+        return th, lo, idx
+
+    def set_shard(self, offset: int, total: int):
+        """Declares this handle's particles offset .. offset + M - 1 of a swarm of `total`."""
+        self._check(self._lib.sird_pso_set_shard(self.h, int(offset), int(total)))
+        return self
+
+    def shard_best(self):
+        """(FP32 loss, global index, z [P] float32) of the best personal best among this
+        handle's particles."""
+        f = C.c_float()
+        i = C.c_int()
+        z = np.zeros(self.P, dtype=np.float32)
+        self._check(self._lib.sird_pso_shard_best(self.h, C.byref(f), C.byref(i),
+                                                  z.ctypes.data_as(C.POINTER(C.c_float))))
+        return float(f.value), int(i.value), z
+
+    def set_gbest(self, z, loss: float, index: int):
+        """The swarm's global best (position z in the search coordinates) for the next step."""
+        z = np.ascontiguousarray(np.asarray(z, dtype=np.float32))
+        self._check(self._lib.sird_pso_set_gbest(self.h, z.ctypes.data_as(C.POINTER(C.c_float)), float(loss),
+                                                 int(index)))
 
     def get_state(self) -> dict:
         n = C.c_size_t(0)
