@@ -49,19 +49,19 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 # DRAM bytes per launch of the dominant kernel from committed ncu captures, valid only for the
 # kernel sources they were taken on (sha256[:16] of the files listed).
 PROFILED = {
-    "batch512": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "6b9e9b7c79328125",
-           "traffic_bytes": 14521856, "fma_pipe": 0.6546, "profile": "profiles/pso_batch_f32_batch512.md"},
+    "batch512": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "62051028ac05fff1",
+           "traffic_bytes": 14925568, "fma_pipe": 0.6545, "profile": "profiles/pso_batch_f32_batch512.md"},
     "window60": {"files": ["pso_persistent.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "838214511d57ce23", "traffic_bytes": 448000, "fma_pipe": 0.3726,
+           "sha": "4eb126cfce801d54", "traffic_bytes": 447232, "fma_pipe": 0.3729,
            "profile": "profiles/pso_f32_persistent_window60.md"},
-    "gradient90": {"files": ["adjoint_f32.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "86313126d365c9fb",
-           "traffic_bytes": 165888, "fma_pipe": 0.0737, "profile": "profiles/loss_grad_f32_gradient90.md"},
-    "paper": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "6b9e9b7c79328125",
-           "traffic_bytes": 24208924000, "fma_pipe": 0.4687, "profile": "profiles/pso_flat_f32_paper.md"},
-    "paper_ird": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "6b9e9b7c79328125",
-           "traffic_bytes": 24142548000, "fma_pipe": 0.4502, "profile": "profiles/pso_flat_f32_paper_ird.md"},
-    "swarm2p20": {"files": ["pso_kernels.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "6875c43733950da4",
-           "traffic_bytes": 276303616, "fma_pipe": 0.7505, "profile": "profiles/pso_f32_kernel_swarm2p20.md"},
+    "gradient90": {"files": ["adjoint_f32.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "070a4a24b1962a90",
+           "traffic_bytes": 166144, "fma_pipe": 0.0737, "profile": "profiles/loss_grad_f32_gradient90.md"},
+    "paper": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "62051028ac05fff1",
+           "traffic_bytes": 24306185000, "fma_pipe": 0.4677, "profile": "profiles/pso_flat_f32_paper.md"},
+    "paper_ird": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "62051028ac05fff1",
+           "traffic_bytes": 24273381000, "fma_pipe": 0.4481, "profile": "profiles/pso_flat_f32_paper_ird.md"},
+    "swarm2p20": {"files": ["pso_kernels.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "ffdd83a8f5592f57",
+           "traffic_bytes": 276096256, "fma_pipe": 0.7496, "profile": "profiles/pso_f32_kernel_swarm2p20.md"},
 }
 
 
