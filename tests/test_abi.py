@@ -73,4 +73,11 @@ def test_null_handle_calls_are_safe(L):
     assert L.sird_pso_init(None) == 1
     assert L.sird_pso_step(None, 1) == 1
     assert L.sird_pso_num_params(None) == 0
+    f, i = C.c_float(), C.c_int()
+    z = (C.c_float * 4)()
+    d = (C.c_double * 4)()
+    assert L.sird_pso_set_shard(None, 0, 10) == 1
+    assert L.sird_pso_shard_best(None, C.byref(f), C.byref(i), z) == 1
+    assert L.sird_pso_set_gbest(None, z, 0.0, 0) == 1
+    assert L.sird_pso_topk_indexed(None, 1, d, d, C.byref(i)) == 1
     L.sird_pso_destroy(None)

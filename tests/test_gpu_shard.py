@@ -136,3 +136,33 @@ def test_shards_on_two_gloo_ranks_follow_the_unsharded_swarm():
     for t in got:
         assert t[4] == want["index"] and t[5] == want["loss"]
         assert t[3][1] == int(np.lexsort((np.arange(TOTAL), want_f))[0])
+
+
+def test_shard_calls_check_their_arguments():
+    y, N, kw = setup()
+    cal = sird.Calibrator(y, N, particles=64, launch_mode=sird.LAUNCH_PER_ITER, **kw)
+
+    def status(fn, *a):
+        with pytest.raises(sird.SirdError) as e:
+            fn(*a)
+        cal._lib.sird_pso_clear_error(cal.h)
+        return e.value.status
+
+    assert status(cal.set_shard, TOTAL - 10, TOTAL) == 1  # particles past the end of the swarm
+    assert status(cal.set_shard, -1, TOTAL) == 1
+    cal.set_shard(64, TOTAL)
+    assert status(cal.shard_best) == 5  # before init
+    assert status(cal.calibrate) == 5  # a shard does not calibrate on its own
+    assert status(cal.get_state) == 7
+    cal.init()
+    assert status(cal.set_shard, 0, TOTAL) == 5  # after init
+    assert status(cal.set_gbest, np.full(7, 50.0, np.float32), 1.0, 0) == 1  # outside the box
+    loss, idx, z = cal.shard_best()
+    assert 64 <= idx < 128
+    assert status(cal.set_gbest, z, loss, TOTAL) == 1  # index past the swarm
+    cal.set_gbest(z, loss, idx)
+    cal.step(1)
+    c64 = sird.Calibrator(y, N, particles=64, **dict(kw, precision=64))
+    with pytest.raises(sird.SirdError) as e:
+        c64.set_shard(0, TOTAL)
+    assert e.value.status == 7
