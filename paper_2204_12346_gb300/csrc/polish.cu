@@ -55,91 +55,108 @@ __global__ void polish_init_kernel(PolishState s, const unsigned long long* __re
     }
 }
 
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);  // every lane: the same sum
+    return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    return v;
+}
+
 // After an adjoint launch at the accepted points (theta in tht slot 0, loss lnew, gradient gth):
-// convert the gradient to z, push (s, y) into the history, keep the best point.
+// convert the gradient to z, push (s, y) into the history, keep the best point.  One warp per
+// candidate, lane = dimension (P <= 32).
 __global__ void polish_accept_kernel(PolishState s, uint32_t logmask, int first) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= s.k) return;
-    const int P = s.P, k = s.k, kt = k * kTrials;
+    const int j = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (j >= s.k) return;  // whole warps
+    const int P = s.P, k = s.k, kt = k * kTrials, d = lane;
+    const bool on = lane < P;
     const double fnew = s.f32 ? (double)s.lnewf[j] : s.lnew[j];
-    double sy = 0.0, yy = 0.0, ss = 0.0;
-    for (int d = 0; d < P; ++d) {
+    const int head = s.head[j], cnt = s.count[j];
+    const double best = s.best_f[j];
+    double sd = 0.0, yd = 0.0;
+    if (on) {
         const bool lg = (logmask >> d) & 1u;
         const double th = s.tht[(size_t)d * kt + j];
         const double gr = s.f32 ? (double)s.gthf[(size_t)d * k + j] : s.gth[(size_t)d * k + j];
         const double gz = lg ? th * gr : gr;
         if (!first) {
-            const double sd = s.zt[(size_t)d * k + j] - s.z[(size_t)d * k + j];
-            const double yd = gz - s.g[(size_t)d * k + j];
-            sy += sd * yd;
-            yy += yd * yd;
-            ss += sd * sd;
-            s.S[((size_t)s.head[j] * P + d) * k + j] = sd;
-            s.Y[((size_t)s.head[j] * P + d) * k + j] = yd;
+            sd = s.zt[(size_t)d * k + j] - s.z[(size_t)d * k + j];
+            yd = gz - s.g[(size_t)d * k + j];
+            s.S[((size_t)head * P + d) * k + j] = sd;
+            s.Y[((size_t)head * P + d) * k + j] = yd;
+            s.z[(size_t)d * k + j] = s.zt[(size_t)d * k + j];
         }
         s.g[(size_t)d * k + j] = gz;
+        if (fnew < best) s.best_th[(size_t)d * k + j] = th;
     }
     if (!first) {
-        for (int d = 0; d < P; ++d) s.z[(size_t)d * k + j] = s.zt[(size_t)d * k + j];
-        if (sy > 1e-14 * sqrt(ss * yy)) {  // curvature condition: keep the pair
-            s.rho[(size_t)s.head[j] * k + j] = 1.0 / sy;
-            s.head[j] = (s.head[j] + 1) % kMem;
-            if (s.count[j] < kMem) ++s.count[j];
+        const double sy = warp_sum_d(sd * yd), yy = warp_sum_d(yd * yd), ss = warp_sum_d(sd * sd);
+        if (lane == 0 && sy > 1e-14 * sqrt(ss * yy)) {  // curvature condition: keep the pair
+            s.rho[(size_t)head * k + j] = 1.0 / sy;
+            s.head[j] = (head + 1) % kMem;
+            if (cnt < kMem) s.count[j] = cnt + 1;
         }
     }
-    s.f[j] = fnew;
-    if (fnew < s.best_f[j]) {
-        s.best_f[j] = fnew;
-        for (int d = 0; d < P; ++d) s.best_th[(size_t)d * k + j] = s.tht[(size_t)d * kt + j];
+    __syncwarp();
+    if (lane == 0) {
+        s.f[j] = fnew;
+        if (fnew < best) s.best_f[j] = fnew;
     }
 }
 
-// Two-loop recursion and the trial points z + 2^-q d, clamped to the box.
+// Two-loop recursion for the direction d = -H g: one warp per candidate, lane = dimension
+// (P <= 32), dot products summed across the warp; the candidate's history is loaded up front.
 __global__ void polish_direction_kernel(PolishState s, PsoCoeffs<double> c, double first_step) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= s.k) return;
+    (void)c;
+    const int j = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (j >= s.k) return;  // whole warps
     const int P = s.P, k = s.k;
-    double q[kMaxParams], a[kMem];
-    for (int d = 0; d < P; ++d) q[d] = s.g[(size_t)d * k + j];
-    const int cnt = s.count[j];
-    for (int i = 0; i < cnt; ++i) {
-        const int h = (s.head[j] - 1 - i + 2 * kMem) % kMem;
-        double dot = 0.0;
-        for (int d = 0; d < P; ++d) dot += s.S[((size_t)h * P + d) * k + j] * q[d];
-        a[i] = s.rho[(size_t)h * k + j] * dot;
-        for (int d = 0; d < P; ++d) q[d] -= a[i] * s.Y[((size_t)h * P + d) * k + j];
+    const bool on = lane < P;
+    const double g = on ? s.g[(size_t)lane * k + j] : 0.0;
+    const int cnt = s.count[j], head = s.head[j];
+    double Sh[kMem], Yh[kMem], rh[kMem], a[kMem];
+#pragma unroll
+    for (int i = 0; i < kMem; ++i) {  // i-th most recent pair
+        const int h = (head - 1 - i + 2 * kMem) % kMem;
+        const bool use = on && i < cnt;
+        Sh[i] = use ? s.S[((size_t)h * P + lane) * k + j] : 0.0;
+        Yh[i] = use ? s.Y[((size_t)h * P + lane) * k + j] : 0.0;
+        rh[i] = i < cnt ? s.rho[(size_t)h * k + j] : 0.0;
+    }
+    double q = g;
+#pragma unroll
+    for (int i = 0; i < kMem; ++i) {
+        if (i < cnt) {
+            a[i] = rh[i] * warp_sum_d(Sh[i] * q);
+            q -= a[i] * Yh[i];
+        }
     }
     if (cnt > 0) {
-        const int h = (s.head[j] - 1 + kMem) % kMem;
-        double yy = 0.0;
-        for (int d = 0; d < P; ++d) yy += s.Y[((size_t)h * P + d) * k + j] * s.Y[((size_t)h * P + d) * k + j];
-        const double gamma = 1.0 / (s.rho[(size_t)h * k + j] * yy);
-        for (int d = 0; d < P; ++d) q[d] *= gamma;
+        const double yy = warp_sum_d(Yh[0] * Yh[0]);
+        q *= 1.0 / (rh[0] * yy);
     } else {
-        double gmax = 0.0;
-        for (int d = 0; d < P; ++d) gmax = fmax(gmax, fabs(q[d]));
-        const double sc = gmax > 0.0 ? first_step / gmax : 0.0;
-        for (int d = 0; d < P; ++d) q[d] *= sc;
+        const double gmax = warp_max_d(fabs(q));
+        q *= gmax > 0.0 ? first_step / gmax : 0.0;
     }
-    for (int i = cnt - 1; i >= 0; --i) {
-        const int h = (s.head[j] - 1 - i + 2 * kMem) % kMem;
-        double dot = 0.0;
-        for (int d = 0; d < P; ++d) dot += s.Y[((size_t)h * P + d) * k + j] * q[d];
-        const double b = s.rho[(size_t)h * k + j] * dot;
-        for (int d = 0; d < P; ++d) q[d] += (a[i] - b) * s.S[((size_t)h * P + d) * k + j];
+#pragma unroll
+    for (int i = kMem - 1; i >= 0; --i) {
+        if (i < cnt) {
+            const double b = rh[i] * warp_sum_d(Yh[i] * q);
+            q += (a[i] - b) * Sh[i];
+        }
     }
-    double gd = 0.0;
-    for (int d = 0; d < P; ++d) {
-        s.d[(size_t)d * k + j] = -q[d];
-        gd -= q[d] * s.g[(size_t)d * k + j];
-    }
+    const double gd = -warp_sum_d(q * g);
+    double dir = -q;
     if (!(gd < 0.0)) {  // not a descent direction: restart along the scaled steepest descent
-        double gmax = 0.0;
-        for (int d = 0; d < P; ++d) gmax = fmax(gmax, fabs(s.g[(size_t)d * k + j]));
-        const double sc = gmax > 0.0 ? first_step / gmax : 0.0;
-        for (int d = 0; d < P; ++d) s.d[(size_t)d * k + j] = -sc * s.g[(size_t)d * k + j];
-        s.count[j] = 0;
+        const double gmax = warp_max_d(fabs(g));
+        dir = -(gmax > 0.0 ? first_step / gmax : 0.0) * g;
+        if (lane == 0) s.count[j] = 0;
     }
+    if (on) s.d[(size_t)lane * k + j] = dir;
 }
 
 // The trial points z + 2^-t d, clamped to the box and decoded: one thread per (dimension, trial,
@@ -157,35 +174,43 @@ __global__ void polish_trials_kernel(PolishState s, PsoCoeffs<double> c) {
 }
 
 // Armijo choice among the evaluated trials; the accepted theta goes to trial slot 0 and z to zt.
-// One thread per (dimension, candidate): each makes the candidate's (identical) choice and
-// decodes its own dimension; the dimension-0 thread records whether the candidate stops.
+// One warp per candidate: lane t tests trial t, lane d decodes dimension d.
 __global__ void polish_select_kernel(PolishState s, PsoCoeffs<double> c) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= s.P * s.k) return;
-    const int P = s.P, k = s.k, kt = k * kTrials;
-    const int j = i % k, dd = i / k;
+    const int j = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (j >= s.k) return;  // whole warps
+    const int P = s.P, k = s.k, kt = k * kTrials, d = lane;
+    const bool on = lane < P;
     const double f0 = s.f[j];
-    double gd = 0.0;
-    for (int d = 0; d < P; ++d) gd += s.g[(size_t)d * k + j] * s.d[(size_t)d * k + j];
-    int pick = -1;
-    double fbest = f0;
-    int tbest = -1;
-    for (int t = 0; t < kTrials; ++t) {
-        const double ft = s.f32 ? (double)s.ftf[(size_t)t * k + j] : s.ft[(size_t)t * k + j];
-        if (pick < 0 && ft <= f0 + 1e-4 * ldexp(1.0, -t) * gd) pick = t;
-        if (ft < fbest) {
-            fbest = ft;
-            tbest = t;
-        }
+    const double gd = warp_sum_d(on ? s.g[(size_t)d * k + j] * s.d[(size_t)d * k + j] : 0.0);
+    double ft = INFINITY;
+    bool armijo = false;
+    if (lane < kTrials) {
+        ft = s.f32 ? (double)s.ftf[(size_t)lane * k + j] : s.ft[(size_t)lane * k + j];
+        armijo = ft <= f0 + 1e-4 * ldexp(1.0, -lane) * gd;
     }
-    if (pick < 0) pick = tbest;  // no Armijo step: take the lowest trial if it improves
-    if (pick < 0 || !s.active[j]) {
-        // a candidate stops for good; its other threads reach pick = -1 as well, whichever value
-        // of active[j] they read, since the trial choice above is the same in all of them
-        if (dd == 0) s.active[j] = 0;
+    const unsigned ok = __ballot_sync(0xFFFFFFFFu, armijo);
+    int pick = ok ? __ffs(ok) - 1 : -1;  // the largest step that satisfies the Armijo condition
+    if (pick < 0) {  // else the lowest trial below f0 (the first of equals)
+        double fb = ft < f0 ? ft : INFINITY;
+        int tb = ft < f0 ? lane : 32;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double fo = __shfl_xor_sync(0xFFFFFFFFu, fb, o);
+            const int to = __shfl_xor_sync(0xFFFFFFFFu, tb, o);
+            if (fo < fb || (fo == fb && to < tb)) {
+                fb = fo;
+                tb = to;
+            }
+        }
+        pick = tb < 32 ? tb : -1;
+    }
+    const int active = s.active[j];
+    __syncwarp();
+    if (pick < 0 || !active) {
+        if (lane == 0) s.active[j] = 0;  // the candidate stops for good
         pick = -1;
     }
-    const int d = dd;
+    if (!on) return;
     double zn;
     if (pick >= 0) {
         zn = fmin(fmax(s.z[(size_t)d * k + j] + ldexp(1.0, -pick) * s.d[(size_t)d * k + j], c.zlb[d]), c.zub[d]);
@@ -296,17 +321,18 @@ cudaError_t launch_polish(const WindowDev& w, const ModelDev& m, const ObsDev& o
                                           ckpt_every, st);
     };
     (void)cudaGetLastError();
+    const unsigned grid_warps = (unsigned)((32 * (size_t)k + 127) / 128);  // a warp per candidate
     polish_init_kernel<<<grid, 128, 0, st>>>(s, keys, pb, ld, c.logmask);
     cudaError_t e = cudaGetLastError();
     // loss and gradient at the starting points (trial slot 0 holds their theta)
     if (e == cudaSuccess) e = grad_at_slot0();
     if (e == cudaSuccess) {
-        polish_accept_kernel<<<grid, 128, 0, st>>>(s, c.logmask, 1);
+        polish_accept_kernel<<<grid_warps, 128, 0, st>>>(s, c.logmask, 1);
         e = cudaGetLastError();
     }
-    const unsigned grid_trials = (unsigned)((P * kt + 127) / 128), grid_dims = (unsigned)((P * k + 127) / 128);
+    const unsigned grid_trials = (unsigned)((P * kt + 127) / 128);
     for (int it = 0; it < iters && e == cudaSuccess; ++it) {
-        polish_direction_kernel<<<grid, 128, 0, st>>>(s, c, first_step);
+        polish_direction_kernel<<<grid_warps, 128, 0, st>>>(s, c, first_step);
         e = cudaGetLastError();
         if (e == cudaSuccess) {
             polish_trials_kernel<<<grid_trials, 128, 0, st>>>(s, c);
@@ -316,11 +342,11 @@ cudaError_t launch_polish(const WindowDev& w, const ModelDev& m, const ObsDev& o
             e = f32 ? launch_eval_f32(w, m, o, s.thf, kt, kt, s.ftf, 128, nullptr, st)
                     : launch_eval_f64(w, m, o, s.tht, kt, kt, s.ft, 64, nullptr, st);
         if (e != cudaSuccess) break;
-        polish_select_kernel<<<grid_dims, 128, 0, st>>>(s, c);
+        polish_select_kernel<<<grid_warps, 128, 0, st>>>(s, c);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = grad_at_slot0();
         if (e != cudaSuccess) break;
-        polish_accept_kernel<<<grid, 128, 0, st>>>(s, c.logmask, 0);
+        polish_accept_kernel<<<grid_warps, 128, 0, st>>>(s, c.logmask, 0);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;
