@@ -60,6 +60,8 @@ PROFILED = {
            "traffic_bytes": 24306185000, "fma_pipe": 0.4677, "profile": "profiles/pso_flat_f32_paper.md"},
     "paper_ird": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "62051028ac05fff1",
            "traffic_bytes": 24273381000, "fma_pipe": 0.4481, "profile": "profiles/pso_flat_f32_paper_ird.md"},
+    "stability": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "62051028ac05fff1",
+           "traffic_bytes": 347684622080, "fma_pipe": 0.5046, "profile": "profiles/pso_batch_f32_stability.md"},
     "swarm2p20": {"files": ["pso_kernels.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "ffdd83a8f5592f57",
            "traffic_bytes": 276096256, "fma_pipe": 0.7496, "profile": "profiles/pso_f32_kernel_swarm2p20.md"},
 }
