@@ -57,11 +57,11 @@ PROFILED = {
     "gradient90": {"files": ["adjoint_f32.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "070a4a24b1962a90",
            "traffic_bytes": 166144, "fma_pipe": 0.0737, "profile": "profiles/loss_grad_f32_gradient90.md"},
     "paper": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "62051028ac05fff1",
-           "traffic_bytes": 24306185000, "fma_pipe": 0.4677, "profile": "profiles/pso_flat_f32_paper.md"},
+           "traffic_bytes": 17555847000, "fma_pipe": 0.4852, "profile": "profiles/pso_flat_f32_paper.md"},
     "paper_ird": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "62051028ac05fff1",
-           "traffic_bytes": 24273381000, "fma_pipe": 0.4481, "profile": "profiles/pso_flat_f32_paper_ird.md"},
+           "traffic_bytes": 17637922000, "fma_pipe": 0.4625, "profile": "profiles/pso_flat_f32_paper_ird.md"},
     "stability": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "62051028ac05fff1",
-           "traffic_bytes": 347684622080, "fma_pipe": 0.5046, "profile": "profiles/pso_batch_f32_stability.md"},
+           "traffic_bytes": 300353260800, "fma_pipe": 0.5136, "profile": "profiles/pso_batch_f32_stability.md"},
     "swarm2p20": {"files": ["pso_kernels.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "ffdd83a8f5592f57",
            "traffic_bytes": 276096256, "fma_pipe": 0.7496, "profile": "profiles/pso_f32_kernel_swarm2p20.md"},
 }
@@ -121,7 +121,9 @@ def batch_windows(name: str, seed_offset: int = 0):
     Philox stream words r*W .. r*W + W - 1."""
     c = dict(configs.CONFIGS[name])
     ser = synth.load_series(c["series"])
-    if c.get("objective") == "ird":
+    fit_I0 = c.get("fit_I0", True)
+    ird = c.get("objective") == "ird"
+    if ird or not fit_I0:  # reported I and R: observed series, or the windows' initial state
         ser = synth.reported_IR(ser, c["seed"])
     lay = synth.rolling_windows(W=c["W"], L_min=c["L_min"], L_max=c["L_max"], M_min=c["M_min"], M_max=c["M_max"],
                                 delta=c["delta"], seed=c["seed"])
@@ -129,13 +131,17 @@ def batch_windows(name: str, seed_offset: int = 0):
     for i, w in enumerate(wins):
         w["seed"] = c["seed"]
         w["stream_id"] = seed_offset * c["W"] + i
+        if not ird:  # F_D fits deaths only
+            w.pop("yI", None)
+            w.pop("yR", None)
     if c.get("beta_form") == "ramp":
-        lb, ub = configs.bounds_ramp()
+        lb, ub = configs.bounds_ramp(fit_I0=fit_I0)
         model = dict(K=1, beta_form=1, log_scale=None)
     else:
         lb, ub = configs.bounds(c["K"], c["log"])
         model = dict(K=c["K"], beta_form=0, log_scale=[1] * len(lb) if c["log"] else None)
-    model["objective"] = 1 if c.get("objective") == "ird" else 0
+    model["fit_I0"] = fit_I0
+    model["objective"] = 1 if ird else 0
     model["cost"] = {"mse": 0, "mxse": 1, "mae": 2, "mape": 3}[c.get("cost", "mse")]
     return c, wins, lb, ub, model
 
@@ -148,11 +154,13 @@ def describe(name: str) -> str:
         "window60": ("single window FP32 + Kahan loss: 60 days, beta piecewise constant over 4 segments (7 params), "
                "log-uniform PSO box, 4096 particles, 1000 iterations, dt=0.1, FP64 re-evaluation of the 32 best"),
         "plain64": "plain method FP64: constant beta, gamma, mu + I0, 30 days, 64 particles, 200 iterations, dt=0.1",
-        "paper": ("the paper's setting, batched FP32: ramp beta(t) (beta1, beta2, t1, t2, gamma, mu, I0), 139 "
+        "paper": ("the paper's setting, batched FP32: ramp beta(t) (beta1, beta2, t1, t2, gamma, mu; initial state from "
+                  "the reported I, R, D of the window's first day), 139 "
                   "rolling windows of 35 days shifted by 3 days over a 450-day series, 10000 particles per window, "
                   "linear PSO box, 100 iterations, dt=0.1, one persistent launch, FP64 re-evaluation per window"),
         "paper_ird": ("the paper's setting on its representative objective F_IRD^MXSE, batched FP32: ramp beta(t), "
-                      "139 rolling 35-day windows shifted by 3 days, reported I, R, D, 10000 particles per window, "
+                      "139 rolling 35-day windows shifted by 3 days, reported I, R, D (the initial state from their first "
+                      "day), 10000 particles per window, "
                       "linear PSO box, 100 iterations, dt=0.1, one persistent launch, FP64 re-evaluation per window"),
         "stability": ("the paper's stability test (Sec. 4.2): 2 windows of 35 days each calibrated 1000 times "
                       "(independent Philox streams, 10000 particles, ramp beta(t), F_IRD^MXSE, 100 iterations) in "
@@ -417,11 +425,13 @@ def run_stability(args, rank, world):
     from paper_2204_12346_gb300 import sird
 
     c, ser, wins = stability_windows(rank)
-    lb, ub = configs.bounds_ramp()
+    fit_I0 = c.get("fit_I0", True)
+    lb, ub = configs.bounds_ramp(fit_I0=fit_I0)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         batch = sird.Batch(wins, K=1, beta_form=sird.BETA_RAMP, spd=c["spd"], iters=c["iters"], lb=lb, ub=ub,
-                           cost=sird.COST_MXSE, objective=sird.FIT_IRD, block_size=args.block, stream=stream)
+                           fit_I0=fit_I0, cost=sird.COST_MXSE, objective=sird.FIT_IRD, block_size=args.block,
+                           stream=stream)
         ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
         ev[0].record(stream)
         ev[1].record(stream)
@@ -435,7 +445,8 @@ def run_stability(args, rank, world):
             th = np.array([r["theta"] for r in res[t * reps:(t + 1) * reps]])
             w = wins[t * reps]
             bands.append(sird.ensemble_bands(w["yD"], w["N"], th, c["horizon"], c["fractions"], K=1,
-                                             beta_form=sird.BETA_RAMP, R0=w["R0"], spd=c["spd"], stream=stream))
+                                             beta_form=sird.BETA_RAMP, R0=w["R0"], I0=w["I0"], fit_I0=fit_I0,
+                                             spd=c["spd"], stream=stream))
         return res, bands
 
     with torch.cuda.stream(stream):
@@ -729,7 +740,8 @@ def _oracle_windows_worker(args):
         w = wins[i]
         pb = O.Problem(yD=w["yD"], N=w["N"], R0=w["R0"], K=model["K"], spd=c["spd"],
                        beta_form=O.BETA_RAMP if model["beta_form"] == 1 else O.BETA_PWC, cost=model["cost"],
-                       objective=model["objective"], yI=w.get("yI"), yR=w.get("yR"))
+                       objective=model["objective"], yI=w.get("yI"), yR=w.get("yR"), fit_I0=model["fit_I0"],
+                       I0=w.get("I0", 0.0))
         O.PSO(pb, w["particles"], zlb, zub, logdim=logd, seed=w["seed"], stream=w["stream_id"],
               store_f32=True).init().step(1)
         units += w["particles"] * w["L"] * 2
@@ -776,7 +788,8 @@ def cpu_baseline(name: str, budget_s: float = 15.0, iters_cap: int | None = None
                 break
             pb = O.Problem(yD=w["yD"], N=w["N"], R0=w["R0"], K=model["K"], spd=c["spd"],
                            beta_form=O.BETA_RAMP if model["beta_form"] == 1 else O.BETA_PWC, cost=model["cost"],
-                           objective=model["objective"], yI=w.get("yI"), yR=w.get("yR"))
+                           objective=model["objective"], yI=w.get("yI"), yR=w.get("yR"), fit_I0=model["fit_I0"],
+                           I0=w.get("I0", 0.0))
             O.PSO(pb, w["particles"], zlb, zub, logdim=logd, seed=w["seed"], stream=w["stream_id"],
                   store_f32=True).init().step(1)
             units += w["particles"] * w["L"] * 2
@@ -784,13 +797,14 @@ def cpu_baseline(name: str, budget_s: float = 15.0, iters_cap: int | None = None
         sample = f"{done} windows x (init + 1 PSO iteration), full swarms"
     elif name == "stability":
         c, ser, wins = stability_windows(0)
-        lb, ub = configs.bounds_ramp()
+        fit_I0 = c.get("fit_I0", True)
+        lb, ub = configs.bounds_ramp(fit_I0=fit_I0)
         done = 0
         for w in wins:
             if time.perf_counter() - t0 >= budget_s or (iters_cap is not None and done >= iters_cap):
                 break
             pb = O.Problem(yD=w["yD"], N=w["N"], R0=w["R0"], beta_form=O.BETA_RAMP, spd=c["spd"], cost=O.MXSE,
-                           objective=O.FIT_IRD, yI=w["yI"], yR=w["yR"])
+                           objective=O.FIT_IRD, yI=w["yI"], yR=w["yR"], fit_I0=fit_I0, I0=w["I0"])
             O.PSO(pb, w["particles"], lb, ub, logdim=[0] * len(lb), seed=w["seed"], stream=w["stream_id"],
                   store_f32=True).init().step(1)
             units += w["particles"] * w["L"] * 2

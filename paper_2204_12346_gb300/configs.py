@@ -23,11 +23,13 @@ def bounds(K: int, log: bool):
     return lb, ub
 
 
-def bounds_ramp(t_max: float = 28.0):
-    """Linear box of the paper's ramp form (beta1, beta2, t1, t2, gamma, mu, I0): the second,
+def bounds_ramp(t_max: float = 28.0, fit_I0: bool = True):
+    """Linear box of the paper's ramp form (beta1, beta2, t1, t2, gamma, mu[, I0]): the second,
     narrowed box of Sec. 3.2 (beta in [0, 2], gamma in [0, 1], mu in [0, 0.1]) with the ramp's
-    end at most t_max = 28 days after the window start; I0 in [0, 1e6]."""
-    return [0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0], [2.0, 2.0, t_max, t_max, 1.0, 0.1, 1e6]
+    end at most t_max = 28 days after the window start; I0 in [0, 1e6] when it is fitted (the
+    paper's own setting takes the initial state from the data instead, Sec. 3.1)."""
+    lb, ub = [0.0, 0.0, 0.0, 0.0, 0.0, 0.0], [2.0, 2.0, t_max, t_max, 1.0, 0.1]
+    return (lb + [0.0], ub + [1e6]) if fit_I0 else (lb, ub)
 
 
 CONFIGS = {
@@ -44,21 +46,24 @@ CONFIGS = {
     "gradient90": dict(name="gradient-90d-4096-points", series="90d", K=4, days=90, spd=20, M=4096, iters=200,
                precision=32, log=True, seed=0, ckpt=16, polish_topk=32, reeval_topk=32),
     # The paper's own setting (Sec. 3.1-3.3): ramp beta(t), 139 rolling windows of tau = 35 days
-    # shifted by delta = 3 days over the 450-day series, 10000 particles, 100 iterations.
+    # shifted by delta = 3 days over the 450-day series, 10000 particles, 100 iterations; the
+    # window's initial state from the data (reported I, R, D on its first day), so theta =
+    # (beta1, beta2, t1, t2, gamma, mu).
     "paper": dict(name="paper-ramp-139-windows", series="450d", beta_form="ramp", W=139, iters=100, spd=10,
-                  precision=32, log=False, seed=0, L_min=35, L_max=35, M_min=10000, M_max=10000, delta=3),
+                  precision=32, log=False, seed=0, L_min=35, L_max=35, M_min=10000, M_max=10000, delta=3,
+                  fit_I0=False),
     # The same with the paper's representative objective F_IRD^MXSE (Sec. 3.1, the cost its
     # timings are quoted on): reported I and R series alongside D.
     "paper_ird": dict(name="paper-ramp-139-windows-F_IRD-MXSE", series="450d", beta_form="ramp", objective="ird",
                       cost="mxse", W=139, iters=100, spd=10, precision=32, log=False, seed=0, L_min=35, L_max=35,
-                      M_min=10000, M_max=10000, delta=3),
+                      M_min=10000, M_max=10000, delta=3, fit_I0=False),
     # The stability test of Sec. 4.2: two windows (tau = 35 days) each calibrated 1000 times with
     # independent random streams (10000 particles, ramp beta(t), F_IRD^MXSE) in one batched
     # launch, then per day the median and 95/90/50% bands of beta, R0, S, I, R, D over the
     # window and a 21-day extension.
     "stability": dict(name="stability-2x1000-repetitions", series="450d", beta_form="ramp", objective="ird",
                       cost="mxse", windows_T=(120, 330), L=35, reps=1000, M=10000, iters=100, spd=10,
-                      precision=32, log=False, seed=0, horizon=21, fractions=(0.95, 0.9, 0.5)),
+                      precision=32, log=False, seed=0, horizon=21, fractions=(0.95, 0.9, 0.5), fit_I0=False),
     # 2^20 particles, 10 segments, 120 days at dt = 0.05 day, then a 14-day forecast.
     "swarm2p20": dict(name="swarm-2^20-particles-120d", series="134d", K=10, days=120, spd=20, M=1 << 20, iters=100,
                precision=32, log=True, seed=0, horizon=14, forecast_topk=1024, reeval_topk=32, polish_topk=32,

@@ -78,19 +78,20 @@ def load_series(name: str) -> dict:
 def rolling_window_problems(series: dict, layout: dict) -> list:
     """Cuts windows out of a long stored series: window w covers days T_w .. T_w + L_w; its
     observed deaths are the noisy cumulative counts on those days (the Euler scheme starts from
-    the first one), R0 is the series' recovered count on day T_w rounded (the reported one when
-    the series carries reported I and R, which the window then carries too), and its swarm size
-    is layout["M"][w]."""
+    the first one), R0 is the series' recovered count on day T_w rounded (when the series
+    carries reported I and R, the window carries them too and takes R0 and I0 from their values
+    on day T_w), and its swarm size is layout["M"][w]."""
     y = series["yD"]
     R = series["R_true"]
     out = []
     for w, (L, M, T) in enumerate(zip(layout["L"], layout["M"], layout["T"])):
         win = {"yD": y[T:T + L + 1].copy(), "N": float(series["N"]), "R0": float(np.round(R[T])),
                "particles": int(M), "T": int(T), "L": int(L)}
-        if "yI" in series:  # reported I and R (F_IRD); R0 is then the reported R on day T
+        if "yI" in series:  # reported I and R: R0 and I0 are then the reported values on day T
             win["yI"] = series["yI"][T:T + L + 1].copy()
             win["yR"] = series["yR"][T:T + L + 1].copy()
             win["R0"] = float(win["yR"][0])
+            win["I0"] = float(win["yI"][0])
         out.append(win)
     return out
 

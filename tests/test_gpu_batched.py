@@ -122,23 +122,28 @@ def test_batch_ramp_windows_match_single_window_calibrations():
 
 
 def test_paper_layout_against_the_oracle_at_initialisation():
-    # the paper's setting: 139 windows of 35 days shifted by 3 days, 10000 particles, ramp beta(t)
+    # the paper's setting: 139 windows of 35 days shifted by 3 days, 10000 particles, ramp beta(t),
+    # each window's initial state from the reported I, R, D of its first day (theta: 6 rates)
     c = configs.CONFIGS["paper"]
-    ser = synth.load_series(c["series"])
+    assert c["fit_I0"] is False
+    ser = synth.reported_IR(synth.load_series(c["series"]), c["seed"])
     lay = synth.rolling_windows(W=c["W"], L_min=c["L_min"], L_max=c["L_max"], M_min=c["M_min"], M_max=c["M_max"],
                                 delta=c["delta"], seed=c["seed"])
     wins = synth.rolling_window_problems(ser, lay)
+    for w in wins:  # F_D: deaths only
+        w.pop("yI")
+        w.pop("yR")
     assert len(wins) == 139 and all(w["particles"] == 10000 and w["L"] == 35 for w in wins)
     assert [w["T"] for w in wins[:3]] == [0, 3, 6] and wins[-1]["T"] == 414
-    kw = ramp_shared()
+    lb, ub = configs.bounds_ramp(fit_I0=False)
+    kw = dict(K=1, spd=10, beta_form=sird.BETA_RAMP, lb=lb, ub=ub, log_scale=None, seed=5, fit_I0=False)
     res = sird.Batch(wins, iters=0, **kw).calibrate()
     assert len(res) == 139 and all(np.isfinite(r["loss"]) for r in res)
-    lb, ub = configs.bounds_ramp()
     zlb, zub = f32(lb), f32(ub)
     for i in (0, 70, 138):
         w = wins[i]
-        pb = O.Problem(yD=w["yD"], N=w["N"], R0=w["R0"], beta_form=O.BETA_RAMP, spd=10)
-        pso = O.PSO(pb, w["particles"], zlb, zub, logdim=[0] * 7, seed=kw["seed"], stream=i, store_f32=True).init()
+        pb = O.Problem(yD=w["yD"], N=w["N"], R0=w["R0"], I0=w["I0"], fit_I0=False, beta_form=O.BETA_RAMP, spd=10)
+        pso = O.PSO(pb, w["particles"], zlb, zub, logdim=[0] * 6, seed=kw["seed"], stream=i, store_f32=True).init()
         # the best of 10000 is a good fit, where FP32 resolves the loss only to fp32_loss_tol
         th_best = np.array(pso.pbest[pso.gbest_idx])  # linear box: theta = z
         tol = fp32_loss_tol(O, pb, th_best)
