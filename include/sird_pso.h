@@ -70,7 +70,9 @@ typedef enum sird_launch_mode {
     SIRD_LAUNCH_PERSISTENT = 2,
     /* batches (configs[0].launch_mode, with configs[0].block_size given): */
     SIRD_LAUNCH_WINDOW_PER_BLOCK = 3, /* a block runs one window at a time (the default) */
-    SIRD_LAUNCH_FLAT = 4              /* every window's swarm spread over the whole grid */
+    SIRD_LAUNCH_FLAT = 4,             /* every window's swarm spread over the whole grid */
+    /* one window (FP32): all iterations in one launch of one thread-block cluster */
+    SIRD_LAUNCH_CLUSTER = 5
 } sird_launch_mode;
 
 /* Main objective: F_D^C (deaths only) or F_IRD^C (max over I, R, D), Sec. 3.1. */
@@ -133,10 +135,14 @@ typedef struct sird_problem {
  *                 and the best of them is reported (0 = report the FP32 global best as is)
  *   block_size    threads per block for the swarm kernels (0 = library default; else a
  *                 multiple of 32 in 32..1024)
- *   launch_mode   SIRD_LAUNCH_AUTO, SIRD_LAUNCH_PER_ITER (one kernel per iteration) or
+ *   launch_mode   SIRD_LAUNCH_AUTO, SIRD_LAUNCH_PER_ITER (one kernel per iteration),
  *                 SIRD_LAUNCH_PERSISTENT (FP32 only: all iterations in one cooperative launch
- *                 with the swarm in shared memory; needs every block co-resident).  AUTO
- *                 picks persistent when it fits.  Both give bit-identical swarms.
+ *                 with the swarm in shared memory, the blocks' best exchanged through global
+ *                 memory; needs every block co-resident) or SIRD_LAUNCH_CLUSTER (FP32 only:
+ *                 the same in one thread-block cluster of at most 16 blocks, the best
+ *                 exchanged through distributed shared memory; block_size 0 = the swarm split
+ *                 over 16 blocks).  AUTO picks the cluster when the swarm fills 4 to 16 blocks
+ *                 of block_size, else persistent when it fits.  All give bit-identical swarms.
  */
 typedef struct sird_pso_config {
     int particles;
@@ -181,8 +187,8 @@ sird_status sird_pso_clear_error(sird_pso_t h);
 sird_status sird_pso_set_stream(sird_pso_t h, void* cuda_stream);
 /* Number of parameters P of the handle's theta layout (0 if h is NULL). */
 int sird_pso_num_params(sird_pso_t h);
-/* Launch mode the handle uses for its iterations: SIRD_LAUNCH_PER_ITER or
- * SIRD_LAUNCH_PERSISTENT (what SIRD_LAUNCH_AUTO resolved to); 0 if h is NULL. */
+/* Launch mode the handle uses for its iterations: SIRD_LAUNCH_PER_ITER, SIRD_LAUNCH_PERSISTENT
+ * or SIRD_LAUNCH_CLUSTER (what SIRD_LAUNCH_AUTO resolved to); 0 if h is NULL. */
 int sird_pso_launch_mode(sird_pso_t h);
 
 /* ---------------------------------------------------------------- fitness */

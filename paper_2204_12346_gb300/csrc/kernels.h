@@ -85,6 +85,13 @@ cudaError_t launch_pso_f64(const WindowDev& w, const ModelDev& m, const ObsDev& 
 size_t smem_bytes_persistent(const WindowDev& w, const ModelDev& m, int block, int grid);
 int persistent_capacity(const WindowDev& w, const ModelDev& m, int block, int grid);
 constexpr int kMaxPersistentBlocks = 128;
+// The same with the grid as one thread-block cluster of at most kMaxClusterBlocks blocks,
+// exchanging the blocks' best through distributed shared memory (no slots).
+constexpr int kMaxClusterBlocks = 16;
+bool cluster_fits(const WindowDev& w, const ModelDev& m, int block, int grid);
+cudaError_t launch_pso_f32_cluster(const WindowDev& w, const ModelDev& m, const ObsDev& o, const PsoCoeffs<float>& c,
+                                   const SwarmDev<float>& sw, const ReduceScratch& r, int iter0, int n_iters, int block,
+                                   cudaStream_t s);
 cudaError_t launch_pso_f32_persistent(const WindowDev& w, const ModelDev& m, const ObsDev& o,
                                       const PsoCoeffs<float>& c, const SwarmDev<float>& sw, const ReduceScratch& r,
                                       ExchangeSlot* slots, int iter0, int n_iters, int block, cudaStream_t s);

@@ -17,6 +17,8 @@
 // kernel returns with the swarm written back.
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "kernels.h"
 
 namespace sird {
@@ -38,7 +40,12 @@ __device__ __forceinline__ unsigned long long tagged(unsigned tag, uint32_t v) {
     return ((unsigned long long)tag << 32) | v;
 }
 
-template <int SPD, int COST>
+// CLUSTER: the grid is one thread-block cluster (at most 16 blocks) and the blocks exchange their
+// best through distributed shared memory -- each block's (key, position) in its own shared
+// memory, double-buffered by iteration parity, read by every block after one cluster barrier --
+// instead of the global slots; no wait is spun (the hardware barrier needs every block to
+// arrive, and every block runs the same iterations).
+template <int SPD, int COST, bool CLUSTER>
 __global__ void __launch_bounds__(1024) pso_f32_persistent(WindowDev w, ModelDev m, ObsDev o, PsoCoeffs<float> c,
                                                             SwarmDev<float> sw, ReduceScratch r,
                                                             ExchangeSlot* __restrict__ slots, int iter0, int n_iters,
@@ -47,6 +54,8 @@ __global__ void __launch_bounds__(1024) pso_f32_persistent(WindowDev w, ModelDev
     __shared__ unsigned long long wk[32];
     __shared__ int s_flag;
     __shared__ unsigned long long s_gkey;
+    __shared__ unsigned long long ex_key[2];    // CLUSTER: this block's best of the iteration
+    __shared__ float ex_pos[2][kMaxParams];     // and its position
     const int B = blockDim.x, tid = threadIdx.x, P = m.P, G = gridDim.x;
     const int npairs = (P + 1) >> 1;
     float* ys = smem;
@@ -123,6 +132,48 @@ __global__ void __launch_bounds__(1024) pso_f32_persistent(WindowDev w, ModelDev
         __syncthreads();
         const unsigned tag = (unsigned)it;
         ExchangeSlot* row = slots + (size_t)(it & 1) * G;
+        if (CLUSTER) {
+            const int par = it & 1;
+            if (tid < 32) {
+                const unsigned long long bkey = warp_min_key((tid < (B + 31) / 32) ? wk[tid] : ~0ull);
+                const int j = (int)(bkey & 0xFFFFFFFFu) - base;  // the block's best is one of its own particles
+                if (tid < P) ex_pos[par][tid] = pbs[tid * B + j];
+                if (tid == 0) ex_key[par] = bkey;
+                if (B == 32 && it < iter0 + n_iters && active)  // a one-warp block draws its own
+                    draw_iteration(rnd + tid, npairs, B, (uint32_t)p, (uint32_t)(it + 1), c);
+            } else if (it < iter0 + n_iters) {  // the next iteration's random numbers meanwhile
+                for (int i = tid - 32; i < npairs * B; i += B - 32) {
+                    const int j = i / B, q = i - j * B;
+                    if (base + q < sw.M)
+                        rnd[i] = philox4x32_10(make_uint4((uint32_t)(base + q), (uint32_t)(it + 1), (uint32_t)j,
+                                                          c.stream_id), c.key0, c.key1);
+                }
+            }
+            cooperative_groups::this_cluster().sync();
+            if (tid < 32) {
+                auto cl = cooperative_groups::this_cluster();
+                unsigned long long best = ~0ull;
+                int bblk = 0;
+                if (tid < G) {
+                    best = *cl.map_shared_rank(&ex_key[par], (unsigned)tid);
+                    bblk = tid;
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const unsigned long long k2 = __shfl_xor_sync(0xFFFFFFFFu, best, off);
+                    const int b2 = __shfl_xor_sync(0xFFFFFFFFu, bblk, off);
+                    if (k2 < best) {
+                        best = k2;
+                        bblk = b2;
+                    }
+                }
+                if (tid < P) g_s[tid] = *cl.map_shared_rank(&ex_pos[par][tid], (unsigned)bblk);
+                if (tid == 0) s_gkey = best;
+            }
+            __syncthreads();
+            gkey = s_gkey;
+            continue;
+        }
         if (tid < 32) {
             // block minimum, then publish it: every word carries the iteration number
             const unsigned long long bkey = warp_min_key((tid < (B + 31) / 32) ? wk[tid] : ~0ull);
@@ -208,6 +259,8 @@ __global__ void __launch_bounds__(1024) pso_f32_persistent(WindowDev w, ModelDev
         gkey = s_gkey;
     }
 
+    // no block leaves while another may still read its exchange words
+    if (CLUSTER && n_iters > 0) cooperative_groups::this_cluster().sync();
     // write the swarm back
     for (int i = tid; i < P * B; i += B) {
         const int d = i / B, j = i - d * B, q = base + j;
@@ -237,6 +290,36 @@ size_t smem_bytes_persistent(const WindowDev& w, const ModelDev& m, int block, i
 }
 
 // Largest grid of `block`-thread blocks that can be co-resident for this problem (0 if none).
+// Whether the whole grid fits as one thread-block cluster (at most kMaxClusterBlocks blocks).
+bool cluster_fits(const WindowDev& w, const ModelDev& m, int block, int grid) {
+    if (grid < 1 || grid > kMaxClusterBlocks) return false;
+    const size_t sm = smem_bytes_persistent(w, m, block, grid);
+    const void* fn = (const void*)pso_f32_persistent<0, COST_MSE, true>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    if (sm > 48 * 1024 && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = sm;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)grid;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, fn, &cfg);
+    (void)cudaGetLastError();
+    return e == cudaSuccess && n >= 1;
+}
+
 int persistent_capacity(const WindowDev& w, const ModelDev& m, int block, int grid) {
     const size_t sm = smem_bytes_persistent(w, m, block, grid);
     int dev = 0, nsm = 0, per = 0, coop = 0;
@@ -245,7 +328,7 @@ int persistent_capacity(const WindowDev& w, const ModelDev& m, int block, int gr
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     const void* fn = nullptr;
     switch (m.cost) {  // every instantiation has the same resources; use the MSE / runtime-spd one
-        default: fn = (const void*)pso_f32_persistent<0, COST_MSE>; break;
+        default: fn = (const void*)pso_f32_persistent<0, COST_MSE, false>; break;
     }
     if (sm > 48 * 1024 && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
         return 0;
@@ -280,7 +363,7 @@ cudaError_t launch_pso_f32_persistent(const WindowDev& w, const ModelDev& m, con
     if (e == cudaSuccess) e = cudaMemsetAsync(r.abort, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     SIRD_DISPATCH_SPD(m.spd, SIRD_DISPATCH_COST(m.cost, {
-        auto kern = pso_f32_persistent<S_, C_>;
+        auto kern = pso_f32_persistent<S_, C_, false>;
         if (sm > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e == cudaSuccess) {
             cudaLaunchConfig_t cfg = {};
@@ -295,6 +378,38 @@ cudaError_t launch_pso_f32_persistent(const WindowDev& w, const ModelDev& m, con
             cfg.numAttrs = 1;
             e = cudaLaunchKernelEx(&cfg, kern, w, m, o, c, sw, r, slots, iter0, n_iters,
                                    bounded_wait_limit(kSpinLimit));
+        }
+    }));
+    return e;
+}
+
+cudaError_t launch_pso_f32_cluster(const WindowDev& w, const ModelDev& m, const ObsDev& o, const PsoCoeffs<float>& c,
+                                   const SwarmDev<float>& sw, const ReduceScratch& r, int iter0, int n_iters, int block,
+                                   cudaStream_t s) {
+    const unsigned grid = (unsigned)((sw.M + block - 1) / block);
+    if (grid > (unsigned)kMaxClusterBlocks) return cudaErrorInvalidValue;
+    const size_t sm = smem_bytes_persistent(w, m, block, (int)grid);
+    (void)cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    SIRD_DISPATCH_SPD(m.spd, SIRD_DISPATCH_COST(m.cost, {
+        auto kern = pso_f32_persistent<S_, C_, true>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess && sm > 48 * 1024)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(grid);
+            cfg.blockDim = dim3(block);
+            cfg.dynamicSmemBytes = sm;
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = grid;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            e = cudaLaunchKernelEx(&cfg, kern, w, m, o, c, sw, r, (ExchangeSlot*)nullptr, iter0, n_iters, 0u);
         }
     }));
     return e;

@@ -21,7 +21,7 @@ COST_MSE, COST_MXSE, COST_MAE, COST_MAPE = 0, 1, 2, 3
 COSTS = {"mse": COST_MSE, "mxse": COST_MXSE, "mae": COST_MAE, "mape": COST_MAPE}
 BETA_PWC, BETA_RAMP = 0, 1
 FIT_D, FIT_IRD = 0, 1
-LAUNCH_AUTO, LAUNCH_PER_ITER, LAUNCH_PERSISTENT, LAUNCH_WINDOW_PER_BLOCK, LAUNCH_FLAT = 0, 1, 2, 3, 4
+LAUNCH_AUTO, LAUNCH_PER_ITER, LAUNCH_PERSISTENT, LAUNCH_WINDOW_PER_BLOCK, LAUNCH_FLAT, LAUNCH_CLUSTER = 0, 1, 2, 3, 4, 5
 
 # Symbols the header declares (checked by the ABI test).
 EXPORTS = [

@@ -251,6 +251,38 @@ def test_one_day_window():
     assert rel_err(gpu_eval(cal, th, 32), want).max() <= TOL32
 
 
+@pytest.mark.parametrize("M,block", [(4096, 0), (4096, 256), (1000, 64), (77, 32), (16384, 0), (333, 0)])
+def test_cluster_and_per_iteration_launches_agree_bit_for_bit(M, block):
+    # all iterations in one thread-block cluster, the blocks' best exchanged in shared memory
+    y, N, _, _ = window("60d")
+    lb, ub = log_box(4)
+    kw = dict(K=4, spd=10, particles=M, iters=25, lb=lb, ub=ub, log_scale=[1] * 7, precision=32, seed=5,
+              reeval_topk=8, block_size=block)
+    a = sird.Calibrator(y, N, launch_mode=sird.LAUNCH_PER_ITER, **kw)
+    b = sird.Calibrator(y, N, launch_mode=sird.LAUNCH_CLUSTER, **kw)
+    assert b.launch_mode == sird.LAUNCH_CLUSTER
+    ra, rb = a.calibrate(), b.calibrate()
+    assert ra["index"] == rb["index"] and ra["loss"] == rb["loss"] and ra["loss_search"] == rb["loss_search"]
+    sa, sb = a.get_state(), b.get_state()
+    for k in ("x", "v", "pbest", "pbest_f", "gbest_idx"):
+        assert np.array_equal(np.asarray(sa[k]), np.asarray(sb[k])), k
+    c = sird.Calibrator(y, N, launch_mode=sird.LAUNCH_CLUSTER, **kw).init()
+    c.step(10)
+    c.step(15)
+    sc = c.get_state()
+    for k in ("x", "v", "pbest", "pbest_f", "gbest_idx"):
+        assert np.array_equal(np.asarray(sa[k]), np.asarray(sc[k])), k
+
+
+def test_cluster_launch_refuses_a_swarm_beyond_one_cluster():
+    y, N, _, _ = window("60d", 20)
+    lb, ub = log_box(4)
+    with pytest.raises(sird.SirdError) as e:
+        sird.Calibrator(y, N, K=4, spd=10, particles=4096, iters=2, lb=lb, ub=ub, log_scale=[1] * 7, precision=32,
+                        block_size=128, launch_mode=sird.LAUNCH_CLUSTER)  # 32 blocks
+    assert e.value.status == 7
+
+
 @pytest.mark.parametrize("M,block", [(4096, 128), (1000, 64), (77, 32)])
 def test_persistent_and_per_iteration_launches_agree_bit_for_bit(M, block):
     y, N, _, _ = window("60d")
