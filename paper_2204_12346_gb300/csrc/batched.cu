@@ -22,6 +22,9 @@ namespace {
 
 __host__ __device__ __forceinline__ int pad4(int n) { return (n + 3) & ~3; }
 
+// A last wave of at most this many particles runs one particle per thread.
+constexpr int kSingleWaveMax = 384;
+
 template <int SPD, int COST>
 __global__ void __launch_bounds__(768) pso_batch_f32(const BatchWindow* __restrict__ wins, const int* __restrict__ order,
                                                      int W, ModelDev m, PsoCoeffs<float> c, const float* __restrict__ yf_all,
@@ -105,13 +108,28 @@ __global__ void __launch_bounds__(768) pso_batch_f32(const BatchWindow* __restri
                 const unsigned long long kj = argmin_key(best, (uint32_t)j);
                 key = kj < key ? kj : key;
             };
-            // a thread takes particle j0 and, when the window has more particles than the block
-            // has threads, also j0 + B; a pair is integrated together in packed form (one
-            // instruction stream for both), so a window of up to 2B particles takes one pass
-            for (int j0 = tid; j0 < M; j0 += B2) {
-                const int j1 = j0 + B;
+            // waves of 2B particles, thread t taking particle t of the wave and particle B + t
+            // with it -- a pair, integrated together in packed form (one instruction stream for
+            // both).  The last wave holds the rest: its Tw threads take particle t and, for
+            // t < cnt - Tw, also Tw + t, with Tw = cnt/2 rounded up to whole groups of four warps,
+            // so its pairs sit in the lowest warps and every warp scheduler gets the same share;
+            // a small rest runs one particle per thread on as many warps as it fills.
+            for (int base = 0; base < M; base += B2) {
+                const int cnt = M - base < B2 ? M - base : B2;
+                int Tw = B;
+                if (cnt < B2) {
+                    Tw = cnt;
+                    if (cnt > kSingleWaveMax && cnt > 1) {
+                        Tw = (((cnt + 1) >> 1) + 127) & ~127;
+                        if (Tw > B) Tw = B;
+                        if (Tw > cnt) Tw = cnt;
+                    }
+                    if (Tw > B) Tw = B;
+                }
+                if (tid >= Tw || tid >= cnt) continue;
+                const int j0 = base + tid, j1 = base + Tw + tid;
                 update(j0, tid);
-                if (j1 < M) {
+                if (Tw + tid < cnt) {
                     update(j1, B + tid);
                     float fa, fb;
                     fitness_f32x2<SPD, COST>(w, m, ys, invys, th_s + tid, th_s + B + tid, B2, fa, fb);
