@@ -49,19 +49,19 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 # DRAM bytes per launch of the dominant kernel from committed ncu captures, valid only for the
 # kernel sources they were taken on (sha256[:16] of the files listed).
 PROFILED = {
-    "batch512": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "c5e39c604696e820",
-           "traffic_bytes": 14237696, "fma_pipe": 0.6547, "profile": "profiles/pso_batch_f32_batch512.md"},
+    "batch512": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "e33e6bd7ec2fd256",
+           "traffic_bytes": 14921728, "fma_pipe": 0.6651, "profile": "profiles/pso_batch_f32_batch512.md"},
     "window60": {"files": ["pso_persistent.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"],
            "sha": "c5d3e50e2434bb01", "traffic_bytes": 446464, "fma_pipe": 0.3710,
            "profile": "profiles/pso_f32_persistent_window60.md"},
     "gradient90": {"files": ["adjoint_f32.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "4e59aa10f7c4bd00",
            "traffic_bytes": 165888, "fma_pipe": 0.0737, "profile": "profiles/loss_grad_f32_gradient90.md"},
-    "paper": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "c5e39c604696e820",
-           "traffic_bytes": 17674678000, "fma_pipe": 0.4859, "profile": "profiles/pso_flat_f32_paper.md"},
-    "paper_ird": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "c5e39c604696e820",
-           "traffic_bytes": 17776082000, "fma_pipe": 0.4610, "profile": "profiles/pso_flat_f32_paper_ird.md"},
-    "stability": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "c5e39c604696e820",
-           "traffic_bytes": 300451985920, "fma_pipe": 0.5138, "profile": "profiles/pso_batch_f32_stability.md"},
+    "paper": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "e33e6bd7ec2fd256",
+           "traffic_bytes": 17560492000, "fma_pipe": 0.4856, "profile": "profiles/pso_flat_f32_paper.md"},
+    "paper_ird": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "e33e6bd7ec2fd256",
+           "traffic_bytes": 17636036000, "fma_pipe": 0.4623, "profile": "profiles/pso_flat_f32_paper_ird.md"},
+    "stability": {"files": ["batched.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "e33e6bd7ec2fd256",
+           "traffic_bytes": 300430231040, "fma_pipe": 0.5098, "profile": "profiles/pso_batch_f32_stability.md"},
     "swarm2p20": {"files": ["pso_kernels.cu", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "0fd47436f9d0b4cd",
            "traffic_bytes": 276988160, "fma_pipe": 0.7481, "profile": "profiles/pso_f32_kernel_swarm2p20.md"},
 }
