@@ -1,0 +1,40 @@
+"""Consistency of the benchmark's bookkeeping (CPU): every workload it can run has a
+description and a configuration, and every profiled kernel's summary under profiles/ exists and
+names the source hash the bench compares against."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def test_every_workload_is_described_and_configured():
+    import bench
+    from paper_2204_12346_gb300 import configs
+
+    for name in ("batch512", "window60", "plain64", "gradient90", "swarm2p20", "paper", "paper_ird", "stability"):
+        assert name in configs.CONFIGS
+        assert len(bench.describe(name)) > 40
+
+
+def test_profile_summaries_name_their_source_hash():
+    import bench
+
+    for name, p in bench.PROFILED.items():
+        path = os.path.join(ROOT, p["profile"])
+        assert os.path.exists(path), path
+        text = open(path).read()
+        assert p["sha"] and f"`{p['sha']}`" in text, (name, p["sha"])
+        assert p["traffic_bytes"] > 0 and 0.0 < p["fma_pipe"] < 1.0
+        for f in p["files"]:
+            assert os.path.exists(os.path.join(ROOT, "paper_2204_12346_gb300", "csrc", f)), f
+
+
+def test_algorithmic_flop_counts():
+    import bench
+
+    # 8 flops per Euler step and 3 per day; the ramp adds 5 per step, F_IRD 2 per step and 6 per day
+    assert bench.algorithmic_flops_per_particle_day(10) == 83
+    assert bench.algorithmic_flops_per_particle_day(20) == 163
+    assert bench.algorithmic_flops_per_particle_day(10, ramp=True) == 133
+    assert bench.algorithmic_flops_per_particle_day(10, ramp=True, ird=True) == 159
