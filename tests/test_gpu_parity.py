@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI (GPU only).
 
-Tolerances (BASELINE contract): FP32 fitness within 1e-5 relative of the oracle, FP64
+Tolerances: FP32 fitness within 1e-5 relative of the oracle, FP64
 within 1e-12; the FP64 path is written in the paper's operation order without FMA
 contraction, so it is expected to match the oracle bit for bit.  Parameter vectors are
 drawn from the PSO search box and rounded to FP32 before both sides see them.
