@@ -81,3 +81,34 @@ def test_null_handle_calls_are_safe(L):
     assert L.sird_pso_set_gbest(None, z, 0.0, 0) == 1
     assert L.sird_pso_topk_indexed(None, 1, d, d, C.byref(i)) == 1
     L.sird_pso_destroy(None)
+
+
+def test_header_is_plain_c_and_a_c_program_calls_the_library(L, tmp_path):
+    # the boundary is a C ABI: the header compiles as pedantic C99, and a C program links
+    # against the library and gets its argument errors without touching a GPU
+    import shutil
+    import subprocess
+
+    from paper_2204_12346_gb300 import build
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "sird_pso.h"\n'
+        "int main(void) {\n"
+        "    sird_pso_t h = 0;\n"
+        "    sird_status s = sird_pso_create(0, 0, 0, &h);\n"
+        '    printf("%d %d %s\\n", (int)s, h == 0, sird_last_error(0));\n'
+        "    return s == SIRD_ERR_ARG && h == 0 ? 0 : 1;\n"
+        "}\n")
+    exe = tmp_path / "use"
+    lib_dir = os.path.dirname(build.LIB)
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                        os.path.join(ROOT, "include"), str(src), "-L", lib_dir, "-l:" + os.path.basename(build.LIB),
+                        "-Wl,-rpath," + lib_dir, "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0, (run.stdout, run.stderr)
+    assert run.stdout.split()[0] == "1" and "NULL" in run.stdout
