@@ -218,6 +218,11 @@ def test_r2_and_ird(orc):
     pb = mkpb(orc, days=days)
     tr = orc.simulate(pb, th)
     assert orc.r2_D(mkpb(orc, days=days, yD=tr["D"]), th) == 1.0
+    # R^2 = 1 - SS_res / SS_tot by its definition: D offset by c on days 1.. gives SS_res = (n-1) c^2
+    yc = tr["D"].copy()
+    yc[1:] += 120.0
+    want_r2 = 1.0 - (n - 1) * 120.0 ** 2 / np.sum((yc - yc.mean()) ** 2)
+    assert orc.r2_D(mkpb(orc, days=days, yD=yc), th) == pytest.approx(want_r2, rel=1e-12)
     # F_IRD^MSE with exact I and R and D offset by c: (c/range(yD))^2 (n-1)/n
     c = 50.0
     yD = tr["D"].copy()
@@ -233,9 +238,12 @@ def test_r2_and_ird(orc):
     rngI = yI.max() - yI.min()
     want = max((0.5 * (tr["I"].max() - tr["I"].min()) / rngI) ** 2, (c / rngD) ** 2)
     assert orc.loss(p2, th) == pytest.approx(want, rel=1e-9)
-    # MAPE is not normalised
-    p3 = mkpb(orc, yI=tr["I"], yR=tr["R"] * 1.1, cost=orc.MAPE, **common)
-    assert orc.loss(p3, th) == pytest.approx(100 * (0.1 / 1.1) * (n - 1) / (n - 1), rel=1e-9)
+    # MAPE is not normalised: relative offsets of 20% on I (day 0 included, I0 != 0) and 10% on
+    # R (day 0 skipped, R0 = 0); the max is I's 100 * 0.2 / 1.2, R's alone 100 * 0.1 / 1.1
+    p3 = mkpb(orc, yI=tr["I"] * 1.2, yR=tr["R"] * 1.1, cost=orc.MAPE, **common)
+    assert orc.loss(p3, th) == pytest.approx(100 * 0.2 / 1.2, rel=1e-9)
+    p4 = mkpb(orc, yI=tr["I"], yR=tr["R"] * 1.1, cost=orc.MAPE, **common)
+    assert orc.loss(p4, th) == pytest.approx(100 * (0.1 / 1.1) * (n - 1) / (n - 1), rel=1e-9)
 
 
 # ------------------------------------------------------------------ adjoint
@@ -250,7 +258,7 @@ def _fd(orc, pb, th, j, h_rel=1e-6):
 
 
 @pytest.mark.parametrize("form,cost", [("pwc", "mse"), ("pwc", "mae"), ("pwc", "mxse"), ("pwc", "mape"),
-                                       ("ramp", "mse")])
+                                       ("ramp", "mse"), ("ramp_swapped", "mae")])
 def test_adjoint_matches_central_fd(orc, form, cost):
     ser = synth.load_series("60d")
     y = ser["yD"][:41]
@@ -260,6 +268,8 @@ def test_adjoint_matches_central_fd(orc, form, cost):
     else:
         pb = mkpb(orc, days=40, beta_form=orc.BETA_RAMP, yD=y, cost=orc.COSTS[cost])
         th = [0.24, 0.15, 11.37, 27.61, 0.1, 0.0019, 1.05e4]
+        if form == "ramp_swapped":  # t1 > t2 in theta: the derivatives follow the swap
+            th[2], th[3] = th[3], th[2]
     L, g, gu = orc.loss_grad(pb, th)
     assert L == pytest.approx(orc.loss(pb, th), rel=1e-14)
     fd = np.array([_fd(orc, pb, th, j) for j in range(len(th))])
@@ -367,10 +377,28 @@ def test_pso_update_rule_special_cases(orc):
     assert np.all((t >= 0) & (t < 1))
 
 
+def test_swarm_part_numbered_from_an_offset_is_that_part_of_the_swarm(orc):
+    # particles are numbered globally in the random-number counter: a swarm of 7 starting at
+    # particle 5 draws what particles 5..11 of a swarm of 16 draw
+    full = orc.PSO(None, 16, [-1.0] * 5, [2.0] * 5, seed=21, stream=3, objective_kind=orc.OBJ_SPHERE).init()
+    part = orc.PSO(None, 7, [-1.0] * 5, [2.0] * 5, seed=21, stream=3, objective_kind=orc.OBJ_SPHERE,
+                   p_offset=5).init()
+    assert np.array_equal(part.x, full.x[5:12]) and np.array_equal(part.v, full.v[5:12])
+    assert np.array_equal(part.pbest_f, full.pbest_f[5:12])
+    # with the whole swarm's global best set between steps, the part keeps following it
+    for _ in range(3):
+        part.set_state(part.x, part.v, part.pbest, part.pbest_f, 0, part.iter)
+        part.gbest[:] = full.gbest
+        full.step()
+        part.step()
+        assert np.array_equal(part.x, full.x[5:12]) and np.array_equal(part.pbest, full.pbest[5:12])
+
+
 def test_argmin_nan_and_ties(orc):
     assert orc.argmin([3.0, np.nan, 1.0, 1.0]) == 2
     assert orc.argmin([np.nan, np.nan]) == 0
     assert orc.argmin([np.inf, 5.0, np.nan, 5.0]) == 1
+    assert orc.argmin([np.nan, 5.0, 3.0]) == 2  # a NaN in front ranks last too
 
 
 def test_store_f32_rounds_state(orc):
@@ -389,6 +417,17 @@ def test_reeval_topk_is_best_of_k(orc):
     order = sorted(range(48), key=lambda p: (pso.pbest_f[p], p))[:8]
     exact = [orc.loss(pb, np.exp(pso.pbest[p])) for p in order]
     assert idx == order[int(np.argmin(exact))] and f == min(exact)
+    # stored values that rank the candidates opposite to their true losses: the re-evaluation
+    # looks at exactly the k best by stored value and returns the truly best of those
+    true = np.array([orc.loss(pb, np.exp(z)) for z in pso.pbest])
+    rank = np.argsort(-true, kind="stable")  # worst first
+    fake = np.empty(48)
+    fake[rank] = np.arange(48, dtype=float)
+    pso.set_state(pso.x, pso.v, pso.pbest, fake, int(rank[0]), pso.iter)
+    for k in (1, 5, 48, 60):
+        idx, f = pso.reeval_topk(k)
+        j = int(rank[min(k, 48) - 1])
+        assert idx == j and f == true[j], k
 
 
 # ------------------------------------------------------------------ calibration
@@ -485,3 +524,14 @@ def test_ensemble_bands_reproduction_number_closed_form(orc):
     r = np.sort(th[:, 0] / (th[:, 1] + th[:, 2]))
     assert np.all(b["R0"][:, 0] == (r[0] + r[1]) * 0.5)
     assert b["R0"].shape == (31 + 21, 1)
+
+
+def test_ensemble_bands_beta_is_the_ramp_at_each_day(orc):
+    # one member of the ramp form: the beta band on day d is eq. (beta) at t = d, written out
+    s = synth.load_series("30d")
+    pb = orc.Problem(yD=s["yD"], N=s["N"], beta_form=orc.BETA_RAMP, spd=10)
+    b1, b2, t1, t2 = 0.31, 0.12, 7.5, 19.25
+    b = orc.ensemble_bands(pb, [b1, b2, t2, t1, 0.1, 0.002, 1e4], 5, fractions=())
+    t = np.arange(31 + 5, dtype=float)
+    want = np.where(t < t1, b1, np.where(t < t2, b1 + (b2 - b1) * (t - t1) / (t2 - t1), b2))
+    assert np.allclose(b["beta"][:, 0], want, rtol=1e-14, atol=0)
