@@ -110,7 +110,7 @@ MUTANTS = [
 ]
 
 
-def _run_pins_on(name, fname, old, new, workdir):
+def _run_pins_on(name, fname, old, new, workdir, extra_env=None, extra_args=()):
     src_dir = os.path.join(ROOT, "oracle")
     dst = os.path.join(workdir, name)
     pkg = os.path.join(dst, "oracle")
@@ -121,9 +121,9 @@ def _run_pins_on(name, fname, old, new, workdir):
     text = open(path).read()
     assert text.count(old) == 1, f"{name}: the mutated text must occur exactly once in {fname}"
     open(path, "w").write(text.replace(old, new))
-    env = dict(os.environ, PYTHONPATH=os.pathsep.join([dst, ROOT]), PYTHONDONTWRITEBYTECODE="1")
+    env = dict(os.environ, PYTHONPATH=os.pathsep.join([dst, ROOT]), PYTHONDONTWRITEBYTECODE="1", **(extra_env or {}))
     # cwd = the copy, so that `import oracle` finds the mutant first
-    r = subprocess.run([sys.executable, "-m", "pytest", PINS, "-x", "-q", "-p", "no:cacheprovider"],
+    r = subprocess.run([sys.executable, "-m", "pytest", PINS, "-x", "-q", "-p", "no:cacheprovider", *extra_args],
                        cwd=dst, env=env, capture_output=True, text=True, timeout=600)
     return name, r.returncode, r.stdout[-2000:] + r.stderr[-2000:]
 
@@ -155,3 +155,20 @@ def test_pins_catch_the_mutant(mutant_runs, name):
     rc, out = mutant_runs[name]
     # 1: tests ran and at least one failed (not a build or collection error, not a crash)
     assert rc == 1, f"mutant {name} survived the pins (exit {rc}):\n{out}"
+
+
+def test_pins_pass_with_the_oracle_under_address_and_undefined_behaviour_sanitizers(tmp_path):
+    # the oracle built with ASan + UBSan (aborting on the first report) runs every pin cleanly:
+    # no out-of-bounds access, use after free, signed overflow or out-of-range float conversion
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    asan = subprocess.run([gcc, "-print-file-name=libasan.so"], capture_output=True, text=True).stdout.strip()
+    if not os.path.isabs(asan) or not os.path.exists(asan):
+        pytest.skip("no ASan runtime")
+    flags = '"-fsanitize=address,undefined,float-cast-overflow", "-fno-sanitize-recover=all", "-o", tmp'
+    # -s: pytest leaves stderr alone, so a sanitizer's report reaches the output checked here
+    _, rc, out = _run_pins_on("sanitized", PY_SRC, '"-o", tmp', flags, str(tmp_path),
+                              extra_env={"LD_PRELOAD": asan, "ASAN_OPTIONS": "detect_leaks=0"}, extra_args=("-s",))
+    assert rc == 0, out
+    assert "runtime error" not in out and "AddressSanitizer" not in out, out
