@@ -837,7 +837,7 @@ def cpu_baseline(name: str, budget_s: float = 15.0, iters_cap: int | None = None
         sample = f"{M} particles x {c['days']} days, init + {its} PSO iterations"
     dt = time.perf_counter() - t0
     return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": cpu_model(),
-            "sample": f"{sample}, single thread, FP64 ({dt:.1f} s)"}
+            "sample": f"{sample}, single thread, FP64 ({dt:.3g} s)"}
 
 
 def run_reference(args, rank, world):
