@@ -343,9 +343,11 @@ sird_status sird_ensemble_bands(const sird_problem* problem, const double* theta
  *
  * problems[W], configs[W] are host arrays.  Every window must share beta_form, K,
  * steps_per_day, cost, objective, fit_I0, precision (32), w, c1, c2, iters, the bounds and
- * log_scale; n_obs, observations, N, I0, R0, particles (1..2^20), seed and stream_id may
- * differ.  Two forms run a batch: one window per block (a block takes the next window from a
- * queue, longest first), or flat (every window's particle pairs spread over all threads of a
+ * log_scale; n_obs, observations, N, I0, R0, particles (1..2^20 per window, at most
+ * SIRD_MAX_PARTICLES over all windows), seed and stream_id may differ.  SIRD_ERR_ARG on
+ * settings that break these rules, SIRD_ERR_NOMEM when host or device memory runs out.
+ * Two forms run a batch: one window per block (a block takes the next window from a queue,
+ * longest first), or flat (every window's particle pairs spread over all threads of a
  * co-resident grid, one bounded grid barrier per iteration, the last item of a window to
  * finish an iteration publishing its global best; SIRD_ERR_TIMEOUT if a barrier wait runs
  * out).  Both give the same results.  configs[0].block_size = 0 lets the library pick the form,

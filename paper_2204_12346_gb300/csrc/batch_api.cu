@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <numeric>
 #include <string>
@@ -187,14 +188,17 @@ cudaError_t autotune(sird_batch* b, long long work) {
 
 }  // namespace
 
-extern "C" sird_status sird_batch_create(int W, const sird_problem* problems, const sird_pso_config* configs,
-                                         void* cuda_stream, sird_batch_t* out) {
+namespace {
+
+sird_status batch_create(int W, const sird_problem* problems, const sird_pso_config* configs, void* cuda_stream,
+                         sird_batch_t* out) {
     if (!out) return berr(SIRD_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (W < 1 || W > (1 << 20) || !problems || !configs) return berr(SIRD_ERR_ARG, "bad W or NULL arrays");
     const sird_problem& p0 = problems[0];
     const sird_pso_config& c0 = configs[0];
     std::string why;
+    long long all_particles = 0;
     for (int i = 0; i < W; ++i) {
         const sird_problem& p = problems[i];
         const sird_pso_config& c = configs[i];
@@ -206,10 +210,13 @@ extern "C" sird_status sird_batch_create(int W, const sird_problem* problems, co
         if (c.precision != 32) return berr(SIRD_ERR_UNSUPPORTED, "batched calibration is FP32 only");
         if (c.particles < 1 || c.particles > (1 << 20))
             return berr(SIRD_ERR_ARG, "particles per window out of range [1, 2^20]");
+        all_particles += c.particles;
         if (c.iters != c0.iters || c.w != c0.w || c.c1 != c0.c1 || c.c2 != c0.c2 || c.iters < 0)
             return berr(SIRD_ERR_ARG, "window " + std::to_string(i) + ": PSO coefficients or iterations differ");
         if (!c.lb || !c.ub) return berr(SIRD_ERR_ARG, "lb/ub is NULL");
     }
+    if (all_particles > SIRD_MAX_PARTICLES)
+        return berr(SIRD_ERR_ARG, "more than SIRD_MAX_PARTICLES particles over all windows");
     const int P = (p0.beta_form == SIRD_BETA_RAMP ? 6 : p0.K + 2) + (p0.fit_I0 ? 1 : 0);
     for (int i = 0; i < W; ++i)
         for (int d = 0; d < P; ++d) {
@@ -221,7 +228,10 @@ extern "C" sird_status sird_batch_create(int W, const sird_problem* problems, co
     if (c0.block_size != 0 && (c0.block_size < 32 || c0.block_size > 1024 || c0.block_size % 32))
         return berr(SIRD_ERR_ARG, "block_size must be 0 (autotune) or a multiple of 32 in [32, 1024]");
 
-    sird_batch* b = new (std::nothrow) sird_batch();
+    // owned by the guard until the batch is complete: every early return (and a failed host
+    // allocation, thrown as std::bad_alloc) releases what was allocated
+    std::unique_ptr<sird_batch, void (*)(sird_batch*)> guard(new (std::nothrow) sird_batch(), sird_batch_destroy);
+    sird_batch* b = guard.get();
     if (!b) return berr(SIRD_ERR_NOMEM, "host allocation failed");
     b->W = W;
     b->P = P;
@@ -255,10 +265,7 @@ extern "C" sird_status sird_batch_create(int W, const sird_problem* problems, co
     });
     for (int d = 0; d < P; ++d) {
         const bool lg = c0.log_scale && c0.log_scale[d];
-        if (lg && !(c0.lb[d] > 0)) {
-            delete b;
-            return berr(SIRD_ERR_ARG, "log_scale needs lb > 0");
-        }
+        if (lg && !(c0.lb[d] > 0)) return berr(SIRD_ERR_ARG, "log_scale needs lb > 0");
         if (lg) b->c.logmask |= 1u << d;
         b->c.zlb[d] = (float)(lg ? std::log(c0.lb[d]) : c0.lb[d]);
         b->c.zub[d] = (float)(lg ? std::log(c0.ub[d]) : c0.ub[d]);
@@ -317,7 +324,7 @@ extern "C" sird_status sird_batch_create(int W, const sird_problem* problems, co
     auto bail = [&](cudaError_t err, const char* what) {
         std::string m = std::string(what) + ": " + cudaGetErrorString(err);
         (void)cudaGetLastError();
-        sird_batch_destroy(b);
+        guard.reset();
         return berr(err == cudaErrorMemoryAllocation ? SIRD_ERR_NOMEM : SIRD_ERR_CUDA, m);
     };
     if (e != cudaSuccess) return bail(e, "allocating the batch");
@@ -370,16 +377,25 @@ extern "C" sird_status sird_batch_create(int W, const sird_problem* problems, co
     if (c0.block_size) {
         b->block = c0.block_size;
         b->flat = c0.launch_mode == SIRD_LAUNCH_FLAT ? 1 : 0;
-        if (b->flat && flat_blocks_per_sm(b->mdl, b->block) <= 0) {
-            sird_batch_destroy(b);
+        if (b->flat && flat_blocks_per_sm(b->mdl, b->block) <= 0)
             return berr(SIRD_ERR_ARG, "block_size does not fit the flat form");
-        }
     } else {
         e = autotune(b, work);
         if (e != cudaSuccess) return bail(e, "autotuning");
     }
-    *out = b;
+    *out = guard.release();
     return SIRD_OK;
+}
+
+}  // namespace
+
+extern "C" sird_status sird_batch_create(int W, const sird_problem* problems, const sird_pso_config* configs,
+                                         void* cuda_stream, sird_batch_t* out) {
+    try {  // no exception crosses the C ABI
+        return batch_create(W, problems, configs, cuda_stream, out);
+    } catch (const std::bad_alloc&) {
+        return berr(SIRD_ERR_NOMEM, "host allocation failed");
+    }
 }
 
 extern "C" void sird_batch_destroy(sird_batch_t b) {

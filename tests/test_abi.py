@@ -69,6 +69,46 @@ def test_create_rejects_bad_arguments_without_a_gpu(L, over, status):
     assert st == status and msg and not h.value
 
 
+def _batch_create(L, windows, **over):
+    from paper_2204_12346_gb300 import sird
+
+    kw = dict(K=1, spd=10, cost=0, beta_form=0, fit_I0=True, iters=5, lb=[0, 0, 0, 0], ub=[2, 1, 0.1, 1e6],
+              log_scale=None, w=0.5, c1=0.5, c2=0.5, particles=64, seed=0, block_size=0)
+    kw.update(over)
+    pbs, cfgs, keep = sird._batch_structs(windows, **kw)
+    h = C.c_void_p()
+    st = L.sird_batch_create(len(windows), pbs, cfgs, None, C.byref(h))
+    return st, L.sird_last_error(None).decode(), h
+
+
+@pytest.mark.parametrize("case", ["too_many_particles", "window_particles", "differing_K", "log_lb_zero", "block"])
+def test_batch_create_rejects_bad_arguments_without_a_gpu(L, case):
+    y = np.arange(31, dtype=float)
+    wins = [{"yD": y, "N": 38e6}, {"yD": y[:21], "N": 38e6}]
+    over = {}
+    if case == "too_many_particles":  # 65 windows of 2^20 particles: more than SIRD_MAX_PARTICLES in all
+        wins = [{"yD": y, "N": 38e6, "particles": 1 << 20} for _ in range(65)]
+    elif case == "window_particles":
+        wins[1]["particles"] = (1 << 20) + 1
+    elif case == "differing_K":  # every window must share the model settings
+        from paper_2204_12346_gb300 import sird
+
+        pbs, cfgs, keep = sird._batch_structs(wins, K=1, spd=10, cost=0, beta_form=0, fit_I0=True, iters=5,
+                                              lb=[0] * 4, ub=[1] * 4, log_scale=None, w=0.5, c1=0.5, c2=0.5,
+                                              particles=64, seed=0, block_size=0)
+        pbs[1].K = 2
+        h = C.c_void_p()
+        assert L.sird_batch_create(2, pbs, cfgs, None, C.byref(h)) == 1 and not h.value
+        assert "differ" in L.sird_last_error(None).decode()
+        return
+    elif case == "log_lb_zero":
+        over = dict(log_scale=[1, 1, 1, 1])
+    elif case == "block":
+        over = dict(block_size=48)
+    st, msg, h = _batch_create(L, wins, **over)
+    assert st == 1 and msg and not h.value, (st, msg)
+
+
 def test_null_handle_calls_are_safe(L):
     assert L.sird_pso_init(None) == 1
     assert L.sird_pso_step(None, 1) == 1
