@@ -312,7 +312,10 @@ sird_status sird_pso_polish(sird_pso_t h, int k, int iters, double first_step, i
  * Deaths forecast (Sec. 4.2): for each of k parameter vectors (host, row-major [k][P]),
  * integrates the window and `horizon` more days with the last transmission rate, gamma
  * and mu, and writes D on days n_obs .. n_obs+horizon-1 of the window's numbering to
- * out_D (host, [k][horizon]).  precision 32 or 64.  Blocks until out_D is written.
+ * out_D (host, [k][horizon]).  precision 32 or 64; k in 1..SIRD_MAX_PARTICLES, horizon in
+ * 1..100000.  Blocks until out_D is written.  SIRD_ERR_ARG on a bad problem, NULL pointers or
+ * sizes out of range, SIRD_ERR_NOMEM when host or device memory for k x horizon values runs
+ * out, SIRD_ERR_CUDA on a failed launch or copy; sird_last_error(NULL) gives the reason.
  */
 sird_status sird_forecast(const sird_problem* problem, const double* theta, int k, int horizon,
                           double* out_D, int precision, void* cuda_stream);
@@ -327,7 +330,10 @@ sird_status sird_forecast(const sird_problem* problem, const double* theta, int 
  * for even k) and, for each fractions[b] in (0, 1], the central band holding that fraction:
  * the sorted values at floor(k (1 - f) / 2) from either end.
  *   out (host) [6][n_obs + horizon][1 + 2 n_bands]: median, low_0, high_0, low_1, high_1, ...
- * k in 1..4096, n_bands in 0..16, horizon >= 0.  Blocks until out is written.
+ * k in 1..4096, n_bands in 0..16, horizon in 0..100000.  Blocks until out is written.
+ * SIRD_ERR_ARG on a bad problem, NULL pointers, sizes out of range, a fraction outside (0, 1]
+ * or a non-finite theta; SIRD_ERR_NOMEM when memory runs out; SIRD_ERR_CUDA on a failed launch
+ * or copy; sird_last_error(NULL) gives the reason.
  */
 sird_status sird_ensemble_bands(const sird_problem* problem, const double* theta, int k, int horizon,
                                 const double* fractions, int n_bands, double* out, void* cuda_stream);

@@ -775,8 +775,8 @@ extern "C" sird_status sird_pso_polish(sird_pso_t h, int k, int iters, double fi
     return SIRD_OK;
 }
 
-extern "C" sird_status sird_forecast(const sird_problem* pb, const double* theta, int k, int horizon, double* out_D,
-                                     int precision, void* cuda_stream) {
+static sird_status forecast_impl(const sird_problem* pb, const double* theta, int k, int horizon, double* out_D,
+                                 int precision, void* cuda_stream) {
     std::string why;
     sird_status st = sird_check_problem(pb, why);
     if (st != SIRD_OK) return g_create_error = why, st;
@@ -807,15 +807,25 @@ extern "C" sird_status sird_forecast(const sird_problem* pb, const double* theta
     cudaFree(dmem);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
-        return g_create_error = std::string("forecast: ") + cudaGetErrorString(e), SIRD_ERR_CUDA;
+        g_create_error = std::string("forecast: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? SIRD_ERR_NOMEM : SIRD_ERR_CUDA;
     }
     for (size_t i = 0; i < (size_t)k * horizon; ++i)
         out_D[i] = precision == 32 ? (double)((float*)hout.data())[i] : ((double*)hout.data())[i];
     return SIRD_OK;
 }
 
-extern "C" sird_status sird_ensemble_bands(const sird_problem* pb, const double* theta, int k, int horizon,
-                                           const double* fractions, int n_bands, double* out, void* cuda_stream) {
+extern "C" sird_status sird_forecast(const sird_problem* pb, const double* theta, int k, int horizon, double* out_D,
+                                     int precision, void* cuda_stream) {
+    try {  // the host copies scale with k and horizon: a failed allocation is reported, not thrown
+        return forecast_impl(pb, theta, k, horizon, out_D, precision, cuda_stream);
+    } catch (const std::bad_alloc&) {
+        return g_create_error = "forecast: host allocation failed", SIRD_ERR_NOMEM;
+    }
+}
+
+static sird_status ensemble_bands_impl(const sird_problem* pb, const double* theta, int k, int horizon,
+                                       const double* fractions, int n_bands, double* out, void* cuda_stream) {
     std::string why;
     sird_status st = sird_check_problem(pb, why);
     if (st != SIRD_OK) return g_create_error = why, st;
@@ -857,9 +867,19 @@ extern "C" sird_status sird_ensemble_bands(const sird_problem* pb, const double*
     cudaFree(dmem);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
-        return g_create_error = std::string("ensemble_bands: ") + cudaGetErrorString(e), SIRD_ERR_CUDA;
+        g_create_error = std::string("ensemble_bands: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? SIRD_ERR_NOMEM : SIRD_ERR_CUDA;
     }
     return SIRD_OK;
+}
+
+extern "C" sird_status sird_ensemble_bands(const sird_problem* pb, const double* theta, int k, int horizon,
+                                           const double* fractions, int n_bands, double* out, void* cuda_stream) {
+    try {
+        return ensemble_bands_impl(pb, theta, k, horizon, fractions, n_bands, out, cuda_stream);
+    } catch (const std::bad_alloc&) {
+        return g_create_error = "ensemble_bands: host allocation failed", SIRD_ERR_NOMEM;
+    }
 }
 
 static sird_status topk_impl(sird_pso_t h, int k, double* theta_out, double* loss_out, int* index_out);

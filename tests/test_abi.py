@@ -109,6 +109,40 @@ def test_batch_create_rejects_bad_arguments_without_a_gpu(L, case):
     assert st == 1 and msg and not h.value, (st, msg)
 
 
+@pytest.mark.parametrize("case", ["k0", "horizon0", "horizon_big", "null_out", "precision", "bad_problem"])
+def test_forecast_rejects_bad_arguments_without_a_gpu(L, case):
+    from paper_2204_12346_gb300 import sird
+
+    y = np.arange(31, dtype=float)
+    pb, keep = sird.make_problem(y if case != "bad_problem" else y[:1], 38e6)
+    th = np.array([[0.2, 0.1, 0.002, 1e4]])
+    out = np.zeros(14)
+    k, horizon, prec = 1, 14, 64
+    k = 0 if case == "k0" else k
+    horizon = {"horizon0": 0, "horizon_big": 100001}.get(case, horizon)
+    prec = 16 if case == "precision" else prec
+    dout = None if case == "null_out" else out.ctypes.data_as(C.POINTER(C.c_double))
+    st = L.sird_forecast(C.byref(pb), th.ctypes.data_as(C.POINTER(C.c_double)), k, horizon, dout, prec, None)
+    assert st == 1 and L.sird_last_error(None).decode()
+
+
+@pytest.mark.parametrize("case", ["k_big", "fraction0", "fraction_above_1", "nan_theta", "bands17"])
+def test_ensemble_bands_reject_bad_arguments_without_a_gpu(L, case):
+    from paper_2204_12346_gb300 import sird
+
+    pb, keep = sird.make_problem(np.arange(31, dtype=float), 38e6)
+    k = 4097 if case == "k_big" else 2
+    th = np.tile([0.2, 0.1, 0.002, 1e4], (k, 1))
+    if case == "nan_theta":
+        th[1, 0] = np.nan
+    fr = {"fraction0": [0.0], "fraction_above_1": [1.5], "bands17": [0.5] * 17}.get(case, [0.9])
+    fr = np.array(fr)
+    out = np.zeros(6 * 40 * (1 + 2 * len(fr)))
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    st = L.sird_ensemble_bands(C.byref(pb), dp(th), k, 9, dp(fr), len(fr), dp(out), None)
+    assert st == 1 and L.sird_last_error(None).decode()
+
+
 def test_null_handle_calls_are_safe(L):
     assert L.sird_pso_init(None) == 1
     assert L.sird_pso_step(None, 1) == 1
