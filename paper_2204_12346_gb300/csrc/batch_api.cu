@@ -12,6 +12,7 @@
 
 #include "../../include/sird_pso.h"
 #include "kernels.h"
+#include "trace.h"
 
 using namespace sird;
 
@@ -391,6 +392,7 @@ sird_status batch_create(int W, const sird_problem* problems, const sird_pso_con
 
 extern "C" sird_status sird_batch_create(int W, const sird_problem* problems, const sird_pso_config* configs,
                                          void* cuda_stream, sird_batch_t* out) {
+    TraceRange trace("sird_batch_create");
     try {  // no exception crosses the C ABI
         return batch_create(W, problems, configs, cuda_stream, out);
     } catch (const std::bad_alloc&) {
@@ -434,6 +436,7 @@ extern "C" int sird_batch_blocks_per_sm(sird_batch_t b) {
 }
 
 extern "C" sird_status sird_batch_calibrate(sird_batch_t b, sird_result* results) {
+    TraceRange trace("sird_batch_calibrate");
     if (!b || !results) return berr(SIRD_ERR_ARG, "batch or results is NULL");
     cudaError_t e = cudaSuccess;
     if (!b->graph) {
@@ -482,6 +485,7 @@ extern "C" sird_status sird_batch_calibrate(sird_batch_t b, sird_result* results
 
 extern "C" sird_status sird_batch_set_observations(sird_batch_t b, const double* y_all, long long n_total,
                                                    size_t* h2d_bytes) {
+    TraceRange trace("sird_batch_set_observations");
     if (!b || !y_all) return berr(SIRD_ERR_ARG, "batch or y_all is NULL");
     const int nser = b->mdl.ird ? 3 : 1;  // F_IRD: each window's D, I, R series
     long long need = 0;

@@ -10,6 +10,7 @@
 
 #include "../../include/sird_pso.h"
 #include "kernels.h"
+#include "trace.h"
 
 using namespace sird;
 
@@ -504,6 +505,7 @@ extern "C" sird_status sird_pso_eval(sird_pso_t h, const void* d_theta, int M, i
 // ---------------------------------------------------------------- swarm
 
 extern "C" sird_status sird_pso_init(sird_pso_t h) {
+    TraceRange trace("sird_pso_init");
     if (!h) return SIRD_ERR_ARG;
     if (h->sticky) return h->sticky;
     sird_status s = h->cuda(h->enqueue_iter(0, h->stream), "init launch");
@@ -513,6 +515,7 @@ extern "C" sird_status sird_pso_init(sird_pso_t h) {
 }
 
 extern "C" sird_status sird_pso_step(sird_pso_t h, int n_iters) {
+    TraceRange trace("sird_pso_step");
     if (!h) return SIRD_ERR_ARG;
     if (h->sticky) return h->sticky;
     if (n_iters < 0) return h->fail(SIRD_ERR_ARG, "step: n_iters < 0");
@@ -597,6 +600,7 @@ extern "C" sird_status sird_pso_result(sird_pso_t h, sird_result* out) {
 }
 
 extern "C" sird_status sird_pso_calibrate(sird_pso_t h, sird_result* out) {
+    TraceRange trace("sird_pso_calibrate");
     if (!h || !out) return SIRD_ERR_ARG;
     if (h->sticky) return h->sticky;
     if (h->shard_total > 0)
@@ -706,6 +710,7 @@ extern "C" sird_status sird_pso_set_state(sird_pso_t h, const void* buf, size_t 
 
 extern "C" sird_status sird_loss_grad(sird_pso_t h, const void* d_theta, int M, int ld, void* d_loss, void* d_grad,
                                       int ld_grad, void* d_grad_u0, int precision, int ckpt_every) {
+    TraceRange trace("sird_loss_grad");
     if (!h) return SIRD_ERR_ARG;
     if (h->sticky) return h->sticky;
     if (M < 0 || ld < M || ld_grad < M || (M > 0 && (!d_theta || !d_loss || !d_grad)))
@@ -740,6 +745,7 @@ extern "C" sird_status sird_loss_grad(sird_pso_t h, const void* d_theta, int M, 
 
 extern "C" sird_status sird_pso_polish(sird_pso_t h, int k, int iters, double first_step, int ckpt_every,
                                        int precision, sird_result* out) {
+    TraceRange trace("sird_pso_polish");
     if (!h || !out) return SIRD_ERR_ARG;
     if (h->sticky) return h->sticky;
     if (h->shard_total > 0) return h->fail(SIRD_ERR_STATE, "polish: not for a shard of a swarm");
@@ -817,6 +823,7 @@ static sird_status forecast_impl(const sird_problem* pb, const double* theta, in
 
 extern "C" sird_status sird_forecast(const sird_problem* pb, const double* theta, int k, int horizon, double* out_D,
                                      int precision, void* cuda_stream) {
+    TraceRange trace("sird_forecast");
     try {  // the host copies scale with k and horizon: a failed allocation is reported, not thrown
         return forecast_impl(pb, theta, k, horizon, out_D, precision, cuda_stream);
     } catch (const std::bad_alloc&) {
@@ -875,6 +882,7 @@ static sird_status ensemble_bands_impl(const sird_problem* pb, const double* the
 
 extern "C" sird_status sird_ensemble_bands(const sird_problem* pb, const double* theta, int k, int horizon,
                                            const double* fractions, int n_bands, double* out, void* cuda_stream) {
+    TraceRange trace("sird_ensemble_bands");
     try {
         return ensemble_bands_impl(pb, theta, k, horizon, fractions, n_bands, out, cuda_stream);
     } catch (const std::bad_alloc&) {
@@ -895,6 +903,7 @@ extern "C" sird_status sird_pso_topk_indexed(sird_pso_t h, int k, double* theta_
 }
 
 static sird_status topk_impl(sird_pso_t h, int k, double* theta_out, double* loss_out, int* index_out) {
+    TraceRange trace("sird_pso_topk");
     if (!h) return SIRD_ERR_ARG;
     if (h->sticky) return h->sticky;
     if (h->precision != 32) return h->fail(SIRD_ERR_UNSUPPORTED, "topk: FP32 swarms only");
