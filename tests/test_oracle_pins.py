@@ -231,6 +231,11 @@ def test_r2_and_ird(orc):
     p = mkpb(orc, yI=tr["I"], yR=tr["R"], cost=orc.MSE, **common)
     rngD = yD.max() - yD.min()
     assert orc.loss(p, th) == pytest.approx((c / rngD) ** 2 * (n - 1) / n, rel=1e-9)
+    # each compartment is scaled by its own series' range: R offset by c alone gives (c/range(yR))^2 (n-1)/n
+    yR = tr["R"].copy()
+    yR[1:] += c
+    pR = mkpb(orc, days=days, yD=tr["D"], yI=tr["I"], yR=yR, cost=orc.MSE, objective=orc.FIT_IRD, fit_I0=True)
+    assert orc.loss(pR, th) == pytest.approx((c / (yR.max() - yR.min())) ** 2 * (n - 1) / n, rel=1e-9)
     # the max picks the worst compartment: shift I by a larger relative amount
     yI = tr["I"] * 1.0
     yI[1:] += 0.5 * (yI.max() - yI.min())
