@@ -1,4 +1,5 @@
-"""Writes the stored synthetic series ``series_<name>.json`` (run from the repo root).
+"""Writes the stored synthetic series ``series_<name>.json`` (into this folder, or the folder
+given as the first argument).
 
 The noise-free curves are integrated by the FP64 oracle (explicit Euler on
 eq. (SIRD), Sec. 2.2 / 3.1) at ground-truth rates; deaths are then observed
@@ -59,7 +60,8 @@ def long_series(seed=0):
     }
 
 
-def main():
+def main(out_dir=None):
+    """Writes every series into out_dir (default: this folder, where the stored copies live)."""
     out = {
         "30d": window_series("30d", 1, [0.25], 30, 10, 1e4),
         "60d": window_series("60d", 4, [0.22, 0.19, 0.16, 0.13], 60, 10, 1e4),
@@ -68,7 +70,7 @@ def main():
                             120, 20, 1e4, extra_days=14),
         "450d": long_series(),
     }
-    here = os.path.dirname(os.path.abspath(__file__))
+    here = out_dir or os.path.dirname(os.path.abspath(__file__))
     for name, d in out.items():
         with open(os.path.join(here, f"series_{name}.json"), "w") as f:
             json.dump(d, f, indent=None, separators=(",", ":"))
@@ -76,4 +78,4 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    main(sys.argv[1] if len(sys.argv) > 1 else None)
