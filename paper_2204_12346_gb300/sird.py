@@ -142,10 +142,27 @@ def current_stream_handle(stream=None) -> int:
     return int(s.cuda_stream)
 
 
+def n_params(K=1, beta_form=BETA_PWC, fit_I0=True) -> int:
+    """Entries of theta: beta_1..beta_K (or beta1, beta2, t1, t2 of the ramp), gamma, mu[, I0]."""
+    return (6 if int(beta_form) == BETA_RAMP else int(K) + 2) + (1 if fit_I0 else 0)
+
+
+def _check_box(P, lb, ub, log_scale):
+    """The library reads P entries of lb, ub and log_scale: shorter arrays are refused here."""
+    for name, a in (("lb", lb), ("ub", ub), ("log_scale", log_scale)):
+        if a is not None and np.asarray(a).size < P:
+            raise ValueError(f"{name} has {np.asarray(a).size} entries; the model has {P} parameters")
+    if lb is None or ub is None:
+        raise ValueError("lb and ub are required")
+
+
 def make_problem(yD, N, K=1, spd=10, R0=0.0, I0=0.0, fit_I0=True, beta_form=BETA_PWC, cost=COST_MSE,
                  objective=FIT_D, yI=None, yR=None):
     """Builds a Problem struct; the returned keep-alive list must outlive the call that uses it."""
     yD = _f64(yD)
+    for name, a in (("yI", yI), ("yR", yR)):  # the library reads len(yD) values of each
+        if a is not None and np.asarray(a).size < yD.size:
+            raise ValueError(f"{name} has {np.asarray(a).size} values; yD has {yD.size}")
     keep = [yD]
     null = C.POINTER(C.c_double)()
     pI = pR = null
@@ -186,6 +203,7 @@ class Calibrator:
                  yI=None, yR=None):
         self._lib = lib()
         self.problem, k1 = make_problem(yD, N, K, spd, R0, I0, fit_I0, beta_form, cost, objective, yI, yR)
+        _check_box(n_params(K, beta_form, fit_I0), lb, ub, log_scale)
         self.config, k2 = make_config(particles, iters, lb, ub, log_scale, w, c1, c2, precision, seed, stream_id,
                                       reeval_topk, block_size, launch_mode)
         self._keep = k1 + k2
@@ -345,6 +363,8 @@ class Calibrator:
     def set_gbest(self, z, loss: float, index: int):
         """The swarm's global best (position z in the search coordinates) for the next step."""
         z = np.ascontiguousarray(np.asarray(z, dtype=np.float32))
+        if z.size != self.P:
+            raise ValueError(f"z has {z.size} entries; the model has {self.P} parameters")
         self._check(self._lib.sird_pso_set_gbest(self.h, z.ctypes.data_as(C.POINTER(C.c_float)), float(loss),
                                                  int(index)))
 
@@ -404,6 +424,7 @@ except ImportError:  # the binding still loads for CPU-only tooling
 def _batch_structs(windows, K, spd, cost, beta_form, fit_I0, iters, lb, ub, log_scale, w, c1, c2, particles, seed,
                    block_size, objective=FIT_D, launch_mode=0):
     W = len(windows)
+    _check_box(n_params(K, beta_form, fit_I0), lb, ub, log_scale)
     keep = []
     pbs = (Problem * W)()
     cfgs = (Config * W)()
@@ -503,6 +524,8 @@ def forecast(yD, N, theta, horizon, *, K=1, spd=10, R0=0.0, I0=0.0, fit_I0=True,
     L = lib()
     pb, keep = make_problem(yD, N, K, spd, R0, I0, fit_I0, beta_form)
     th = _f64(np.atleast_2d(theta))
+    if th.ndim != 2 or th.shape[1] != n_params(K, beta_form, fit_I0):
+        raise ValueError(f"theta must be [k, {n_params(K, beta_form, fit_I0)}]")
     out = np.zeros((th.shape[0], int(horizon)))
     st = L.sird_forecast(C.byref(pb), _dptr(th), th.shape[0], int(horizon), _dptr(out), int(precision),
                          C.c_void_p(current_stream_handle(stream)))
@@ -522,6 +545,8 @@ def ensemble_bands(yD, N, theta, horizon, fractions=(0.95, 0.9, 0.5), *, K=1, sp
     L = lib()
     pb, keep = make_problem(yD, N, K, spd, R0, I0, fit_I0, beta_form)
     th = _f64(np.atleast_2d(theta))
+    if th.ndim != 2 or th.shape[1] != n_params(K, beta_form, fit_I0):
+        raise ValueError(f"theta must be [k, {n_params(K, beta_form, fit_I0)}]")
     fr = _f64(fractions)
     n_days = len(_f64(yD)) + int(horizon)
     nq = 1 + 2 * len(fr)
@@ -541,6 +566,7 @@ def step_f32_noalloc(yD, N, obs, x, v, pbest, pbest_f, gbest, iteration, *, gbes
     gbest: [P]; obs: [n_obs] float32 observations; gbest_index: optional int32 CUDA tensor [1]."""
     L = lib()
     pb, k1 = make_problem(yD, N, K, spd, R0, I0, fit_I0, beta_form, cost)
+    _check_box(n_params(K, beta_form, fit_I0), lb, ub, log_scale)
     M = int(particles if particles is not None else x.shape[1])
     cfg, k2 = make_config(M, 1, lb, ub, log_scale, w, c1, c2, 32, seed, stream_id, 0, block_size, 0)
     ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None

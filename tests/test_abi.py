@@ -143,6 +143,29 @@ def test_ensemble_bands_reject_bad_arguments_without_a_gpu(L, case):
     assert st == 1 and L.sird_last_error(None).decode()
 
 
+def test_binding_refuses_short_arrays_before_calling_the_library(L):
+    # the library reads P bounds, n_obs values of each series and P entries of each theta row:
+    # shorter arrays are refused by the binding (no GPU needed to see it)
+    from paper_2204_12346_gb300 import sird
+
+    y = np.arange(31, dtype=float)
+    assert sird.n_params(4) == 7 and sird.n_params(beta_form=sird.BETA_RAMP, fit_I0=False) == 6
+    with pytest.raises(ValueError, match="lb"):
+        sird.Calibrator(y, 38e6, K=4, lb=[0] * 6, ub=[1] * 7)
+    with pytest.raises(ValueError, match="log_scale"):
+        sird.Calibrator(y, 38e6, K=4, lb=[1e-3] * 7, ub=[1] * 7, log_scale=[1] * 3)
+    with pytest.raises(ValueError, match="lb and ub"):
+        sird.Calibrator(y, 38e6)
+    with pytest.raises(ValueError, match="yR"):
+        sird.make_problem(y, 38e6, yI=y, yR=y[:10], objective=sird.FIT_IRD)
+    with pytest.raises(ValueError, match="lb"):
+        sird.Batch([{"yD": y, "N": 38e6}], K=2, lb=[0] * 4, ub=[1] * 5)
+    with pytest.raises(ValueError, match="theta"):
+        sird.forecast(y, 38e6, np.zeros((3, 5)), 7, K=1)
+    with pytest.raises(ValueError, match="theta"):
+        sird.ensemble_bands(y, 38e6, np.zeros((3, 3)), 7, K=1)
+
+
 def test_null_handle_calls_are_safe(L):
     assert L.sird_pso_init(None) == 1
     assert L.sird_pso_step(None, 1) == 1

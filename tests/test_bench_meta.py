@@ -38,3 +38,25 @@ def test_algorithmic_flop_counts():
     assert bench.algorithmic_flops_per_particle_day(20) == 163
     assert bench.algorithmic_flops_per_particle_day(10, ramp=True) == 133
     assert bench.algorithmic_flops_per_particle_day(10, ramp=True, ird=True) == 159
+
+
+def test_every_workload_fits_the_binding_checks():
+    # the boxes, series and model settings each workload passes satisfy the binding's checks
+    import bench
+    from paper_2204_12346_gb300 import configs, sird
+
+    for name in bench.BATCHED:
+        c, wins, lb, ub, model = bench.batch_windows(name)
+        P = sird.n_params(model["K"], model["beta_form"], model["fit_I0"])
+        sird._check_box(P, lb, ub, model["log_scale"])
+        assert len(lb) == P
+        for w in wins:
+            sird.make_problem(w["yD"], w["N"], yI=w.get("yI"), yR=w.get("yR"))
+    for name in ("window60", "plain64", "gradient90", "swarm2p20"):
+        c, ser, y, lb, ub = bench.single_window(name)
+        P = sird.n_params(c["K"])
+        sird._check_box(P, lb, ub, [1] * len(lb) if c["log"] else None)
+        assert len(lb) == P
+    c, ser, wins = bench.stability_windows()
+    lb, ub = configs.bounds_ramp(fit_I0=c.get("fit_I0", True))
+    assert len(lb) == sird.n_params(beta_form=sird.BETA_RAMP, fit_I0=c.get("fit_I0", True))
