@@ -94,6 +94,10 @@ MUTANTS = [
      "double t = (double)(k + 1) / (double)pb->spd;\n    if (t < t1) return b1;"),
     ("pwc_past_window_boundary", C_SRC, "if (k >= steps_window) return K - 1;", "if (k > steps_window) return K - 1;"),
     ("fixed_I0_ignored", C_SRC, "double I0 = pb->fit_I0 ? theta[idx_I0(pb)] : pb->I0;", "double I0 = pb->fit_I0 ? theta[idx_I0(pb)] : 0.0;"),
+    ("window_one_day_long", C_SRC, "long steps_window = (long)(pb->n_obs - 1) * pb->spd;",
+     "long steps_window = (long)pb->n_obs * pb->spd;"),
+    ("ramp_after_t2_is_beta1", C_SRC, "    return b2;\n}", "    return b1;\n}"),
+    ("r2_total_unsquared", C_SRC, "ss_tot += (pb->yD[i] - mean) * (pb->yD[i] - mean);", "ss_tot += fabs(pb->yD[i] - mean);"),
     # the forecast of Sec. 4.2
     ("forecast_repeats_last_day", C_SRC, "D_out[h] = D[L + 1 + h];", "D_out[h] = D[L + h];"),
     # the PSO of Sec. 3.3
@@ -115,6 +119,8 @@ MUTANTS = [
     ("pso_no_lower_clamp", C_SRC, "if (xn < cfg->zlb[d]) xn = cfg->zlb[d];", ""),
     ("gbest_from_positions", C_SRC, "memcpy(st->gbest, st->pbest + (size_t)g * cfg->P, sizeof(double) * cfg->P);",
      "memcpy(st->gbest, st->x + (size_t)g * cfg->P, sizeof(double) * cfg->P);"),
+    ("pbest_position_not_copied", C_SRC, "memcpy(st->pbest + (size_t)p * P, x, sizeof(double) * P);", ""),
+    ("nan_loss_not_infinite", C_SRC, "return isnan(f) ? INFINITY : f;", "return f;"),
     ("pso_particle_offset_ignored", C_SRC, "(uint32_t)p + cfg->p_offset", "(uint32_t)p"),
     ("store_f32_ignored", C_SRC, "return cfg->store_f32 ? (double)(float)x : x;", "return x;"),
     # the ensemble bands of Sec. 4.2

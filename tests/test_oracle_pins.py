@@ -406,6 +406,15 @@ def test_argmin_nan_and_ties(orc):
     assert orc.argmin([np.nan, 5.0, 3.0]) == 2  # a NaN in front ranks last too
 
 
+def test_nan_loss_counts_as_infinite(orc):
+    # a parameter vector whose loss is NaN ranks last: the swarm's objective returns +inf for it
+    pb = mkpb(orc, days=30, yD=np.arange(31.0))
+    pso = orc.PSO(pb, 4, [0.0] * 4, [1.0] * 4)
+    assert math.isnan(orc.loss(pb, [np.nan, 0.1, 0.002, 1e4]))
+    assert pso.objective([np.nan, 0.1, 0.002, 1e4]) == np.inf
+    assert pso.objective([0.2, 0.1, 0.002, 1e4]) == orc.loss(pb, [0.2, 0.1, 0.002, 1e4])
+
+
 def test_store_f32_rounds_state(orc):
     pso = orc.PSO(None, 8, [-1.0] * 3, [1.0] * 3, seed=2, store_f32=True, objective_kind=orc.OBJ_SPHERE).init()
     pso.step(3)
