@@ -767,7 +767,7 @@ def cpu_baseline_all_cores(name: str, windows_per_core: int = 16) -> dict:
         units = sum(pool.map(_oracle_windows_worker, jobs))
         dt = time.perf_counter() - t0
     return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
-            "sample": f"{n} windows x (init + 1 PSO iteration), one process per core, FP64 ({dt:.1f} s)"}
+            "sample": f"{n} windows x (init + 1 PSO iteration), one process per core, FP64 ({dt:.3g} s)"}
 
 
 def cpu_baseline(name: str, budget_s: float = 15.0, iters_cap: int | None = None) -> dict:
