@@ -63,6 +63,19 @@ def _create(L, **over):
     (dict(lb=[0, 0, 0, 2e6]), 1),
     (dict(log_scale=[1, 1, 1, 1]), 1),
     (dict(lb=[0, 0, 0, np.inf]), 1),
+    (dict(y=np.arange(4097, dtype=float)), 1),  # more than SIRD_MAX_OBS observations
+    (dict(N=np.inf), 1),
+    (dict(spd=1001), 1),
+    (dict(beta_form=2), 1),
+    (dict(fit_I0=2), 1),
+    (dict(lb=[0, 0, 0, 10.0], ub=[2, 1, 0.1, 5.0]), 1),  # lb > ub
+    (dict(launch_mode=9), 1),
+    (dict(precision=64, launch_mode=2), 7),  # the persistent and cluster launches are FP32 only
+    (dict(precision=64, launch_mode=5), 7),
+    (dict(launch_mode=4), 1),  # a batch form is not a handle's launch mode
+    (dict(precision=64, block_size=512), 1),
+    (dict(particles=(1 << 26) + 1), 1),
+    (dict(iters=-1), 1),
 ])
 def test_create_rejects_bad_arguments_without_a_gpu(L, over, status):
     st, msg, h = _create(L, **over)
