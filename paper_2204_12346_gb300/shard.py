@@ -13,6 +13,11 @@ gathered from the shards.
 A shard is any object with init(), step(n), shard_best() -> (loss, index, z),
 set_gbest(z, loss, index), topk(k, with_index=True) -> (theta [k, P], loss [k], index [k])
 and eval64(theta [k, P]) -> FP64 losses: sird.Calibrator (after set_shard) on a GPU.
+
+Failure detection: the exchange is the only point where ranks wait on one another, and it runs
+on the host between launches.  A rank that leaves (between steps, with nothing in flight) makes
+the others' next exchange fail -- the backend reports the closed connection, or the process
+group's timeout ends the wait -- and ShardedSwarm raises ShardFailure naming the exchange.
 """
 from __future__ import annotations
 
@@ -78,6 +83,15 @@ def exchange_best(loss: float, index: int, z, offsets: list[int], group=None, de
     return gloss, gidx, zt.cpu().numpy()
 
 
+class ShardFailure(RuntimeError):
+    """The exchange after `step` completed iterations (0: after the initialisation) failed,
+    e.g. because another rank left the process group."""
+
+    def __init__(self, step: int, cause: BaseException):
+        super().__init__(f"shard exchange after iteration {step} failed: {cause}")
+        self.step = int(step)
+
+
 class ShardedSwarm:
     """Runs a sharded swarm: shard is this rank's part (see the module docstring), offsets the
     first particle of every rank's part plus the total (shard_offsets)."""
@@ -89,19 +103,22 @@ class ShardedSwarm:
         self.device = device
         self.gbest = None
 
-    def _exchange(self):
+    def _exchange(self, step: int):
         loss, index, z = self.shard.shard_best()
-        self.gbest = exchange_best(loss, index, z, self.offsets, self.group, self.device)
+        try:
+            self.gbest = exchange_best(loss, index, z, self.offsets, self.group, self.device)
+        except RuntimeError as e:  # the backends raise RuntimeError subclasses for lost peers and timeouts
+            raise ShardFailure(step, e) from e
         self.shard.set_gbest(self.gbest[2], self.gbest[0], self.gbest[1])
 
     def run(self, iters: int):
         """Initialisation and iters synchronous iterations; returns the global best (loss,
-        index, z) after the last."""
+        index, z) after the last.  Raises ShardFailure if an exchange fails."""
         self.shard.init()
-        self._exchange()
-        for _ in range(int(iters)):
+        self._exchange(0)
+        for t in range(int(iters)):
             self.shard.step(1)
-            self._exchange()
+            self._exchange(t + 1)
         return self.gbest
 
     def result(self, k: int) -> dict:

@@ -136,3 +136,73 @@ def test_best_key_orders_by_loss_then_index():
         f, j = S.key_parts(S.best_key(v, i))
         assert j == i and (f == v or (np.isnan(v) and f == np.inf))
     assert all(-(1 << 63) <= S.best_key(v, i) < (1 << 63) for v, i in vals)
+
+
+class _LeavingShard:
+    """Wraps a shard; the rank with leave=True exits the process at the start of its step number
+    `at` (between steps: its previous exchange is complete, nothing of it is in flight)."""
+
+    def __init__(self, shard, leave, at):
+        self.shard, self.leave, self.at, self.steps = shard, leave, at, 0
+
+    def __getattr__(self, name):
+        return getattr(self.shard, name)
+
+    def step(self, n):
+        self.steps += 1
+        if self.leave and self.steps == self.at:
+            os._exit(3)
+        self.shard.step(n)
+
+
+def _rank_leave_main(rank, world, port, q, leaving_rank, at):
+    from datetime import timedelta
+
+    import torch.distributed as dist
+
+    import oracle as O
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=timedelta(seconds=20))
+    pb, lb, ub = _problem(O)
+    off, cnt = S.shard_range(TOTAL, rank, world)
+    sh = _LeavingShard(OracleShard(O, pb, off, cnt, lb, ub), rank == leaving_rank, at)
+    try:
+        S.ShardedSwarm(sh, S.shard_offsets(TOTAL, world)).run(ITERS)
+        q.put((rank, "finished", None))
+    except S.ShardFailure as e:
+        q.put((rank, "failed", e.step))
+    q.close()
+    q.join_thread()
+    os._exit(0)  # the process group lost a member: leave without a collective shutdown
+
+
+def test_a_rank_that_leaves_is_detected_at_the_next_exchange():
+    # failure detection on the host: rank 2 of 3 leaves at the start of its second step; the
+    # other two finish that step and their next exchange fails (a lost peer or the process
+    # group's timeout), reported as ShardFailure naming the exchange after iteration 2
+    import time
+
+    import torch.multiprocessing as mp
+
+    import oracle as O
+
+    O.build()
+    world, leaving, at = 3, 2, 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_leave_main, args=(r, world, port, q, leaving, at)) for r in range(world)]
+    t0 = time.monotonic()
+    for p in procs:
+        p.start()
+    try:
+        got = sorted((q.get(timeout=120) for _ in range(world - 1)), key=lambda t: t[0])
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    assert got == [(0, "failed", at), (1, "failed", at)], got
+    assert procs[leaving].exitcode == 3 and procs[0].exitcode == 0 and procs[1].exitcode == 0
+    assert time.monotonic() - t0 < 90
