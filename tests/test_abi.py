@@ -222,3 +222,16 @@ def test_header_is_plain_c_and_a_c_program_calls_the_library(L, tmp_path):
     run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert run.returncode == 0, (run.stdout, run.stderr)
     assert run.stdout.split()[0] == "1" and "NULL" in run.stdout
+
+
+def test_binding_constants_match_the_header():
+    # every enumerator and limit the header defines has the same value in the Python binding
+    from paper_2204_12346_gb300 import sird
+
+    header = open(os.path.join(ROOT, "include", "sird_pso.h")).read()
+    header = re.sub(r"/\*.*?\*/", "", header, flags=re.S)
+    values = {m.group(1): int(m.group(2)) for m in re.finditer(r"\bSIRD_([A-Z0-9_]+)\s*=\s*(\d+)", header)}
+    assert len(values) >= 20
+    for name, v in values.items():
+        assert getattr(sird, name) == v, name
+    assert re.search(r"#define SIRD_MAX_PARAMS (\d+)", header).group(1) == str(sird.MAX_PARAMS)
