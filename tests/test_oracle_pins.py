@@ -212,6 +212,17 @@ def test_cost_closed_forms(orc, D0):
         assert orc.loss(mkpb(orc, days=days, yD=Dh, cost=cost), th) == 0.0
 
 
+def test_one_day_window(orc):
+    # two observations: D after one day at beta = 0 is D0 + mu/(gamma+mu) (I0 - I0 (1 - dt (gamma+mu))^spd),
+    # and the MSE is e_1^2 / 2 (e_0 = 0: the scheme starts from the first observation)
+    g, m, I0, spd, D0 = 0.1, 0.004, 2e4, 10, 30.0
+    D1 = D0 + m / (g + m) * (I0 - I0 * (1 - (g + m) / spd) ** spd)
+    for cost, want in ((orc.MSE, 25.0 ** 2 / 2), (orc.MAE, 25.0 / 2), (orc.MXSE, 25.0 ** 2)):
+        pb = mkpb(orc, days=1, K=1, spd=spd, yD=[D0, D1 + 25.0], cost=cost)
+        assert orc.loss(pb, [0.0, g, m, I0]) == pytest.approx(want, rel=1e-9)
+    assert orc.simulate(mkpb(orc, days=1, yD=[D0, 0.0]), [0.0, g, m, I0])["D"][1] == pytest.approx(D1, rel=1e-14)
+
+
 def test_r2_and_ird(orc):
     days, th = 35, [0.3, 0.1, 0.004, 1e4]
     n = days + 1
