@@ -98,6 +98,8 @@ MUTANTS = [
      "long steps_window = (long)pb->n_obs * pb->spd;"),
     ("ramp_after_t2_is_beta1", C_SRC, "    return b2;\n}", "    return b1;\n}"),
     ("r2_total_unsquared", C_SRC, "ss_tot += (pb->yD[i] - mean) * (pb->yD[i] - mean);", "ss_tot += fabs(pb->yD[i] - mean);"),
+    ("schedule_rate_one_step_late", C_SRC, "euler_step(N, beta_steps[k], gamma, mu, dt, u);",
+     "euler_step(N, beta_steps[k > 0 ? k - 1 : 0], gamma, mu, dt, u);"),
     # the forecast of Sec. 4.2
     ("forecast_repeats_last_day", C_SRC, "D_out[h] = D[L + 1 + h];", "D_out[h] = D[L + h];"),
     # the PSO of Sec. 3.3

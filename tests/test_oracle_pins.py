@@ -212,6 +212,21 @@ def test_cost_closed_forms(orc, D0):
         assert orc.loss(mkpb(orc, days=days, yD=Dh, cost=cost), th) == 0.0
 
 
+def test_per_step_schedule_is_the_same_scheme(orc):
+    # the generator of the long synthetic series integrates with a per-step rate; fed the PWC
+    # model's rates step by step it gives the model's trajectory bit for bit (and so inherits the
+    # scheme's pins above)
+    days, spd, K = 40, 10, 4
+    th = [0.3, 0.2, 0.25, 0.12, 0.1, 0.003, 1.5e4]
+    pb = mkpb(orc, days=days, K=K, spd=spd, R0=300.0, yD=np.full(days + 1, 12.0))
+    beta = [orc.beta_at(pb, th, k) for k in range(days * spd)]
+    tr = orc.simulate(pb, th)
+    S0 = N - th[-1] - 300.0 - 12.0
+    sc = orc.simulate_schedule(N, (S0, th[-1], 300.0, 12.0), beta, th[K], th[K + 1], spd, days)
+    for q in "SIRD":
+        assert np.array_equal(sc[q], tr[q]), q
+
+
 def test_one_day_window(orc):
     # two observations: D after one day at beta = 0 is D0 + mu/(gamma+mu) (I0 - I0 (1 - dt (gamma+mu))^spd),
     # and the MSE is e_1^2 / 2 (e_0 = 0: the scheme starts from the first observation)
