@@ -60,3 +60,24 @@ def test_every_workload_fits_the_binding_checks():
     c, ser, wins = bench.stability_windows()
     lb, ub = configs.bounds_ramp(fit_I0=c.get("fit_I0", True))
     assert len(lb) == sird.n_params(beta_form=sird.BETA_RAMP, fit_I0=c.get("fit_I0", True))
+
+
+def test_reference_arm_line_has_the_contract_keys():
+    import json
+    import subprocess
+
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3",
+                        "--ref-units", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e", "impl"):
+        assert k in out, k
+    assert out["impl"] == "reference" and out["n_gpus"] == 1 and out["steps"] == 1 and out["warmup"] == 3
+    assert out["value"] > 0 and out["higher_is_better"] is True and out["vs_baseline"] is None
+    assert out["dtype"] == "f64" and out["data"] == "synthetic" and "512" in out["config"]["workload"]
+    cb = out["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == out["value"] and cb["sample"]
+    assert out["e2e"] == {"value": out["value"], "unit": out["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
