@@ -206,3 +206,52 @@ def test_a_rank_that_leaves_is_detected_at_the_next_exchange():
     assert got == [(0, "failed", at), (1, "failed", at)], got
     assert procs[leaving].exitcode == 3 and procs[0].exitcode == 0 and procs[1].exitcode == 0
     assert time.monotonic() - t0 < 90
+
+
+def _rank_groups_main(rank, world, port, q):
+    import torch.distributed as dist
+
+    import oracle as O
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    groups = [dist.new_group([0, 1]), dist.new_group([2, 3])]  # every rank creates every group
+    g = rank // 2
+    pb, lb, ub = _problem(O)
+    sub_rank, sub_world = rank % 2, 2
+    off, cnt = S.shard_range(TOTAL, sub_rank, sub_world)
+    sh = OracleShard(O, pb, off, cnt, lb, ub)
+    sh.pso = O.PSO(pb, cnt, lb, ub, logdim=[0] * len(lb), seed=SEED + g, store_f32=True, p_offset=off)
+    sw = S.ShardedSwarm(sh, S.shard_offsets(TOTAL, sub_world), group=groups[g])
+    gb = sw.run(ITERS)
+    res = sw.result(TOPK)
+    q.put((rank, gb[:2], res["index"], res["loss"]))
+    dist.destroy_process_group()
+
+
+def test_two_swarms_on_subgroups_of_four_ranks():
+    # two windows' swarms side by side, each split over its own pair of ranks: the exchange
+    # addresses the owner through its global rank, and each pair reproduces its own swarm
+    import torch.multiprocessing as mp
+
+    import oracle as O
+
+    O.build()
+    world = 4
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_groups_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = sorted((q.get(timeout=300) for _ in procs), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    pb, lb, ub = _problem(O)
+    for g in (0, 1):
+        ref = O.PSO(pb, TOTAL, lb, ub, logdim=[0] * len(lb), seed=SEED + g, store_f32=True).init().step(ITERS)
+        idx, f = ref.reeval_topk(TOPK)
+        for t in got[2 * g:2 * g + 2]:
+            assert t[1] == (ref.gbest_f, ref.gbest_idx) and t[2] == idx and t[3] == f
+    assert got[0][1] != got[2][1]  # the two swarms differ
