@@ -16,9 +16,10 @@ re-scoring of the result) must reach (1 + 1e-6) L_ref.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload batch512|window60|plain64|gradient90|swarm2p20|paper|paper_ird|stability]
 
-With --gpus N > 1 (one process per GPU under torchrun) every rank calibrates its own batch of
-windows (its own Philox stream words); there is no data-path collective, and value = all ranks'
-particle-days / the slowest rank's time (weak scaling).
+With --gpus N > 1 every rank (one process per GPU; started here through torch.distributed.run
+unless an outer launcher already set WORLD_SIZE, which must then equal N) calibrates its own batch
+of windows (its own Philox stream words); there is no data-path collective, and value = all
+ranks' particle-days / the slowest rank's time (weak scaling).
 """
 from __future__ import annotations
 
@@ -863,6 +864,23 @@ def run_reference(args, rank, world):
     }
 
 
+def _free_port() -> int:
+    import socket
+
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def relaunch_under_torchrun(n: int):
+    """Replaces this process by `torch.distributed.run` starting n ranks of this script with the
+    same arguments (rendezvous on 127.0.0.1); the ranks print as a launched job would."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", f"--master-port={_free_port()}", os.path.abspath(__file__)] + sys.argv[1:]
+    sys.stdout.flush()
+    os.execv(sys.executable, cmd)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -880,8 +898,14 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-
+    if args.gpus < 1:
+        ap.error("--gpus must be >= 1")
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        # one process per GPU: start the ranks here rather than asking for an outer launcher
+        relaunch_under_torchrun(args.gpus)
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world != args.gpus:
+        ap.error(f"--gpus {args.gpus} but WORLD_SIZE={world}: launch one rank per GPU")
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:
         import torch

@@ -75,7 +75,7 @@ def test_topk_launch_count():
 def test_reference_arm_two_ranks_prints_one_line():
     port = _free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
-           "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--gpus", "2", "--impl", "reference",
            "--workload", "plain64", "--steps", "1", "--warmup", "3", "--ref-units", "1"]
     env = dict(os.environ, OMP_NUM_THREADS="1")
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=540, env=env)
@@ -85,3 +85,26 @@ def test_reference_arm_two_ranks_prints_one_line():
     out = json.loads(lines[0])
     assert out["impl"] == "reference" and out["n_gpus"] == 2 and out["value"] > 0
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["cpu_baseline"]["kind"] == "oracle"
+
+
+@pytest.mark.timeout(600)
+def test_bench_starts_its_own_ranks_for_several_gpus():
+    """`bench.py --gpus 2` without an outer launcher starts two ranks itself and prints one line
+    with n_gpus 2."""
+    cmd = [sys.executable, "bench.py", "--gpus", "2", "--impl", "reference", "--workload", "plain64", "--steps", "1",
+           "--warmup", "3", "--ref-units", "1"]
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    env["OMP_NUM_THREADS"] = "1"
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=540, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    assert out["impl"] == "reference" and out["n_gpus"] == 2
+
+
+def test_bench_refuses_a_rank_count_that_differs_from_gpus():
+    env = dict(os.environ, WORLD_SIZE="2", RANK="0", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, "bench.py", "--gpus", "4", "--impl", "reference"], cwd=ROOT,
+                       capture_output=True, text=True, timeout=120, env=env)
+    assert r.returncode != 0 and "WORLD_SIZE" in r.stderr
