@@ -405,8 +405,9 @@ sird_status sird_pso_calibrate_batched(int W, const sird_problem* problems, cons
  *
  * Same kernel and same results as sird_pso_step with SIRD_LAUNCH_PER_ITER on a handle built
  * from the same problem and config.  Inputs and outputs are the caller's:
- *   problem, config  host structs as for sird_pso_create (precision must be 32; only the
- *                    values of y_D[0] and the count of zeros in y_D are read from y_D)
+ *   problem, config  host structs as for sird_pso_create, checked the same way (precision
+ *                    must be 32, objective F_D); y_D gives D0 = y_D[0], the zeros that MAPE
+ *                    skips and, for MAPE, the reciprocals 1/y_D rounded to float
  *   d_obs            device [n_obs] float observations of D (the float values of y_D)
  *   d_x, d_v, d_pbest  device [P][ld] float, read and written (layout of sird_pso_eval)
  *   d_pbest_f        device [ld] float, read and written
@@ -422,7 +423,9 @@ sird_status sird_pso_calibrate_batched(int W, const sird_problem* problems, cons
  * must start at zero, but calls that overlap on the GPU (different streams, other threads) race
  * on it -- serialise them.  n_obs above SIRD_NOALLOC_MAX_OBS is rejected with SIRD_ERR_ARG; the
  * message is available from sird_last_error(NULL).  No cudaMalloc, cudaFree or other allocating
- * call is made.
+ * call is made.  The kernels' device-side error bits (a loss that came out NaN, counted as
+ * +inf; index checks of a SIRD_DEBUG_BOUNDS build) are not reported by this entry point: the
+ * array's error word is cleared by every call and not read back.
  */
 sird_status sird_pso_step_f32_noalloc(const sird_problem* problem, const sird_pso_config* config,
                                       const float* d_obs, float* d_x, float* d_v, float* d_pbest,

@@ -16,11 +16,17 @@
 // as an ordinary pointer.
 #include <cmath>
 #include <mutex>
+#include <string>
 
 #include "../../include/sird_pso.h"
 #include "kernels.h"
 
 using namespace sird;
+
+// The handle path's argument checks and window constants (sird_pso_api.cu), so that this entry
+// point derives exactly what sird_pso_create derives.
+sird_status sird_check_problem(const sird_problem* pb, std::string& why);
+void sird_fill_window(const sird_problem* pb, WindowDev& w, ModelDev& m);
 
 namespace {
 
@@ -51,12 +57,6 @@ cudaError_t noalloc_scratch(unsigned char** out) {
     return cudaSuccess;
 }
 
-// Reciprocals of the FP32 observations (0 where y == 0), as the handle path stores them.
-__global__ void noalloc_reciprocals(const float* __restrict__ y, int n, float* __restrict__ inv) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) inv[i] = y[i] != 0.f ? (float)(1.0 / (double)y[i]) : 0.f;
-}
-
 // The message goes where sird_last_error(NULL) reads it.
 sird_status fail(sird_status s, const char* msg) {
     sird::set_global_error(msg);
@@ -72,13 +72,14 @@ extern "C" sird_status sird_pso_step_f32_noalloc(const sird_problem* pb, const s
     if (!pb || !cfg) return fail(SIRD_ERR_ARG, "problem or config is NULL");
     if (pb->n_obs < 2 || pb->n_obs > kNoAllocMaxObs)
         return fail(SIRD_ERR_ARG, "n_obs out of range [2, SIRD_NOALLOC_MAX_OBS]");
-    if (!pb->y_D) return fail(SIRD_ERR_ARG, "y_D is NULL (its first value is D0 and its zeros count for MAPE)");
-    if (!(pb->N > 0) || !std::isfinite(pb->N)) return fail(SIRD_ERR_ARG, "N must be finite and positive");
-    if (pb->steps_per_day < 1 || pb->steps_per_day > 1000) return fail(SIRD_ERR_ARG, "steps_per_day out of range");
-    if (pb->beta_form != SIRD_BETA_PWC && pb->beta_form != SIRD_BETA_RAMP) return fail(SIRD_ERR_ARG, "unknown beta_form");
-    if (pb->beta_form == SIRD_BETA_PWC && (pb->K < 1 || pb->K > SIRD_MAX_PARAMS - 3))
-        return fail(SIRD_ERR_ARG, "K out of range");
-    if (pb->cost < SIRD_COST_MSE || pb->cost > SIRD_COST_MAPE) return fail(SIRD_ERR_ARG, "unknown cost");
+    {
+        std::string why;  // touched only when a check fails
+        const sird_status st = sird_check_problem(pb, why);
+        if (st != SIRD_OK) {
+            sird::set_global_error(why.c_str());
+            return st;
+        }
+    }
     if (pb->objective != SIRD_FIT_D) return fail(SIRD_ERR_UNSUPPORTED, "only the F_D objective");
     if (cfg->precision != 32) return fail(SIRD_ERR_UNSUPPORTED, "the no-allocation step is FP32 only");
     const int P = (pb->beta_form == SIRD_BETA_RAMP ? 6 : pb->K + 2) + (pb->fit_I0 ? 1 : 0);
@@ -90,32 +91,11 @@ extern "C" sird_status sird_pso_step_f32_noalloc(const sird_problem* pb, const s
     const int block = cfg->block_size ? cfg->block_size : 128;
     if (block < 32 || block > 1024 || block % 32) return fail(SIRD_ERR_ARG, "block_size must be a multiple of 32 in [32, 1024]");
 
-    // window constants, as the handle path derives them
+    // window constants, exactly as the handle path derives them
     WindowDev w{};
     ModelDev m{};
+    sird_fill_window(pb, w, m);
     const int n = pb->n_obs;
-    w.n_obs = n;
-    for (int i = 0; i < n; ++i) w.n_kept += (pb->y_D[i] != 0.0);
-    w.N = pb->N;
-    w.I0 = pb->I0;
-    w.R0 = pb->R0;
-    w.D0 = pb->y_D[0];
-    w.dt = 1.0 / (double)pb->steps_per_day;
-    auto split = [](double x, float& h, float& l) {
-        h = (float)x;
-        l = (float)(x - (double)h);
-    };
-    split(pb->N, w.Nh, w.Nl);
-    split(pb->R0 + pb->y_D[0], w.RD0h, w.RD0l);
-    w.I0f = (float)pb->I0;
-    split(w.dt / pb->N, w.cbn_h, w.cbn_l);
-    split(w.dt, w.dt_h, w.dt_l);
-    m.P = P;
-    m.K = pb->beta_form == SIRD_BETA_PWC ? pb->K : 1;
-    m.spd = pb->steps_per_day;
-    m.beta_form = pb->beta_form;
-    m.fit_I0 = pb->fit_I0;
-    m.cost = pb->cost;
 
     PsoCoeffs<float> c{};
     for (int d = 0; d < P; ++d) {
@@ -148,8 +128,11 @@ extern "C" sird_status sird_pso_step_f32_noalloc(const sird_problem* pb, const s
     e = cudaMemsetAsync(s, 0, kNoAllocHeader, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(r.gkey, 0xFF, sizeof(unsigned long long), st);
     if (e == cudaSuccess && m.cost == COST_MAPE) {
-        noalloc_reciprocals<<<(n + 255) / 256, 256, 0, st>>>(d_obs, n, inv);
-        e = cudaGetLastError();
+        // reciprocals of the double observations, rounded to float as the handle path stores them
+        // (a fixed host array: the copy from pageable memory is staged before the call returns)
+        float inv_h[kNoAllocMaxObs];
+        for (int i = 0; i < n; ++i) inv_h[i] = pb->y_D[i] != 0.0 ? (float)(1.0 / pb->y_D[i]) : 0.f;
+        e = cudaMemcpyAsync(inv, inv_h, sizeof(float) * n, cudaMemcpyHostToDevice, st);
     }
     if (e != cudaSuccess) return fail(SIRD_ERR_CUDA, cudaGetErrorString(e));
     ObsDev o{d_obs, inv, nullptr};

@@ -558,6 +558,56 @@ def ensemble_bands(yD, N, theta, horizon, fractions=(0.95, 0.9, 0.5), *, K=1, sp
     return {q: out[i] for i, q in enumerate(BAND_QUANTITIES)}
 
 
+def check_noalloc_buffers(P, M, n_obs, obs, x, v, pbest, pbest_f, gbest, gbest_index=None, require_cuda=True):
+    """Refuses, before any library call, buffers that the no-allocation step would read or write
+    past their ends: x, v and pbest float32 [P, ld] with one leading dimension ld >= M and unit
+    stride along particles; pbest_f float32 with at least ld entries; gbest float32 with at
+    least P; obs float32 with at least n_obs; gbest_index int32 with at least one; every tensor
+    contiguous where it is read as a flat array and on the current CUDA device."""
+    import torch
+
+    def flat(t, name, dtype, n):
+        if t.dtype != dtype:
+            raise ValueError(f"{name} must be {dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() < n:
+            raise ValueError(f"{name} holds {t.numel()} entries, needs at least {n}")
+
+    tensors = {"obs": obs, "x": x, "v": v, "pbest": pbest, "pbest_f": pbest_f, "gbest": gbest}
+    if gbest_index is not None:
+        tensors["gbest_index"] = gbest_index
+    if require_cuda:
+        if not torch.cuda.is_available():
+            raise ValueError("the buffers must be tensors on the current CUDA device (no CUDA device is available)")
+        dev = torch.cuda.current_device()
+        for name, t in tensors.items():
+            if not t.is_cuda or t.device.index != dev:
+                raise ValueError(f"{name} must be a tensor on the current CUDA device (cuda:{dev})")
+    ld = None
+    for name, t in (("x", x), ("v", v), ("pbest", pbest)):
+        if t.dtype != torch.float32:
+            raise ValueError(f"{name} must be float32")
+        if t.dim() != 2 or t.shape[0] < P:
+            raise ValueError(f"{name} must be [P={P}, ld]")
+        if t.stride(1) != 1:
+            raise ValueError(f"{name} must have unit stride along particles")
+        if ld is None:
+            ld = t.stride(0)
+        elif t.stride(0) != ld:
+            raise ValueError("x, v and pbest must share one leading dimension")
+        if t.shape[1] < M or ld < M:
+            raise ValueError(f"{name} holds fewer than {M} particles per row")
+        if t.storage_offset() + (P - 1) * ld + M > t.untyped_storage().nbytes() // 4:
+            raise ValueError(f"{name} is too short for [P={P}, ld={ld}]")
+    flat(pbest_f, "pbest_f", torch.float32, ld)
+    flat(gbest, "gbest", torch.float32, P)
+    flat(obs, "obs", torch.float32, n_obs)
+    if gbest_index is not None:
+        flat(gbest_index, "gbest_index", torch.int32, 1)
+    return ld
+
+
 def step_f32_noalloc(yD, N, obs, x, v, pbest, pbest_f, gbest, iteration, *, gbest_index=None, stream=None,
                      K=1, spd=10, R0=0.0, I0=0.0, fit_I0=True, beta_form=BETA_PWC, cost=COST_MSE, particles=None,
                      lb=None, ub=None, log_scale=None, w=0.5, c1=0.5, c2=0.5, seed=0, stream_id=0, block_size=0):
@@ -566,8 +616,10 @@ def step_f32_noalloc(yD, N, obs, x, v, pbest, pbest_f, gbest, iteration, *, gbes
     gbest: [P]; obs: [n_obs] float32 observations; gbest_index: optional int32 CUDA tensor [1]."""
     L = lib()
     pb, k1 = make_problem(yD, N, K, spd, R0, I0, fit_I0, beta_form, cost)
-    _check_box(n_params(K, beta_form, fit_I0), lb, ub, log_scale)
+    P = n_params(K, beta_form, fit_I0)
+    _check_box(P, lb, ub, log_scale)
     M = int(particles if particles is not None else x.shape[1])
+    check_noalloc_buffers(P, M, len(_f64(yD)), obs, x, v, pbest, pbest_f, gbest, gbest_index)
     cfg, k2 = make_config(M, 1, lb, ub, log_scale, w, c1, c2, 32, seed, stream_id, 0, block_size, 0)
     ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
     st = L.sird_pso_step_f32_noalloc(C.byref(pb), C.byref(cfg), ptr(obs), ptr(x), ptr(v), ptr(pbest), ptr(pbest_f),
