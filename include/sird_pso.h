@@ -134,7 +134,9 @@ typedef struct sird_problem {
  *   reeval_topk   FP32 only: at the end, the k best personal bests are re-evaluated in FP64
  *                 and the best of them is reported (0 = report the FP32 global best as is)
  *   block_size    threads per block for the swarm kernels (0 = library default; else a
- *                 multiple of 32 in 32..1024)
+ *                 multiple of 32 in 32..1024; the FP32 per-iteration kernels run blocks of at
+ *                 most 256 threads, the FP64 kernels accept at most 256; results do not depend
+ *                 on the block shape)
  *   launch_mode   SIRD_LAUNCH_AUTO, SIRD_LAUNCH_PER_ITER (one kernel per iteration),
  *                 SIRD_LAUNCH_PERSISTENT (FP32 only: all iterations in one cooperative launch
  *                 with the swarm in shared memory, the blocks' best exchanged through global
@@ -361,7 +363,9 @@ sird_status sird_ensemble_bands(const sird_problem* problem, const double* theta
  * (cached in the file named by the environment variable SIRD_TUNE_CACHE when it is set; with
  * SIRD_TUNE_VERBOSE=1 every candidate's time goes to stderr);
  * otherwise a multiple of 32 in 32..1024 with as many blocks per SM as fit, in the form
- * configs[0].launch_mode names (SIRD_LAUNCH_FLAT, else one window per block).
+ * configs[0].launch_mode names (SIRD_LAUNCH_FLAT, else one window per block).  The kernels are
+ * compiled for at most 768 threads per block (PWC beta, F_D) or 384 (the ramp, F_IRD); a larger
+ * block_size is refused with SIRD_ERR_ARG.
  */
 typedef struct sird_batch* sird_batch_t;
 sird_status sird_batch_create(int W, const sird_problem* problems, const sird_pso_config* configs, void* cuda_stream,

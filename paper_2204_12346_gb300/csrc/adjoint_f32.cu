@@ -10,11 +10,12 @@
 //     dL/dmu     =  dt sum_k I_k (lambda_D - lambda_I)_{k+1}
 // and dL/dI0 = lambda_I(0) - lambda_S(0) (S0 = N - I0 - R0 - D0).
 //
-// The forward pass is the compensated FP32 integration of the evaluation kernels, operation for
+// The forward pass is the FP32 trajectory of the evaluation kernels (traj_f32.cuh), operation for
 // operation, so the loss equals the FP32 evaluation's bit for bit.  It stores the state at the
-// start of every day (Sday, I, its low part, and the day's error e_d) in global scratch
-// [day][4][M]; the reverse pass re-integrates one day at a time, staging each step's S, I and
-// coefficient in shared memory, and sweeps the day backwards.  lambda_S and lambda_I carry
+// start of every day (S, I, its low part, and the day's error e_d) in global scratch
+// [day][4][M]; the reverse pass re-integrates one day at a time from it in the C-form step
+// (euler_f32), staging each step's S, I and coefficient in shared memory, and sweeps the day
+// backwards.  lambda_S and lambda_I carry
 // their rounding errors in low parts folded in once a day (their per-step increments are tiny
 // against them, so plain FP32 sums would drift by up to steps x 2^-24); the gradient's per-step
 // terms are summed per day in FP32 and the day sums in FP64.
@@ -159,43 +160,61 @@ __device__ __forceinline__ float cb_of_f32(const WindowDev& w, float beta) {
     return __fmaf_rn(beta, w.cbn_h, __fmul_rn(beta, w.cbn_l));
 }
 
-// Forward pass: the FP32 evaluation's arithmetic, plus the day-start checkpoints (Sday, I, Il,
-// e_day) at ck[(day * 4 + q) * cs].  Returns the loss; e_last = e_L, imax = the MXSE day.
-template <int SPD, int COST, bool RAMP>
-__device__ __forceinline__ float forward_checkpointed(const WindowDev& w, const ModelDev& m, const float* ys,
-                                                      const float* invys, const float* th, int B, const CoefF32& cf,
-                                                      float* ck, size_t cs, float& e_last, int& imax) {
-    const int n = w.n_obs, L = n - 1, spd = SPD > 0 ? SPD : m.spd, steps = L * spd, K = m.K;
-    float I = cf.I0, Il = 0.f;
-    DayStateF32 ds;
-    ds.init(w, I, ys[0]);
-    LossF32<COST> lossacc;
-    float emax = 0.f, e_prev = 0.f;  // e_0 = y_0 - D_0 = 0
-    imax = 0;
-    int seg = 0, next_b = (!RAMP && K > 1) ? segment_start(1, steps, K) : INT_MAX;
-    float cb = RAMP ? 0.f : cb_of_f32(w, th[0]);
-    for (int day = 0; day < L; ++day) {
-        float* c = ck + (size_t)day * 4 * cs;
-        c[0] = ds.Sday;
-        c[cs] = I;
-        c[2 * cs] = Il;
-        c[3 * cs] = e_prev;
-        float cday = 0.f, dday = 0.f;
-        day_steps<SPD, RAMP, false>(day, spd, steps, K, th, B, cf.rp, cf.a, cf.dm, w, ds.Sday, cday, dday, I, Il, seg,
-                                    next_b, cb, nullptr, nullptr, nullptr);
-        const float e = ds.close_day(w, cday, dday, ys[day + 1], I, Il);
-        lossacc.add(e, COST == COST_MAPE ? invys[day + 1] : 0.f);
+// Forward pass: the FP32 evaluation's trajectory and cost (traj_f32.cuh), so the loss equals
+// the FP32 evaluation's bit for bit, plus the day-start checkpoints (S, I, its low part, and the
+// day's error e_d) at ck[(day * 4 + q) * cs].  Returns the loss; e_last = e_L, imax = the MXSE
+// day (the first with the largest e^2).
+template <int COST>
+struct CkptObs {
+    CostT<float, COST> c;
+    const float* invys;
+    float* ck;
+    size_t cs;
+    float emax, e_last;
+    int imax;
+    __device__ __forceinline__ void day_start(int day, float Qh, float Ql, float Ih, float Il, float e) {
+        float* q = ck + (size_t)day * 4 * cs;
+        q[0] = __fadd_rn(__fsub_rn(Qh, Ih), __fsub_rn(Ql, Il));  // S = Q - I at the day's start
+        q[cs] = Ih;
+        q[2 * cs] = Il;
+        q[3 * cs] = e;
+    }
+    __device__ __forceinline__ void day_end(int day, float e, float, float, float) {
+        c.add(e, COST == COST_MAPE ? invys[day] : 0.f);
         if (COST == COST_MXSE) {
             const float e2 = __fmul_rn(e, e);
             if (e2 > emax) {
                 emax = e2;
-                imax = day + 1;
+                imax = day;
             }
         }
-        e_prev = e;
+        e_last = e;
     }
-    e_last = e_prev;
-    return lossacc.result(n, w.n_kept);
+};
+
+template <int SPD, int COST, bool RAMP>
+__device__ __forceinline__ float forward_checkpointed(const WindowDev& w, const ModelDev& m, const float* ys,
+                                                      const float* invys, const float* th, int B, const CoefF32&,
+                                                      float* ck, size_t cs, float& e_last, int& imax) {
+    CkptObs<COST> o;
+    o.c.init();
+    o.invys = invys;
+    o.ck = ck;
+    o.cs = cs;
+    o.emax = 0.f;
+    o.e_last = 0.f;
+    o.imax = 0;
+    // the evaluation's arithmetic, including its choice of the compensated growth rate
+    const int L = w.n_obs - 1;
+    if (L * (SPD > 0 ? SPD : m.spd) > kExactGrowthSteps)
+        trajectory_f32<float, SPD, RAMP, false, false, true>(w, m, ys, nullptr, ThetaF1{th, B}, L, o);
+    else
+        trajectory_f32<float, SPD, RAMP, false>(w, m, ys, nullptr, ThetaF1{th, B}, L, o);
+    e_last = o.e_last;
+    imax = o.imax;
+    float fa, fb;
+    o.c.result(w.n_obs, w.n_kept, fa, fb);
+    return fa;
 }
 
 // Re-integrates one day from its checkpoint (ck as above), staging each step's S, I and cb at

@@ -149,7 +149,7 @@ cudaError_t autotune(sird_batch* b, long long work) {
     const char* vv = std::getenv("SIRD_TUNE_VERBOSE");  // candidate timings to stderr when set
     const bool verbose = vv && *vv && *vv != '0';
     for (int flat = 0; flat < 2 && e == cudaSuccess; ++flat) {
-        for (int block : {128, 256, 512, 640, 768, 1024}) {
+        for (int block : {128, 256, 384, 512, 640, 768, 1024}) {
             const int maxper = flat ? flat_blocks_per_sm(b->mdl, block) : batch_blocks_per_sm(b->mdl, block, b->n_max);
             for (int ci = 0; ci < 3; ++ci) {
                 // each distinct (block, blocks per SM) that fits, once: 1, 2 and the maximum
@@ -380,6 +380,8 @@ sird_status batch_create(int W, const sird_problem* problems, const sird_pso_con
         b->flat = c0.launch_mode == SIRD_LAUNCH_FLAT ? 1 : 0;
         if (b->flat && flat_blocks_per_sm(b->mdl, b->block) <= 0)
             return berr(SIRD_ERR_ARG, "block_size does not fit the flat form");
+        if (!b->flat && batch_blocks_per_sm(b->mdl, b->block, b->n_max) <= 0)
+            return berr(SIRD_ERR_ARG, "block_size does not fit the batched kernel of this form (its launch bound)");
     } else {
         e = autotune(b, work);
         if (e != cudaSuccess) return bail(e, "autotuning");

@@ -25,8 +25,13 @@ __host__ __device__ __forceinline__ int pad4(int n) { return (n + 3) & ~3; }
 // A last wave of at most this many particles runs one particle per thread.
 constexpr int kSingleWaveMax = 384;
 
+// Threads per block the batched kernels are compiled for: 768 (80 registers) for PWC beta and
+// F_D, 384 (up to 168) for the ramp and for F_IRD, whose per-step coefficients and three misfits
+// need more registers than 80.
+__host__ __device__ constexpr int batch_launch_bound(int variant) { return variant_form(variant) == 0 ? 768 : 384; }
+
 template <int SPD, int COST>
-__global__ void __launch_bounds__(768) pso_batch_f32(const BatchWindow* __restrict__ wins, const int* __restrict__ order,
+__global__ void __launch_bounds__(batch_launch_bound(COST)) pso_batch_f32(const BatchWindow* __restrict__ wins, const int* __restrict__ order,
                                                      int W, ModelDev m, PsoCoeffs<float> c, const float* __restrict__ yf_all,
                                                      const float* __restrict__ invy_all, float* __restrict__ swarm,
                                                      unsigned* __restrict__ queue, BatchOut* __restrict__ out, int iters,
@@ -37,8 +42,8 @@ __global__ void __launch_bounds__(768) pso_batch_f32(const BatchWindow* __restri
     const int B = blockDim.x, B2 = 2 * B, tid = threadIdx.x, P = m.P;
     float* ys = smem;
     const int obs_region = pad4(n_max) * (m.ird ? 3 : 1);  // the stacked series of the longest window
-    float* invys = (COST == COST_MAPE) ? ys + obs_region : ys;
-    float* th_s = smem + obs_region * (COST == COST_MAPE ? 2 : 1);  // [P][2B]
+    float* invys = (variant_cost(COST) == COST_MAPE) ? ys + obs_region : ys;
+    float* th_s = smem + obs_region * (variant_cost(COST) == COST_MAPE ? 2 : 1);  // [P][2B]
     float* g_s = th_s + P * B2;
     float* lb_s = g_s + kMaxParams;
     float* ub_s = lb_s + kMaxParams;
@@ -58,7 +63,7 @@ __global__ void __launch_bounds__(768) pso_batch_f32(const BatchWindow* __restri
         const WindowDev& w = bw.w;
         for (int i = tid, span = obs_span(w, m); i < span; i += B) {
             ys[i] = yf_all[bw.obs_off + i];
-            if (COST == COST_MAPE) invys[i] = invy_all[bw.obs_off + i];
+            if (variant_cost(COST) == COST_MAPE) invys[i] = invy_all[bw.obs_off + i];
         }
         float* X = swarm + bw.sw_off;
         float* V = X + (size_t)P * bw.ld;
@@ -202,7 +207,7 @@ __device__ __forceinline__ bool flat_grid_sync(const FlatScratch& fs, unsigned s
 }
 
 template <int SPD, int COST>
-__global__ void __launch_bounds__(768) pso_flat_f32(const BatchWindow* __restrict__ wins,
+__global__ void __launch_bounds__(batch_launch_bound(COST)) pso_flat_f32(const BatchWindow* __restrict__ wins,
                                                     const int* __restrict__ n_items_w,
                                                     const int4* __restrict__ items, int n_items, ModelDev m,
                                                     PsoCoeffs<float> c, const float* __restrict__ yf_all,
@@ -344,32 +349,24 @@ size_t batch_smem_bytes(const ModelDev& m, int block, int n_max) {
            sizeof(float);
 }
 
-#define SIRD_DISPATCH_COST(COSTV, ...)                          \
-    switch (COSTV) {                                            \
-        case COST_MSE: { constexpr int C_ = COST_MSE; __VA_ARGS__; } break;   \
-        case COST_MXSE: { constexpr int C_ = COST_MXSE; __VA_ARGS__; } break; \
-        case COST_MAE: { constexpr int C_ = COST_MAE; __VA_ARGS__; } break;   \
-        default: { constexpr int C_ = COST_MAPE; __VA_ARGS__; } break;        \
-    }
-
-#define SIRD_DISPATCH_SPD(SPDV, ...)                            \
-    switch (SPDV) {                                             \
-        case 10: { constexpr int S_ = 10; __VA_ARGS__; } break; \
-        case 20: { constexpr int S_ = 20; __VA_ARGS__; } break; \
-        default: { constexpr int S_ = 0; __VA_ARGS__; } break;  \
-    }
+// Blocks of `block` threads a kernel can keep per SM; 0 when the block exceeds the kernel's
+// compiled limit (its launch bound) or anything else fails.
+template <class K>
+int blocks_per_sm_of(K kern, int block, size_t sm) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess || block > fa.maxThreadsPerBlock) return 0;
+    if (sm > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        return 0;
+    int per = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, block, sm) == cudaSuccess ? per : 0;
+}
 
 int batch_blocks_per_sm(const ModelDev& m, int block, int n_max) {
     const size_t sm = batch_smem_bytes(m, block, n_max);
     int per = 0;
-    cudaError_t e = cudaSuccess;
-    SIRD_DISPATCH_SPD(m.spd, SIRD_DISPATCH_COST(m.cost, {
-        auto kern = pso_batch_f32<S_, C_>;
-        if (sm > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, block, sm);
-    }));
+    SIRD_DISPATCH_F32(m, { per = blocks_per_sm_of(pso_batch_f32<S_, C_>, block, sm); });
     (void)cudaGetLastError();
-    return e == cudaSuccess ? per : 0;
+    return per;
 }
 
 cudaError_t launch_batch(const BatchWindow* wins, const int* order, int W, const ModelDev& m, const PsoCoeffs<float>& c,
@@ -380,12 +377,12 @@ cudaError_t launch_batch(const BatchWindow* wins, const int* order, int W, const
     (void)cudaGetLastError();
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    SIRD_DISPATCH_SPD(m.spd, SIRD_DISPATCH_COST(m.cost, {
+    SIRD_DISPATCH_F32(m, {
         auto kern = pso_batch_f32<S_, C_>;
         if (sm > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e == cudaSuccess)
             kern<<<grid, block, sm, s>>>(wins, order, W, m, c, yf_all, invy_all, swarm, queue, out, iters, n_max);
-    }));
+    });
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess && reeval) e = launch_batch_reeval(wins, W, m, c.logmask, yd_all, out, s);
     return e;
@@ -405,14 +402,9 @@ size_t flat_smem_bytes(const ModelDev& m, int block) {
 int flat_blocks_per_sm(const ModelDev& m, int block) {
     const size_t sm = flat_smem_bytes(m, block);
     int per = 0;
-    cudaError_t e = cudaSuccess;
-    SIRD_DISPATCH_SPD(m.spd, SIRD_DISPATCH_COST(m.cost, {
-        auto kern = pso_flat_f32<S_, C_>;
-        if (sm > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, block, sm);
-    }));
+    SIRD_DISPATCH_F32(m, { per = blocks_per_sm_of(pso_flat_f32<S_, C_>, block, sm); });
     (void)cudaGetLastError();
-    return e == cudaSuccess ? per : 0;
+    return per;
 }
 
 cudaError_t launch_flat(const BatchWindow* wins, const int* n_items_w, const int4* items, int n_items, int W,
@@ -427,7 +419,7 @@ cudaError_t launch_flat(const BatchWindow* wins, const int* n_items_w, const int
     // bar_count, bar_gen, err, abort are four consecutive words
     if (e == cudaSuccess) e = cudaMemsetAsync(fs.bar_count, 0, 4 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    SIRD_DISPATCH_SPD(m.spd, SIRD_DISPATCH_COST(m.cost, {
+    SIRD_DISPATCH_F32(m, {
         auto kern = pso_flat_f32<S_, C_>;
         if (sm > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e == cudaSuccess) {
@@ -444,7 +436,7 @@ cudaError_t launch_flat(const BatchWindow* wins, const int* n_items_w, const int
             e = cudaLaunchKernelEx(&cfg, kern, wins, n_items_w, items, n_items, m, c, yf_all, invy_all, swarm, fs,
                                    out, iters, bounded_wait_limit(kFlatSpinLimit));
         }
-    }));
+    });
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 

@@ -1,8 +1,9 @@
 // forecast.cu -- deaths forecast: the fitted window extended past its last day (Sec. 4.2).
 //
 // One thread per parameter vector integrates the window from its start (the same Euler
-// scheme as the fitness) and `horizon` more days with the last transmission rate (the last
-// PWC segment, or beta2 of the ramp), gamma and mu, writing D on the days after the window.
+// scheme as the fitness: FP64 in the paper's operation order, or the FP32 trajectory of
+// traj_f32.cuh) and `horizon` more days with the last transmission rate (the last PWC segment,
+// or beta2 of the ramp), gamma and mu, writing D on the days after the window.
 #include <climits>
 
 #include "kernels.h"
@@ -63,54 +64,32 @@ __global__ void forecast_f64_kernel(WindowDev w, ModelDev m, const double* __res
     }
 }
 
+// D on the days after the window: the trajectory run with its misfit tracking -D (DTRACK), so
+// that D keeps its own relative accuracy whatever the fit.
+struct ForecastObs {
+    int L, horizon;
+    float* out;
+    __device__ __forceinline__ void day_start(int, float, float, float, float, float) {}
+    __device__ __forceinline__ void day_end(int day, float e, float, float, float) {
+        if (day > L) out[day - L - 1] = -e;
+    }
+};
+
 __global__ void forecast_f32_kernel(WindowDev w, ModelDev m, const float* __restrict__ theta, int ld, int k,
-                                    int horizon, float* __restrict__ out) {
+                                    int horizon, const float* __restrict__ yf, float* __restrict__ out) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= k) return;
-    const float* th = theta + j;
-    const int stride = ld;
-    const int spd = m.spd, L = w.n_obs - 1, steps_w = L * spd;
-    const int gi = (m.beta_form == BETA_RAMP) ? 4 : m.K;
-    const float gam = th[gi * stride], mu = th[(gi + 1) * stride];
-    float I = m.fit_I0 ? th[(gi + 2) * stride] : w.I0f;
-    float Il = 0.f;
-    const float gm = __fadd_rn(gam, mu);
-    const float a = __fmaf_rn(gm, w.dt_h, __fmul_rn(gm, w.dt_l));
-    const float dm = __fmaf_rn(mu, w.dt_h, __fmul_rn(mu, w.dt_l));
-    float rb1 = 0, rb2 = 0, rt1 = 0, rt2 = 0, slope = 0;
-    if (m.beta_form == BETA_RAMP) {
-        rb1 = th[0];
-        rb2 = th[stride];
-        rt1 = fminf(th[2 * stride], th[3 * stride]);
-        rt2 = fmaxf(th[2 * stride], th[3 * stride]);
-        slope = (rt2 > rt1) ? __fdiv_rn(__fsub_rn(rb2, rb1), __fsub_rn(rt2, rt1)) : 0.f;
-    }
-    const float dtf = __fadd_rn(w.dt_h, w.dt_l);
-    DayStateF32 ds;
-    ds.init(w, I, (float)w.D0);
-    long long s = 0;
-    for (int day = 1; day <= L + horizon; ++day) {
-        float cday = 0.f, dday = 0.f;
-        for (int q = 0; q < spd; ++q, ++s) {
-            float beta;
-            if (m.beta_form == BETA_RAMP) {
-                const float t = __fmul_rn((float)s, dtf);
-                beta = (t < rt1) ? rb1 : ((t < rt2) ? __fmaf_rn(slope, __fsub_rn(t, rt1), rb1) : rb2);
-            } else {
-                beta = th[pwc_seg(s, steps_w, m.K) * stride];
-            }
-            const float cb = __fmaf_rn(beta, w.cbn_h, __fmul_rn(beta, w.cbn_l));
-            euler_f32(cb, a, dm, ds.Sday, cday, dday, I, Il);
-        }
-        ds.close_day(w, cday, dday, 0.f, I, Il);
-        if (day > L) out[(size_t)j * horizon + (day - L - 1)] = ds.Dh;
-    }
+    const int L = w.n_obs - 1;
+    ForecastObs o{L, horizon, out + (size_t)j * horizon};
+    const ThetaF1 th{theta + j, ld};
+    if (m.beta_form == BETA_RAMP) trajectory_f32<float, 0, true, false, true, true>(w, m, yf, nullptr, th, L + horizon, o);
+    else trajectory_f32<float, 0, false, false, true, true>(w, m, yf, nullptr, th, L + horizon, o);
 }
 
 }  // namespace
 
 cudaError_t launch_forecast(const WindowDev& w, const ModelDev& m, const void* theta, int ld, int k, int horizon,
-                            void* out, int precision, cudaStream_t s) {
+                            const float* yf, void* out, int precision, cudaStream_t s) {
     if (k <= 0 || horizon <= 0) return cudaSuccess;
     (void)cudaGetLastError();
     const int block = 128;
@@ -118,7 +97,7 @@ cudaError_t launch_forecast(const WindowDev& w, const ModelDev& m, const void* t
     if (precision == 64)
         forecast_f64_kernel<<<grid, block, 0, s>>>(w, m, (const double*)theta, ld, k, horizon, (double*)out);
     else
-        forecast_f32_kernel<<<grid, block, 0, s>>>(w, m, (const float*)theta, ld, k, horizon, (float*)out);
+        forecast_f32_kernel<<<grid, block, 0, s>>>(w, m, (const float*)theta, ld, k, horizon, yf, (float*)out);
     return cudaGetLastError();
 }
 

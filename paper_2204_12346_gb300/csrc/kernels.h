@@ -8,6 +8,38 @@
 
 namespace sird {
 
+// Largest block of the per-iteration FP32 kernels (their launch bound: up to 255 registers a
+// thread, enough for every form without spilling); larger requested blocks run as this size.
+constexpr int kF32IterMaxBlock = 256;
+
+// Dispatch of the FP32 kernels over (steps per day, variant): defines S_ (steps per day fixed at
+// compile time, 0 = any) and C_ (cost | form << 2) for the body.  F_D with PWC beta -- the
+// benchmark's form -- is unrolled for 10 and 20 steps per day, the ramp for 10, the rest generic.
+#define SIRD_F32_COSTS(FORMV, SPDC, ...)                                                        \
+    switch (m.cost) {                                                                           \
+        case COST_MSE: { constexpr int S_ = SPDC; constexpr int C_ = COST_MSE | (FORMV << 2); __VA_ARGS__; } break;   \
+        case COST_MXSE: { constexpr int S_ = SPDC; constexpr int C_ = COST_MXSE | (FORMV << 2); __VA_ARGS__; } break; \
+        case COST_MAE: { constexpr int S_ = SPDC; constexpr int C_ = COST_MAE | (FORMV << 2); __VA_ARGS__; } break;   \
+        default: { constexpr int S_ = SPDC; constexpr int C_ = COST_MAPE | (FORMV << 2); __VA_ARGS__; } break;        \
+    }
+#define SIRD_DISPATCH_F32(m, ...)                                                        \
+    switch (form_of(m)) {                                                               \
+        case FORM_PWC_D:                                                                \
+            if (m.spd == 10) { SIRD_F32_COSTS(FORM_PWC_D, 10, __VA_ARGS__) }            \
+            else if (m.spd == 20) { SIRD_F32_COSTS(FORM_PWC_D, 20, __VA_ARGS__) }       \
+            else { SIRD_F32_COSTS(FORM_PWC_D, 0, __VA_ARGS__) }                         \
+            break;                                                                      \
+        case FORM_PWC_IRD: { SIRD_F32_COSTS(FORM_PWC_IRD, 0, __VA_ARGS__) } break;      \
+        case FORM_RAMP_D:                                                               \
+            if (m.spd == 10) { SIRD_F32_COSTS(FORM_RAMP_D, 10, __VA_ARGS__) }           \
+            else { SIRD_F32_COSTS(FORM_RAMP_D, 0, __VA_ARGS__) }                        \
+            break;                                                                      \
+        default:                                                                        \
+            if (m.spd == 10) { SIRD_F32_COSTS(FORM_RAMP_IRD, 10, __VA_ARGS__) }         \
+            else { SIRD_F32_COSTS(FORM_RAMP_IRD, 0, __VA_ARGS__) }                      \
+            break;                                                                      \
+    }
+
 // Swarm in structure-of-arrays layout: entry d of particle p at [d*ld + p].
 template <typename T>
 struct SwarmDev {
@@ -99,7 +131,7 @@ cudaError_t launch_pso_f32_persistent(const WindowDev& w, const ModelDev& m, con
 // Deaths forecast of k parameter vectors (theta [P][ld], float or double by precision) into
 // out[k][horizon] (same type): D on days n_obs .. n_obs+horizon-1 of the window's numbering.
 cudaError_t launch_forecast(const WindowDev& w, const ModelDev& m, const void* theta, int ld, int k, int horizon,
-                            void* out, int precision, cudaStream_t s);
+                            const float* yf, void* out, int precision, cudaStream_t s);
 
 // The k personal bests named by keys (FP32 swarm), decoded to theta in FP64: theta_out[k][P],
 // loss_out[k] = their stored FP32 values.

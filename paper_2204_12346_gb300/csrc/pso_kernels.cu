@@ -22,18 +22,18 @@ __host__ __device__ __forceinline__ int pad4(int n) { return (n + 3) & ~3; }
 template <int COST>
 __device__ __forceinline__ float* stage_obs_f32(float* smem, const WindowDev& w, const ModelDev& m, const ObsDev& o) {
     float* ys = smem;
-    float* invys = (COST == COST_MAPE) ? ys + obs_span_pad(w, m) : ys;
+    float* invys = (variant_cost(COST) == COST_MAPE) ? ys + obs_span_pad(w, m) : ys;
     const int span = obs_span(w, m);
     for (int i = threadIdx.x; i < span; i += blockDim.x) {
         ys[i] = o.yf[i];
-        if (COST == COST_MAPE) invys[i] = o.invyf[i];
+        if (variant_cost(COST) == COST_MAPE) invys[i] = o.invyf[i];
     }
     return invys;
 }
 
 template <int COST>
 __device__ __forceinline__ float* after_obs_f32(float* smem, const WindowDev& w, const ModelDev& m) {
-    return smem + obs_span_pad(w, m) * (COST == COST_MAPE ? 2 : 1);
+    return smem + obs_span_pad(w, m) * (variant_cost(COST) == COST_MAPE ? 2 : 1);
 }
 
 // ------------------------------------------------------------------ FP32 eval
@@ -41,7 +41,7 @@ __device__ __forceinline__ float* after_obs_f32(float* smem, const WindowDev& w,
 // A thread evaluates two parameter vectors, p0 = block * 2B + thread and p1 = p0 + B, together
 // in packed f32x2 form (each loss equal to the one-at-a-time evaluation bit for bit).
 template <int SPD, int COST>
-__global__ void __launch_bounds__(1024) eval_f32_kernel(WindowDev w, ModelDev m, ObsDev o,
+__global__ void __launch_bounds__(kF32IterMaxBlock, 1) eval_f32_kernel(WindowDev w, ModelDev m, ObsDev o,
                                                          const float* __restrict__ theta, int ld, int M,
                                                          float* __restrict__ loss) {
     extern __shared__ float smem[];
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(1024) eval_f32_kernel(WindowDev w, ModelDev m,
 // ------------------------------------------------------------------ FP32 PSO iteration
 
 template <int SPD, int COST>
-__global__ void __launch_bounds__(1024) pso_f32_kernel(WindowDev w, ModelDev m, ObsDev o, PsoCoeffs<float> c,
+__global__ void __launch_bounds__(kF32IterMaxBlock, 1) pso_f32_kernel(WindowDev w, ModelDev m, ObsDev o, PsoCoeffs<float> c,
                                                         SwarmDev<float> sw, ReduceScratch r, int iter) {
     extern __shared__ float smem[];
     __shared__ unsigned long long wk[32];
@@ -442,23 +442,17 @@ static size_t smem_bytes_f64(const WindowDev& w, const ModelDev& m, int block, b
         default: { constexpr int C_ = COST_MAPE; __VA_ARGS__; } break;        \
     }
 
-#define SIRD_DISPATCH_SPD(SPDV, ...)                            \
-    switch (SPDV) {                                             \
-        case 10: { constexpr int S_ = 10; __VA_ARGS__; } break; \
-        case 20: { constexpr int S_ = 20; __VA_ARGS__; } break; \
-        default: { constexpr int S_ = 0; __VA_ARGS__; } break;  \
-    }
-
 cudaError_t launch_eval_f32(const WindowDev& w, const ModelDev& m, const ObsDev& o, const float* theta, int ld,
                             int M, float* loss, int block, unsigned*, cudaStream_t s) {
     if (M <= 0) return cudaSuccess;
+    if (block > kF32IterMaxBlock) block = kF32IterMaxBlock;  // results do not depend on the block shape
     const size_t sm = smem_bytes_f32(w, m, block, true);
     cudaError_t e = cudaSuccess;
-    SIRD_DISPATCH_SPD(m.spd, SIRD_DISPATCH_COST(m.cost, {
+    SIRD_DISPATCH_F32(m, {
         auto kern = eval_f32_kernel<S_, C_>;
         e = set_smem(kern, sm);
         if (e == cudaSuccess) kern<<<grid_for_pairs(M, block), block, sm, s>>>(w, m, o, theta, ld, M, loss);
-    }));
+    });
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -477,13 +471,14 @@ cudaError_t launch_eval_f64(const WindowDev& w, const ModelDev& m, const ObsDev&
 
 cudaError_t launch_pso_f32(const WindowDev& w, const ModelDev& m, const ObsDev& o, const PsoCoeffs<float>& c,
                            const SwarmDev<float>& sw, const ReduceScratch& r, int iter, int block, cudaStream_t s) {
+    if (block > kF32IterMaxBlock) block = kF32IterMaxBlock;  // results do not depend on the block shape
     const size_t sm = smem_bytes_f32(w, m, block, true);
     cudaError_t e = cudaSuccess;
-    SIRD_DISPATCH_SPD(m.spd, SIRD_DISPATCH_COST(m.cost, {
+    SIRD_DISPATCH_F32(m, {
         auto kern = pso_f32_kernel<S_, C_>;
         e = set_smem(kern, sm);
         if (e == cudaSuccess) kern<<<grid_for_pairs(sw.M, block), block, sm, s>>>(w, m, o, c, sw, r, iter);
-    }));
+    });
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 

@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(1024) pso_f32_persistent(WindowDev w, ModelDev
     const int B = blockDim.x, tid = threadIdx.x, P = m.P, G = gridDim.x;
     const int npairs = (P + 1) >> 1;
     float* ys = smem;
-    float* invys = (COST == COST_MAPE) ? ys + obs_span_pad(w, m) : ys;
-    float* th_s = smem + obs_span_pad(w, m) * (COST == COST_MAPE ? 2 : 1);
+    float* invys = (variant_cost(COST) == COST_MAPE) ? ys + obs_span_pad(w, m) : ys;
+    float* th_s = smem + obs_span_pad(w, m) * (variant_cost(COST) == COST_MAPE ? 2 : 1);
     float* xs = th_s + P * B;
     float* vs = xs + P * B;
     float* pbs = vs + P * B;
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(1024) pso_f32_persistent(WindowDev w, ModelDev
 
     for (int i = tid, span = obs_span(w, m); i < span; i += B) {
         ys[i] = o.yf[i];
-        if (COST == COST_MAPE) invys[i] = o.invyf[i];
+        if (variant_cost(COST) == COST_MAPE) invys[i] = o.invyf[i];
     }
     const int base = blockIdx.x * B;
     for (int i = tid; i < P * B; i += B) {
@@ -337,21 +337,6 @@ int persistent_capacity(const WindowDev& w, const ModelDev& m, int block, int gr
     return per * nsm;
 }
 
-#define SIRD_DISPATCH_COST(COSTV, ...)                          \
-    switch (COSTV) {                                            \
-        case COST_MSE: { constexpr int C_ = COST_MSE; __VA_ARGS__; } break;   \
-        case COST_MXSE: { constexpr int C_ = COST_MXSE; __VA_ARGS__; } break; \
-        case COST_MAE: { constexpr int C_ = COST_MAE; __VA_ARGS__; } break;   \
-        default: { constexpr int C_ = COST_MAPE; __VA_ARGS__; } break;        \
-    }
-
-#define SIRD_DISPATCH_SPD(SPDV, ...)                            \
-    switch (SPDV) {                                             \
-        case 10: { constexpr int S_ = 10; __VA_ARGS__; } break; \
-        case 20: { constexpr int S_ = 20; __VA_ARGS__; } break; \
-        default: { constexpr int S_ = 0; __VA_ARGS__; } break;  \
-    }
-
 cudaError_t launch_pso_f32_persistent(const WindowDev& w, const ModelDev& m, const ObsDev& o,
                                       const PsoCoeffs<float>& c, const SwarmDev<float>& sw, const ReduceScratch& r,
                                       ExchangeSlot* slots, int iter0, int n_iters, int block, cudaStream_t s) {
@@ -362,7 +347,7 @@ cudaError_t launch_pso_f32_persistent(const WindowDev& w, const ModelDev& m, con
     cudaError_t e = cudaMemsetAsync(slots, 0, 2 * (size_t)grid * sizeof(ExchangeSlot), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(r.abort, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    SIRD_DISPATCH_SPD(m.spd, SIRD_DISPATCH_COST(m.cost, {
+    SIRD_DISPATCH_F32(m, {
         auto kern = pso_f32_persistent<S_, C_, false>;
         if (sm > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e == cudaSuccess) {
@@ -379,7 +364,7 @@ cudaError_t launch_pso_f32_persistent(const WindowDev& w, const ModelDev& m, con
             e = cudaLaunchKernelEx(&cfg, kern, w, m, o, c, sw, r, slots, iter0, n_iters,
                                    bounded_wait_limit(kSpinLimit));
         }
-    }));
+    });
     return e;
 }
 
@@ -391,7 +376,7 @@ cudaError_t launch_pso_f32_cluster(const WindowDev& w, const ModelDev& m, const 
     const size_t sm = smem_bytes_persistent(w, m, block, (int)grid);
     (void)cudaGetLastError();
     cudaError_t e = cudaSuccess;
-    SIRD_DISPATCH_SPD(m.spd, SIRD_DISPATCH_COST(m.cost, {
+    SIRD_DISPATCH_F32(m, {
         auto kern = pso_f32_persistent<S_, C_, true>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e == cudaSuccess && sm > 48 * 1024)
@@ -411,7 +396,7 @@ cudaError_t launch_pso_f32_cluster(const WindowDev& w, const ModelDev& m, const 
             cfg.numAttrs = 1;
             e = cudaLaunchKernelEx(&cfg, kern, w, m, o, c, sw, r, (ExchangeSlot*)nullptr, iter0, n_iters, 0u);
         }
-    }));
+    });
     return e;
 }
 

@@ -213,6 +213,9 @@ void sird_fill_window(const sird_problem* pb, WindowDev& w, ModelDev& m) {
     s = split(pb->R0);
     w.R0h = s.h;
     w.R0l = s.l;
+    s = split(pb->N - pb->R0 - pb->y_D[0]);  // S0 + I0, whatever I0
+    w.Q0h = s.h;
+    w.Q0l = s.l;
     // F_IRD: ranges of the reported series for the min-max normalisation (a flat series: 1)
     auto range = [n](const double* y) {
         double lo = y[0], hi = y[0];
@@ -229,6 +232,7 @@ void sird_fill_window(const sird_problem* pb, WindowDev& w, ModelDev& m) {
     w.inv_rng_D = (float)(1.0 / w.rng_D);
     w.inv_rng_I = (float)(1.0 / w.rng_I);
     w.inv_rng_R = (float)(1.0 / w.rng_R);
+    w.eR0 = ird ? (float)(pb->y_R[0] - pb->R0) : 0.f;
     w.n_kept_I = w.n_kept_R = 0;
     if (ird)
         for (int i = 0; i < n; ++i) {
@@ -795,7 +799,10 @@ static sird_status forecast_impl(const sird_problem* pb, const double* theta, in
     const int P = m.P;
     const size_t tsz = precision == 32 ? 4 : 8;
     const size_t th_bytes = (size_t)P * k * tsz, out_bytes = (size_t)k * horizon * tsz;
-    std::vector<unsigned char> hth(th_bytes), hout(out_bytes);
+    const size_t y_bytes = precision == 32 ? (size_t)pb->n_obs * sizeof(float) : 0;
+    std::vector<unsigned char> hth(th_bytes + y_bytes), hout(out_bytes);
+    for (size_t i = 0; i < y_bytes / sizeof(float); ++i)  // the FP32 trajectory follows y_D's float values
+        ((float*)(hth.data() + th_bytes))[i] = (float)pb->y_D[i];
     for (int j = 0; j < k; ++j)
         for (int d = 0; d < P; ++d) {
             const double v = theta[(size_t)j * P + d];
@@ -804,10 +811,13 @@ static sird_status forecast_impl(const sird_problem* pb, const double* theta, in
         }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     void* dmem = nullptr;
-    cudaError_t e = cudaMalloc(&dmem, th_bytes + out_bytes);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dmem, hth.data(), th_bytes, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_forecast(w, m, dmem, k, k, horizon, (unsigned char*)dmem + th_bytes, precision, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hout.data(), (unsigned char*)dmem + th_bytes, out_bytes,
+    // device: theta | observations (FP32) | forecast
+    cudaError_t e = cudaMalloc(&dmem, th_bytes + y_bytes + out_bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dmem, hth.data(), th_bytes + y_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = launch_forecast(w, m, dmem, k, k, horizon, (const float*)((unsigned char*)dmem + th_bytes),
+                            (unsigned char*)dmem + th_bytes + y_bytes, precision, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hout.data(), (unsigned char*)dmem + th_bytes + y_bytes, out_bytes,
                                               cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(dmem);

@@ -8,7 +8,7 @@ import torch
 import oracle as O
 from paper_2204_12346_gb300 import configs, sird, synth
 from test_gpu_adjoint import check_f32_gradient, f32_loss_grad, gpu_loss_grad
-from util import RHO_F32, box_thetas, f32, fp32_loss_tol, rel_err, window
+from util import assert_fp32_losses, box_thetas, f32, rel_err, window
 
 pytestmark = pytest.mark.gpu
 
@@ -99,11 +99,8 @@ def test_max_observations_eval():
     got64 = gpu_eval(calibrator(y, N, 8, 10, 64), th, 64)
     assert np.array_equal(got64, want), rel_err(got64, want).max()
     got32 = gpu_eval(calibrator(y, N, 8, 10, 32), th, 32)
-    # the FP32 trajectory's relative error grows with the steps and day folds integrated
-    steps, days = 10 * (N_OBS_MAX - 1), N_OBS_MAX - 1
-    rho = RHO_F32 * (np.sqrt(steps) + days) / (np.sqrt(1800) + 90)
-    for j in range(th.shape[0]):
-        assert rel_err(got32[j], want[j]) <= fp32_loss_tol(O, pb, th[j], rho=rho), j
+    # 40950 steps: the long-window mode of the FP32 trajectory keeps the contract's 1e-5
+    print("largest relative error", assert_fp32_losses(got32, want, "4096 observations"))
 
 
 def test_max_observations_batch_equals_single_windows():
@@ -150,8 +147,7 @@ def test_degenerate_parameters(cost):
     got64 = gpu_eval(calibrator(y, N, K, 10, 64, sird.COSTS[cost]), th, 64)
     assert np.array_equal(got64, want), rel_err(got64, want).max()
     got32 = gpu_eval(calibrator(y, N, K, 10, 32, sird.COSTS[cost]), th, 32)
-    for j in range(th.shape[0]):
-        assert rel_err(got32[j], want[j]) <= fp32_loss_tol(O, pb, th[j], cost), (j, got32[j], want[j])
+    assert_fp32_losses(got32, want, cost)
     # no removal (gamma = mu = 0) or no infected (I0 = 0): D stays at D0 = y_0, so the cost is
     # that of the constant y_0
     e = np.asarray(y, dtype=np.float64) - y[0]
