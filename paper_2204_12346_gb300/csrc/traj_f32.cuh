@@ -280,7 +280,7 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
         T Psh, Psl;
         tprod(fspd, Is, Psh, Psl);
         Psl = tadd(Psl, tsub(W, A));
-        tnorm(Psh, Psl);
+        if (EXACTG) tnorm(Psh, Psl);  // short windows: Q's low part may grow, it is carried as is
         Il = tfma(Gh_, W, tfma(tfma(ncbl_, Is, Gl_), isum, Il));
         tnorm(Ih, Il);
         {   // Q -= a (day's sum)
