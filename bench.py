@@ -321,6 +321,58 @@ def s_to_calibrate() -> dict:
     return out
 
 
+def s_to_calibrate_batch(batch, c, wins, lb, ub, model, stride=32) -> dict:
+    """The 512-window batch: on every stride-th window (a subsample spanning the window lengths)
+    the plain FP64 swarm -- the window's own particles and Philox stream, 10x the batch's PSO
+    iterations -- sets L_ref; then the wall seconds of the batched FP32 swarm followed by the
+    batched L-BFGS polish of every window's 32 best personal bests (FP32 trials and adjoint,
+    FP64 re-scoring) until every subsampled window's FP64 loss is <= (1 + 1e-6) L_ref."""
+    import torch
+
+    from paper_2204_12346_gb300 import sird
+
+    sub = list(range(0, len(wins), stride))
+    it64 = 10 * c["iters"]
+    t64, ref = 0.0, {}
+    for i in sub:
+        w = wins[i]
+        cal = sird.Calibrator(w["yD"], w["N"], R0=w["R0"], particles=w["particles"], iters=it64, precision=64,
+                              seed=w["seed"], stream_id=w["stream_id"], spd=c["spd"], lb=lb, ub=ub, K=model["K"],
+                              beta_form=model["beta_form"], log_scale=model["log_scale"], fit_I0=model["fit_I0"],
+                              cost=model["cost"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ref[i] = cal.calibrate()["loss"]
+        torch.cuda.synchronize()
+        t64 += time.perf_counter() - t0
+    pd = {i: wins[i]["particles"] * wins[i]["L"] for i in range(len(wins))}
+    scale = sum(pd.values()) / sum(pd[i] for i in sub)  # FP64 seconds scale with particle-days
+    out = {"windows": f"every {stride}th of {len(wins)} ({len(sub)} windows, {min(wins[i]['L'] for i in sub)}.."
+                      f"{max(wins[i]['L'] for i in sub)} days)",
+           "L_ref": f"plain FP64 swarm, {it64} iterations, the window's own particles and stream",
+           "target": "(1 + 1e-6) L_ref on every subsampled window",
+           "fp64_pso_s_subsample": t64, "fp64_pso_s_all_windows_est": t64 * scale, "trials": []}
+    for n in (0, 10, 20, 40, 80, 160):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = batch.calibrate()
+        t_swarm = time.perf_counter() - t0
+        pol = batch.polish(k=32, iters=n, first_step=1e-2) if n else res
+        dt = time.perf_counter() - t0
+        got = {i: min(res[i]["loss"], pol[i]["loss"]) for i in sub}
+        ok = [got[i] <= ref[i] * (1 + 1e-6) for i in sub]
+        frac = sum(ok) / len(sub)
+        out["trials"].append({"polish_iters": n, "s": dt, "swarm_s": t_swarm, "fraction_reached": frac,
+                              "median_loss_over_L_ref": float(np.median([got[i] / ref[i] for i in sub]))})
+        if frac == 1.0:
+            out.update({"fp32_batch_plus_polish_s": dt, "polish_iters": n, "reached": True,
+                        "speedup_vs_fp64_all_windows_est": t64 * scale / dt})
+            return out
+    last = out["trials"][-1]
+    out.update({"reached": False, "fraction_reached": last["fraction_reached"], "fp32_batch_plus_polish_s": last["s"]})
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_batched(args, rank, world):
@@ -400,6 +452,8 @@ def run_batched(args, rank, world):
                     "TITAN V with the cost on the CPU; ours is the batch's wall time spread over its window-iterations"}
     if not args.no_s2c and name == "batch512":
         out["s_to_calibrate"] = s_to_calibrate()
+        with torch.cuda.stream(stream):
+            out["s_to_calibrate_batch"] = s_to_calibrate_batch(batch, c, wins, lb, ub, model)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(name, budget_s=args.cpu_budget)
         out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(name)

@@ -383,6 +383,20 @@ sird_status sird_batch_calibrate(sird_batch_t b, sird_result* results);
  * n_total or a non-finite value.
  */
 sird_status sird_batch_set_observations(sird_batch_t b, const double* y_all, long long n_total, size_t* h2d_bytes);
+/*
+ * Gradient polish of every window of a calibrated batch (after sird_batch_calibrate): per window,
+ * the k best personal bests of its swarm (k in 1..min(1024, smallest swarm)) get iters L-BFGS
+ * iterations exactly as sird_pso_polish with precision 32 gives them (FP32 trials and adjoint,
+ * FP64 algebra, FP64 re-scoring of the best point), all windows together: each step is one
+ * launch over every window, and each window's result equals a one-window sird_pso_polish of the
+ * same swarm bit for bit.  results[W] (host): theta, FP64 loss, r2_D, index = the particle whose
+ * personal best the reported point started from, loss_search = that personal best's FP32 loss.
+ * The swarms are not changed.  F_D objective, steps_per_day 10, 20 or at most 64, W <= 65535
+ * (else SIRD_ERR_UNSUPPORTED); SIRD_ERR_STATE before the first calibration; SIRD_ERR_ARG on bad
+ * k, iters < 0 or first_step <= 0.  The scratch is kept with the batch and grows on demand.
+ * Blocks.
+ */
+sird_status sird_batch_polish(sird_batch_t b, int k, int iters, double first_step, sird_result* results);
 /* Threads per block and blocks per SM the batch runs with (autotuned or given); 0 if b is NULL. */
 int sird_batch_block_size(sird_batch_t b);
 int sird_batch_blocks_per_sm(sird_batch_t b);

@@ -338,11 +338,10 @@ __device__ __forceinline__ void rev_write(const RevF32& r, const double* gacc, c
 // One thread per parameter vector: forward pass, then per day (last to first) re-integration
 // into shared memory and the reverse sweep.  Any form and steps per day.
 template <int SPD, int COST, bool RAMP>
-__global__ void __launch_bounds__(64) loss_grad_f32_kernel(WindowDev w, ModelDev m, ObsDev o,
-                                                            const float* __restrict__ theta, int ld, int M,
-                                                            float* __restrict__ loss, float* __restrict__ grad,
-                                                            int ldg, float* __restrict__ grad_u0,
-                                                            float* __restrict__ ckpt) {
+__device__ __forceinline__ void loss_grad_f32_body(const WindowDev& w, const ModelDev& m, const ObsDev& o,
+                                                   const float* __restrict__ theta, int ld, int M,
+                                                   float* __restrict__ loss, float* __restrict__ grad, int ldg,
+                                                   float* __restrict__ grad_u0, float* __restrict__ ckpt, int blk) {
     extern __shared__ float smem[];
     const int B = blockDim.x, tid = threadIdx.x, P = m.P;
     const int n = w.n_obs;
@@ -357,7 +356,7 @@ __global__ void __launch_bounds__(64) loss_grad_f32_kernel(WindowDev w, ModelDev
         ys[i] = o.yf[i];
         invys[i] = o.invyf[i];
     }
-    const int p = blockIdx.x * B + tid;
+    const int p = blk * B + tid;
     const bool active = p < M;
     if (active)
         for (int d = 0; d < P; ++d) th_all[d * B + tid] = theta[(size_t)d * ld + p];
@@ -381,6 +380,30 @@ __global__ void __launch_bounds__(64) loss_grad_f32_kernel(WindowDev w, ModelDev
     rev_write<RAMP>(r, gacc, w, m, p, Lval, loss, grad, ldg, grad_u0);
 }
 
+template <int SPD, int COST, bool RAMP>
+__global__ void __launch_bounds__(64) loss_grad_f32_kernel(WindowDev w, ModelDev m, ObsDev o,
+                                                            const float* __restrict__ theta, int ld, int M,
+                                                            float* __restrict__ loss, float* __restrict__ grad,
+                                                            int ldg, float* __restrict__ grad_u0,
+                                                            float* __restrict__ ckpt) {
+    loss_grad_f32_body<SPD, COST, RAMP>(w, m, o, theta, ld, M, loss, grad, ldg, grad_u0, ckpt, blockIdx.x);
+}
+
+// Table form: block row blockIdx.y takes window blockIdx.y (PolishWin) with its own constants.
+template <int SPD, int COST, bool RAMP>
+__global__ void __launch_bounds__(64) loss_grad_f32_tab_kernel(const PolishWin* __restrict__ tab, ModelDev m,
+                                                                const float* __restrict__ theta, long long th_ws,
+                                                                int ld, int M, float* __restrict__ loss,
+                                                                long long loss_ws, float* __restrict__ grad,
+                                                                long long grad_ws, int ldg, float* __restrict__ ckpt,
+                                                                long long ck_ws) {
+    const int i = blockIdx.y;
+    const WindowDev w = tab[i].w;
+    const ObsDev o = tab[i].o;
+    loss_grad_f32_body<SPD, COST, RAMP>(w, m, o, theta + i * th_ws, ld, M, loss + i * loss_ws, grad + i * grad_ws,
+                                        ldg, nullptr, ckpt + i * ck_ws, blockIdx.x);
+}
+
 // Warp-specialised form (PWC, 10 or 20 steps per day): a block of two warps owns 32 parameter
 // vectors.  Warp 0 runs the forward pass and then re-integrates the days, last to first, into a
 // double-buffered stage in shared memory; warp 1 sweeps each staged day backwards while warp 0
@@ -391,11 +414,11 @@ __global__ void __launch_bounds__(64) loss_grad_f32_kernel(WindowDev w, ModelDev
 constexpr int kWsVectors = 32;
 
 template <int SPD, int COST>
-__global__ void __launch_bounds__(64) loss_grad_f32_ws_kernel(WindowDev w, ModelDev m, ObsDev o,
-                                                               const float* __restrict__ theta, int ld, int M,
-                                                               float* __restrict__ loss, float* __restrict__ grad,
-                                                               int ldg, float* __restrict__ grad_u0,
-                                                               float* __restrict__ ckpt, int Mpad) {
+__device__ __forceinline__ void loss_grad_f32_ws_body(const WindowDev& w, const ModelDev& m, const ObsDev& o,
+                                                      const float* __restrict__ theta, int ld, int M,
+                                                      float* __restrict__ loss, float* __restrict__ grad, int ldg,
+                                                      float* __restrict__ grad_u0, float* __restrict__ ckpt, int Mpad,
+                                                      int blk) {
     extern __shared__ float smem[];
     constexpr int V = kWsVectors;
     const int tid = threadIdx.x, lane = tid & 31, P = m.P, n = w.n_obs, L = n - 1, steps = L * SPD;
@@ -409,7 +432,7 @@ __global__ void __launch_bounds__(64) loss_grad_f32_ws_kernel(WindowDev w, Model
         ys[i] = o.yf[i];
         invys[i] = o.invyf[i];
     }
-    const int p = blockIdx.x * V + lane;
+    const int p = blk * V + lane;
     const bool active = p < M;
     if (fwd) {
         const int src = active ? p : M - 1;
@@ -452,6 +475,30 @@ __global__ void __launch_bounds__(64) loss_grad_f32_ws_kernel(WindowDev w, Model
         __syncthreads();
     }
     if (!fwd && active) rev_write<false>(r, gacc, w, m, p, xch[2 * V + lane], loss, grad, ldg, grad_u0);
+}
+
+template <int SPD, int COST>
+__global__ void __launch_bounds__(64) loss_grad_f32_ws_kernel(WindowDev w, ModelDev m, ObsDev o,
+                                                               const float* __restrict__ theta, int ld, int M,
+                                                               float* __restrict__ loss, float* __restrict__ grad,
+                                                               int ldg, float* __restrict__ grad_u0,
+                                                               float* __restrict__ ckpt, int Mpad) {
+    loss_grad_f32_ws_body<SPD, COST>(w, m, o, theta, ld, M, loss, grad, ldg, grad_u0, ckpt, Mpad, blockIdx.x);
+}
+
+template <int SPD, int COST>
+__global__ void __launch_bounds__(64) loss_grad_f32_ws_tab_kernel(const PolishWin* __restrict__ tab, ModelDev m,
+                                                                   const float* __restrict__ theta, long long th_ws,
+                                                                   int ld, int M, float* __restrict__ loss,
+                                                                   long long loss_ws, float* __restrict__ grad,
+                                                                   long long grad_ws, int ldg,
+                                                                   float* __restrict__ ckpt, long long ck_ws,
+                                                                   int Mpad) {
+    const int i = blockIdx.y;
+    const WindowDev w = tab[i].w;
+    const ObsDev o = tab[i].o;
+    loss_grad_f32_ws_body<SPD, COST>(w, m, o, theta + i * th_ws, ld, M, loss + i * loss_ws, grad + i * grad_ws, ldg,
+                                     nullptr, ckpt + i * ck_ws, Mpad, blockIdx.x);
 }
 
 }  // namespace
@@ -507,6 +554,69 @@ cudaError_t launch_loss_grad_f32(const WindowDev& w, const ModelDev& m, const Ob
         if (sm > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
         if (e == cudaSuccess)                                                                                 \
             kern<<<(M + block - 1) / block, block, sm, s>>>(w, m, o, theta, ld, M, loss, grad, ldg, grad_u0, ckpt); \
+    }
+#define SIRD_LG32_COST(SV, RV)                              \
+    switch (m.cost) {                                       \
+        case COST_MSE: SIRD_LG32(SV, COST_MSE, RV) break;   \
+        case COST_MXSE: SIRD_LG32(SV, COST_MXSE, RV) break; \
+        case COST_MAE: SIRD_LG32(SV, COST_MAE, RV) break;   \
+        default: SIRD_LG32(SV, COST_MAPE, RV) break;        \
+    }
+    if (m.beta_form == BETA_RAMP) {
+        SIRD_LG32_COST(0, true)
+    } else {
+        SIRD_LG32_COST(0, false)
+    }
+#undef SIRD_LG32_COST
+#undef SIRD_LG32
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_loss_grad_f32_tab(const PolishWin* tab, int nw, int n_max, const ModelDev& m, const float* theta,
+                                     long long th_ws, int ld, int M, float* loss, long long loss_ws, float* grad,
+                                     long long grad_ws, int ldg, float* ckpt, long long ck_ws, cudaStream_t s) {
+    if (M <= 0 || nw <= 0) return cudaSuccess;
+    if (m.spd < 1 || m.spd > kMaxSpdGeneric || nw > 65535) return cudaErrorInvalidValue;
+    (void)cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    const size_t obs = 2 * (size_t)((n_max + 3) & ~3);
+    if (m.beta_form != BETA_RAMP && (m.spd == 10 || m.spd == 20)) {
+        const int Mpad = (M + kWsVectors - 1) / kWsVectors * kWsVectors;
+        const size_t sm = (obs + (size_t)m.P * kWsVectors + 6 * (size_t)m.spd * kWsVectors + 3 * kWsVectors) * sizeof(float);
+        const dim3 grid((unsigned)(Mpad / kWsVectors), (unsigned)nw);
+#define SIRD_LGWS(SV, CV)                                                                                            \
+    {                                                                                                                \
+        auto kern = loss_grad_f32_ws_tab_kernel<SV, CV>;                                                             \
+        if (sm > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);   \
+        if (e == cudaSuccess)                                                                                        \
+            kern<<<grid, 2 * kWsVectors, sm, s>>>(tab, m, theta, th_ws, ld, M, loss, loss_ws, grad, grad_ws, ldg,     \
+                                                  ckpt, ck_ws, Mpad);                                                \
+    }
+#define SIRD_LGWS_COST(SV)                                \
+    switch (m.cost) {                                     \
+        case COST_MSE: SIRD_LGWS(SV, COST_MSE) break;     \
+        case COST_MXSE: SIRD_LGWS(SV, COST_MXSE) break;   \
+        case COST_MAE: SIRD_LGWS(SV, COST_MAE) break;     \
+        default: SIRD_LGWS(SV, COST_MAPE) break;          \
+    }
+        if (m.spd == 10) {
+            SIRD_LGWS_COST(10)
+        } else {
+            SIRD_LGWS_COST(20)
+        }
+#undef SIRD_LGWS_COST
+#undef SIRD_LGWS
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
+    const int block = 64;
+    const size_t sm = (obs + (size_t)m.P * block + 3 * (size_t)m.spd * block) * sizeof(float);
+    const dim3 grid((unsigned)((M + block - 1) / block), (unsigned)nw);
+#define SIRD_LG32(SV, CV, RV)                                                                                 \
+    {                                                                                                         \
+        auto kern = loss_grad_f32_tab_kernel<SV, CV, RV>;                                                     \
+        if (sm > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        if (e == cudaSuccess)                                                                                 \
+            kern<<<grid, block, sm, s>>>(tab, m, theta, th_ws, ld, M, loss, loss_ws, grad, grad_ws, ldg, ckpt, ck_ws); \
     }
 #define SIRD_LG32_COST(SV, RV)                              \
     switch (m.cost) {                                       \

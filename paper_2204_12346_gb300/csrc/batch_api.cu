@@ -49,6 +49,13 @@ struct sird_batch {
     size_t nobs = 0, wins_bytes = 0, obs_bytes = 0;
     unsigned char* h_stage = nullptr;
     cudaEvent_t ev_upload = nullptr;
+    // polish (sird_batch_polish): the FP64 box, a calibration done, the device scratch (window
+    // table | keys | polish state | checkpoints | results) and the pinned results
+    PsoCoeffs<double> c64{};
+    bool calibrated = false;
+    void* pmem = nullptr;
+    size_t pmem_bytes = 0;
+    ResultDev* h_pres = nullptr;
 };
 
 namespace {
@@ -268,9 +275,17 @@ sird_status batch_create(int W, const sird_problem* problems, const sird_pso_con
         const bool lg = c0.log_scale && c0.log_scale[d];
         if (lg && !(c0.lb[d] > 0)) return berr(SIRD_ERR_ARG, "log_scale needs lb > 0");
         if (lg) b->c.logmask |= 1u << d;
-        b->c.zlb[d] = (float)(lg ? std::log(c0.lb[d]) : c0.lb[d]);
-        b->c.zub[d] = (float)(lg ? std::log(c0.ub[d]) : c0.ub[d]);
+        const double zl = lg ? std::log(c0.lb[d]) : c0.lb[d];
+        const double zu = lg ? std::log(c0.ub[d]) : c0.ub[d];
+        b->c.zlb[d] = (float)zl;
+        b->c.zub[d] = (float)zu;
+        b->c64.zlb[d] = zl;
+        b->c64.zub[d] = zu;
     }
+    b->c64.logmask = b->c.logmask;
+    b->c64.w = c0.w;
+    b->c64.c1 = c0.c1;
+    b->c64.c2 = c0.c2;
     b->c.w = (float)c0.w;
     b->c.c1 = (float)c0.c1;
     b->c.c2 = (float)c0.c2;
@@ -411,6 +426,8 @@ extern "C" void sird_batch_destroy(sird_batch_t b) {
     if (b->h_out) cudaFreeHost(b->h_out);
     if (b->h_stage) cudaFreeHost(b->h_stage);
     if (b->ev_upload) cudaEventDestroy(b->ev_upload);
+    if (b->pmem) cudaFree(b->pmem);
+    if (b->h_pres) cudaFreeHost(b->h_pres);
     delete b;
 }
 
@@ -480,6 +497,98 @@ extern "C" sird_status sird_batch_calibrate(sird_batch_t b, sird_result* results
         r.loss_search = (double)b->h_out[i].loss;
         r.r2_D = b->ss_tot[i] > 0 ? 1.0 - b->h_out[i].sse / b->ss_tot[i] : NAN;
         r.index = b->h_out[i].index;
+        r.iters_done = b->iters;
+    }
+    b->calibrated = true;
+    return SIRD_OK;
+}
+
+extern "C" sird_status sird_batch_polish(sird_batch_t b, int k, int iters, double first_step, sird_result* results) {
+    TraceRange trace("sird_batch_polish");
+    if (!b || !results) return berr(SIRD_ERR_ARG, "batch or results is NULL");
+    if (b->mdl.ird) return berr(SIRD_ERR_UNSUPPORTED, "polish: the adjoint covers F_D only");
+    if (b->mdl.spd != 10 && b->mdl.spd != 20 && b->mdl.spd > 64)
+        return berr(SIRD_ERR_UNSUPPORTED, "polish: FP32 needs steps_per_day <= 64");
+    if (b->W > 65535) return berr(SIRD_ERR_UNSUPPORTED, "polish: at most 65535 windows");
+    if (!b->calibrated) return berr(SIRD_ERR_STATE, "polish before the first sird_batch_calibrate");
+    int m_min = INT32_MAX;
+    for (const auto& hw : b->h_wins) m_min = std::min(m_min, hw.M);
+    if (k < 1 || k > kTopkTabMax || k > m_min || iters < 0 || !(first_step > 0))
+        return berr(SIRD_ERR_ARG, "polish: bad k (1..min(1024, smallest swarm)), iters or first_step");
+    const int W = b->W, P = b->P;
+    auto r256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
+    const size_t tab_b = r256(sizeof(PolishWin) * W), keys_b = r256(sizeof(unsigned long long) * W * (size_t)k),
+                 st_b = r256(polish_scratch_doubles(P, W * k) * sizeof(double)),
+                 ck_b = r256(polish_ckpt_floats(b->n_max, k) * sizeof(float) * W),
+                 res_b = r256(sizeof(ResultDev) * W);
+    const size_t need = tab_b + keys_b + st_b + ck_b + res_b;
+    cudaError_t e = cudaSuccess;
+    if (b->pmem_bytes < need) {
+        if (b->pmem) {
+            e = cudaStreamSynchronize(b->stream);
+            cudaFree(b->pmem);
+            b->pmem = nullptr;
+            b->pmem_bytes = 0;
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&b->pmem, need);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            b->pmem = nullptr;
+            return berr(e == cudaErrorMemoryAllocation ? SIRD_ERR_NOMEM : SIRD_ERR_CUDA,
+                        std::string("polish scratch: ") + cudaGetErrorString(e));
+        }
+        b->pmem_bytes = need;
+    }
+    if (!b->h_pres) {
+        e = cudaMallocHost((void**)&b->h_pres, sizeof(ResultDev) * W);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            b->h_pres = nullptr;
+            return berr(SIRD_ERR_NOMEM, "polish: pinned results");
+        }
+    }
+    unsigned char* q = (unsigned char*)b->pmem;
+    PolishWin* tab = (PolishWin*)q;
+    unsigned long long* keys = (unsigned long long*)(q + tab_b);
+    double* scratch = (double*)(q + tab_b + keys_b);
+    float* ckpt = (float*)(q + tab_b + keys_b + st_b);
+    ResultDev* res = (ResultDev*)(q + tab_b + keys_b + st_b + ck_b);
+    // the window table: each window's constants (as the last set_observations left them), its
+    // observations and its swarm's personal bests
+    std::vector<PolishWin> ht(W);
+    for (int i = 0; i < W; ++i) {
+        const BatchWindow& bw = b->h_wins[i];
+        PolishWin& t = ht[i];
+        t.w = bw.w;
+        t.o.yf = b->yf + bw.obs_off;
+        t.o.invyf = b->invy + bw.obs_off;
+        t.o.yd = b->yd + bw.obs_off;
+        t.pb = b->swarm + bw.sw_off + 2 * (size_t)P * bw.ld;
+        t.pbf = b->swarm + bw.sw_off + 3 * (size_t)P * bw.ld;
+        t.ld = bw.ld;
+        t.M = bw.M;
+    }
+    e = cudaMemcpyAsync(tab, ht.data(), sizeof(PolishWin) * W, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = launch_topk_tab(tab, W, k, keys, b->stream);
+    if (e == cudaSuccess)
+        e = launch_polish(tab, W, b->n_max, ht[0].w, ht[0].o, b->mdl, b->c64, keys, k, iters, first_step, 32, scratch,
+                          ckpt, 1, res, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_pres, res, sizeof(ResultDev) * W, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return berr(SIRD_ERR_CUDA, std::string("polish: ") + cudaGetErrorString(e));
+    }
+    for (int i = 0; i < W; ++i) {
+        const ResultDev& rd = b->h_pres[i];
+        sird_result& r = results[i];
+        std::memset(&r, 0, sizeof(r));
+        r.n_params = P;
+        for (int d = 0; d < P; ++d) r.theta[d] = rd.theta[d];
+        r.loss = rd.loss;
+        r.loss_search = rd.loss_search;
+        r.r2_D = b->ss_tot[i] > 0 ? 1.0 - rd.sse / b->ss_tot[i] : NAN;
+        r.index = rd.index;
         r.iters_done = b->iters;
     }
     return SIRD_OK;
@@ -552,6 +661,7 @@ extern "C" sird_status sird_batch_set_observations(sird_batch_t b, const double*
         return berr(SIRD_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
     }
     if (h2d_bytes) *h2d_bytes = b->wins_bytes + b->obs_bytes;
+    b->calibrated = false;  // the swarms' personal-best losses belong to the old observations
     return SIRD_OK;
 }
 

@@ -99,6 +99,34 @@ struct ObsDev {
 
 size_t smem_bytes_f32(const WindowDev& w, const ModelDev& m, int block, bool with_theta);
 
+// One window of a table-form launch (the polish of many windows at once): its constants, its
+// observations and its swarm's personal bests.  A table-form kernel's block row blockIdx.y
+// works on window blockIdx.y, with the window's own constants and the arithmetic of the
+// one-window kernel, so each window's results equal a one-window launch's bit for bit.
+struct PolishWin {
+    WindowDev w;
+    ObsDev o;
+    const float* pb;   // personal-best positions [P][ld], search coordinates
+    const float* pbf;  // personal-best values [ld]
+    int ld, M;
+};
+
+// Table forms of the FP32 evaluation and loss gradient: window i < nw takes its M vectors at
+// theta + i * th_ws (leading dimension ld) and writes loss + i * loss_ws (and, for the
+// gradient, grad + i * grad_ws with leading dimension ldg; checkpoints at ckpt + i * ck_ws,
+// ck_ws >= adjoint_ckpt_bytes_f32 of an n_max-observation window / 4).  n_max bounds the
+// windows' n_obs.
+cudaError_t launch_eval_f32_tab(const PolishWin* tab, int nw, int n_max, const ModelDev& m, const float* theta,
+                                long long th_ws, int ld, int M, float* loss, long long loss_ws, int block,
+                                cudaStream_t s);
+cudaError_t launch_loss_grad_f32_tab(const PolishWin* tab, int nw, int n_max, const ModelDev& m, const float* theta,
+                                     long long th_ws, int ld, int M, float* loss, long long loss_ws, float* grad,
+                                     long long grad_ws, int ldg, float* ckpt, long long ck_ws, cudaStream_t s);
+// The k smallest keys (packed loss, index) of every window's personal bests, ascending, into
+// keys[i * k .. i * k + k - 1]; k <= kTopkTabMax and k <= each window's M.
+constexpr int kTopkTabMax = 1024;
+cudaError_t launch_topk_tab(const PolishWin* tab, int nw, int k, unsigned long long* keys, cudaStream_t s);
+
 cudaError_t launch_eval_f32(const WindowDev& w, const ModelDev& m, const ObsDev& o, const float* theta, int ld,
                             int M, float* loss, int block, unsigned* err, cudaStream_t s);
 cudaError_t launch_eval_f64(const WindowDev& w, const ModelDev& m, const ObsDev& o, const double* theta, int ld,
@@ -162,14 +190,17 @@ size_t ensemble_traj_bytes(int k, int n_days);
 cudaError_t launch_ensemble_bands(const WindowDev& w, const ModelDev& m, const double* theta, int k, int n_days,
                                   const int* drop, int n_bands, double* traj, double* out, cudaStream_t s);
 
-// L-BFGS polish of the k candidates named by keys (FP32 swarm): iters iterations with a
-// parallel line search, trials and gradient in FP32 (precision 32) or FP64 (64), best point kept,
-// the best candidate's theta / FP64 loss / sse into *res.  scratch: polish_scratch_doubles(P, k)
-// doubles; ckpt: adjoint_ckpt_bytes_f32(w, k) or adjoint_ckpt_bytes(w, m, k, ckpt_every) bytes.
+// L-BFGS polish, for each of the nw windows of tab, of its k candidates named by keys[i * k ..]
+// (personal bests of its FP32 swarm): iters iterations with a parallel line search, trials and
+// gradient in FP32 (precision 32) or, for one window (nw == 1, w and o its constants and
+// observations), FP64 (64); best point kept; each window's best candidate's theta / FP64 loss /
+// sse into res[i].  scratch: polish_scratch_doubles(P, nw * k) doubles; ckpt: nw windows of
+// polish_ckpt_floats(n_max, k) floats (FP32), or adjoint_ckpt_bytes(w, m, k, ckpt_every) bytes.
 size_t polish_scratch_doubles(int P, int k);
-cudaError_t launch_polish(const WindowDev& w, const ModelDev& m, const ObsDev& o, const PsoCoeffs<double>& c,
-                          const unsigned long long* keys, int k, const float* pb, const float* pbf, int ld, int iters,
-                          double first_step, int precision, double* scratch, void* ckpt, int ckpt_every,
+size_t polish_ckpt_floats(int n_max, int k);
+cudaError_t launch_polish(const PolishWin* tab, int nw, int n_max, const WindowDev& w, const ObsDev& o,
+                          const ModelDev& m, const PsoCoeffs<double>& c, const unsigned long long* keys, int k,
+                          int iters, double first_step, int precision, double* scratch, void* ckpt, int ckpt_every,
                           ResultDev* res, cudaStream_t s);
 
 // ---------------------------------------------------------------- batched windows

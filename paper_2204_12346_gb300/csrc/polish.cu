@@ -15,6 +15,11 @@
 // Precision 64 evaluates the trials and the gradient in FP64; precision 32 uses the compensated
 // FP32 evaluation and the FP32 adjoint (about 15x faster per iteration) while the L-BFGS
 // algebra stays in FP64.
+//
+// The windows of a batch (Sec. 3.1: rolling windows, each calibrated on its own) are polished
+// together: candidate g of the nw * k belongs to window g / k, every step above is one launch
+// over all windows (the evaluations and gradients in table form, block row = window), and a
+// window's candidates see exactly the arithmetic of a one-window polish.
 #include <cmath>
 
 #include "kernels.h"
@@ -26,32 +31,40 @@ namespace {
 constexpr int kMem = 8;
 constexpr int kTrials = 16;
 
-// Per-candidate state, structure of arrays with candidate j at [.. * k + j].
+// Per-candidate state, structure of arrays with candidate g (window g / k, its candidate g % k)
+// at [.. * kk + g], kk = nw * k.  Trial t of candidate g sits at column tcol(g, t) of the
+// [.. * kt * nw] trial arrays: each window's kt = k * kTrials trials contiguous, trial-major.
 struct PolishState {
     double *z, *g, *f, *d, *zt, *tht, *ft, *S, *Y, *rho, *best_f, *best_th, *gth, *lnew;
     float *thf, *ftf, *gthf, *lnewf;  // FP32 mode: trial thetas, their losses, gradient, loss
     int *head, *count, *active, *cand;
-    int P, k, f32;
+    int P, k, nw, kk, f32;
+    __device__ __forceinline__ size_t tcol(int g, int t) const {
+        return (size_t)(g / k) * k * kTrials + (size_t)t * k + g % k;
+    }
+    __device__ __forceinline__ size_t tcols() const { return (size_t)kk * kTrials; }
 };
 
 __device__ __forceinline__ double decode(double z, bool lg) { return lg ? exp(z) : z; }
 
-__global__ void polish_init_kernel(PolishState s, const unsigned long long* __restrict__ keys, const float* __restrict__ pb,
-                                   int ld, uint32_t logmask) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= s.k) return;
-    const int idx = (int)(keys[j] & 0xFFFFFFFFu);
-    s.cand[j] = idx;
-    s.head[j] = 0;
-    s.count[j] = 0;
-    s.active[j] = 1;
-    s.best_f[j] = INFINITY;
+__global__ void polish_init_kernel(PolishState s, const PolishWin* __restrict__ tab,
+                                   const unsigned long long* __restrict__ keys, uint32_t logmask) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= s.kk) return;
+    const PolishWin& pw = tab[g / s.k];
+    const int idx = (int)(keys[g] & 0xFFFFFFFFu);
+    s.cand[g] = idx;
+    s.head[g] = 0;
+    s.count[g] = 0;
+    s.active[g] = 1;
+    s.best_f[g] = INFINITY;
+    const size_t KT = s.tcols(), c0 = s.tcol(g, 0);
     for (int d = 0; d < s.P; ++d) {
-        const double z = (double)pb[(size_t)d * ld + idx];
-        s.z[(size_t)d * s.k + j] = z;
+        const double z = (double)pw.pb[(size_t)d * pw.ld + idx];
+        s.z[(size_t)d * s.kk + g] = z;
         const double th = decode(z, (logmask >> d) & 1u);
-        s.tht[(size_t)d * s.k * kTrials + j] = th;  // slot 0: gradient point
-        if (s.f32) s.thf[(size_t)d * s.k * kTrials + j] = (float)th;
+        s.tht[(size_t)d * KT + c0] = th;  // slot 0: gradient point
+        if (s.f32) s.thf[(size_t)d * KT + c0] = (float)th;
     }
 }
 
@@ -71,8 +84,9 @@ __device__ __forceinline__ double warp_max_d(double v) {
 // candidate, lane = dimension (P <= 32).
 __global__ void polish_accept_kernel(PolishState s, uint32_t logmask, int first) {
     const int j = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (j >= s.k) return;  // whole warps
-    const int P = s.P, k = s.k, kt = k * kTrials, d = lane;
+    if (j >= s.kk) return;  // whole warps
+    const int P = s.P, k = s.kk, d = lane;
+    const size_t KT = s.tcols(), c0 = s.tcol(j, 0);
     const bool on = lane < P;
     const double fnew = s.f32 ? (double)s.lnewf[j] : s.lnew[j];
     const int head = s.head[j], cnt = s.count[j];
@@ -80,7 +94,7 @@ __global__ void polish_accept_kernel(PolishState s, uint32_t logmask, int first)
     double sd = 0.0, yd = 0.0;
     if (on) {
         const bool lg = (logmask >> d) & 1u;
-        const double th = s.tht[(size_t)d * kt + j];
+        const double th = s.tht[(size_t)d * KT + c0];
         const double gr = s.f32 ? (double)s.gthf[(size_t)d * k + j] : s.gth[(size_t)d * k + j];
         const double gz = lg ? th * gr : gr;
         if (!first) {
@@ -113,8 +127,8 @@ __global__ void polish_accept_kernel(PolishState s, uint32_t logmask, int first)
 __global__ void polish_direction_kernel(PolishState s, PsoCoeffs<double> c, double first_step) {
     (void)c;
     const int j = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (j >= s.k) return;  // whole warps
-    const int P = s.P, k = s.k;
+    if (j >= s.kk) return;  // whole warps
+    const int P = s.P, k = s.kk;
     const bool on = lane < P;
     const double g = on ? s.g[(size_t)lane * k + j] : 0.0;
     const int cnt = s.count[j], head = s.head[j];
@@ -159,33 +173,38 @@ __global__ void polish_direction_kernel(PolishState s, PsoCoeffs<double> c, doub
     if (on) s.d[(size_t)lane * k + j] = dir;
 }
 
-// The trial points z + 2^-t d, clamped to the box and decoded: one thread per (dimension, trial,
-// candidate), so that the decodes (an exp each on log dimensions) run side by side.
+// The trial points z + 2^-t d, clamped to the box and decoded: one thread per (dimension, trial
+// column), so that the decodes (an exp each on log dimensions) run side by side.
 __global__ void polish_trials_kernel(PolishState s, PsoCoeffs<double> c) {
     const int k = s.k, kt = k * kTrials;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= s.P * kt) return;
-    const int j = i % k, t = (i / k) % kTrials, d = i / kt;
+    const size_t KT = s.tcols();
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)s.P * KT) return;
+    const size_t col = i % KT;
+    const int d = (int)(i / KT), wi = (int)(col / kt), r = (int)(col % kt);
+    const int t = r / k, g = wi * k + r % k;
     const double alpha = ldexp(1.0, -t);
-    const double zn = fmin(fmax(s.z[(size_t)d * k + j] + alpha * s.d[(size_t)d * k + j], c.zlb[d]), c.zub[d]);
+    const double zn = fmin(fmax(s.z[(size_t)d * s.kk + g] + alpha * s.d[(size_t)d * s.kk + g], c.zlb[d]), c.zub[d]);
     const double th = decode(zn, (c.logmask >> d) & 1u);
-    s.tht[(size_t)d * kt + (size_t)t * k + j] = th;
-    if (s.f32) s.thf[(size_t)d * kt + (size_t)t * k + j] = (float)th;
+    s.tht[i] = th;
+    if (s.f32) s.thf[i] = (float)th;
 }
 
 // Armijo choice among the evaluated trials; the accepted theta goes to trial slot 0 and z to zt.
 // One warp per candidate: lane t tests trial t, lane d decodes dimension d.
 __global__ void polish_select_kernel(PolishState s, PsoCoeffs<double> c) {
     const int j = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (j >= s.k) return;  // whole warps
-    const int P = s.P, k = s.k, kt = k * kTrials, d = lane;
+    if (j >= s.kk) return;  // whole warps
+    const int P = s.P, k = s.kk, d = lane;
+    const size_t KT = s.tcols();
     const bool on = lane < P;
     const double f0 = s.f[j];
     const double gd = warp_sum_d(on ? s.g[(size_t)d * k + j] * s.d[(size_t)d * k + j] : 0.0);
     double ft = INFINITY;
     bool armijo = false;
     if (lane < kTrials) {
-        ft = s.f32 ? (double)s.ftf[(size_t)lane * k + j] : s.ft[(size_t)lane * k + j];
+        const size_t ct = s.tcol(j, lane);
+        ft = s.f32 ? (double)s.ftf[ct] : s.ft[ct];
         armijo = ft <= f0 + 1e-4 * ldexp(1.0, -lane) * gd;
     }
     const unsigned ok = __ballot_sync(0xFFFFFFFFu, armijo);
@@ -219,19 +238,22 @@ __global__ void polish_select_kernel(PolishState s, PsoCoeffs<double> c) {
     }
     s.zt[(size_t)d * k + j] = zn;
     const double th = decode(zn, (c.logmask >> d) & 1u);
-    s.tht[(size_t)d * kt + j] = th;
-    if (s.f32) s.thf[(size_t)d * kt + j] = (float)th;
+    const size_t c0 = s.tcol(j, 0);
+    s.tht[(size_t)d * KT + c0] = th;
+    if (s.f32) s.thf[(size_t)d * KT + c0] = (float)th;
 }
 
-// Best candidate: theta, FP64 loss and sum of squared errors (for R^2) into *res.
-__global__ void polish_pick_kernel(WindowDev w, ModelDev m, ObsDev o, PolishState s, const float* __restrict__ pbf,
-                                   ResultDev* res) {
+// Each window's best candidate (one block per window): theta, FP64 loss and sum of squared
+// errors (for R^2) into res[window].
+__global__ void polish_pick_kernel(const PolishWin* __restrict__ tab, ModelDev m, PolishState s, ResultDev* res) {
     extern __shared__ double dsm[];
     __shared__ double wf[32];
     __shared__ int wi[32];
-    const int tid = threadIdx.x, B = blockDim.x, k = s.k;
-    for (int i = tid, span = obs_span(w, m); i < span; i += B) dsm[i] = o.yd[i];
-    double f = tid < k ? s.best_f[tid] : INFINITY;
+    const int tid = threadIdx.x, B = blockDim.x, k = s.k, win = blockIdx.x, g0 = win * k;
+    const WindowDev w = tab[win].w;
+    const double* yd = tab[win].o.yd;
+    for (int i = tid, span = obs_span(w, m); i < span; i += B) dsm[i] = yd[i];
+    double f = tid < k ? s.best_f[g0 + tid] : INFINITY;
     int j = tid < k ? tid : INT_MAX;
     warp_min_pair(f, j);
     if ((tid & 31) == 0) {
@@ -245,29 +267,34 @@ __global__ void polish_pick_kernel(WindowDev w, ModelDev m, ObsDev o, PolishStat
         warp_min_pair(f2, j2);
         if (tid == 0 && j2 < k) {
             double sse = 0.0, fl = 0.0;
-            const double* th = s.best_th + j2;
+            const double* th = s.best_th + g0 + j2;
+            const int ld = s.kk;
             switch (m.cost) {
-                case COST_MSE: fl = fitness_f64<COST_MSE>(w, m, dsm, th, k, &sse); break;
-                case COST_MXSE: fl = fitness_f64<COST_MXSE>(w, m, dsm, th, k, &sse); break;
-                case COST_MAE: fl = fitness_f64<COST_MAE>(w, m, dsm, th, k, &sse); break;
-                default: fl = fitness_f64<COST_MAPE>(w, m, dsm, th, k, &sse); break;
+                case COST_MSE: fl = fitness_f64<COST_MSE>(w, m, dsm, th, ld, &sse); break;
+                case COST_MXSE: fl = fitness_f64<COST_MXSE>(w, m, dsm, th, ld, &sse); break;
+                case COST_MAE: fl = fitness_f64<COST_MAE>(w, m, dsm, th, ld, &sse); break;
+                default: fl = fitness_f64<COST_MAPE>(w, m, dsm, th, ld, &sse); break;
             }
-            for (int d = 0; d < m.P; ++d) res->theta[d] = th[(size_t)d * k];
-            res->loss = fl;
-            res->sse = sse;
-            res->index = s.cand[j2];
-            res->loss_search = (double)pbf[s.cand[j2]];
-            res->count = k;
+            ResultDev* r = res + win;
+            for (int d = 0; d < m.P; ++d) r->theta[d] = th[(size_t)d * ld];
+            r->loss = fl;
+            r->sse = sse;
+            r->index = s.cand[g0 + j2];
+            r->loss_search = (double)tab[win].pbf[s.cand[g0 + j2]];
+            r->count = k;
         }
     }
 }
 
-PolishState carve(double* base, int P, int k, int f32) {
+PolishState carve(double* base, int P, int k, int nw, int f32) {
     PolishState s{};
     s.P = P;
     s.k = k;
+    s.nw = nw;
+    s.kk = k * nw;
     s.f32 = f32;
-    const size_t pk = (size_t)P * k;
+    const int kk = s.kk;
+    const size_t pk = (size_t)P * kk;
     double* q = base;
     s.z = q; q += pk;
     s.g = q; q += pk;
@@ -278,59 +305,69 @@ PolishState carve(double* base, int P, int k, int f32) {
     s.tht = q; q += pk * kTrials;
     s.S = q; q += pk * kMem;
     s.Y = q; q += pk * kMem;
-    s.rho = q; q += (size_t)k * kMem;
-    s.f = q; q += k;
-    s.ft = q; q += (size_t)k * kTrials;
-    s.best_f = q; q += k;
-    s.lnew = q; q += k;
+    s.rho = q; q += (size_t)kk * kMem;
+    s.f = q; q += kk;
+    s.ft = q; q += (size_t)kk * kTrials;
+    s.best_f = q; q += kk;
+    s.lnew = q; q += kk;
     float* fq = (float*)q;
     s.thf = fq; fq += pk * kTrials;
-    s.ftf = fq; fq += (size_t)k * kTrials;
+    s.ftf = fq; fq += (size_t)kk * kTrials;
     s.gthf = fq; fq += pk;
-    s.lnewf = fq; fq += k;
+    s.lnewf = fq; fq += kk;
     int* iq = (int*)fq;
-    s.head = iq; iq += k;
-    s.count = iq; iq += k;
-    s.active = iq; iq += k;
+    s.head = iq; iq += kk;
+    s.count = iq; iq += kk;
+    s.active = iq; iq += kk;
     s.cand = iq;
     return s;
 }
 
 }  // namespace
 
+// k here is the number of candidates over all windows (nw * k of launch_polish).
 size_t polish_scratch_doubles(int P, int k) {
     const size_t pk = (size_t)P * k;
     const size_t floats = pk * (kTrials + 1) + (size_t)k * (kTrials + 1);
     return pk * (6 + kTrials + 2 * kMem) + (size_t)k * (kMem + kTrials + 3) + (floats + 1) / 2 + 2 * (size_t)k + 8;
 }
 
+size_t polish_ckpt_floats(int n_max, int k) {
+    const size_t kpad = ((size_t)k + 31) / 32 * 32;  // the adjoint's vectors, padded to whole warps
+    return (size_t)(n_max - 1) * 4 * kpad;
+}
+
 int polish_trials() { return kTrials; }
 
-cudaError_t launch_polish(const WindowDev& w, const ModelDev& m, const ObsDev& o, const PsoCoeffs<double>& c,
-                          const unsigned long long* keys, int k, const float* pb, const float* pbf, int ld, int iters,
-                          double first_step, int precision, double* scratch, void* ckpt, int ckpt_every,
+cudaError_t launch_polish(const PolishWin* tab, int nw, int n_max, const WindowDev& w, const ObsDev& o,
+                          const ModelDev& m, const PsoCoeffs<double>& c, const unsigned long long* keys, int k,
+                          int iters, double first_step, int precision, double* scratch, void* ckpt, int ckpt_every,
                           ResultDev* res, cudaStream_t st) {
     const int P = m.P;
     const bool f32 = precision == 32;
-    PolishState s = carve(scratch, P, k, f32 ? 1 : 0);
-    const unsigned grid = (unsigned)((k + 127) / 128);
-    const int kt = k * kTrials;
+    if (nw < 1 || nw > 65535 || (!f32 && nw != 1)) return cudaErrorInvalidValue;
+    PolishState s = carve(scratch, P, k, nw, f32 ? 1 : 0);
+    const int kk = s.kk, kt = k * kTrials;
+    const long long KT = (long long)kk * kTrials;
+    const long long ck_ws = (long long)polish_ckpt_floats(n_max, k);
+    // loss and gradient at every candidate's accepted point (trial slot 0 of its window)
     auto grad_at_slot0 = [&]() {
-        return f32 ? launch_loss_grad_f32(w, m, o, s.thf, kt, k, s.lnewf, s.gthf, k, nullptr, (float*)ckpt, st)
+        return f32 ? launch_loss_grad_f32_tab(tab, nw, n_max, m, s.thf, kt, (int)KT, k, s.lnewf, k, s.gthf, k, kk,
+                                              (float*)ckpt, ck_ws, st)
                    : launch_loss_grad_f64(w, m, o, s.tht, kt, k, s.lnew, s.gth, k, nullptr, (double*)ckpt,
                                           ckpt_every, st);
     };
     (void)cudaGetLastError();
-    const unsigned grid_warps = (unsigned)((32 * (size_t)k + 127) / 128);  // a warp per candidate
-    polish_init_kernel<<<grid, 128, 0, st>>>(s, keys, pb, ld, c.logmask);
+    const unsigned grid = (unsigned)((kk + 127) / 128);
+    const unsigned grid_warps = (unsigned)((32 * (size_t)kk + 127) / 128);  // a warp per candidate
+    polish_init_kernel<<<grid, 128, 0, st>>>(s, tab, keys, c.logmask);
     cudaError_t e = cudaGetLastError();
-    // loss and gradient at the starting points (trial slot 0 holds their theta)
     if (e == cudaSuccess) e = grad_at_slot0();
     if (e == cudaSuccess) {
         polish_accept_kernel<<<grid_warps, 128, 0, st>>>(s, c.logmask, 1);
         e = cudaGetLastError();
     }
-    const unsigned grid_trials = (unsigned)((P * kt + 127) / 128);
+    const unsigned grid_trials = (unsigned)(((size_t)P * KT + 127) / 128);
     for (int it = 0; it < iters && e == cudaSuccess; ++it) {
         polish_direction_kernel<<<grid_warps, 128, 0, st>>>(s, c, first_step);
         e = cudaGetLastError();
@@ -339,7 +376,7 @@ cudaError_t launch_polish(const WindowDev& w, const ModelDev& m, const ObsDev& o
             e = cudaGetLastError();
         }
         if (e == cudaSuccess)
-            e = f32 ? launch_eval_f32(w, m, o, s.thf, kt, kt, s.ftf, 128, nullptr, st)
+            e = f32 ? launch_eval_f32_tab(tab, nw, n_max, m, s.thf, kt, (int)KT, kt, s.ftf, kt, 128, st)
                     : launch_eval_f64(w, m, o, s.tht, kt, kt, s.ft, 64, nullptr, st);
         if (e != cudaSuccess) break;
         polish_select_kernel<<<grid_warps, 128, 0, st>>>(s, c);
@@ -351,7 +388,14 @@ cudaError_t launch_polish(const WindowDev& w, const ModelDev& m, const ObsDev& o
     }
     if (e != cudaSuccess) return e;
     const int block = ((k + 31) / 32) * 32;
-    polish_pick_kernel<<<1, block, (size_t)obs_span(w, m) * sizeof(double), st>>>(w, m, o, s, pbf, res);
+    WindowDev wmax{};
+    wmax.n_obs = n_max;
+    const size_t sm = (size_t)obs_span(wmax, m) * sizeof(double);
+    if (sm > 48 * 1024) {
+        e = cudaFuncSetAttribute(polish_pick_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    polish_pick_kernel<<<(unsigned)nw, block, sm, st>>>(tab, m, s, res);
     return cudaGetLastError();
 }
 

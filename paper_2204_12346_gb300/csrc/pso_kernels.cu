@@ -7,6 +7,7 @@
 #include <cmath>
 
 #include "kernels.h"
+#include "launch_util.cuh"
 
 namespace sird {
 
@@ -14,56 +15,6 @@ namespace {
 
 constexpr int kTopkThreads = 1024;
 constexpr int kTopkChunk = 4096;
-
-__host__ __device__ __forceinline__ int pad4(int n) { return (n + 3) & ~3; }
-
-// Copies the observations (all stacked series) into shared memory; returns the reciprocal table
-// (or ys).
-template <int COST>
-__device__ __forceinline__ float* stage_obs_f32(float* smem, const WindowDev& w, const ModelDev& m, const ObsDev& o) {
-    float* ys = smem;
-    float* invys = (variant_cost(COST) == COST_MAPE) ? ys + obs_span_pad(w, m) : ys;
-    const int span = obs_span(w, m);
-    for (int i = threadIdx.x; i < span; i += blockDim.x) {
-        ys[i] = o.yf[i];
-        if (variant_cost(COST) == COST_MAPE) invys[i] = o.invyf[i];
-    }
-    return invys;
-}
-
-template <int COST>
-__device__ __forceinline__ float* after_obs_f32(float* smem, const WindowDev& w, const ModelDev& m) {
-    return smem + obs_span_pad(w, m) * (variant_cost(COST) == COST_MAPE ? 2 : 1);
-}
-
-// ------------------------------------------------------------------ FP32 eval
-
-// A thread evaluates two parameter vectors, p0 = block * 2B + thread and p1 = p0 + B, together
-// in packed f32x2 form (each loss equal to the one-at-a-time evaluation bit for bit).
-template <int SPD, int COST>
-__global__ void __launch_bounds__(kF32IterMaxBlock, 1) eval_f32_kernel(WindowDev w, ModelDev m, ObsDev o,
-                                                         const float* __restrict__ theta, int ld, int M,
-                                                         float* __restrict__ loss) {
-    extern __shared__ float smem[];
-    float* ys = smem;
-    float* invys = stage_obs_f32<COST>(smem, w, m, o);
-    float* th_s = after_obs_f32<COST>(smem, w, m);  // [P][2B]
-    const int B = blockDim.x, B2 = 2 * B, tid = threadIdx.x;
-    const int p0 = blockIdx.x * B2 + tid, p1 = p0 + B;
-    for (int d = 0; d < m.P; ++d) {
-        if (p0 < M) th_s[d * B2 + tid] = theta[(size_t)d * ld + p0];
-        if (p1 < M) th_s[d * B2 + B + tid] = theta[(size_t)d * ld + p1];
-    }
-    __syncthreads();
-    if (p1 < M) {
-        float fa, fb;
-        fitness_f32x2<SPD, COST>(w, m, ys, invys, th_s + tid, th_s + B + tid, B2, fa, fb);
-        loss[p0] = fa;
-        loss[p1] = fb;
-    } else if (p0 < M) {
-        loss[p0] = fitness_f32<SPD, COST>(w, m, ys, invys, th_s + tid, B2);
-    }
-}
 
 // ------------------------------------------------------------------ FP32 PSO iteration
 
@@ -305,21 +256,8 @@ __global__ void __launch_bounds__(256) pso_f64_kernel(WindowDev w, ModelDev m, O
 
 // ------------------------------------------------------------------ top-k
 
-// Sorts a chunk of kTopkChunk keys ascending in shared memory (bitonic network) and writes
-// the first k.  Keys come from the personal-best values (pbf != nullptr) or from a previous pass.
-__global__ void __launch_bounds__(kTopkThreads) topk_kernel(const float* __restrict__ pbf,
-                                                             const unsigned long long* __restrict__ in, int n, int k,
-                                                             unsigned long long* __restrict__ out) {
-    __shared__ unsigned long long s[kTopkChunk];
-    const int tid = threadIdx.x;
-    const long long base = (long long)blockIdx.x * kTopkChunk;
-    for (int i = tid; i < kTopkChunk; i += kTopkThreads) {
-        const long long j = base + i;
-        unsigned long long v = ~0ull;
-        if (j < n) v = pbf ? argmin_key(pbf[j], (uint32_t)j) : in[j];
-        s[i] = v;
-    }
-    __syncthreads();
+// Sorts the kTopkChunk keys of s ascending (bitonic network); ends with a block barrier.
+__device__ __forceinline__ void bitonic_sort_chunk(unsigned long long* s, int tid) {
     for (int size = 2; size <= kTopkChunk; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             for (int i = tid; i < kTopkChunk / 2; i += kTopkThreads) {
@@ -335,7 +273,46 @@ __global__ void __launch_bounds__(kTopkThreads) topk_kernel(const float* __restr
             __syncthreads();
         }
     }
+}
+
+// Sorts a chunk of kTopkChunk keys ascending in shared memory and writes the first k.  Keys come
+// from the personal-best values (pbf != nullptr) or from a previous pass.
+__global__ void __launch_bounds__(kTopkThreads) topk_kernel(const float* __restrict__ pbf,
+                                                             const unsigned long long* __restrict__ in, int n, int k,
+                                                             unsigned long long* __restrict__ out) {
+    __shared__ unsigned long long s[kTopkChunk];
+    const int tid = threadIdx.x;
+    const long long base = (long long)blockIdx.x * kTopkChunk;
+    for (int i = tid; i < kTopkChunk; i += kTopkThreads) {
+        const long long j = base + i;
+        unsigned long long v = ~0ull;
+        if (j < n) v = pbf ? argmin_key(pbf[j], (uint32_t)j) : in[j];
+        s[i] = v;
+    }
+    __syncthreads();
+    bitonic_sort_chunk(s, tid);
     for (int i = tid; i < k; i += kTopkThreads) out[(size_t)blockIdx.x * k + i] = s[i];
+}
+
+// Table form, one block per window: s[0, k) holds the window's k smallest keys so far and is
+// sorted together with the next kTopkChunk - k keys of its personal bests, chunk by chunk.  The k
+// smallest keys are unique (the index breaks ties), so they equal the chunked passes' result.
+__global__ void __launch_bounds__(kTopkThreads) topk_tab_kernel(const PolishWin* __restrict__ tab, int k,
+                                                                 unsigned long long* __restrict__ keys) {
+    __shared__ unsigned long long s[kTopkChunk];
+    const int tid = threadIdx.x, per = kTopkChunk - k;
+    const float* pbf = tab[blockIdx.x].pbf;
+    const int M = tab[blockIdx.x].M;
+    for (int i = tid; i < k; i += kTopkThreads) s[i] = ~0ull;
+    for (int base = 0; base < M; base += per) {
+        for (int i = tid; i < per; i += kTopkThreads) {
+            const int j = base + i;
+            s[k + i] = j < M ? argmin_key(pbf[j], (uint32_t)j) : ~0ull;
+        }
+        __syncthreads();
+        bitonic_sort_chunk(s, tid);
+    }
+    for (int i = tid; i < k; i += kTopkThreads) keys[(size_t)blockIdx.x * k + i] = s[i];
 }
 
 // ------------------------------------------------------------------ FP64 re-evaluation
@@ -408,27 +385,7 @@ __global__ void topk_gather_kernel(const unsigned long long* __restrict__ keys, 
     loss_out[j] = (double)pbf[idx];
 }
 
-template <typename K>
-cudaError_t set_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-unsigned grid_for(int M, int block) {
-    (void)cudaGetLastError();  // launch errors are read right after each launch; start clean
-    return (unsigned)((M + block - 1) / block);
-}
-
-// FP32 eval / iteration kernels: two particles per thread
-unsigned grid_for_pairs(int M, int block) { return grid_for(M, 2 * block); }
-
 }  // namespace
-
-size_t smem_bytes_f32(const WindowDev& w, const ModelDev& m, int block, bool with_theta) {
-    size_t n = (size_t)obs_span_pad(w, m) * (m.cost == COST_MAPE ? 2 : 1);
-    if (with_theta) n += (size_t)m.P * 2 * block + 3 * kMaxParams;  // theta of two particles per thread
-    return n * sizeof(float);
-}
 
 static size_t smem_bytes_f64(const WindowDev& w, const ModelDev& m, int block, bool with_g) {
     return ((size_t)obs_span(w, m) + (size_t)m.P * block + (with_g ? kMaxParams : 0)) * sizeof(double);
@@ -441,20 +398,6 @@ static size_t smem_bytes_f64(const WindowDev& w, const ModelDev& m, int block, b
         case COST_MAE: { constexpr int C_ = COST_MAE; __VA_ARGS__; } break;   \
         default: { constexpr int C_ = COST_MAPE; __VA_ARGS__; } break;        \
     }
-
-cudaError_t launch_eval_f32(const WindowDev& w, const ModelDev& m, const ObsDev& o, const float* theta, int ld,
-                            int M, float* loss, int block, unsigned*, cudaStream_t s) {
-    if (M <= 0) return cudaSuccess;
-    if (block > kF32IterMaxBlock) block = kF32IterMaxBlock;  // results do not depend on the block shape
-    const size_t sm = smem_bytes_f32(w, m, block, true);
-    cudaError_t e = cudaSuccess;
-    SIRD_DISPATCH_F32(m, {
-        auto kern = eval_f32_kernel<S_, C_>;
-        e = set_smem(kern, sm);
-        if (e == cudaSuccess) kern<<<grid_for_pairs(M, block), block, sm, s>>>(w, m, o, theta, ld, M, loss);
-    });
-    return e != cudaSuccess ? e : cudaGetLastError();
-}
 
 cudaError_t launch_eval_f64(const WindowDev& w, const ModelDev& m, const ObsDev& o, const double* theta, int ld,
                             int M, double* loss, int block, unsigned*, cudaStream_t s) {
@@ -521,6 +464,14 @@ cudaError_t launch_topk_f32(const float* pbf, int M, int k, unsigned long long* 
         src = dst;
         dst = (dst == tmp_a) ? tmp_b : tmp_a;
     }
+}
+
+cudaError_t launch_topk_tab(const PolishWin* tab, int nw, int k, unsigned long long* keys, cudaStream_t s) {
+    if (nw <= 0) return cudaSuccess;
+    if (k < 1 || k > kTopkTabMax) return cudaErrorInvalidValue;
+    (void)cudaGetLastError();
+    topk_tab_kernel<<<(unsigned)nw, kTopkThreads, 0, s>>>(tab, k, keys);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_topk_gather(const unsigned long long* keys, int k, const float* pb, const float* pbf, int ld,

@@ -762,20 +762,33 @@ extern "C" sird_status sird_pso_polish(sird_pso_t h, int k, int iters, double fi
         return h->fail(SIRD_ERR_UNSUPPORTED, "polish: FP32 needs steps_per_day <= 64");
     if (h->iter < 0) return h->fail(SIRD_ERR_STATE, "polish before init");
     const size_t nk = topk_scratch_keys(h->M, k);
-    const size_t ck = precision == 32 ? adjoint_ckpt_bytes_f32(h->win, k) : adjoint_ckpt_bytes(h->win, h->mdl, k, ckpt_every);
-    const size_t bytes = 2 * nk * sizeof(unsigned long long) + polish_scratch_doubles(h->P, k) * sizeof(double) + ck;
+    const size_t ck = precision == 32 ? polish_ckpt_floats(h->win.n_obs, k) * sizeof(float)
+                                      : adjoint_ckpt_bytes(h->win, h->mdl, k, ckpt_every);
+    // device: the window's table entry | top-k keys (two buffers) | polish state | checkpoints
+    const size_t tab_bytes = (sizeof(PolishWin) + 255) & ~(size_t)255;
+    const size_t bytes =
+        tab_bytes + 2 * nk * sizeof(unsigned long long) + polish_scratch_doubles(h->P, k) * sizeof(double) + ck;
     void* dmem = nullptr;
     sird_status st = h->cuda(cudaMalloc(&dmem, bytes), "polish scratch");
     if (st) return st;
-    unsigned long long* a = (unsigned long long*)dmem;
+    PolishWin* tab = (PolishWin*)dmem;
+    unsigned long long* a = (unsigned long long*)((unsigned char*)dmem + tab_bytes);
     unsigned long long* b = a + nk;
     double* scratch = (double*)(b + nk);
     void* ckpt = scratch + polish_scratch_doubles(h->P, k);
+    PolishWin hw{};
+    hw.w = h->win;
+    hw.o = h->obs;
+    hw.pb = (const float*)h->pb;
+    hw.pbf = (const float*)h->pbf;
+    hw.ld = h->ld;
+    hw.M = h->M;
     unsigned long long* keys = nullptr;
-    cudaError_t e = launch_topk_f32((const float*)h->pbf, h->M, k, a, b, &keys, h->stream);
+    cudaError_t e = cudaMemcpyAsync(tab, &hw, sizeof(PolishWin), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = launch_topk_f32((const float*)h->pbf, h->M, k, a, b, &keys, h->stream);
     if (e == cudaSuccess)
-        e = launch_polish(h->win, h->mdl, h->obs, h->c64, keys, k, (const float*)h->pb, (const float*)h->pbf, h->ld,
-                          iters, first_step, precision, scratch, ckpt, ckpt_every, h->d_res, h->stream);
+        e = launch_polish(tab, 1, h->win.n_obs, h->win, h->obs, h->mdl, h->c64, keys, k, iters, first_step, precision,
+                          scratch, ckpt, ckpt_every, h->d_res, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_res, h->d_res, sizeof(ResultDev), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(dmem);

@@ -31,6 +31,7 @@ EXPORTS = [
     "sird_forecast", "sird_pso_calibrate_batched", "sird_pso_set_observations", "sird_pso_set_timing", "sird_pso_launch_mode",
     "sird_pso_step_f32_noalloc", "sird_pso_topk", "sird_ensemble_bands", "sird_pso_polish", "sird_batch_create", "sird_batch_calibrate", "sird_batch_set_observations", "sird_batch_launch_mode",
     "sird_batch_block_size", "sird_batch_blocks_per_sm", "sird_batch_destroy", "sird_batch_set_timing",
+    "sird_batch_polish",
     "sird_pso_topk_indexed", "sird_pso_set_shard", "sird_pso_shard_best", "sird_pso_set_gbest",
 ]
 
@@ -114,6 +115,7 @@ def lib():
         L.sird_pso_set_gbest.argtypes = [vp, C.POINTER(C.c_float), C.c_float, ip]
         L.sird_batch_create.argtypes = [ip, C.POINTER(Problem), C.POINTER(Config), vp, C.POINTER(vp)]
         L.sird_batch_calibrate.argtypes = [vp, C.POINTER(Result)]
+        L.sird_batch_polish.argtypes = [vp, ip, ip, C.c_double, C.POINTER(Result)]
         L.sird_batch_block_size.argtypes = [vp]
         L.sird_batch_blocks_per_sm.argtypes = [vp]
         L.sird_batch_launch_mode.argtypes = [vp]
@@ -487,6 +489,15 @@ class Batch:
     def calibrate(self):
         res = (Result * self.W)()
         st = self._lib.sird_batch_calibrate(self.h, res)
+        if st != OK:
+            raise SirdError(st, self._lib.sird_last_error(None).decode())
+        return [r.as_dict() for r in res]
+
+    def polish(self, k=32, iters=40, first_step=1e-2):
+        """L-BFGS polish of every window's k best personal bests (FP32 trials and adjoint, FP64
+        algebra and re-scoring), all windows together; one result dict per window."""
+        res = (Result * self.W)()
+        st = self._lib.sird_batch_polish(self.h, int(k), int(iters), float(first_step), res)
         if st != OK:
             raise SirdError(st, self._lib.sird_last_error(None).decode())
         return [r.as_dict() for r in res]
