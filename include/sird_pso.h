@@ -298,7 +298,8 @@ sird_status sird_loss_grad(sird_pso_t h, const void* d_theta, int M, int ld, voi
  * L-BFGS iterations on the search coordinates (dL/dz = theta dL/dtheta on log dimensions;
  * 8 stored pairs, algebra in FP64), each with one sird_loss_grad evaluation and a line search
  * that evaluates 16 step lengths 2^-q in one launch and takes the longest one meeting the
- * Armijo condition; positions are clamped to the box.  precision 64: trials and gradients in
+ * Armijo condition; positions are clamped to the box, and a coordinate on a bound whose gradient
+ * points out of the box is held while the others move (projected L-BFGS).  precision 64: trials and gradients in
  * the paper's FP64 arithmetic (checkpoints every ckpt_every steps, 1..64); precision 32: the
  * compensated FP32 evaluation and the FP32 adjoint (steps_per_day 10, 20 or <= 64).
  * first_step is the largest change of any search coordinate in the first (steepest-descent)

@@ -2,14 +2,18 @@
 //
 // PSO (Sec. 3.3) needs no gradient; near its optimum the swarm resolves the loss only as far
 // as its search does.  The discrete adjoint gives the exact gradient of the FP64 loss, so the
-// k best personal bests are refined by L-BFGS in the search coordinates (z = ln theta on log
-// dimensions, where dL/dz = theta dL/dtheta), positions clamped to the box.  Each iteration:
-//   1. direction d = -H g by the two-loop recursion over the last kMem (s, y) pairs,
+// k best personal bests are refined by projected L-BFGS in the search coordinates (z = ln theta
+// on log dimensions, where dL/dz = theta dL/dtheta), positions clamped to the box.  Each
+// iteration:
+//   1. direction d = -H g by the two-loop recursion over the last kMem (s, y) pairs, on the
+//      dimensions not held at a bound of the box (a calibration's optimum often has beta or I0
+//      on the box's edge; an unprojected step there is cut back by the clamp and stalls),
 //   2. kTrials trial points z + 2^-q d (q = 0..kTrials-1) for every candidate, evaluated in ONE
 //      launch -- an evaluation of a few candidates is latency-bound, so 16 trials cost about
 //      what one does,
 //   3. the largest step that satisfies the Armijo condition (else the best trial if it lowers
-//      the loss, else the candidate stops),
+//      the loss, else a curvature probe that leaves the point where it is; kProbes + 1
+//      failures in a row stop the candidate),
 //   4. the gradient at the accepted point (adjoint launch) and the history update.
 // The best point ever evaluated is re-scored in FP64 (the paper's operation order) and reported.
 // Precision 64 evaluates the trials and the gradient in FP64; precision 32 uses the compensated
@@ -30,12 +34,13 @@ namespace {
 
 constexpr int kMem = 8;
 constexpr int kTrials = 16;
+constexpr int kProbes = 4;  // curvature probes in a row before a candidate stops
 
 // Per-candidate state, structure of arrays with candidate g (window g / k, its candidate g % k)
 // at [.. * kk + g], kk = nw * k.  Trial t of candidate g sits at column tcol(g, t) of the
 // [.. * kt * nw] trial arrays: each window's kt = k * kTrials trials contiguous, trial-major.
 struct PolishState {
-    double *z, *g, *f, *d, *zt, *tht, *ft, *S, *Y, *rho, *best_f, *best_th, *gth, *lnew;
+    double *z, *g, *f, *d, *zt, *tht, *ft, *S, *Y, *best_f, *best_th, *gth, *lnew;
     float *thf, *ftf, *gthf, *lnewf;  // FP32 mode: trial thetas, their losses, gradient, loss
     int *head, *count, *active, *cand;
     int P, k, nw, kk, f32;
@@ -47,8 +52,11 @@ struct PolishState {
 
 __device__ __forceinline__ double decode(double z, bool lg) { return lg ? exp(z) : z; }
 
+// Candidate g starts at its personal best, projected onto the box (the FP32 swarm searches the
+// box rounded to FP32, which can reach a hair past the FP64 bounds; a start outside would turn
+// every trial's clamp into a step of its own).
 __global__ void polish_init_kernel(PolishState s, const PolishWin* __restrict__ tab,
-                                   const unsigned long long* __restrict__ keys, uint32_t logmask) {
+                                   const unsigned long long* __restrict__ keys, PsoCoeffs<double> c) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= s.kk) return;
     const PolishWin& pw = tab[g / s.k];
@@ -60,9 +68,9 @@ __global__ void polish_init_kernel(PolishState s, const PolishWin* __restrict__ 
     s.best_f[g] = INFINITY;
     const size_t KT = s.tcols(), c0 = s.tcol(g, 0);
     for (int d = 0; d < s.P; ++d) {
-        const double z = (double)pw.pb[(size_t)d * pw.ld + idx];
+        const double z = fmin(fmax((double)pw.pb[(size_t)d * pw.ld + idx], c.zlb[d]), c.zub[d]);
         s.z[(size_t)d * s.kk + g] = z;
-        const double th = decode(z, (logmask >> d) & 1u);
+        const double th = decode(z, (c.logmask >> d) & 1u);
         s.tht[(size_t)d * KT + c0] = th;  // slot 0: gradient point
         if (s.f32) s.thf[(size_t)d * KT + c0] = (float)th;
     }
@@ -90,6 +98,7 @@ __global__ void polish_accept_kernel(PolishState s, uint32_t logmask, int first)
     const bool on = lane < P;
     const double fnew = s.f32 ? (double)s.lnewf[j] : s.lnew[j];
     const int head = s.head[j], cnt = s.count[j];
+    const bool probe = !first && s.active[j] >= 2;  // keep the point, take only the pair
     const double best = s.best_f[j];
     double sd = 0.0, yd = 0.0;
     if (on) {
@@ -102,63 +111,83 @@ __global__ void polish_accept_kernel(PolishState s, uint32_t logmask, int first)
             yd = gz - s.g[(size_t)d * k + j];
             s.S[((size_t)head * P + d) * k + j] = sd;
             s.Y[((size_t)head * P + d) * k + j] = yd;
-            s.z[(size_t)d * k + j] = s.zt[(size_t)d * k + j];
+            if (!probe) s.z[(size_t)d * k + j] = s.zt[(size_t)d * k + j];
         }
-        s.g[(size_t)d * k + j] = gz;
+        if (!probe) s.g[(size_t)d * k + j] = gz;
         if (fnew < best) s.best_th[(size_t)d * k + j] = th;
     }
     if (!first) {
         const double sy = warp_sum_d(sd * yd), yy = warp_sum_d(yd * yd), ss = warp_sum_d(sd * sd);
         if (lane == 0 && sy > 1e-14 * sqrt(ss * yy)) {  // curvature condition: keep the pair
-            s.rho[(size_t)head * k + j] = 1.0 / sy;
             s.head[j] = (head + 1) % kMem;
             if (cnt < kMem) s.count[j] = cnt + 1;
         }
     }
     __syncwarp();
     if (lane == 0) {
-        s.f[j] = fnew;
+        if (!probe) s.f[j] = fnew;
         if (fnew < best) s.best_f[j] = fnew;
     }
 }
 
-// Two-loop recursion for the direction d = -H g: one warp per candidate, lane = dimension
-// (P <= 32), dot products summed across the warp; the candidate's history is loaded up front.
+// Direction of projected L-BFGS: one warp per candidate, lane = dimension (P <= 32), dot
+// products summed across the warp.  A dimension whose coordinate sits on a bound of the box with
+// the gradient pointing out of the box (z at its lower bound and g > 0, or at its upper bound and
+// g < 0) is held; the gradient and the stored pairs (s, y) are restricted to the free dimensions,
+// each pair's curvature s.y recomputed there (a pair without positive curvature on them drops
+// out), and the two-loop recursion gives d = -H g on the free dimensions, 0 on the held ones.
+// With no dimension held this is plain L-BFGS.  Not a descent direction: scaled steepest descent
+// on the free dimensions, history cleared.
 __global__ void polish_direction_kernel(PolishState s, PsoCoeffs<double> c, double first_step) {
-    (void)c;
     const int j = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (j >= s.kk) return;  // whole warps
     const int P = s.P, k = s.kk;
     const bool on = lane < P;
     const double g = on ? s.g[(size_t)lane * k + j] : 0.0;
+    const double z = on ? s.z[(size_t)lane * k + j] : 0.0;
+    const bool held = on && ((z <= c.zlb[lane] && g > 0.0) || (z >= c.zub[lane] && g < 0.0));
+    const bool fr = on && !held;
+    const double gf = fr ? g : 0.0;
     const int cnt = s.count[j], head = s.head[j];
     double Sh[kMem], Yh[kMem], rh[kMem], a[kMem];
+    int newest = -1;  // the most recent pair with curvature on the free dimensions
+    double yy_newest = 0.0;
 #pragma unroll
     for (int i = 0; i < kMem; ++i) {  // i-th most recent pair
         const int h = (head - 1 - i + 2 * kMem) % kMem;
-        const bool use = on && i < cnt;
+        const bool use = fr && i < cnt;
         Sh[i] = use ? s.S[((size_t)h * P + lane) * k + j] : 0.0;
         Yh[i] = use ? s.Y[((size_t)h * P + lane) * k + j] : 0.0;
-        rh[i] = i < cnt ? s.rho[(size_t)h * k + j] : 0.0;
+        rh[i] = 0.0;
+        if (i < cnt) {
+            const double sy = warp_sum_d(Sh[i] * Yh[i]), yy = warp_sum_d(Yh[i] * Yh[i]),
+                         ss = warp_sum_d(Sh[i] * Sh[i]);
+            if (sy > 1e-14 * sqrt(ss * yy) && sy > 0.0) {
+                rh[i] = 1.0 / sy;
+                if (newest < 0) {
+                    newest = i;
+                    yy_newest = yy;
+                }
+            }
+        }
     }
-    double q = g;
+    double q = gf;
 #pragma unroll
     for (int i = 0; i < kMem; ++i) {
-        if (i < cnt) {
+        if (rh[i] != 0.0) {
             a[i] = rh[i] * warp_sum_d(Sh[i] * q);
             q -= a[i] * Yh[i];
         }
     }
-    if (cnt > 0) {
-        const double yy = warp_sum_d(Yh[0] * Yh[0]);
-        q *= 1.0 / (rh[0] * yy);
+    if (newest >= 0) {
+        q *= 1.0 / (rh[newest] * yy_newest);
     } else {
         const double gmax = warp_max_d(fabs(q));
         q *= gmax > 0.0 ? first_step / gmax : 0.0;
     }
 #pragma unroll
     for (int i = kMem - 1; i >= 0; --i) {
-        if (i < cnt) {
+        if (rh[i] != 0.0) {
             const double b = rh[i] * warp_sum_d(Yh[i] * q);
             q += (a[i] - b) * Sh[i];
         }
@@ -166,8 +195,8 @@ __global__ void polish_direction_kernel(PolishState s, PsoCoeffs<double> c, doub
     const double gd = -warp_sum_d(q * g);
     double dir = -q;
     if (!(gd < 0.0)) {  // not a descent direction: restart along the scaled steepest descent
-        const double gmax = warp_max_d(fabs(g));
-        dir = -(gmax > 0.0 ? first_step / gmax : 0.0) * g;
+        const double gmax = warp_max_d(fabs(gf));
+        dir = -(gmax > 0.0 ? first_step / gmax : 0.0) * gf;
         if (lane == 0) s.count[j] = 0;
     }
     if (on) s.d[(size_t)lane * k + j] = dir;
@@ -223,16 +252,27 @@ __global__ void polish_select_kernel(PolishState s, PsoCoeffs<double> c) {
         }
         pick = tb < 32 ? tb : -1;
     }
-    const int active = s.active[j];
+    // No trial lowers the loss: on a badly scaled valley the first steps can only lower it by
+    // less than the FP32 evaluation resolves.  Instead of stopping, the candidate stays put and
+    // takes the gradient at a probe point, the longest trial step whose loss rose by at most
+    // 1e-4 relative, whose (s, y) pair gives the next direction more curvature.  kProbes failures
+    // in a row stop the candidate for good.
+    const int active = s.active[j];  // 0 stopped, 1 moving, 1 + n slot 0 holds the n-th probe in a row
+    const unsigned near = __ballot_sync(0xFFFFFFFFu, lane < kTrials && ft <= f0 + 1e-4 * fabs(f0));
     __syncwarp();
-    if (pick < 0 || !active) {
-        if (lane == 0) s.active[j] = 0;  // the candidate stops for good
+    int probe = -1;
+    if (pick >= 0 && active) {
+        if (lane == 0) s.active[j] = 1;
+    } else {
+        if (active >= 1 && active <= kProbes) probe = near ? __ffs(near) - 1 : kTrials - 1;
+        if (lane == 0) s.active[j] = probe >= 0 ? active + 1 : 0;
         pick = -1;
     }
     if (!on) return;
     double zn;
-    if (pick >= 0) {
-        zn = fmin(fmax(s.z[(size_t)d * k + j] + ldexp(1.0, -pick) * s.d[(size_t)d * k + j], c.zlb[d]), c.zub[d]);
+    if (pick >= 0 || probe >= 0) {
+        const int t = pick >= 0 ? pick : probe;
+        zn = fmin(fmax(s.z[(size_t)d * k + j] + ldexp(1.0, -t) * s.d[(size_t)d * k + j], c.zlb[d]), c.zub[d]);
     } else {
         zn = s.z[(size_t)d * k + j];
     }
@@ -305,7 +345,6 @@ PolishState carve(double* base, int P, int k, int nw, int f32) {
     s.tht = q; q += pk * kTrials;
     s.S = q; q += pk * kMem;
     s.Y = q; q += pk * kMem;
-    s.rho = q; q += (size_t)kk * kMem;
     s.f = q; q += kk;
     s.ft = q; q += (size_t)kk * kTrials;
     s.best_f = q; q += kk;
@@ -329,7 +368,7 @@ PolishState carve(double* base, int P, int k, int nw, int f32) {
 size_t polish_scratch_doubles(int P, int k) {
     const size_t pk = (size_t)P * k;
     const size_t floats = pk * (kTrials + 1) + (size_t)k * (kTrials + 1);
-    return pk * (6 + kTrials + 2 * kMem) + (size_t)k * (kMem + kTrials + 3) + (floats + 1) / 2 + 2 * (size_t)k + 8;
+    return pk * (6 + kTrials + 2 * kMem) + (size_t)k * (kTrials + 3) + (floats + 1) / 2 + 2 * (size_t)k + 8;
 }
 
 size_t polish_ckpt_floats(int n_max, int k) {
@@ -360,7 +399,7 @@ cudaError_t launch_polish(const PolishWin* tab, int nw, int n_max, const WindowD
     (void)cudaGetLastError();
     const unsigned grid = (unsigned)((kk + 127) / 128);
     const unsigned grid_warps = (unsigned)((32 * (size_t)kk + 127) / 128);  // a warp per candidate
-    polish_init_kernel<<<grid, 128, 0, st>>>(s, tab, keys, c.logmask);
+    polish_init_kernel<<<grid, 128, 0, st>>>(s, tab, keys, c);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = grad_at_slot0();
     if (e == cudaSuccess) {
