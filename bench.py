@@ -496,19 +496,19 @@ def run_stability(args, rank, world):
 
     def step():
         res = batch.calibrate()
-        bands = []
+        bands, pbands = [], []
         for t in range(len(c["windows_T"])):
             th = np.array([r["theta"] for r in res[t * reps:(t + 1) * reps]])
             w = wins[t * reps]
-            bands.append(sird.ensemble_bands(w["yD"], w["N"], th, c["horizon"], c["fractions"], K=1,
-                                             beta_form=sird.BETA_RAMP, R0=w["R0"], I0=w["I0"], fit_I0=fit_I0,
-                                             spd=c["spd"], stream=stream))
-        return res, bands
+            kw = dict(K=1, beta_form=sird.BETA_RAMP, R0=w["R0"], I0=w["I0"], fit_I0=fit_I0, spd=c["spd"], stream=stream)
+            bands.append(sird.ensemble_bands(w["yD"], w["N"], th, c["horizon"], c["fractions"], **kw))
+            pbands.append(sird.parameter_bands(w["yD"], w["N"], th, c["fractions"], **kw))
+        return res, bands, pbands
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
-    total_ms, kern_ms, clocks, (res, bands) = timed_steps(args, world, stream, step, ev)
+    total_ms, kern_ms, clocks, (res, bands, pbands) = timed_steps(args, world, stream, step, ev)
     # end to end: every step also uploads all windows' D, I, R series from host memory
     y_host = np.concatenate([np.concatenate([w["yD"], w["yI"], w["yR"]]) for w in wins])
     e2e, h2d = [], 0
@@ -536,9 +536,11 @@ def run_stability(args, rank, world):
             b = bands[t][q][days]
             cover[q] = {"inside_95": float(np.mean((b[:, 1] <= rep_) & (rep_ <= b[:, 2]))),
                         "median_max_rel_err": float(np.max(np.abs(b[:, 0] - rep_) / np.abs(rep_)))}
-        th = np.array([r["theta"] for r in res[t * reps:(t + 1) * reps]])
+        names = ["beta1", "beta2", "t1", "t2", "gamma", "mu"] + ([] if not fit_I0 else ["I0"])
+        cols = ["median"] + [f"{e}_{int(round(100 * f))}" for f in c["fractions"] for e in ("low", "high")]
         held[f"window_day_{T}"] = {"extension_vs_reported": cover,
-                                   "theta_median": np.median(th, axis=0).tolist(),
+                                   "parameter_bands": {n: dict(zip(cols, map(float, pbands[t][i])))
+                                                       for i, n in enumerate(names)},
                                    "beta_R0_last_day_median": [float(bands[t]["beta"][L, 0]),
                                                                float(bands[t]["R0"][L, 0])]}
     return {
@@ -557,10 +559,14 @@ def run_stability(args, rank, world):
                      "avg_launch_us": kms * 1e3, "flops_per_launch": flops,
                      "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
         "e2e": {"value": units * args.steps * world / (e2e_total / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": h2d + 2 * reps * 7 * 8,
-                "d2h_bytes_per_step": len(wins) * BATCH_OUT_BYTES + 2 * 6 * (c["L"] + 1 + c["horizon"]) * 7 * 8,
+                # per window: theta ([reps][P] doubles) for each of the two band calls, the bands back
+                "h2d_bytes_per_step": h2d + len(c["windows_T"]) * 2 * reps * len(lb) * 8,
+                "d2h_bytes_per_step": len(wins) * BATCH_OUT_BYTES + len(c["windows_T"]) * (
+                    6 * (c["L"] + 1 + c["horizon"]) + len(lb)) * (1 + 2 * len(c["fractions"])) * 8,
                 "ms_per_step": e2e_total / args.steps},
-        "gpu_launches": args.steps * (2 + 2 * 2),
+        # the batch and its re-evaluation; per window two kernels of the ensemble bands and two of
+        # the parameter bands (the ramp's change times ordered, then the sort)
+        "gpu_launches": args.steps * (2 + len(c["windows_T"]) * 4),
         "clocks": clocks,
         "result": held,
         **({} if args.no_cpu_baseline else {"cpu_baseline": cpu_baseline("stability", budget_s=args.cpu_budget)}),

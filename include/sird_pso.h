@@ -341,6 +341,22 @@ sird_status sird_forecast(const sird_problem* problem, const double* theta, int 
 sird_status sird_ensemble_bands(const sird_problem* problem, const double* theta, int k, int horizon,
                                 const double* fractions, int n_bands, double* out, void* cuda_stream);
 
+/*
+ * Stability of the fitted parameters over repeated calibrations (Sec. 4.2): for k parameter
+ * vectors (host, row-major [k][P]) the median and the central bands of each parameter, with the
+ * order statistics of sird_ensemble_bands (median: the middle value, or the mean of the two
+ * middle ones for even k; band b: the sorted values at floor(k (1 - fractions[b]) / 2) from either
+ * end).  The parameters in theta's order: beta_1 .. beta_K (PWC) or beta1, beta2, t1, t2 (ramp),
+ * then gamma, mu and, when fitted, I0; the ramp's change times enter as t1 = min(t_a, t_b) and
+ * t2 = max(t_a, t_b), the order in which the model uses them.
+ *   out (host) [P][1 + 2 n_bands]: median, low_0, high_0, low_1, high_1, ...
+ * k in 1..4096, n_bands in 0..16.  Blocks until out is written.  SIRD_ERR_ARG on a bad problem
+ * (it names the model form), NULL pointers, sizes out of range, a fraction outside (0, 1] or a
+ * non-finite theta; SIRD_ERR_NOMEM when memory runs out; SIRD_ERR_CUDA on a failed launch or copy.
+ */
+sird_status sird_parameter_bands(const sird_problem* problem, const double* theta, int k, const double* fractions,
+                                 int n_bands, double* out, void* cuda_stream);
+
 /* ---------------------------------------------------------------- batched */
 
 /*

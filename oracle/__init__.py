@@ -249,6 +249,12 @@ def forecast(pb: Problem, theta, horizon: int) -> np.ndarray:
     return out
 
 
+def _band_drops(k: int, fractions) -> list:
+    """Sorted values the central band holding the fraction f of k values leaves out at either end:
+    floor(k (1 - f) / 2) (the small offset keeps e.g. k = 1000, f = 0.9 at exactly 50)."""
+    return [int(np.floor(k * (1.0 - f) / 2.0 + 1e-9)) for f in fractions]
+
+
 def ensemble_bands(pb: Problem, thetas, horizon: int, fractions=(0.95, 0.9, 0.5)) -> dict:
     """Per-day summaries of an ensemble of parameter vectors (Sec. 4.2): each member simulated
     over the window and `horizon` more days; per day the values of beta(t) (at the day's first
@@ -268,7 +274,7 @@ def ensemble_bands(pb: Problem, thetas, horizon: int, fractions=(0.95, 0.9, 0.5)
         vals["R0"][:, j] = beta / (th[j, gi] + th[j, gi + 1])
         for q in "SIRD":
             vals[q][:, j] = tr[q]
-    drops = [int(np.floor(k * (1.0 - f) / 2.0 + 1e-9)) for f in fractions]
+    drops = _band_drops(k, fractions)
     out = {}
     for q, v in vals.items():
         v = np.sort(v, axis=1)
@@ -277,6 +283,32 @@ def ensemble_bands(pb: Problem, thetas, horizon: int, fractions=(0.95, 0.9, 0.5)
         for dr in drops:
             cols += [v[:, dr], v[:, k - 1 - dr]]
         out[q] = np.stack(cols, axis=1)
+    return out
+
+
+def parameter_bands(pb: Problem, thetas, fractions=(0.95, 0.9, 0.5)) -> np.ndarray:
+    """Stability of the fitted parameters over repeated calibrations (Sec. 4.2): for each
+    parameter, its values over the k members sorted, the median (mean of the two middle values for
+    an even count) and, for each fraction f, the central band that leaves floor(k (1 - f) / 2)
+    sorted values out at either end -- the summary ensemble_bands gives per day.  The ramp's change
+    times enter as t1 = min and t2 = max of the pair, the order the model uses them in (eq. (beta)).
+    Returns [P, 1 + 2 len(fractions)] with columns median, low_0, high_0, ..."""
+    th = np.array(np.atleast_2d(_f64(thetas)), dtype=np.float64)
+    k, P = th.shape
+    if P != pb.n_params:
+        raise ValueError(f"thetas must be [k, {pb.n_params}]")
+    if pb.beta_form == BETA_RAMP:
+        ta, tb = th[:, 2].copy(), th[:, 3].copy()
+        th[:, 2] = np.minimum(ta, tb)
+        th[:, 3] = np.maximum(ta, tb)
+    drops = _band_drops(k, fractions)
+    out = np.zeros((P, 1 + 2 * len(drops)))
+    for d in range(P):
+        v = np.sort(th[:, d])
+        out[d, 0] = v[k // 2] if k % 2 else (v[k // 2 - 1] + v[k // 2]) * 0.5
+        for b, dr in enumerate(drops):
+            out[d, 1 + 2 * b] = v[dr]
+            out[d, 2 + 2 * b] = v[k - 1 - dr]
     return out
 
 

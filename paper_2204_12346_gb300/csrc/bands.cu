@@ -5,6 +5,10 @@
 // for beta(t), the basic reproduction number R0(t) = beta(t) / (gamma + mu) and the compartments
 // over the window and its extension past the last day (the last transmission rate, gamma, mu).
 //
+// The fitted parameters themselves (beta's segments or the ramp's beta1, beta2, t1, t2, then gamma,
+// mu and a fitted I0) get the same summary over the repetitions: the stability of the estimates
+// is what the repetitions measure.
+//
 // Two kernels: one thread per ensemble member integrates the window and the extension in FP64
 // (the paper's operation order, as the forecast) and writes per day beta, R0, S, I, R, D into
 // [quantity][day][member]; then one block per (day, quantity) sorts the k member values in
@@ -122,7 +126,32 @@ __global__ void __launch_bounds__(kBandsThreads) bands_kernel(const double* __re
     }
 }
 
+// The ramp's two change times form an unordered pair (beta follows the earlier one first), so
+// their bands summarise t1 = min(t_a, t_b) and t2 = max(t_a, t_b): reordered in place in the
+// parameter-major copy theta [P][k].
+__global__ void ramp_times_kernel(double* __restrict__ theta, int k) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= k) return;
+    const double ta = theta[2 * (size_t)k + j], tb = theta[3 * (size_t)k + j];
+    theta[2 * (size_t)k + j] = ta < tb ? ta : tb;
+    theta[3 * (size_t)k + j] = ta < tb ? tb : ta;
+}
+
 }  // namespace
+
+cudaError_t launch_parameter_bands(const ModelDev& m, double* theta, int k, const int* drop, int n_bands, double* out,
+                                   cudaStream_t s) {
+    if (k < 1 || k > kMaxEnsemble) return cudaErrorInvalidValue;
+    (void)cudaGetLastError();
+    if (m.beta_form == BETA_RAMP) {
+        ramp_times_kernel<<<(k + 127) / 128, 128, 0, s>>>(theta, k);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // one "day" per parameter: block (0, d) sorts parameter d's k values
+    bands_kernel<<<dim3(1u, (unsigned)m.P), kBandsThreads, 0, s>>>(theta, k, 1, drop, n_bands, out);
+    return cudaGetLastError();
+}
 
 size_t ensemble_traj_bytes(int k, int n_days) { return (size_t)kBandQuantities * n_days * k * sizeof(double); }
 

@@ -189,6 +189,10 @@ constexpr int kBandQuantities = 6;
 size_t ensemble_traj_bytes(int k, int n_days);
 cudaError_t launch_ensemble_bands(const WindowDev& w, const ModelDev& m, const double* theta, int k, int n_days,
                                   const int* drop, int n_bands, double* traj, double* out, cudaStream_t s);
+// The same summary of the parameters themselves: theta [P][k] (device; the ramp's change times
+// are reordered in place to t1 <= t2) into out [P][1 + 2 n_bands].
+cudaError_t launch_parameter_bands(const ModelDev& m, double* theta, int k, const int* drop, int n_bands, double* out,
+                                   cudaStream_t s);
 
 // L-BFGS polish, for each of the nw windows of tab, of its k candidates named by keys[i * k ..]
 // (personal bests of its FP32 swarm): iters iterations with a parallel line search, trials and

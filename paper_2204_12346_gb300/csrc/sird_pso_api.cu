@@ -854,6 +854,19 @@ extern "C" sird_status sird_forecast(const sird_problem* pb, const double* theta
     }
 }
 
+// Values left out at each end of k sorted ones by the central band holding each fraction:
+// floor(k (1 - f) / 2) (the small offset keeps e.g. k = 1000, f = 0.9 at exactly 50).  False on a
+// fraction outside (0, 1].
+static bool band_drops(int k, const double* fractions, int n_bands, std::vector<int>& drop) {
+    drop.assign(n_bands > 0 ? n_bands : 1, 0);
+    for (int b = 0; b < n_bands; ++b) {
+        const double f = fractions[b];
+        if (!(f > 0.0 && f <= 1.0)) return false;
+        drop[b] = (int)std::floor((double)k * (1.0 - f) / 2.0 + 1e-9);
+    }
+    return true;
+}
+
 static sird_status ensemble_bands_impl(const sird_problem* pb, const double* theta, int k, int horizon,
                                        const double* fractions, int n_bands, double* out, void* cuda_stream) {
     std::string why;
@@ -862,14 +875,9 @@ static sird_status ensemble_bands_impl(const sird_problem* pb, const double* the
     if (!theta || !out || k < 1 || k > kMaxEnsemble || horizon < 0 || horizon > 100000 || n_bands < 0 ||
         n_bands > 16 || (n_bands > 0 && !fractions))
         return g_create_error = "ensemble_bands: bad theta/out/k/horizon/bands", SIRD_ERR_ARG;
-    std::vector<int> drop(n_bands > 0 ? n_bands : 1, 0);
-    for (int b = 0; b < n_bands; ++b) {
-        const double f = fractions[b];
-        if (!(f > 0.0 && f <= 1.0)) return g_create_error = "ensemble_bands: fractions must be in (0, 1]", SIRD_ERR_ARG;
-        // a central band holding the fraction f of the sorted values: floor(k (1 - f) / 2) left out at
-        // each end (the small offset keeps e.g. k = 1000, f = 0.9 at exactly 50)
-        drop[b] = (int)std::floor((double)k * (1.0 - f) / 2.0 + 1e-9);
-    }
+    std::vector<int> drop;
+    if (!band_drops(k, fractions, n_bands, drop))
+        return g_create_error = "ensemble_bands: fractions must be in (0, 1]", SIRD_ERR_ARG;
     WindowDev w{};
     ModelDev m{};
     sird_fill_window(pb, w, m);
@@ -910,6 +918,57 @@ extern "C" sird_status sird_ensemble_bands(const sird_problem* pb, const double*
         return ensemble_bands_impl(pb, theta, k, horizon, fractions, n_bands, out, cuda_stream);
     } catch (const std::bad_alloc&) {
         return g_create_error = "ensemble_bands: host allocation failed", SIRD_ERR_NOMEM;
+    }
+}
+
+static sird_status parameter_bands_impl(const sird_problem* pb, const double* theta, int k, const double* fractions,
+                                        int n_bands, double* out, void* cuda_stream) {
+    std::string why;
+    sird_status st = sird_check_problem(pb, why);
+    if (st != SIRD_OK) return g_create_error = why, st;
+    if (!theta || !out || k < 1 || k > kMaxEnsemble || n_bands < 0 || n_bands > 16 || (n_bands > 0 && !fractions))
+        return g_create_error = "parameter_bands: bad theta/out/k/bands", SIRD_ERR_ARG;
+    std::vector<int> drop;
+    if (!band_drops(k, fractions, n_bands, drop))
+        return g_create_error = "parameter_bands: fractions must be in (0, 1]", SIRD_ERR_ARG;
+    WindowDev w{};
+    ModelDev m{};
+    sird_fill_window(pb, w, m);
+    const int P = m.P, nq = 1 + 2 * n_bands;
+    for (size_t i = 0; i < (size_t)k * P; ++i)
+        if (!std::isfinite(theta[i])) return g_create_error = "parameter_bands: non-finite theta", SIRD_ERR_ARG;
+    const size_t th_bytes = ((size_t)P * k * sizeof(double) + 255) & ~(size_t)255, drop_bytes = 256;
+    const size_t out_count = (size_t)P * nq;
+    std::vector<double> hth((size_t)P * k);
+    for (int j = 0; j < k; ++j)
+        for (int d = 0; d < P; ++d) hth[(size_t)d * k + j] = theta[(size_t)j * P + d];
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    unsigned char* dmem = nullptr;
+    cudaError_t e = cudaMalloc((void**)&dmem, th_bytes + drop_bytes + out_count * sizeof(double));
+    double* dth = (double*)dmem;
+    int* ddrop = (int*)(dmem + th_bytes);
+    double* dout = (double*)(dmem + th_bytes + drop_bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dth, hth.data(), (size_t)P * k * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ddrop, drop.data(), sizeof(int) * drop.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_parameter_bands(m, dth, k, ddrop, n_bands, dout, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, out_count * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dmem);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        g_create_error = std::string("parameter_bands: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? SIRD_ERR_NOMEM : SIRD_ERR_CUDA;
+    }
+    return SIRD_OK;
+}
+
+extern "C" sird_status sird_parameter_bands(const sird_problem* pb, const double* theta, int k,
+                                            const double* fractions, int n_bands, double* out, void* cuda_stream) {
+    TraceRange trace("sird_parameter_bands");
+    try {
+        return parameter_bands_impl(pb, theta, k, fractions, n_bands, out, cuda_stream);
+    } catch (const std::bad_alloc&) {
+        return g_create_error = "parameter_bands: host allocation failed", SIRD_ERR_NOMEM;
     }
 }
 

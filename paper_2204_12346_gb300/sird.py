@@ -31,7 +31,7 @@ EXPORTS = [
     "sird_forecast", "sird_pso_calibrate_batched", "sird_pso_set_observations", "sird_pso_set_timing", "sird_pso_launch_mode",
     "sird_pso_step_f32_noalloc", "sird_pso_topk", "sird_ensemble_bands", "sird_pso_polish", "sird_batch_create", "sird_batch_calibrate", "sird_batch_set_observations", "sird_batch_launch_mode",
     "sird_batch_block_size", "sird_batch_blocks_per_sm", "sird_batch_destroy", "sird_batch_set_timing",
-    "sird_batch_polish",
+    "sird_batch_polish", "sird_parameter_bands",
     "sird_pso_topk_indexed", "sird_pso_set_shard", "sird_pso_shard_best", "sird_pso_set_gbest",
 ]
 
@@ -104,6 +104,7 @@ def lib():
         L.sird_loss_grad.argtypes = [vp, vp, ip, ip, vp, vp, ip, vp, ip, ip]
         L.sird_forecast.argtypes = [C.POINTER(Problem), dp, ip, ip, dp, ip, vp]
         L.sird_ensemble_bands.argtypes = [C.POINTER(Problem), dp, ip, ip, dp, ip, dp, vp]
+        L.sird_parameter_bands.argtypes = [C.POINTER(Problem), dp, ip, dp, ip, dp, vp]
         L.sird_pso_calibrate_batched.argtypes = [ip, C.POINTER(Problem), C.POINTER(Config), vp, C.POINTER(Result)]
         L.sird_pso_set_observations.argtypes = [vp, dp, ip]
         L.sird_pso_set_timing.argtypes = [vp, vp, vp]
@@ -567,6 +568,26 @@ def ensemble_bands(yD, N, theta, horizon, fractions=(0.95, 0.9, 0.5), *, K=1, sp
     if st != OK:
         raise SirdError(st, L.sird_last_error(None).decode())
     return {q: out[i] for i, q in enumerate(BAND_QUANTITIES)}
+
+
+def parameter_bands(yD, N, theta, fractions=(0.95, 0.9, 0.5), *, K=1, spd=10, R0=0.0, I0=0.0, fit_I0=True,
+                    beta_form=BETA_PWC, stream=None) -> np.ndarray:
+    """Median and central bands of each parameter over an ensemble of parameter vectors ([k, P];
+    the ramp's change times as t1 <= t2): [P, 1 + 2 len(fractions)] with columns median, low_0,
+    high_0, low_1, high_1, ..."""
+    L = lib()
+    pb, keep = make_problem(yD, N, K, spd, R0, I0, fit_I0, beta_form)
+    P = n_params(K, beta_form, fit_I0)
+    th = _f64(np.atleast_2d(theta))
+    if th.ndim != 2 or th.shape[1] != P:
+        raise ValueError(f"theta must be [k, {P}]")
+    fr = _f64(fractions)
+    out = np.zeros((P, 1 + 2 * len(fr)))
+    st = L.sird_parameter_bands(C.byref(pb), _dptr(th), th.shape[0], _dptr(fr), len(fr), _dptr(out),
+                                C.c_void_p(current_stream_handle(stream)))
+    if st != OK:
+        raise SirdError(st, L.sird_last_error(None).decode())
+    return out
 
 
 def check_noalloc_buffers(P, M, n_obs, obs, x, v, pbest, pbest_f, gbest, gbest_index=None, require_cuda=True):

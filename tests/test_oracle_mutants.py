@@ -133,6 +133,12 @@ MUTANTS = [
     ("bands_low_index", PY_SRC, "cols += [v[:, dr], v[:, k - 1 - dr]]", "cols += [v[:, min(dr + 1, k - 1)], v[:, k - 1 - dr]]"),
     ("bands_gamma_index", PY_SRC, "gi = 4 if pb.beta_form == BETA_RAMP else pb.K", "gi = 4 if pb.beta_form == BETA_RAMP else pb.K - 1"),
     ("bands_high_index", PY_SRC, "v[:, k - 1 - dr]", "v[:, k - dr - 2 if k - dr - 2 >= 0 else 0]"),
+    # the parameter bands of Sec. 4.2
+    ("pbands_median_upper_middle", PY_SRC, "(v[k // 2 - 1] + v[k // 2]) * 0.5", "v[k // 2]"),
+    ("pbands_low_index", PY_SRC, "out[d, 1 + 2 * b] = v[dr]", "out[d, 1 + 2 * b] = v[min(dr + 1, k - 1)]"),
+    ("pbands_high_index", PY_SRC, "out[d, 2 + 2 * b] = v[k - 1 - dr]", "out[d, 2 + 2 * b] = v[max(k - 2 - dr, 0)]"),
+    ("pbands_ramp_times_unordered", PY_SRC, "th[:, 2] = np.minimum(ta, tb)", "th[:, 2] = ta"),
+    ("pbands_ramp_end_unordered", PY_SRC, "th[:, 3] = np.maximum(ta, tb)", "th[:, 3] = tb"),
 ]
 
 

@@ -575,3 +575,68 @@ def test_ensemble_bands_beta_is_the_ramp_at_each_day(orc):
     t = np.arange(31 + 5, dtype=float)
     want = np.where(t < t1, b1, np.where(t < t2, b1 + (b2 - b1) * (t - t1) / (t2 - t1), b2))
     assert np.allclose(b["beta"][:, 0], want, rtol=1e-14, atol=0)
+
+
+# ---------------------------------------------------------------- parameter bands (Sec. 4.2)
+
+def test_parameter_bands_of_shuffled_ranks(orc):
+    # each parameter's k = 1000 values are c_d + 1 .. c_d + 1000 in a random order: the median is
+    # c_d + 500.5 and the band holding f leaves floor(1000 (1 - f) / 2) = 25, 50, 250 values out
+    s = synth.load_series("30d")
+    pb = orc.Problem(yD=s["yD"], N=s["N"], K=2, spd=10)
+    rng = np.random.default_rng(8)
+    c = np.array([0.0, 10.0, -3.0, 1e4, 0.5])
+    th = np.stack([c[d] + rng.permutation(np.arange(1, 1001, dtype=float)) for d in range(5)], axis=1)
+    b = orc.parameter_bands(pb, th, fractions=(0.95, 0.9, 0.5))
+    assert b.shape == (5, 7)
+    want = np.array([500.5, 26, 975, 51, 950, 251, 750])
+    for d in range(5):
+        assert np.array_equal(b[d], c[d] + want), d
+
+
+def test_parameter_bands_odd_count_and_whole_band(orc):
+    # k = 7: the median is the 4th smallest; f = 1 keeps every value (the band is min .. max);
+    # f = 0.5 leaves floor(7 * 0.25) = 1 out at each end
+    s = synth.load_series("30d")
+    pb = orc.Problem(yD=s["yD"], N=s["N"], K=1, spd=10, fit_I0=False)
+    v = np.array([0.9, 0.1, 0.5, 0.7, 0.3, 1.3, 1.1])
+    th = np.stack([v, 2 * v, -v], axis=1)
+    b = orc.parameter_bands(pb, th, fractions=(1.0, 0.5))
+    assert np.array_equal(b[0], [0.7, 0.1, 1.3, 0.3, 1.1])
+    assert np.array_equal(b[1], 2 * b[0])
+    assert np.array_equal(b[2], [-0.7, -1.3, -0.1, -1.1, -0.3])
+
+
+def test_parameter_bands_count_definition_on_random_values(orc):
+    # brute force: with distinct values, band b's low end has exactly drop_b values below it and
+    # its high end exactly drop_b above; the even-count median lies between two order statistics
+    s = synth.load_series("30d")
+    pb = orc.Problem(yD=s["yD"], N=s["N"], K=1, spd=10)
+    rng = np.random.default_rng(9)
+    for k in (1, 2, 3, 40, 999):
+        th = rng.normal(size=(k, 4))
+        fr = (0.95, 0.9, 0.5)
+        b = orc.parameter_bands(pb, th, fractions=fr)
+        for d in range(4):
+            x = th[:, d]
+            for i, f in enumerate(fr):
+                drop = int(np.floor(k * (1 - f) / 2 + 1e-9))
+                assert np.sum(x < b[d, 1 + 2 * i]) == drop and np.sum(x > b[d, 2 + 2 * i]) == drop
+            assert np.sum(x < b[d, 0]) == k // 2  # the middle value, or strictly between the two
+            if k % 2:
+                assert b[d, 0] in x
+
+
+def test_parameter_bands_ramp_change_times_in_model_order(orc):
+    # the ramp's change times are an unordered pair: t1 summarises min(t_a, t_b), t2 the max
+    s = synth.load_series("30d")
+    pb = orc.Problem(yD=s["yD"], N=s["N"], beta_form=orc.BETA_RAMP, spd=10)
+    k = 5
+    ta = np.array([3.0, 20.0, 4.0, 18.0, 5.0])
+    tb = np.array([15.0, 2.0, 16.0, 1.0, 17.0])
+    th = np.column_stack([np.full(k, 0.3), np.full(k, 0.1), ta, tb, np.full(k, 0.1), np.full(k, 2e-3),
+                          np.full(k, 1e4)])
+    b = orc.parameter_bands(pb, th, fractions=(1.0,))
+    assert np.array_equal(b[2], [3.0, 1.0, 5.0])  # sorted minima 1, 2, 3, 4, 5
+    assert np.array_equal(b[3], [17.0, 15.0, 20.0])  # sorted maxima 15, 16, 17, 18, 20
+    assert np.array_equal(b[0], [0.3, 0.3, 0.3])
