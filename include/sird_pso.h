@@ -381,8 +381,8 @@ sird_status sird_parameter_bands(const sird_problem* problem, const double* thet
  * SIRD_TUNE_VERBOSE=1 every candidate's time goes to stderr);
  * otherwise a multiple of 32 in 32..1024 with as many blocks per SM as fit, in the form
  * configs[0].launch_mode names (SIRD_LAUNCH_FLAT, else one window per block).  The kernels are
- * compiled for at most 768 threads per block (PWC beta, F_D) or 384 (the ramp, F_IRD); a larger
- * block_size is refused with SIRD_ERR_ARG.
+ * compiled for at most 768 threads per block one window per block and 512 flat (PWC beta, F_D),
+ * or 384 in both forms (the ramp, F_IRD); a larger block_size is refused with SIRD_ERR_ARG.
  */
 typedef struct sird_batch* sird_batch_t;
 sird_status sird_batch_create(int W, const sird_problem* problems, const sird_pso_config* configs, void* cuda_stream,

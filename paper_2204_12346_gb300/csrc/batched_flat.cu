@@ -59,7 +59,7 @@ __device__ __forceinline__ bool flat_grid_sync(const FlatScratch& fs, unsigned s
 }
 
 template <int SPD, int COST>
-__global__ void __launch_bounds__(batch_launch_bound(COST)) pso_flat_f32(const BatchWindow* __restrict__ wins,
+__global__ void __launch_bounds__(flat_launch_bound(COST)) pso_flat_f32(const BatchWindow* __restrict__ wins,
                                                     const int* __restrict__ n_items_w,
                                                     const int4* __restrict__ items, int n_items, ModelDev m,
                                                     PsoCoeffs<float> c, const float* __restrict__ yf_all,

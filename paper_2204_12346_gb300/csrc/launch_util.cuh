@@ -43,6 +43,9 @@ inline unsigned grid_for_pairs(int M, int block) { return grid_for(M, 2 * block)
 // F_D, 384 (up to 168) for the ramp and for F_IRD, whose per-step coefficients and three misfits
 // need more registers than 80.
 __host__ __device__ constexpr int batch_launch_bound(int variant) { return variant_form(variant) == 0 ? 768 : 384; }
+// The flat form keeps its items' window constants in registers as well: 512 threads (128
+// registers) for PWC beta and F_D, so that it runs without spilling.
+__host__ __device__ constexpr int flat_launch_bound(int variant) { return variant_form(variant) == 0 ? 512 : 384; }
 
 // Blocks of `block` threads a kernel can keep per SM; 0 when the block exceeds the kernel's
 // compiled limit (its launch bound) or anything else fails.

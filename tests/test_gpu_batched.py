@@ -153,7 +153,7 @@ def test_paper_layout_against_the_oracle_at_initialisation():
         assert res[i]["loss"] == O.loss(pb, res[i]["theta"])
 
 
-@pytest.mark.parametrize("block", [128, 256, 768])
+@pytest.mark.parametrize("block", [128, 256, 512])
 def test_flat_form_equals_one_window_per_block(block):
     # every window's swarm spread over the grid (one grid barrier per iteration) gives the same
     # swarms as one window per block: same Philox counters and arithmetic per particle
@@ -168,6 +168,8 @@ def test_flat_form_equals_one_window_per_block(block):
     for x, y, z in zip(a, b, b2):
         assert x["index"] == y["index"] == z["index"] and x["loss_search"] == y["loss_search"] == z["loss_search"]
         assert x["loss"] == y["loss"] and np.array_equal(x["theta"], y["theta"])
+    with pytest.raises(sird.SirdError, match="flat"):  # above the flat form's launch bound
+        sird.Batch(wins, iters=2, block_size=768, launch_mode=sird.LAUNCH_FLAT, **kw)
 
 
 def test_flat_form_ramp_ird_and_mape():
