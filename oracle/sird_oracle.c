@@ -265,6 +265,31 @@ static void cost_grad_D(const orc_problem* pb, const double* Dh, double* gD) {
     }
 }
 
+/* dC/dyhat_i of one series' low-level cost C (as low_level_cost computes it) over the errors
+ * e_i = (y_i - yhat_i) / scale: MSE -2 e_i / (n scale), MAE -sign(e_i) / (n scale), MXSE
+ * -2 e_i / scale at the first day with the largest e^2 (none when every e is 0), MAPE
+ * -100 sign(y_i - yhat_i) / (|y_i| kept) on the days with y_i != 0. */
+static void cost_grad_series(int cost, int n, const double* y, const double* yhat, double scale, double* g) {
+    int kept = 0, imax = -1;
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (y[i] != 0.0) kept++;
+        double e = (y[i] - yhat[i]) / scale;
+        if (e * e > acc) { acc = e * e; imax = i; }
+    }
+    for (int i = 0; i < n; ++i) {
+        double e = (y[i] - yhat[i]) / scale;
+        double s = (e > 0.0) - (e < 0.0);
+        switch (cost) {
+            case ORC_MSE: g[i] = -2.0 * e / ((double)n * scale); break;
+            case ORC_MAE: g[i] = -s / ((double)n * scale); break;
+            case ORC_MAPE: g[i] = (y[i] != 0.0 && kept > 0) ? -100.0 * s / (fabs(y[i]) * (double)kept) : 0.0; break;
+            case ORC_MXSE: g[i] = (i == imax) ? -2.0 * e / scale : 0.0; break;
+            default: g[i] = NAN;
+        }
+    }
+}
+
 /* d beta(t_k) / d theta for the ramp form (only the four beta-form entries). */
 static void ramp_dbeta(const orc_problem* pb, const double* theta, long k, double dbeta[4]) {
     double b1 = theta[0], b2 = theta[1];
@@ -291,15 +316,16 @@ static void ramp_dbeta(const orc_problem* pb, const double* theta, long k, doubl
 }
 
 double orc_loss_grad(const orc_problem* pb, const double* theta, double* g_theta, double* g_u0) {
-    if (pb->objective != ORC_FIT_D) return NAN;
     int n = pb->n_obs, spd = pb->spd, P = orc_nparams(pb);
     long steps = (long)(n - 1) * spd;
     double dt = 1.0 / (double)spd;
     double gamma = theta[idx_gamma(pb)], mu = theta[idx_mu(pb)];
     double* U = (double*)malloc(sizeof(double) * 4 * (size_t)(steps + 1));
-    double* Dh = (double*)malloc(sizeof(double) * n);
-    double* gD = (double*)malloc(sizeof(double) * n);
-    if (!U || !Dh || !gD) { free(U); free(Dh); free(gD); return NAN; }
+    double* Yh = (double*)malloc(sizeof(double) * 3 * (size_t)n);   /* Ihat | Rhat | Dhat per day */
+    double* gY = (double*)calloc(3 * (size_t)n, sizeof(double));    /* dL/dIhat | dL/dRhat | dL/dDhat */
+    if (!U || !Yh || !gY) { free(U); free(Yh); free(gY); return NAN; }
+    double *Ih = Yh, *Rh = Yh + n, *Dh = Yh + 2 * n;
+    double *gI = gY, *gR = gY + n, *gD = gY + 2 * n;
 
     /* forward sweep, keeping every state */
     initial_state(pb, theta, U);
@@ -307,13 +333,38 @@ double orc_loss_grad(const orc_problem* pb, const double* theta, double* g_theta
         memcpy(U + 4 * (k + 1), U + 4 * k, 4 * sizeof(double));
         euler_step(pb->N, orc_beta(pb, theta, k, steps), gamma, mu, dt, U + 4 * (k + 1));
     }
-    for (int i = 0; i < n; ++i) Dh[i] = U[4 * ((long)i * spd) + 3];
-    double L = low_level_cost(pb->cost, n, pb->yD, Dh, 1.0);
-    cost_grad_D(pb, Dh, gD);
+    for (int i = 0; i < n; ++i) {
+        Ih[i] = U[4 * ((long)i * spd) + 1];
+        Rh[i] = U[4 * ((long)i * spd) + 2];
+        Dh[i] = U[4 * ((long)i * spd) + 3];
+    }
+    double L;
+    if (pb->objective == ORC_FIT_D) {
+        L = low_level_cost(pb->cost, n, pb->yD, Dh, 1.0);
+        cost_grad_D(pb, Dh, gD);
+    } else {
+        /* F_IRD^C = max(C_I, C_R, C_D) (Sec. 3.1): the gradient of the compartment that attains
+         * the maximum (the first of I, R, D on ties), as loss_from_days picks it; each error
+         * divided by its reported range, MAPE unnormalised. */
+        int mape = pb->cost == ORC_MAPE;
+        double sI = mape ? 1.0 : series_range(n, pb->yI);
+        double sR = mape ? 1.0 : series_range(n, pb->yR);
+        double sD = mape ? 1.0 : series_range(n, pb->yD);
+        double cI = low_level_cost(pb->cost, n, pb->yI, Ih, sI);
+        double cR = low_level_cost(pb->cost, n, pb->yR, Rh, sR);
+        double cD = low_level_cost(pb->cost, n, pb->yD, Dh, sD);
+        int which = 0;
+        L = cI;
+        if (cR > L) { L = cR; which = 1; }
+        if (cD > L) { L = cD; which = 2; }
+        if (which == 0) cost_grad_series(pb->cost, n, pb->yI, Ih, sI, gI);
+        else if (which == 1) cost_grad_series(pb->cost, n, pb->yR, Rh, sR, gR);
+        else cost_grad_series(pb->cost, n, pb->yD, Dh, sD, gD);
+    }
 
     /* reverse sweep: lambda_k = lambda_{k+1} + dt (df/du)^T lambda_{k+1} + dL/du_k */
     for (int j = 0; j < P; ++j) g_theta[j] = 0.0;
-    double lS = 0.0, lI = 0.0, lR = 0.0, lD = gD[n - 1];
+    double lS = 0.0, lI = gI[n - 1], lR = gR[n - 1], lD = gD[n - 1];
     for (long k = steps - 1; k >= 0; --k) {
         const double* u = U + 4 * k;
         double S = u[0], I = u[1];
@@ -335,11 +386,15 @@ double orc_loss_grad(const orc_problem* pb, const double* theta, double* g_theta
         double nI = lI + dt * (-b * S * lS + (b * S - gamma - mu) * lI + gamma * lR + mu * lD);
         lS = nS;
         lI = nI;
-        if (k % spd == 0) lD += gD[k / spd];
+        if (k % spd == 0) {
+            lI += gI[k / spd];
+            lR += gR[k / spd];
+            lD += gD[k / spd];
+        }
     }
     if (pb->fit_I0) g_theta[idx_I0(pb)] = lI - lS; /* S0 = N - I0 - R0 - D0 */
     if (g_u0) { g_u0[0] = lS; g_u0[1] = lI; g_u0[2] = lR; g_u0[3] = lD; }
-    free(U); free(Dh); free(gD);
+    free(U); free(Yh); free(gY);
     return L;
 }
 

@@ -98,8 +98,9 @@ double orc_loss(const orc_problem* pb, const double* theta);
 double orc_r2_D(const orc_problem* pb, const double* theta);
 
 /*
- * Gradient of the discrete loss (F_D with MSE, MAE, MAPE or MXSE; sub-gradients
- * where the cost is not smooth) by the discrete adjoint of the Euler map.
+ * Gradient of the discrete loss (F_D or F_IRD with MSE, MAE, MAPE or MXSE; sub-gradients
+ * where the cost is not smooth, F_IRD's max through the compartment that attains it) by the
+ * discrete adjoint of the Euler map.
  * g_theta[P] = dL/dtheta.  g_u0[4] = dL/d(S0, I0, R0, D0) taking the four
  * initial values as independent.  Returns the loss.
  */

@@ -63,8 +63,8 @@ MUTANTS = [
     ("adjoint_gamma_term", C_SRC, "+= dt * I * (lR - lI);", "+= dt * I * (lD - lI);"),
     ("adjoint_state_swapped", C_SRC, "+ gamma * lR + mu * lD);", "+ gamma * lD + mu * lR);"),
     ("adjoint_drops_S_term", C_SRC, "double nI = lI + dt * (-b * S * lS + ", "double nI = lI + dt * ("),
-    ("adjoint_observation_index", C_SRC, "if (k % spd == 0) lD += gD[k / spd];",
-     "if (k % spd == 0) lD += gD[k / spd + 1];"),
+    ("adjoint_observation_index", C_SRC, "lD += gD[k / spd];", "lD += gD[k / spd + 1];"),
+    ("adjoint_ird_I_observation_index", C_SRC, "lI += gI[k / spd];", "lI += gI[k / spd + 1];"),
     ("adjoint_I0_drops_S0", C_SRC, "g_theta[idx_I0(pb)] = lI - lS;", "g_theta[idx_I0(pb)] = lI;"),
     ("adjoint_ramp_t1", C_SRC, "d_t1 = (b2 - b1) * (t - t2) / (len * len);",
      "d_t1 = (b2 - b1) * (t - t1) / (len * len);"),
@@ -125,6 +125,16 @@ MUTANTS = [
     ("nan_loss_not_infinite", C_SRC, "return isnan(f) ? INFINITY : f;", "return f;"),
     ("pso_particle_offset_ignored", C_SRC, "(uint32_t)p + cfg->p_offset", "(uint32_t)p"),
     ("store_f32_ignored", C_SRC, "return cfg->store_f32 ? (double)(float)x : x;", "return x;"),
+    # the F_IRD^C gradient
+    ("ird_grad_drops_R_injection", C_SRC, "lR += gR[k / spd];", "(void)0;"),
+    ("ird_grad_I_unscaled", C_SRC, "cost_grad_series(pb->cost, n, pb->yI, Ih, sI, gI)",
+     "cost_grad_series(pb->cost, n, pb->yI, Ih, 1.0, gI)"),
+    ("ird_grad_mxse_unscaled", C_SRC, "-2.0 * e / scale : 0.0", "-2.0 * e : 0.0"),
+    ("ird_grad_mse_scaled_once", C_SRC, "-2.0 * e / ((double)n * scale)", "-2.0 * e / (double)n"),
+    ("ird_grad_last_day_of_I", C_SRC, "lI = gI[n - 1]", "lI = 0.0"),
+    ("ird_grad_never_I", C_SRC, "if (which == 0) cost_grad_series", "if (0) cost_grad_series"),
+    ("ird_grad_mae_sign", C_SRC, "case ORC_MAE: g[i] = -s / ((double)n * scale); break;",
+     "case ORC_MAE: g[i] = s / ((double)n * scale); break;"),
     # the ensemble bands of Sec. 4.2
     ("bands_median_upper_middle", PY_SRC, "(v[:, k // 2 - 1] + v[:, k // 2]) * 0.5", "v[:, k // 2]"),
     ("bands_R0_drops_mu", PY_SRC, "beta / (th[j, gi] + th[j, gi + 1])", "beta / th[j, gi]"),

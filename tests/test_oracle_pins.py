@@ -308,6 +308,76 @@ def test_adjoint_matches_central_fd(orc, form, cost):
     assert np.all(np.abs(g - fd) <= 2e-5 * scale), (g, fd)
 
 
+def _ird_problem(orc, form, cost, dominant, fit_I0):
+    # reported series from the trajectory at the evaluation point with 0.2% noise, one compartment
+    # moved 5-8% off it so that its normalised cost is the largest of the three (Sec. 3.1,
+    # F_IRD^C = max over I, R, D); returns the problem, theta and the compartment costs
+    ser = synth.load_series("60d")
+    days, R0 = 35, 800.0
+    if form == "pwc":
+        ref = [0.23, 0.19, 0.17, 0.13, 0.1, 0.002, 1.1e4]
+        kw = dict(K=4)
+    else:
+        ref = [0.25, 0.14, 9.5, 24.25, 0.1, 0.002, 1.1e4]
+        kw = dict(beta_form=orc.BETA_RAMP)
+    th = np.array(ref) * (1 + 0.03 * np.sin(np.arange(len(ref)) + 1.0))
+    base = orc.Problem(yD=np.zeros(days + 1), N=ser["N"], R0=R0, spd=10, **kw)
+    tr = orc.simulate(base, th, days)
+    rng = np.random.default_rng(3)
+    wob = lambda v, a: v * (1 + a * rng.normal(size=v.size))
+    yI = wob(tr["I"], 2e-3)
+    yR = R0 + wob(tr["R"] - R0, 2e-3)
+    yD = tr["D"][0] + wob(tr["D"] - tr["D"][0], 2e-3)
+    t = np.linspace(0.0, 1.0, days + 1)
+    if dominant == "I":
+        yI = yI * (1 + 0.08 * t)
+    elif dominant == "R":
+        yR = R0 + (yR - R0) * (1 + 0.08 * t)
+    else:
+        yD = yD + 0.08 * t * (yD - yD[0])
+    pb = orc.Problem(yD=yD, yI=yI, yR=yR, N=ser["N"], R0=R0, I0=float(yI[0]), fit_I0=fit_I0, spd=10,
+                     objective=orc.FIT_IRD, cost=orc.COSTS[cost], **kw)
+    th = th if fit_I0 else th[:-1]
+    tr = orc.simulate(pb, th, days)
+    costs = []
+    for y, yh in ((yI, tr["I"]), (yR, tr["R"]), (yD, tr["D"])):
+        if pb.cost == orc.MAPE:
+            m = y != 0
+            costs.append(100 * np.mean(np.abs((y[m] - yh[m]) / y[m])))
+        else:
+            e = (y - yh) / (y.max() - y.min())
+            costs.append({orc.MSE: np.mean(e * e), orc.MAE: np.mean(np.abs(e)), orc.MXSE: np.max(e * e)}[pb.cost])
+    return pb, th, costs
+
+
+@pytest.mark.parametrize("form,cost,dominant,fit_I0", [
+    ("pwc", "mse", "I", True), ("pwc", "mse", "R", True), ("pwc", "mse", "D", True),
+    ("pwc", "mae", "R", True), ("pwc", "mape", "D", True), ("pwc", "mxse", "I", True),
+    ("ramp", "mxse", "I", False), ("ramp", "mxse", "R", False), ("ramp", "mxse", "D", False),
+    ("ramp", "mse", "D", False), ("ramp", "mape", "I", False), ("ramp", "mae", "D", True)])
+def test_adjoint_f_ird_matches_central_fd(orc, form, cost, dominant, fit_I0):
+    pb, th, costs = _ird_problem(orc, form, cost, dominant, fit_I0)
+    assert "IRD"[int(np.argmax(costs))] == dominant and max(costs) > 2 * sorted(costs)[1], costs
+    L, g, gu = orc.loss_grad(pb, th)
+    assert L == orc.loss(pb, th)
+    fd = np.array([_fd(orc, pb, th, j) for j in range(len(th))])
+    scale = np.abs(fd) + 1e-6 * np.max(np.abs(fd))
+    assert np.all(np.abs(g - fd) <= 2e-5 * scale), (g, fd)
+
+
+def test_adjoint_f_ird_initial_state_gradient(orc):
+    # R0 enters the recovered series (R = R0 + ...) and S0 = N - I0 - R0 - D0
+    pb, th, _ = _ird_problem(orc, "ramp", "mse", "R", False)
+
+    def L_of(R0):
+        return orc.loss(orc.Problem(**{**pb.__dict__, "R0": R0, "_keep": []}), th)
+
+    h = 1e-1
+    _, _, gu = orc.loss_grad(pb, th)
+    fd = (L_of(pb.R0 + h) - L_of(pb.R0 - h)) / (2 * h)
+    assert gu[2] - gu[0] == pytest.approx(fd, rel=1e-5)
+
+
 def test_adjoint_initial_state_gradient(orc):
     ser = synth.load_series("60d")
     th = [0.21, 0.2, 0.15, 0.13, 0.1, 0.002, 1e4]
