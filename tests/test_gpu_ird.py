@@ -95,14 +95,18 @@ def test_ird_fp32_calibration_reports_its_fp64_loss_and_batches_agree():
         assert r["loss"] == O.loss(pb, r["theta"])
 
 
-def test_ird_rejects_the_gradient_calls():
+def test_ird_rejects_the_fp32_gradient_calls():
+    # the FP32 adjoint covers F_D only; F_IRD takes the FP64 one
     yD, yI, yR, N = ird_series("60d", 30)
     lb, ub = configs.bounds(1, log=True)
     cal = sird.Calibrator(yD, N, R0=float(yR[0]), objective=sird.FIT_IRD, yI=yI, yR=yR, particles=64, iters=2,
                           lb=lb, ub=ub, log_scale=[1] * 4, precision=32)
     cal.calibrate()
-    with pytest.raises(sird.SirdError):
-        cal.loss_grad(torch.ones(4, 8, dtype=torch.float64, device="cuda"))
+    with pytest.raises(sird.SirdError, match="UNSUPPORTED"):
+        cal.loss_grad(torch.ones(4, 8, dtype=torch.float32, device="cuda"))
+    assert cal._lib.sird_pso_clear_error(cal.h) == sird.OK  # handle errors are sticky until cleared
+    L, G = cal.loss_grad(torch.ones(4, 8, dtype=torch.float64, device="cuda"))
+    assert L.shape == (8,) and G.shape == (4, 8)
 
 
 def test_ird_batch_set_observations_equals_a_fresh_batch():
@@ -120,3 +124,108 @@ def test_ird_batch_set_observations_equals_a_fresh_batch():
     fresh = sird.Batch([dict(w, R0=o["R0"]) for w, o in zip(nxt, wins)], iters=4, **kw).calibrate()
     for a, b in zip(got, fresh):
         assert a["index"] == b["index"] and a["loss"] == b["loss"] and np.array_equal(a["theta"], b["theta"])
+
+
+# ---------------------------------------------------------------- F_IRD^C gradient (FP64 adjoint)
+
+def dominated_problem(form, cost, dominant, fit_I0):
+    """Reported series from a trajectory with 0.2% noise, one compartment moved 5-8% off it so that
+    its normalised cost is the largest of the three (F_IRD^C, Sec. 3.1); returns the GPU keywords,
+    the oracle problem and parameter vectors around the generating point."""
+    s = synth.load_series("60d")
+    days, R0 = 35, 800.0
+    if form == "pwc":
+        ref, kw, gkw = [0.23, 0.19, 0.17, 0.13, 0.1, 0.002, 1.1e4], dict(K=4), dict(K=4, beta_form=sird.BETA_PWC)
+    else:
+        ref, kw, gkw = [0.25, 0.14, 9.5, 24.25, 0.1, 0.002, 1.1e4], dict(beta_form=O.BETA_RAMP), \
+            dict(K=1, beta_form=sird.BETA_RAMP)
+    th0 = np.array(ref) * (1 + 0.03 * np.sin(np.arange(len(ref)) + 1.0))
+    tr = O.simulate(O.Problem(yD=np.zeros(days + 1), N=s["N"], R0=R0, spd=10, **kw), th0, days)
+    rng = np.random.default_rng(11)
+    wob = lambda v, a: v * (1 + a * rng.normal(size=v.size))
+    yI, yR = wob(tr["I"], 2e-3), R0 + wob(tr["R"] - R0, 2e-3)
+    yD = tr["D"][0] + wob(tr["D"] - tr["D"][0], 2e-3)
+    t = np.linspace(0.0, 1.0, days + 1)
+    if dominant == "I":
+        yI = yI * (1 + 0.08 * t)
+    elif dominant == "R":
+        yR = R0 + (yR - R0) * (1 + 0.08 * t)
+    else:
+        yD = yD + 0.08 * t * (yD - yD[0])
+    pb = O.Problem(yD=yD, yI=yI, yR=yR, N=s["N"], R0=R0, I0=float(yI[0]), fit_I0=fit_I0, spd=10,
+                   objective=O.FIT_IRD, cost=O.COSTS[cost], **kw)
+    th0 = th0 if fit_I0 else th0[:-1]
+    th = th0 * np.exp(np.random.default_rng(12).normal(0.0, 0.01, (48, th0.size)))
+    th[0] = th0
+    P = th.shape[1]
+    common = dict(spd=10, R0=R0, I0=float(yI[0]), fit_I0=fit_I0, cost=sird.COSTS[cost], objective=sird.FIT_IRD,
+                  yI=yI, yR=yR, particles=32, iters=1, lb=[0.0] * P, ub=[1e6] * P, **gkw)
+    return yD, float(s["N"]), pb, th, common
+
+
+def compartment_costs(pb, th):
+    tr = O.simulate(pb, th, len(pb.yD) - 1)
+    out = []
+    for y, yh in ((pb.yI, tr["I"]), (pb.yR, tr["R"]), (pb.yD, tr["D"])):
+        if pb.cost == O.MAPE:
+            m = y != 0
+            out.append(100 * np.mean(np.abs((y[m] - yh[m]) / y[m])))
+        else:
+            e = (y - yh) / (y.max() - y.min())
+            out.append({O.MSE: np.mean(e * e), O.MAE: np.mean(np.abs(e)), O.MXSE: np.max(e * e)}[pb.cost])
+    return out
+
+
+@pytest.mark.parametrize("form,cost,dominant,fit_I0", [
+    ("pwc", "mse", "I", True), ("pwc", "mse", "R", True), ("pwc", "mse", "D", True),
+    ("pwc", "mae", "R", True), ("pwc", "mape", "D", True), ("pwc", "mxse", "I", True), ("pwc", "mxse", "R", False),
+    ("ramp", "mxse", "I", False), ("ramp", "mxse", "R", False), ("ramp", "mxse", "D", False),
+    ("ramp", "mse", "D", False), ("ramp", "mape", "I", False), ("ramp", "mae", "D", True), ("ramp", "mape", "R", True)])
+@pytest.mark.parametrize("ckpt", [1, 7, 16])
+def test_ird_adjoint_f64_bit_exact(form, cost, dominant, fit_I0, ckpt):
+    # the FP64 adjoint of F_IRD^C against the oracle's discrete adjoint: loss, dL/dtheta and
+    # dL/du0 identical, with the named compartment attaining the maximum at the generating point
+    yD, N, pb, th, common = dominated_problem(form, cost, dominant, fit_I0)
+    c = compartment_costs(pb, th[0])
+    assert "IRD"[int(np.argmax(c))] == dominant, c
+    cal = sird.Calibrator(yD, N, precision=64, **common)
+    L, G, GU = cal.loss_grad(torch.from_numpy(np.ascontiguousarray(th.T)).cuda(), ckpt_every=ckpt, grad_u0=True)
+    L, G, GU = L.cpu().numpy(), G.cpu().numpy().T, GU.cpu().numpy().T
+    for j in range(th.shape[0]):
+        Lo, Go, GUo = O.loss_grad(pb, th[j])
+        assert L[j] == Lo, (j, L[j], Lo)
+        assert np.array_equal(G[j], Go), (j, rel_err(G[j], Go))
+        assert np.array_equal(GU[j], GUo), (j, GU[j], GUo)
+
+
+@pytest.mark.parametrize("cost", ["mse", "mxse", "mae", "mape"])
+def test_ird_adjoint_f64_box_samples_bit_exact(cost):
+    # far from a fit too (random vectors, the dominant compartment varying between them)
+    yD, N, th, common, pb = setup(cost, "pwc", days=30)
+    cal = sird.Calibrator(yD, N, precision=64, **common)
+    L, G = cal.loss_grad(torch.from_numpy(np.ascontiguousarray(th.T)).cuda(), ckpt_every=16)
+    L, G = L.cpu().numpy(), G.cpu().numpy().T
+    seen = set()
+    for j in range(th.shape[0]):
+        Lo, Go, _ = O.loss_grad(pb, th[j])
+        assert L[j] == Lo and np.array_equal(G[j], Go), (j, rel_err(G[j], Go))
+        seen.add(int(np.argmax(compartment_costs(pb, th[j]))))
+    print("dominant compartments seen:", sorted("IRD"[i] for i in seen))
+
+
+def test_ird_fp64_polish_never_worsens_and_reports_the_oracle_loss():
+    # the FP64 polish on F_IRD^MXSE (the paper's representative objective, ramp beta)
+    yD, yI, yR, N = ird_series("60d", 35)
+    lb, ub = configs.bounds_ramp(fit_I0=False)
+    cal = sird.Calibrator(yD, N, K=1, spd=10, R0=float(yR[0]), I0=float(yI[0]), fit_I0=False,
+                          beta_form=sird.BETA_RAMP, cost=sird.COSTS["mxse"], objective=sird.FIT_IRD, yI=yI, yR=yR,
+                          particles=1024, iters=30, lb=lb, ub=ub, precision=32, reeval_topk=8, seed=3)
+    r0 = cal.calibrate()
+    r1 = cal.polish(k=8, iters=10, first_step=1e-2, precision=64)
+    assert r1["loss"] <= r0["loss"]
+    assert all(lo <= t <= hi for t, lo, hi in zip(r1["theta"], lb, ub))
+    pb = O.Problem(yD=yD, yI=yI, yR=yR, N=N, R0=float(yR[0]), I0=float(yI[0]), fit_I0=False, spd=10,
+                   beta_form=O.BETA_RAMP, cost=O.MXSE, objective=O.FIT_IRD)
+    assert r1["loss"] == O.loss(pb, r1["theta"])
+    with pytest.raises(sird.SirdError, match="UNSUPPORTED"):
+        cal.polish(k=4, iters=2, first_step=1e-2, precision=32)
