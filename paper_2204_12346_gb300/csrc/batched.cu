@@ -39,8 +39,9 @@ __global__ void __launch_bounds__(batch_launch_bound(COST)) pso_batch_f32(const 
     float* ys = smem;
     const int obs_region = pad4(n_max) * (m.ird ? 3 : 1);  // the stacked series of the longest window
     float* invys = (variant_cost(COST) == COST_MAPE) ? ys + obs_region : ys;
-    float* th_s = smem + obs_region * (variant_cost(COST) == COST_MAPE ? 2 : 1);  // [P][2B]
-    float* g_s = th_s + P * B2;
+    float* th_s = smem + obs_region * (variant_cost(COST) == COST_MAPE ? 2 : 1);  // [P][2B] theta
+    float* zs_s = th_s + P * B2;                                                   // [P][2B] z
+    float* g_s = zs_s + P * B2;
     float* lb_s = g_s + kMaxParams;
     float* ub_s = lb_s + kMaxParams;
     if (tid < P) {
@@ -70,39 +71,60 @@ __global__ void __launch_bounds__(batch_launch_bound(COST)) pso_batch_f32(const 
         unsigned long long gkey = ~0ull;
         for (int it = 0; it <= iters; ++it) {
             unsigned long long key = ~0ull;
-            // particle j's update (initialisation at it == 0), theta decoded into th_s column col
+            // The update (initialisation at it == 0) of particle j: the new position goes to
+            // column col of th_s decoded (theta, which the fitness reads) and of zs_s as search
+            // coordinates (what settle copies into the personal best, with no reload from global
+            // memory).  Dimensions go in pairs (one Philox draw), a pair's swarm state loaded
+            // before its stores, so a pair of dimensions costs one round trip to L2, not two.
             auto update = [&](int j, int col) {
-                uint4 rnd = make_uint4(0, 0, 0, 0);
-                for (int d = 0; d < P; ++d) {
-                    if ((d & 1) == 0)
-                        rnd = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)it, (uint32_t)(d >> 1), bw.stream_id),
-                                            bw.key0, bw.key1);
-                    const float ua = u01f((d & 1) ? rnd.z : rnd.x);
-                    const float ub = u01f((d & 1) ? rnd.w : rnd.y);
-                    const size_t off = (size_t)d * ld + j;
-                    const float lo = lb_s[d], hi = ub_s[d];
-                    float xn, vn;
-                    if (it == 0) {
-                        const float range = __fsub_rn(hi, lo);
-                        xn = fminf(__fmaf_rn(range, ua, lo), hi);
-                        vn = __fmul_rn(range, __fmaf_rn(2.f, ub, -1.f));
-                    } else {
-                        const float x = X[off], v = V[off], pbv = PB[off];
-                        const float t = __fmaf_rn(__fmul_rn(c.c1, ua), __fsub_rn(pbv, x), __fmul_rn(c.w, v));
-                        vn = __fmaf_rn(__fmul_rn(c.c2, ub), __fsub_rn(g_s[d], x), t);
-                        xn = fminf(fmaxf(__fadd_rn(x, vn), lo), hi);
+                for (int d0 = 0; d0 < P; d0 += 2) {
+                    const bool second = d0 + 1 < P;
+                    float x[2] = {0.f, 0.f}, v[2] = {0.f, 0.f}, pbv[2] = {0.f, 0.f};
+                    if (it > 0) {
+                        const size_t o = (size_t)d0 * ld + j;
+                        x[0] = X[o];
+                        v[0] = V[o];
+                        pbv[0] = PB[o];
+                        if (second) {
+                            x[1] = X[o + ld];
+                            v[1] = V[o + ld];
+                            pbv[1] = PB[o + ld];
+                        }
                     }
-                    X[off] = xn;
-                    V[off] = vn;
-                    th_s[d * B2 + col] = ((c.logmask >> d) & 1u) ? expf(xn) : xn;
+                    const uint4 rnd = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)it, (uint32_t)(d0 >> 1), bw.stream_id),
+                                                    bw.key0, bw.key1);
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        if (q == 1 && !second) break;
+                        const int d = d0 + q;
+                        const float ua = u01f(q ? rnd.z : rnd.x);
+                        const float ub = u01f(q ? rnd.w : rnd.y);
+                        const float lo = lb_s[d], hi = ub_s[d];
+                        float xn, vn;
+                        if (it == 0) {
+                            const float range = __fsub_rn(hi, lo);
+                            xn = fminf(__fmaf_rn(range, ua, lo), hi);
+                            vn = __fmul_rn(range, __fmaf_rn(2.f, ub, -1.f));
+                        } else {
+                            const float t = __fmaf_rn(__fmul_rn(c.c1, ua), __fsub_rn(pbv[q], x[q]), __fmul_rn(c.w, v[q]));
+                            vn = __fmaf_rn(__fmul_rn(c.c2, ub), __fsub_rn(g_s[d], x[q]), t);
+                            xn = fminf(fmaxf(__fadd_rn(x[q], vn), lo), hi);
+                        }
+                        const size_t o = (size_t)d * ld + j;
+                        X[o] = xn;
+                        V[o] = vn;
+                        zs_s[d * B2 + col] = xn;
+                        th_s[d * B2 + col] = ((c.logmask >> d) & 1u) ? expf(xn) : xn;
+                    }
                 }
             };
-            auto settle = [&](int j, float f) {  // personal best and the running block minimum
+            // personal best (its position from zs_s column col) and the running block minimum
+            auto settle = [&](int j, int col, float f) {
                 if (f != f) f = INFINITY;
                 float best = f;
                 if (it == 0 || f < PBF[j]) {
                     PBF[j] = f;
-                    for (int d = 0; d < P; ++d) PB[(size_t)d * ld + j] = X[(size_t)d * ld + j];
+                    for (int d = 0; d < P; ++d) PB[(size_t)d * ld + j] = zs_s[d * B2 + col];
                 } else {
                     best = PBF[j];
                 }
@@ -130,14 +152,15 @@ __global__ void __launch_bounds__(batch_launch_bound(COST)) pso_batch_f32(const 
                 if (tid >= Tw || tid >= cnt) continue;
                 const int j0 = base + tid, j1 = base + Tw + tid;
                 update(j0, tid);
+                float fa, fb;
                 if (Tw + tid < cnt) {
                     update(j1, B + tid);
-                    float fa, fb;
                     fitness_f32x2<SPD, COST>(w, m, ys, invys, th_s + tid, th_s + B + tid, B2, fa, fb);
-                    settle(j0, fa);
-                    settle(j1, fb);
+                    settle(j0, tid, fa);
+                    settle(j1, B + tid, fb);
                 } else {
-                    settle(j0, fitness_f32<SPD, COST>(w, m, ys, invys, th_s + tid, B2));
+                    fa = fitness_f32<SPD, COST>(w, m, ys, invys, th_s + tid, B2);
+                    settle(j0, tid, fa);
                 }
             }
             key = warp_min_key(key);
@@ -182,7 +205,7 @@ __global__ void batch_reeval_kernel(const BatchWindow* __restrict__ wins, int W,
 }  // namespace
 
 size_t batch_smem_bytes(const ModelDev& m, int block, int n_max) {
-    return ((size_t)pad4(n_max) * (m.ird ? 3 : 1) * (m.cost == COST_MAPE ? 2 : 1) + (size_t)m.P * 2 * block +
+    return ((size_t)pad4(n_max) * (m.ird ? 3 : 1) * (m.cost == COST_MAPE ? 2 : 1) + (size_t)m.P * 4 * block +
             3 * kMaxParams) *
            sizeof(float);
 }
