@@ -95,9 +95,8 @@ typedef enum sird_objective { SIRD_FIT_D = 0, SIRD_FIT_IRD = 1 } sird_objective;
  *   cost, objective  see the enums.  SIRD_FIT_IRD: the cost of each of I, R, D against y_I,
  *                  y_R, y_D, errors divided by the series' range max - min (1 for a flat
  *                  series; MAPE unnormalised), the loss the largest of the three.  Every
- *                  evaluation, PSO, re-evaluation and batched call takes it, and the FP64
- *                  gradient and polish; the FP32 gradient and polish, sird_batch_polish and
- *                  sird_pso_set_observations answer SIRD_ERR_UNSUPPORTED.
+ *                  evaluation, PSO, re-evaluation, batched, gradient and polish call takes
+ *                  it; sird_pso_set_observations answers SIRD_ERR_UNSUPPORTED.
  *
  * theta layout (P entries):
  *   PWC : beta_1..beta_K, gamma, mu [, I0]          segment j covers steps
@@ -288,10 +287,10 @@ sird_status sird_pso_set_gbest(sird_pso_t h, const float* z, float loss, int ind
  * loss bit for bit), checkpoints at every day start (ckpt_every is checked but not used),
  * steps_per_day 10, 20 or at most 64 (else SIRD_ERR_UNSUPPORTED); its gradient is the exact
  * adjoint of the discrete map evaluated in FP32 (relative error near 1e-5 of the summed terms).
- * Costs: MSE, MAE, MAPE, MXSE (sub-gradients at kinks).  F_IRD^C (precision 64 only; 32 answers
- * SIRD_ERR_UNSUPPORTED): the gradient of the series whose cost attains the maximum (the first of
- * I, R, D on ties), its errors scaled by the series' range, injected into the adjoint of I, R or
- * D on each observation day; checkpoints then hold S, I, R, D.  Asynchronous on the handle's
+ * Costs: MSE, MAE, MAPE, MXSE (sub-gradients at kinks).  F_IRD^C: the gradient of the series whose
+ * cost attains the maximum (the first of I, R, D on ties, as the loss of that precision picks it),
+ * its errors scaled by the series' range, injected into the adjoint of I, R or D on each
+ * observation day; checkpoints then also hold R (FP64) or R's misfit (FP32).  Asynchronous on the handle's
  * stream; the checkpoint scratch grows on demand (that call synchronises the stream).
  */
 sird_status sird_loss_grad(sird_pso_t h, const void* d_theta, int M, int ld, void* d_loss,
@@ -304,9 +303,8 @@ sird_status sird_loss_grad(sird_pso_t h, const void* d_theta, int M, int ld, voi
  * that evaluates 16 step lengths 2^-q in one launch and takes the longest one meeting the
  * Armijo condition; positions are clamped to the box, and a coordinate on a bound whose gradient
  * points out of the box is held while the others move (projected L-BFGS).  precision 64: trials and gradients in
- * the paper's FP64 arithmetic (checkpoints every ckpt_every steps, 1..64; F_D and F_IRD);
- * precision 32: the compensated FP32 evaluation and the FP32 adjoint (steps_per_day 10, 20 or
- * <= 64; F_D only, else SIRD_ERR_UNSUPPORTED).
+ * the paper's FP64 arithmetic (checkpoints every ckpt_every steps, 1..64); precision 32: the
+ * compensated FP32 evaluation and the FP32 adjoint (steps_per_day 10, 20 or <= 64).
  * first_step is the largest change of any search coordinate in the first (steepest-descent)
  * step.  The best point ever evaluated is re-scored in FP64 and reported in *out (FP64 loss;
  * index = the candidate's particle).  The swarm itself is not changed.  Blocks.

@@ -8,7 +8,11 @@
 //     dL/dbeta_j = dt/N sum_{k in segment j} S_k I_k (lambda_I - lambda_S)_{k+1}
 //     dL/dgamma  = -dt sum_k I_k lambda_I,{k+1}
 //     dL/dmu     =  dt sum_k I_k (lambda_D - lambda_I)_{k+1}
-// and dL/dI0 = lambda_I(0) - lambda_S(0) (S0 = N - I0 - R0 - D0).
+// and dL/dI0 = lambda_I(0) - lambda_S(0) (S0 = N - I0 - R0 - D0).  For F_IRD^C the cost
+// gradient of the dominant series (the first of I, R, D attaining the maximum, as the evaluation
+// picks it; errors scaled by the series' range, MAPE unscaled) enters lambda_I, lambda_R or
+// lambda_D on its observation days, lambda_R (constant between them) adds dt gamma lambda_R to
+// lambda_I's step and dL/dgamma becomes dt sum_k I_k (lambda_R - lambda_I)_{k+1}.
 //
 // The forward pass is the FP32 trajectory of the evaluation kernels (traj_f32.cuh), operation for
 // operation, so the loss equals the FP32 evaluation's bit for bit.  It stores the state at the
@@ -70,6 +74,14 @@ __device__ __forceinline__ float grad_D(float e, float invy, int n, int n_kept, 
     if (COST == COST_MAE) return __fdiv_rn(-sg, (float)n);
     if (COST == COST_MAPE) return n_kept > 0 ? __fdiv_rn(__fmul_rn(__fmul_rn(-100.f, sg), invy), (float)n_kept) : 0.f;
     return is_max ? __fmul_rn(-2.f, e) : 0.f;
+}
+
+// dC/dyhat of one F_IRD series on a day with scaled error es = (y - yhat) s (s = 1 / range; MAPE:
+// es = y - yhat unscaled, invy = 1/y) -- grad_D's formulas in the scaled error, times s.
+template <int COST>
+__device__ __forceinline__ float grad_series(float es, float s, float invy, int n, int n_kept, bool is_max) {
+    if (COST == COST_MAPE) return grad_D<COST>(es, invy, n, n_kept, false);
+    return __fmul_rn(grad_D<COST>(es, invy, n, n_kept, is_max), s);
 }
 
 // One day of Euler steps from (Sday, I, Il) with the day's coefficients; when stage is set, the
@@ -192,6 +204,55 @@ struct CkptObs {
     }
 };
 
+// F_IRD forward pass: the three series' costs exactly as the FP32 evaluation forms them
+// (LossObsIRD), the day-start checkpoints (S, I, its low part, D's misfit) and R's misfit of
+// observation d at slot 4 of day d ([day][5][cs]); the last observation's misfits and I pair, the
+// first day of each series' largest scaled e^2 (MXSE) and the dominant series (0 I, 1 R, 2 D).
+template <int COST>
+struct CkptObsIRD {
+    CostT<float, COST> cI, cR, cD;
+    const float *ys, *invys;
+    int ps, L;
+    float sI, sR, sD;
+    float* ck;
+    size_t cs;
+    float mxI, mxR, mxD;
+    int imI, imR, imD;
+    float eD_last, eR_last, Ih_last, Il_last;
+    __device__ __forceinline__ void day_start(int day, float Qh, float Ql, float Ih, float Il, float e) {
+        float* q = ck + (size_t)day * 5 * cs;
+        q[0] = __fadd_rn(__fsub_rn(Qh, Ih), __fsub_rn(Ql, Il));  // S = Q - I at the day's start
+        q[cs] = Ih;
+        q[2 * cs] = Il;
+        q[3 * cs] = e;
+    }
+    __device__ __forceinline__ void day_end(int day, float e, float Ih, float Il, float eR) {
+        const float eI = __fsub_rn(__fsub_rn(ys[ps + day], Ih), Il);
+        float a, b, c;
+        if (COST == COST_MAPE) {
+            cI.add(eI, invys[ps + day]);
+            cR.add(eR, invys[2 * ps + day]);
+            cD.add(e, invys[day]);
+            a = eI, b = eR, c = e;
+        } else {
+            a = __fmul_rn(eI, sI), b = __fmul_rn(eR, sR), c = __fmul_rn(e, sD);
+            cI.add(a, 0.f);
+            cR.add(b, 0.f);
+            cD.add(c, 0.f);
+        }
+        if (COST == COST_MXSE) {  // the first day of each series' largest e^2 (tmaxsq's order)
+            if (__fmul_rn(a, a) > mxI) mxI = __fmul_rn(a, a), imI = day;
+            if (__fmul_rn(b, b) > mxR) mxR = __fmul_rn(b, b), imR = day;
+            if (__fmul_rn(c, c) > mxD) mxD = __fmul_rn(c, c), imD = day;
+        }
+        if (day < L) ck[((size_t)day * 5 + 4) * cs] = eR;
+        eD_last = e;
+        eR_last = eR;
+        Ih_last = Ih;
+        Il_last = Il;
+    }
+};
+
 template <int SPD, int COST, bool RAMP>
 __device__ __forceinline__ float forward_checkpointed(const WindowDev& w, const ModelDev& m, const float* ys,
                                                       const float* invys, const float* th, int B, const CoefF32&,
@@ -219,12 +280,12 @@ __device__ __forceinline__ float forward_checkpointed(const WindowDev& w, const 
 
 // Re-integrates one day from its checkpoint (ck as above), staging each step's S, I and cb at
 // stS/stI/stC[s * B].
-template <int SPD, bool RAMP>
+template <int SPD, bool RAMP, int NQ = 4>
 __device__ __forceinline__ void restage_day(const WindowDev& w, const ModelDev& m, const float* th, int B,
                                             const CoefF32& cf, const float* ck, size_t cs, int day, float* stS,
                                             float* stI, float* stC) {
     const int spd = SPD > 0 ? SPD : m.spd, steps = (w.n_obs - 1) * spd, K = m.K;
-    const float* c = ck + (size_t)day * 4 * cs;
+    const float* c = ck + (size_t)day * NQ * cs;
     const float Sday = c[0];
     float Ir = c[cs], Ilr = c[2 * cs];
     int sg = RAMP ? 0 : seg_of_step(day * spd, steps, K);
@@ -239,7 +300,7 @@ __device__ __forceinline__ void restage_day(const WindowDev& w, const ModelDev& 
 // lambda_D, the segment being swept and the gradient sums.  Kept as separate scalars so that
 // they stay in registers (the sums are indexed by segment and live in local memory).
 struct RevF32 {
-    float lS, lI, lSl, lIl, lD;
+    float lS, lI, lSl, lIl, lD, lR;
     int cur, seg_lo;
 };
 
@@ -254,15 +315,17 @@ __device__ __forceinline__ void rev_begin(RevF32& r, double* gacc, const WindowD
     r.seg_lo = RAMP ? 0 : segment_start(r.cur, steps, m.K);
 }
 
-// The reverse sweep of one staged day (steps spd-1 .. 0), then the day's folds and dL/dDhat_day.
-template <int SPD, int COST, bool RAMP>
+// The reverse sweep of one staged day (steps spd-1 .. 0), then the day's folds and dL/dDhat_day
+// (F_IRD: the caller adds the day's cost gradient; dr = dt gamma enters with lambda_R).
+template <int SPD, int COST, bool RAMP, bool IRD = false>
 __device__ __forceinline__ void rev_day(RevF32& r, double* gacc, const WindowDev& w, const ModelDev& m, const float* invys,
                                         const CoefF32& cf, int day, int steps, const float* stS, const float* stI,
-                                        const float* stC, int B, float e_d, int imax) {
+                                        const float* stC, int B, float e_d, int imax, float dr = 0.f) {
     const int spd = SPD > 0 ? SPD : m.spd, K = m.K, n = w.n_obs, gi = RAMP ? 4 : K;
     const float a = cf.a;
     float pb = 0.f, pg = 0.f, pm = 0.f, pr[4] = {0.f, 0.f, 0.f, 0.f};
-    const float dmlD = __fmul_rn(cf.dm, r.lD);  // lambda_D is constant within the day
+    // lambda_D (and lambda_R) are constant within the day
+    const float dmlD = IRD ? __fmaf_rn(dr, r.lR, __fmul_rn(cf.dm, r.lD)) : __fmul_rn(cf.dm, r.lD);
 #pragma unroll 4
     for (int s = spd - 1; s >= 0; --s) {
         const int k = day * spd + s;
@@ -284,7 +347,7 @@ __device__ __forceinline__ void rev_day(RevF32& r, double* gacc, const WindowDev
         } else {
             pb = __fmaf_rn(SI, q, pb);
         }
-        pg = __fmaf_rn(Iv, r.lI, pg);
+        pg = IRD ? __fmaf_rn(Iv, __fsub_rn(r.lI, r.lR), pg) : __fmaf_rn(Iv, r.lI, pg);
         pm = __fmaf_rn(Iv, __fsub_rn(r.lD, r.lI), pm);
         // lambda_S and lambda_I change by small increments per step; as for I in the forward
         // pass, each sum's rounding error is kept (Fast2Sum) and folded in once a day
@@ -303,7 +366,7 @@ __device__ __forceinline__ void rev_day(RevF32& r, double* gacc, const WindowDev
         r.lS = fs;
         r.lI = fi;
     }
-    r.lD = __fadd_rn(r.lD, grad_D<COST>(e_d, invys[day], n, w.n_kept, COST == COST_MXSE && imax == day));
+    if (!IRD) r.lD = __fadd_rn(r.lD, grad_D<COST>(e_d, invys[day], n, w.n_kept, COST == COST_MXSE && imax == day));
     if (RAMP) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) gacc[j] += (double)pr[j];
@@ -314,7 +377,7 @@ __device__ __forceinline__ void rev_day(RevF32& r, double* gacc, const WindowDev
     gacc[gi + 1] += (double)pm;
 }
 
-template <bool RAMP>
+template <bool RAMP, bool IRD = false>
 __device__ __forceinline__ void rev_write(const RevF32& r, const double* gacc, const WindowDev& w, const ModelDev& m, int p, float Lval,
                                           float* loss, float* grad, int ldg, float* grad_u0) {
     const int K = m.K, gi = RAMP ? 4 : K;
@@ -330,7 +393,7 @@ __device__ __forceinline__ void rev_write(const RevF32& r, const double* gacc, c
     if (grad_u0) {
         grad_u0[p] = lS;
         grad_u0[(size_t)ldg + p] = lI;
-        grad_u0[2 * (size_t)ldg + p] = 0.f;
+        grad_u0[2 * (size_t)ldg + p] = IRD ? r.lR : 0.f;
         grad_u0[3 * (size_t)ldg + p] = r.lD;
     }
 }
@@ -380,17 +443,119 @@ __device__ __forceinline__ void loss_grad_f32_body(const WindowDev& w, const Mod
     rev_write<RAMP>(r, gacc, w, m, p, Lval, loss, grad, ldg, grad_u0);
 }
 
+// F_IRD^C: one thread per parameter vector, as loss_grad_f32_body, with the three series staged
+// (D | I | R, stride obs_stride(n)), checkpoints [day][5][cs] and the dominant series' gradient
+// injected day by day.
 template <int SPD, int COST, bool RAMP>
+__device__ __forceinline__ void loss_grad_f32_ird_body(const WindowDev& w, const ModelDev& m, const ObsDev& o,
+                                                       const float* __restrict__ theta, int ld, int M,
+                                                       float* __restrict__ loss, float* __restrict__ grad, int ldg,
+                                                       float* __restrict__ grad_u0, float* __restrict__ ckpt, int blk) {
+    extern __shared__ float smem[];
+    const int B = blockDim.x, tid = threadIdx.x, P = m.P;
+    const int n = w.n_obs, ps = obs_stride(n), span = 3 * ps;
+    const int spd = SPD > 0 ? SPD : m.spd;
+    float* ys = smem;
+    float* invys = ys + span;
+    float* th_all = invys + span;
+    float* stS = th_all + P * B + tid;  // per-step staging [spd][B] x 3
+    float* stI = stS + spd * B;
+    float* stC = stI + spd * B;
+    for (int i = tid; i < span; i += B) {
+        ys[i] = o.yf[i];
+        invys[i] = o.invyf[i];
+    }
+    const int p = blk * B + tid;
+    const bool active = p < M;
+    if (active)
+        for (int d = 0; d < P; ++d) th_all[d * B + tid] = theta[(size_t)d * ld + p];
+    __syncthreads();
+    if (!active) return;
+    const float* th = th_all + tid;
+    const int L = n - 1, steps = L * spd, gi = RAMP ? 4 : m.K;
+    const CoefF32 cf = coef_f32<RAMP>(w, m, th, B);
+    const float gam = th[gi * B];
+    const float dr = __fmaf_rn(gam, w.dt_h, __fmul_rn(gam, w.dt_l));
+    float* ck = ckpt + p;
+    const size_t cs = (size_t)M;
+    CkptObsIRD<COST> ob;
+    ob.cI.init();
+    ob.cR.init();
+    ob.cD.init();
+    ob.ys = ys;
+    ob.invys = invys;
+    ob.ps = ps;
+    ob.L = L;
+    ob.sI = w.inv_rng_I;
+    ob.sR = w.inv_rng_R;
+    ob.sD = w.inv_rng_D;
+    ob.ck = ck;
+    ob.cs = cs;
+    ob.mxI = ob.mxR = ob.mxD = 0.f;
+    ob.imI = ob.imR = ob.imD = -1;
+    ob.eD_last = ob.eR_last = ob.Ih_last = ob.Il_last = 0.f;
+    // the evaluation's arithmetic, including its choice of the compensated growth rate
+    if (steps > kExactGrowthSteps)
+        trajectory_f32<float, SPD, RAMP, true, false, true>(w, m, ys, ys + 2 * ps, ThetaF1{th, B}, L, ob);
+    else
+        trajectory_f32<float, SPD, RAMP, true>(w, m, ys, ys + 2 * ps, ThetaF1{th, B}, L, ob);
+    float ia, ib, ra, rb, da, db;
+    ob.cI.result(n, w.n_kept_I, ia, ib);
+    ob.cR.result(n, w.n_kept_R, ra, rb);
+    ob.cD.result(n, w.n_kept, da, db);
+    float Lval = ia;
+    int which = 0;  // the dominant series, the first of I, R, D on ties (max3's order)
+    if (ra > Lval) Lval = ra, which = 1;
+    if (da > Lval) Lval = da, which = 2;
+    // the dominant series' cost gradient on observation d from the misfits there
+    const bool mape = COST == COST_MAPE;
+    auto inject = [&](RevF32& r, int d, float Ih, float Il, float eR, float eD) {
+        if (which == 0) {
+            const float eI = __fsub_rn(__fsub_rn(ys[ps + d], Ih), Il);
+            const float g = grad_series<COST>(mape ? eI : __fmul_rn(eI, w.inv_rng_I), w.inv_rng_I, invys[ps + d], n,
+                                              w.n_kept_I, d == ob.imI);
+            float sh, sl;  // lambda_I carries a low part: add with TwoSum
+            two_sum(r.lI, g, sh, sl);
+            r.lI = sh;
+            r.lIl = __fadd_rn(r.lIl, sl);
+        } else if (which == 1) {
+            r.lR = __fadd_rn(r.lR, grad_series<COST>(mape ? eR : __fmul_rn(eR, w.inv_rng_R), w.inv_rng_R,
+                                                      invys[2 * ps + d], n, w.n_kept_R, d == ob.imR));
+        } else {
+            r.lD = __fadd_rn(r.lD, grad_series<COST>(mape ? eD : __fmul_rn(eD, w.inv_rng_D), w.inv_rng_D, invys[d], n,
+                                                      w.n_kept, d == ob.imD));
+        }
+    };
+    RevF32 r;
+    double gacc[kMaxParams];
+    for (int d = 0; d < P; ++d) gacc[d] = 0.0;
+    r.lS = r.lI = r.lSl = r.lIl = r.lD = r.lR = 0.f;
+    r.cur = RAMP ? 0 : seg_of_step(steps - 1, steps, m.K);
+    r.seg_lo = RAMP ? 0 : segment_start(r.cur, steps, m.K);
+    inject(r, L, ob.Ih_last, ob.Il_last, ob.eR_last, ob.eD_last);
+    for (int day = L - 1; day >= 0; --day) {
+        restage_day<SPD, RAMP, 5>(w, m, th, B, cf, ck, cs, day, stS, stI, stC);
+        rev_day<SPD, COST, RAMP, true>(r, gacc, w, m, invys, cf, day, steps, stS, stI, stC, B, 0.f, 0, dr);
+        const float* c = ck + (size_t)day * 5 * cs;
+        inject(r, day, c[cs], c[2 * cs], c[4 * cs], c[3 * cs]);
+    }
+    rev_write<RAMP, true>(r, gacc, w, m, p, Lval, loss, grad, ldg, grad_u0);
+}
+
+template <int SPD, int COST, bool RAMP, bool IRD>
 __global__ void __launch_bounds__(64) loss_grad_f32_kernel(WindowDev w, ModelDev m, ObsDev o,
                                                             const float* __restrict__ theta, int ld, int M,
                                                             float* __restrict__ loss, float* __restrict__ grad,
                                                             int ldg, float* __restrict__ grad_u0,
                                                             float* __restrict__ ckpt) {
-    loss_grad_f32_body<SPD, COST, RAMP>(w, m, o, theta, ld, M, loss, grad, ldg, grad_u0, ckpt, blockIdx.x);
+    if constexpr (IRD)
+        loss_grad_f32_ird_body<SPD, COST, RAMP>(w, m, o, theta, ld, M, loss, grad, ldg, grad_u0, ckpt, blockIdx.x);
+    else
+        loss_grad_f32_body<SPD, COST, RAMP>(w, m, o, theta, ld, M, loss, grad, ldg, grad_u0, ckpt, blockIdx.x);
 }
 
 // Table form: block row blockIdx.y takes window blockIdx.y (PolishWin) with its own constants.
-template <int SPD, int COST, bool RAMP>
+template <int SPD, int COST, bool RAMP, bool IRD>
 __global__ void __launch_bounds__(64) loss_grad_f32_tab_kernel(const PolishWin* __restrict__ tab, ModelDev m,
                                                                 const float* __restrict__ theta, long long th_ws,
                                                                 int ld, int M, float* __restrict__ loss,
@@ -400,8 +565,12 @@ __global__ void __launch_bounds__(64) loss_grad_f32_tab_kernel(const PolishWin* 
     const int i = blockIdx.y;
     const WindowDev w = tab[i].w;
     const ObsDev o = tab[i].o;
-    loss_grad_f32_body<SPD, COST, RAMP>(w, m, o, theta + i * th_ws, ld, M, loss + i * loss_ws, grad + i * grad_ws,
-                                        ldg, nullptr, ckpt + i * ck_ws, blockIdx.x);
+    if constexpr (IRD)
+        loss_grad_f32_ird_body<SPD, COST, RAMP>(w, m, o, theta + i * th_ws, ld, M, loss + i * loss_ws,
+                                                grad + i * grad_ws, ldg, nullptr, ckpt + i * ck_ws, blockIdx.x);
+    else
+        loss_grad_f32_body<SPD, COST, RAMP>(w, m, o, theta + i * th_ws, ld, M, loss + i * loss_ws, grad + i * grad_ws,
+                                            ldg, nullptr, ckpt + i * ck_ws, blockIdx.x);
 }
 
 // Warp-specialised form (PWC, 10 or 20 steps per day): a block of two warps owns 32 parameter
@@ -503,9 +672,9 @@ __global__ void __launch_bounds__(64) loss_grad_f32_ws_tab_kernel(const PolishWi
 
 }  // namespace
 
-size_t adjoint_ckpt_bytes_f32(const WindowDev& w, int M) {
+size_t adjoint_ckpt_bytes_f32(const WindowDev& w, const ModelDev& m, int M) {
     const size_t Mpad = ((size_t)M + kWsVectors - 1) / kWsVectors * kWsVectors;
-    return (size_t)(w.n_obs - 1) * 4 * Mpad * sizeof(float);
+    return (size_t)(w.n_obs - 1) * (m.ird ? 5 : 4) * Mpad * sizeof(float);
 }
 
 cudaError_t launch_loss_grad_f32(const WindowDev& w, const ModelDev& m, const ObsDev& o, const float* theta, int ld,
@@ -515,8 +684,8 @@ cudaError_t launch_loss_grad_f32(const WindowDev& w, const ModelDev& m, const Ob
     if (m.spd < 1 || m.spd > kMaxSpdGeneric) return cudaErrorInvalidValue;
     (void)cudaGetLastError();
     cudaError_t e = cudaSuccess;
-    const size_t obs = 2 * (size_t)((w.n_obs + 3) & ~3);
-    if (m.beta_form != BETA_RAMP && (m.spd == 10 || m.spd == 20)) {
+    const size_t obs = 2 * (size_t)((w.n_obs + 3) & ~3) * (m.ird ? 3 : 1);
+    if (m.beta_form != BETA_RAMP && !m.ird && (m.spd == 10 || m.spd == 20)) {
         // two warps per 32 vectors: the re-integration and the reverse sweep side by side
         const int Mpad = (M + kWsVectors - 1) / kWsVectors * kWsVectors;
         const size_t sm = (obs + (size_t)m.P * kWsVectors + 6 * (size_t)m.spd * kWsVectors + 3 * kWsVectors) * sizeof(float);
@@ -550,7 +719,7 @@ cudaError_t launch_loss_grad_f32(const WindowDev& w, const ModelDev& m, const Ob
     const size_t sm = (obs + (size_t)m.P * block + 3 * (size_t)m.spd * block) * sizeof(float);
 #define SIRD_LG32(SV, CV, RV)                                                                                 \
     {                                                                                                         \
-        auto kern = loss_grad_f32_kernel<SV, CV, RV>;                                                         \
+        auto kern = m.ird ? loss_grad_f32_kernel<SV, CV, RV, true> : loss_grad_f32_kernel<SV, CV, RV, false>;  \
         if (sm > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
         if (e == cudaSuccess)                                                                                 \
             kern<<<(M + block - 1) / block, block, sm, s>>>(w, m, o, theta, ld, M, loss, grad, ldg, grad_u0, ckpt); \
@@ -579,8 +748,8 @@ cudaError_t launch_loss_grad_f32_tab(const PolishWin* tab, int nw, int n_max, co
     if (m.spd < 1 || m.spd > kMaxSpdGeneric || nw > 65535) return cudaErrorInvalidValue;
     (void)cudaGetLastError();
     cudaError_t e = cudaSuccess;
-    const size_t obs = 2 * (size_t)((n_max + 3) & ~3);
-    if (m.beta_form != BETA_RAMP && (m.spd == 10 || m.spd == 20)) {
+    const size_t obs = 2 * (size_t)((n_max + 3) & ~3) * (m.ird ? 3 : 1);
+    if (m.beta_form != BETA_RAMP && !m.ird && (m.spd == 10 || m.spd == 20)) {
         const int Mpad = (M + kWsVectors - 1) / kWsVectors * kWsVectors;
         const size_t sm = (obs + (size_t)m.P * kWsVectors + 6 * (size_t)m.spd * kWsVectors + 3 * kWsVectors) * sizeof(float);
         const dim3 grid((unsigned)(Mpad / kWsVectors), (unsigned)nw);
@@ -613,7 +782,7 @@ cudaError_t launch_loss_grad_f32_tab(const PolishWin* tab, int nw, int n_max, co
     const dim3 grid((unsigned)((M + block - 1) / block), (unsigned)nw);
 #define SIRD_LG32(SV, CV, RV)                                                                                 \
     {                                                                                                         \
-        auto kern = loss_grad_f32_tab_kernel<SV, CV, RV>;                                                     \
+        auto kern = m.ird ? loss_grad_f32_tab_kernel<SV, CV, RV, true> : loss_grad_f32_tab_kernel<SV, CV, RV, false>; \
         if (sm > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
         if (e == cudaSuccess)                                                                                 \
             kern<<<grid, block, sm, s>>>(tab, m, theta, th_ws, ld, M, loss, loss_ws, grad, grad_ws, ldg, ckpt, ck_ws); \

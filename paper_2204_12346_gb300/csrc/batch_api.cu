@@ -506,7 +506,6 @@ extern "C" sird_status sird_batch_calibrate(sird_batch_t b, sird_result* results
 extern "C" sird_status sird_batch_polish(sird_batch_t b, int k, int iters, double first_step, sird_result* results) {
     TraceRange trace("sird_batch_polish");
     if (!b || !results) return berr(SIRD_ERR_ARG, "batch or results is NULL");
-    if (b->mdl.ird) return berr(SIRD_ERR_UNSUPPORTED, "polish: the adjoint covers F_D only");
     if (b->mdl.spd != 10 && b->mdl.spd != 20 && b->mdl.spd > 64)
         return berr(SIRD_ERR_UNSUPPORTED, "polish: FP32 needs steps_per_day <= 64");
     if (b->W > 65535) return berr(SIRD_ERR_UNSUPPORTED, "polish: at most 65535 windows");
@@ -519,7 +518,7 @@ extern "C" sird_status sird_batch_polish(sird_batch_t b, int k, int iters, doubl
     auto r256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
     const size_t tab_b = r256(sizeof(PolishWin) * W), keys_b = r256(sizeof(unsigned long long) * W * (size_t)k),
                  st_b = r256(polish_scratch_doubles(P, W * k) * sizeof(double)),
-                 ck_b = r256(polish_ckpt_floats(b->n_max, k) * sizeof(float) * W),
+                 ck_b = r256(polish_ckpt_floats(b->n_max, k, b->mdl) * sizeof(float) * W),
                  res_b = r256(sizeof(ResultDev) * W);
     const size_t need = tab_b + keys_b + st_b + ck_b + res_b;
     cudaError_t e = cudaSuccess;

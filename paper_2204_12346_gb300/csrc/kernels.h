@@ -175,7 +175,7 @@ cudaError_t launch_loss_grad_f64(const WindowDev& w, const ModelDev& m, const Ob
 
 // The same in FP32 (compensated trajectory; loss identical to the FP32 evaluation), checkpoints
 // at every day start in ckpt (adjoint_ckpt_bytes_f32); steps per day 10, 20 or at most 64.
-size_t adjoint_ckpt_bytes_f32(const WindowDev& w, int M);
+size_t adjoint_ckpt_bytes_f32(const WindowDev& w, const ModelDev& m, int M);
 cudaError_t launch_loss_grad_f32(const WindowDev& w, const ModelDev& m, const ObsDev& o, const float* theta, int ld,
                                  int M, float* loss, float* grad, int ldg, float* grad_u0, float* ckpt,
                                  cudaStream_t s);
@@ -201,7 +201,7 @@ cudaError_t launch_parameter_bands(const ModelDev& m, double* theta, int k, cons
 // sse into res[i].  scratch: polish_scratch_doubles(P, nw * k) doubles; ckpt: nw windows of
 // polish_ckpt_floats(n_max, k) floats (FP32), or adjoint_ckpt_bytes(w, m, k, ckpt_every) bytes.
 size_t polish_scratch_doubles(int P, int k);
-size_t polish_ckpt_floats(int n_max, int k);
+size_t polish_ckpt_floats(int n_max, int k, const ModelDev& m);
 cudaError_t launch_polish(const PolishWin* tab, int nw, int n_max, const WindowDev& w, const ObsDev& o,
                           const ModelDev& m, const PsoCoeffs<double>& c, const unsigned long long* keys, int k,
                           int iters, double first_step, int precision, double* scratch, void* ckpt, int ckpt_every,

@@ -371,9 +371,9 @@ size_t polish_scratch_doubles(int P, int k) {
     return pk * (6 + kTrials + 2 * kMem) + (size_t)k * (kTrials + 3) + (floats + 1) / 2 + 2 * (size_t)k + 8;
 }
 
-size_t polish_ckpt_floats(int n_max, int k) {
+size_t polish_ckpt_floats(int n_max, int k, const ModelDev& m) {
     const size_t kpad = ((size_t)k + 31) / 32 * 32;  // the adjoint's vectors, padded to whole warps
-    return (size_t)(n_max - 1) * 4 * kpad;
+    return (size_t)(n_max - 1) * (m.ird ? 5 : 4) * kpad;  // F_IRD: R's misfit too
 }
 
 int polish_trials() { return kTrials; }
@@ -388,7 +388,7 @@ cudaError_t launch_polish(const PolishWin* tab, int nw, int n_max, const WindowD
     PolishState s = carve(scratch, P, k, nw, f32 ? 1 : 0);
     const int kk = s.kk, kt = k * kTrials;
     const long long KT = (long long)kk * kTrials;
-    const long long ck_ws = (long long)polish_ckpt_floats(n_max, k);
+    const long long ck_ws = (long long)polish_ckpt_floats(n_max, k, m);
     // loss and gradient at every candidate's accepted point (trial slot 0 of its window)
     auto grad_at_slot0 = [&]() {
         return f32 ? launch_loss_grad_f32_tab(tab, nw, n_max, m, s.thf, kt, (int)KT, k, s.lnewf, k, s.gthf, k, kk,

@@ -721,13 +721,11 @@ extern "C" sird_status sird_loss_grad(sird_pso_t h, const void* d_theta, int M, 
         return h->fail(SIRD_ERR_ARG, "loss_grad: bad M/ld/pointers");
     if (ckpt_every < 1 || ckpt_every > 64) return h->fail(SIRD_ERR_ARG, "loss_grad: ckpt_every out of range [1, 64]");
     if (precision != 32 && precision != 64) return h->fail(SIRD_ERR_ARG, "loss_grad: precision must be 32 or 64");
-    if (h->mdl.ird && precision == 32)
-        return h->fail(SIRD_ERR_UNSUPPORTED, "loss_grad: the FP32 adjoint covers F_D only (F_IRD: precision 64)");
     if (precision == 32 && h->mdl.spd != 10 && h->mdl.spd != 20 && h->mdl.spd > 64)
         return h->fail(SIRD_ERR_UNSUPPORTED, "loss_grad: FP32 needs steps_per_day <= 64");
     if (M == 0) return SIRD_OK;
     const size_t need = precision == 64 ? adjoint_ckpt_bytes(h->win, h->mdl, M, ckpt_every)
-                                        : adjoint_ckpt_bytes_f32(h->win, M);
+                                        : adjoint_ckpt_bytes_f32(h->win, h->mdl, M);
     if (need > h->ckpt_bytes) {
         sird_status s = h->cuda(cudaStreamSynchronize(h->stream), "sync");
         if (s) return s;
@@ -755,8 +753,6 @@ extern "C" sird_status sird_pso_polish(sird_pso_t h, int k, int iters, double fi
     if (h->sticky) return h->sticky;
     if (h->shard_total > 0) return h->fail(SIRD_ERR_STATE, "polish: not for a shard of a swarm");
     if (h->precision != 32) return h->fail(SIRD_ERR_UNSUPPORTED, "polish: FP32 swarms only");
-    if (h->mdl.ird && precision == 32)
-        return h->fail(SIRD_ERR_UNSUPPORTED, "polish: the FP32 adjoint covers F_D only (F_IRD: precision 64)");
     if (k < 1 || k > 1024 || k > h->M || iters < 0 || !(first_step > 0) || ckpt_every < 1 || ckpt_every > 64 ||
         (precision != 32 && precision != 64))
         return h->fail(SIRD_ERR_ARG, "polish: bad k/iters/first_step/ckpt_every/precision");
@@ -764,7 +760,7 @@ extern "C" sird_status sird_pso_polish(sird_pso_t h, int k, int iters, double fi
         return h->fail(SIRD_ERR_UNSUPPORTED, "polish: FP32 needs steps_per_day <= 64");
     if (h->iter < 0) return h->fail(SIRD_ERR_STATE, "polish before init");
     const size_t nk = topk_scratch_keys(h->M, k);
-    const size_t ck = precision == 32 ? polish_ckpt_floats(h->win.n_obs, k) * sizeof(float)
+    const size_t ck = precision == 32 ? polish_ckpt_floats(h->win.n_obs, k, h->mdl) * sizeof(float)
                                       : adjoint_ckpt_bytes(h->win, h->mdl, k, ckpt_every);
     // device: the window's table entry | top-k keys (two buffers) | polish state | checkpoints
     const size_t tab_bytes = (sizeof(PolishWin) + 255) & ~(size_t)255;

@@ -113,8 +113,7 @@ def test_batch_polish_refusals():
     bi = sird.Batch(ird, beta_form=sird.BETA_RAMP, objective=sird.FIT_IRD, cost=sird.COST_MXSE, fit_I0=False,
                     iters=2, lb=lb, ub=ub)
     bi.calibrate()
-    with pytest.raises(sird.SirdError, match="UNSUPPORTED"):
-        bi.polish(k=4, iters=1)
+    assert len(bi.polish(k=4, iters=1)) == len(ird)  # F_IRD batches polish too (FP32 F_IRD adjoint)
 
 
 def test_batch_polish_512_window_layout_sampled_windows():

@@ -95,20 +95,6 @@ def test_ird_fp32_calibration_reports_its_fp64_loss_and_batches_agree():
         assert r["loss"] == O.loss(pb, r["theta"])
 
 
-def test_ird_rejects_the_fp32_gradient_calls():
-    # the FP32 adjoint covers F_D only; F_IRD takes the FP64 one
-    yD, yI, yR, N = ird_series("60d", 30)
-    lb, ub = configs.bounds(1, log=True)
-    cal = sird.Calibrator(yD, N, R0=float(yR[0]), objective=sird.FIT_IRD, yI=yI, yR=yR, particles=64, iters=2,
-                          lb=lb, ub=ub, log_scale=[1] * 4, precision=32)
-    cal.calibrate()
-    with pytest.raises(sird.SirdError, match="UNSUPPORTED"):
-        cal.loss_grad(torch.ones(4, 8, dtype=torch.float32, device="cuda"))
-    assert cal._lib.sird_pso_clear_error(cal.h) == sird.OK  # handle errors are sticky until cleared
-    L, G = cal.loss_grad(torch.ones(4, 8, dtype=torch.float64, device="cuda"))
-    assert L.shape == (8,) and G.shape == (4, 8)
-
-
 def test_ird_batch_set_observations_equals_a_fresh_batch():
     ser = synth.reported_IR(synth.load_series("450d"), 4)
     lay = {"L": np.array([25, 40]), "M": np.array([200, 450]), "T": np.array([30, 200])}
@@ -227,5 +213,100 @@ def test_ird_fp64_polish_never_worsens_and_reports_the_oracle_loss():
     pb = O.Problem(yD=yD, yI=yI, yR=yR, N=N, R0=float(yR[0]), I0=float(yI[0]), fit_I0=False, spd=10,
                    beta_form=O.BETA_RAMP, cost=O.MXSE, objective=O.FIT_IRD)
     assert r1["loss"] == O.loss(pb, r1["theta"])
-    with pytest.raises(sird.SirdError, match="UNSUPPORTED"):
-        cal.polish(k=4, iters=2, first_step=1e-2, precision=32)
+
+
+# ---------------------------------------------------------------- F_IRD^C gradient (FP32 adjoint)
+
+RHO_F32 = 4e-6  # relative accuracy assumed of the FP32 trajectory's I, R, D (as for the F_D gradient)
+
+
+def ird_residual_bound(pb, th, cost, which, rho=RHO_F32):
+    """|theta_j| times the change of dL/dtheta_j that relative errors rho of the dominant series'
+    trajectory can cause through its scaled residuals e_i = (y_i - yhat_i) / range (MAPE: unscaled):
+    MSE (2/n) sum_i ((rho yhat_i)/range^2) |dyhat_i/dlog theta_j|, MXSE the same at the largest e_i^2,
+    MAE / MAPE the residuals within the error band, which may change sign.  Sensitivities by
+    central differences of the oracle's trajectory."""
+    key, y = ("I", pb.yI) if which == 0 else (("R", pb.yR) if which == 1 else ("D", pb.yD))
+    y = np.asarray(y, dtype=np.float64)
+    n = len(y)
+    yh = O.simulate(pb, th, n - 1)[key]
+    sc = 1.0 if pb.cost == O.MAPE else (y.max() - y.min())
+    Sens = np.zeros((n, th.size))
+    for j in range(th.size):
+        tp, tm = th.copy(), th.copy()
+        tp[j] *= 1 + 1e-5
+        tm[j] *= 1 - 1e-5
+        Sens[:, j] = (O.simulate(pb, tp, n - 1)[key] - O.simulate(pb, tm, n - 1)[key]) / 2e-5
+    dY = rho * np.abs(yh)
+    e = (y - yh) / sc
+    if cost == "mse":
+        return (2.0 / n) * ((dY / sc ** 2)[:, None] * np.abs(Sens)).sum(0)
+    if cost == "mxse":
+        i = int(np.argmax(e * e))
+        near_tie = np.sort(e * e)[-2] > (1 - 1e-4) * e[i] ** 2
+        return 2.0 * ((dY[i] / sc + (np.abs(e[i]) if near_tie else 0.0)) / sc) * np.abs(Sens[i])
+    w = np.full(n, 1.0 / (n * sc)) if cost == "mae" else np.where(y != 0, 100.0 / np.maximum(np.abs(y), 1e-300)
+                                                                  / max(int((y != 0).sum()), 1), 0.0)
+    flip = np.abs(y - yh) <= dY
+    return 2.0 * ((w * flip)[:, None] * np.abs(Sens)).sum(0)
+
+
+@pytest.mark.parametrize("form,cost,dominant,fit_I0", [
+    ("pwc", "mse", "I", True), ("pwc", "mse", "R", True), ("pwc", "mse", "D", True), ("pwc", "mae", "R", True),
+    ("pwc", "mape", "D", True), ("pwc", "mxse", "I", True), ("ramp", "mxse", "R", False), ("ramp", "mxse", "D", False),
+    ("ramp", "mse", "I", False), ("ramp", "mape", "R", True)])
+def test_ird_adjoint_f32_within_tolerance(form, cost, dominant, fit_I0):
+    # the FP32 adjoint of F_IRD^C: its loss the FP32 evaluation's bit for bit, its gradient the
+    # oracle's FP64 gradient at the same FP32-representable theta within
+    #     |theta_j (g32_j - g64_j)| <= 1e-5 (|theta . g64|_inf + L) + ird_residual_bound_j,
+    # on points where the dominant compartment is clear (top two costs more than 1e-4 apart)
+    yD, N, pb, th, common = dominated_problem(form, cost, dominant, fit_I0)
+    th = f32(th)
+    cal = sird.Calibrator(yD, N, precision=32, **common)
+    T = torch.from_numpy(np.ascontiguousarray(th.T).astype(np.float32)).cuda()
+    L, G, GU = cal.loss_grad(T, grad_u0=True)
+    E = cal.eval(T)
+    L, G, GU, E = L.cpu().numpy(), G.cpu().numpy().T.astype(np.float64), GU.cpu().numpy().T, E.cpu().numpy()
+    assert np.array_equal(L, E)
+    worst, used, seen = 0.0, 0, set()
+    for j in range(th.shape[0]):
+        c = np.array(compartment_costs(pb, th[j]))
+        top = np.sort(c)[::-1]
+        if top[0] - top[1] <= 1e-4 * top[0]:
+            continue
+        which = int(np.argmax(c))
+        seen.add(which)
+        Lo, Go, GUo = O.loss_grad(pb, th[j])
+        tol = 1e-5 * (np.abs(th[j] * Go).max() + abs(Lo)) + ird_residual_bound(pb, th[j], cost, which)
+        worst = max(worst, (np.abs(th[j] * (G[j] - Go)) / tol).max())
+        if which == 1:
+            assert GU[j, 2] != 0.0  # lambda_R(0) carries R's misfit
+        used += 1
+    assert used >= 24, used
+    print("worst gradient error / tolerance", worst, "dominant seen", sorted("IRD"[i] for i in seen))
+    assert worst <= 1.0, worst
+
+
+def test_ird_fp32_polish_and_batch_polish():
+    # FP32 polish of F_IRD^MXSE (the paper's representative objective, ramp beta, initial state
+    # from the data): never worse than the swarm, reports the oracle's FP64 loss of its point, and a
+    # batch of windows polished together gives each window's one-window polish bit for bit
+    ser = synth.reported_IR(synth.load_series("450d"), 2)
+    lay = {"L": np.array([35, 35, 28]), "M": np.array([600, 900, 320]), "T": np.array([40, 160, 300])}
+    wins = synth.rolling_window_problems(ser, lay)
+    lb, ub = configs.bounds_ramp(fit_I0=False)
+    kw = dict(K=1, spd=10, beta_form=sird.BETA_RAMP, fit_I0=False, cost=sird.COSTS["mxse"], objective=sird.FIT_IRD,
+              lb=lb, ub=ub, seed=5)
+    batch = sird.Batch(wins, iters=20, **kw)
+    r0 = batch.calibrate()
+    rb = batch.polish(k=4, iters=8, first_step=1e-2)
+    for i, w in enumerate(wins):
+        pb = O.Problem(yD=w["yD"], yI=w["yI"], yR=w["yR"], N=w["N"], R0=w["R0"], I0=w["I0"], fit_I0=False, spd=10,
+                       beta_form=O.BETA_RAMP, cost=O.MXSE, objective=O.FIT_IRD)
+        assert rb[i]["loss"] <= r0[i]["loss"]
+        assert rb[i]["loss"] == O.loss(pb, rb[i]["theta"])
+        cal = sird.Calibrator(w["yD"], w["N"], R0=w["R0"], I0=w["I0"], yI=w["yI"], yR=w["yR"], particles=w["particles"],
+                              iters=20, precision=32, stream_id=i, **kw)
+        cal.calibrate()
+        r1 = cal.polish(k=4, iters=8, first_step=1e-2, precision=32)
+        assert r1["loss"] == rb[i]["loss"] and np.array_equal(r1["theta"], rb[i]["theta"]), (i, r1, rb[i])
