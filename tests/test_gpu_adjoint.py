@@ -166,6 +166,7 @@ def check_f32_gradient(pb, th, L, G, E, cost="mse"):
         Lo, Go, _ = O.loss_grad(pb, th[j])
         tol = 1e-5 * (np.abs(th[j] * Go).max() + abs(Lo)) + residual_bound(pb, th[j], cost)
         worst = max(worst, (np.abs(th[j] * (G[j] - Go)) / tol).max())
+    print("worst gradient error / tolerance", worst)
     assert worst <= 1.0, worst
 
 
