@@ -156,3 +156,52 @@ def test_degenerate_parameters(cost):
     for j in (1, 2, 3):
         assert rel_err(want[j], const) <= 1e-14, (j, want[j], const)
         assert got64[j] == want[j]
+
+
+# ------------------------------------------------------------------ the shortest window, a batch of one
+
+@pytest.mark.parametrize("cost", ["mse", "mxse", "mae", "mape"])
+@pytest.mark.parametrize("spd", [10, 1])
+def test_one_day_window(cost, spd):
+    # two observations (days 0 and 1): FP64 losses, a plain FP64 calibration and the FP64 adjoint
+    # identical to the oracle's; FP32 losses within 1e-5 and the FP32 loss of the adjoint equal to
+    # the FP32 evaluation's
+    y, N, _, _ = window("60d", 1)
+    assert len(y) == 2
+    th = box_thetas(2, 64, 41)
+    pb = O.Problem(yD=y, N=N, K=2, spd=spd, cost=O.COSTS[cost])
+    want = O.losses(pb, th)
+    c64 = calibrator(y, N, 2, spd, 64, sird.COSTS[cost])
+    assert np.array_equal(gpu_eval(c64, th, 64), want)
+    got32 = gpu_eval(calibrator(y, N, 2, spd, 32, sird.COSTS[cost]), th, 32)
+    assert_fp32_losses(got32, want, ("one day", cost, spd))
+    L, G, GU = gpu_loss_grad(c64, th, 3)
+    for j in range(th.shape[0]):
+        Lo, Go, GUo = O.loss_grad(pb, th[j])
+        assert L[j] == Lo and np.array_equal(G[j], Go) and np.array_equal(GU[j], GUo), j
+    lb, ub = configs.bounds(2, log=False)
+    res = calibrator(y, N, 2, spd, 64, sird.COSTS[cost], M=48, iters=6, lb=lb, ub=ub, seed=4).calibrate()
+    pso = O.PSO(pb, 48, lb, ub, seed=4).init().step(6)
+    assert res["index"] == pso.gbest_idx and res["loss"] == pso.gbest_f
+    assert np.array_equal(res["theta"], pso.gbest)
+    c32 = calibrator(y, N, 2, spd, 32, sird.COSTS[cost])
+    L32, _, _, E32 = f32_loss_grad(c32, f32(th))
+    assert np.array_equal(L32, E32)
+
+
+def test_batch_of_one_window():
+    # a batch holding a single window (one block at work, the rest of the grid idle) equals the
+    # window's own calibration bit for bit, in both launch forms
+    ser = synth.load_series("450d")
+    wins = synth.rolling_window_problems(ser, {"L": np.array([37]), "M": np.array([700]), "T": np.array([90])})
+    lb, ub = configs.bounds(3, log=True)
+    kw = dict(K=3, spd=10, lb=lb, ub=ub, log_scale=[1] * 6, seed=8)
+    w = wins[0]
+    cal = sird.Calibrator(w["yD"], w["N"], R0=w["R0"], particles=w["particles"], iters=9, precision=32, stream_id=0,
+                          reeval_topk=0, **kw)
+    one = cal.calibrate()
+    for mode in (sird.LAUNCH_WINDOW_PER_BLOCK, sird.LAUNCH_FLAT):
+        got = sird.Batch(wins, iters=9, launch_mode=mode, **kw).calibrate()
+        assert len(got) == 1
+        assert got[0]["index"] == one["index"] and got[0]["loss"] == one["loss"], (mode, got[0], one)
+        assert got[0]["loss_search"] == one["loss_search"] and np.array_equal(got[0]["theta"], one["theta"]), mode
