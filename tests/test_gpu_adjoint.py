@@ -122,7 +122,7 @@ def f32_loss_grad(cal, th):
             E.cpu().numpy())
 
 
-RHO_F32 = 4e-6  # relative accuracy of the FP32 trajectory's D: 2^-24 x (sqrt(1800 steps) + 90 day folds) ~ 3.5e-6
+RHO_F32 = 4e-7  # relative accuracy of the FP32 trajectory's D assumed by the gradient bound: 100x what the losses' 1e-5 at good fits imply (~3e-9)
 
 
 def residual_bound(pb, th, cost, rho=RHO_F32):

@@ -217,7 +217,7 @@ def test_ird_fp64_polish_never_worsens_and_reports_the_oracle_loss():
 
 # ---------------------------------------------------------------- F_IRD^C gradient (FP32 adjoint)
 
-RHO_F32 = 4e-6  # relative accuracy assumed of the FP32 trajectory's I, R, D (as for the F_D gradient)
+RHO_F32 = 4e-7  # relative accuracy assumed of the FP32 trajectory's I, R, D (as for the F_D gradient)
 
 
 def ird_residual_bound(pb, th, cost, which, rho=RHO_F32):
