@@ -4,8 +4,8 @@ Sec. 3.3: every particle's trajectory and loss are computed independently; the s
 global best is the only coupling between particles.  Rank r holds the contiguous particles
 offset_r .. offset_r + count_r - 1 (counts differ by at most one).  After the initialisation
 and after every iteration the ranks agree on the particle with the lowest personal-best loss
-(lowest global index on ties) through one all-reduce (minimum) of a 64-bit key, and the rank
-holding it broadcasts its position: 8 + 4P bytes per iteration.  With every shard numbering
+(lowest global index on ties) through one all-gather of every rank's 64-bit key and position:
+(8 + 4P) bytes from each rank per iteration, one collective and one wait.  With every shard numbering
 its particles globally (sird_pso_set_shard), the shards together follow the unsharded swarm
 exactly.  The final answer is the FP64 re-evaluation of the swarm's k best personal bests,
 gathered from the shards.
@@ -66,21 +66,30 @@ def key_parts(key: int) -> tuple[float, int]:
 
 
 def exchange_best(loss: float, index: int, z, offsets: list[int], group=None, device=None):
-    """The swarm's global best from every rank's shard best: all-reduce (minimum) of the key,
-    then the holding rank's position broadcast to all.  Returns (loss, index, z [P] float32)."""
+    """The swarm's global best from every rank's shard best: one all-gather of each rank's record
+    (its 64-bit key, then its position as FP32 bits two to a 64-bit word), then the record with
+    the lowest key -- the same on every rank, with one collective and one wait per exchange.
+    Returns (loss, index, z [P] float32)."""
     import torch
     import torch.distributed as dist
 
-    key = torch.tensor([best_key(loss, index)], dtype=torch.int64, device=device)
-    dist.all_reduce(key, op=dist.ReduceOp.MIN, group=group)
-    gloss, gidx = key_parts(int(key.item()))
-    owner = owner_of(gidx, offsets)
-    rank = dist.get_rank(group)
-    zt = torch.from_numpy(np.ascontiguousarray(np.asarray(z, dtype=np.float32))).to(device) if rank == owner \
-        else torch.empty(len(z), dtype=torch.float32, device=device)
-    src = owner if group is None else dist.get_global_rank(group, owner)
-    dist.broadcast(zt, src=src, group=group)
-    return gloss, gidx, zt.cpu().numpy()
+    zf = np.ascontiguousarray(np.asarray(z, dtype=np.float32)).ravel()
+    P = zf.size
+    words = (P + 1) // 2
+    rec = np.zeros(1 + words, dtype=np.int64)
+    rec[0] = best_key(loss, index)
+    zpad = np.zeros(2 * words, dtype=np.float32)
+    zpad[:P] = zf
+    rec[1:] = zpad.view(np.int64)
+    mine = torch.from_numpy(rec).to(device)
+    parts = [torch.empty_like(mine) for _ in range(dist.get_world_size(group))]
+    dist.all_gather(parts, mine, group=group)
+    recs = torch.stack(parts).cpu().numpy()
+    win = int(np.argmin(recs[:, 0]))  # keys are distinct: every particle index is held once
+    gloss, gidx = key_parts(int(recs[win, 0]))
+    if owner_of(gidx, offsets) != win:
+        raise RuntimeError(f"shard exchange: particle {gidx} reported by rank {win}, which does not hold it")
+    return gloss, gidx, recs[win, 1:].copy().view(np.float32)[:P].copy()
 
 
 class ShardFailure(RuntimeError):
