@@ -330,7 +330,8 @@ def s_to_calibrate_batch(batch, c, wins, lb, ub, model, stride=32) -> dict:
     seconds of the batched FP32 swarm followed by the batched L-BFGS polish of every window's k
     best personal bests (FP32 trials and adjoint, FP64 re-scoring) until every subsampled window's
     FP64 loss is <= (1 + 1e-6) L_ref; the schedule tries 32 candidates per window first, then 128,
-    then the FP32 swarm with the reference's iteration count (with and without the polish)."""
+    then the FP32 swarm with the reference's iteration count and 2x and 4x that (with and without the
+    polish)."""
     import torch
 
     from paper_2204_12346_gb300 import sird
@@ -360,17 +361,19 @@ def s_to_calibrate_batch(batch, c, wins, lb, ub, model, stride=32) -> dict:
            "fp64_pso_s_subsample": t64, "fp64_pso_s_all_windows_est": t64 * scale, "trials": []}
     # the batch's own iterations with the polish first; then (for objectives whose kinks stall the
     # polish, such as F_IRD^MXSE) the FP32 batched swarm run for the FP64 reference's iterations
-    long_batch = None
+    long_batches = {}
     schedule = [(1, 32, 0), (1, 32, 10), (1, 32, 20), (1, 32, 40), (1, 128, 20), (1, 128, 40), (1, 128, 80),
-                (1, 128, 160), (10, 32, 0), (10, 32, 20), (10, 128, 40)]
+                (1, 128, 160), (10, 32, 0), (10, 32, 20), (10, 128, 40), (20, 32, 0), (20, 128, 40), (40, 32, 0),
+                (40, 128, 40)]
     for mult, k, n in schedule:
         b = batch
         if mult != 1:
-            if long_batch is None:
-                long_batch = sird.Batch(wins, spd=c["spd"], iters=mult * c["iters"], lb=lb, ub=ub,
-                                        stream=torch.cuda.current_stream(), **model)
-                long_batch.calibrate()  # warm-up (the autotuner runs at creation)
-            b = long_batch
+            if mult not in long_batches:
+                long_batches.clear()  # one longer batch at a time
+                long_batches[mult] = sird.Batch(wins, spd=c["spd"], iters=mult * c["iters"], lb=lb, ub=ub,
+                                                stream=torch.cuda.current_stream(), **model)
+                long_batches[mult].calibrate()  # warm-up (the autotuner runs at creation)
+            b = long_batches[mult]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         res = b.calibrate()
