@@ -114,12 +114,12 @@ def test_ird_batch_set_observations_equals_a_fresh_batch():
 
 # ---------------------------------------------------------------- F_IRD^C gradient (FP64 adjoint)
 
-def dominated_problem(form, cost, dominant, fit_I0):
+def dominated_problem(form, cost, dominant, fit_I0, days=35):
     """Reported series from a trajectory with 0.2% noise, one compartment moved 5-8% off it so that
     its normalised cost is the largest of the three (F_IRD^C, Sec. 3.1); returns the GPU keywords,
     the oracle problem and parameter vectors around the generating point."""
     s = synth.load_series("60d")
-    days, R0 = 35, 800.0
+    R0 = 800.0
     if form == "pwc":
         ref, kw, gkw = [0.23, 0.19, 0.17, 0.13, 0.1, 0.002, 1.1e4], dict(K=4), dict(K=4, beta_form=sird.BETA_PWC)
     else:
@@ -167,7 +167,7 @@ def compartment_costs(pb, th):
     ("pwc", "mae", "R", True), ("pwc", "mape", "D", True), ("pwc", "mxse", "I", True), ("pwc", "mxse", "R", False),
     ("ramp", "mxse", "I", False), ("ramp", "mxse", "R", False), ("ramp", "mxse", "D", False),
     ("ramp", "mse", "D", False), ("ramp", "mape", "I", False), ("ramp", "mae", "D", True), ("ramp", "mape", "R", True)])
-@pytest.mark.parametrize("ckpt", [1, 7, 16])
+@pytest.mark.parametrize("ckpt", [1, 7, 16, 64])
 def test_ird_adjoint_f64_bit_exact(form, cost, dominant, fit_I0, ckpt):
     # the FP64 adjoint of F_IRD^C against the oracle's discrete adjoint: loss, dL/dtheta and
     # dL/du0 identical, with the named compartment attaining the maximum at the generating point
@@ -251,16 +251,19 @@ def ird_residual_bound(pb, th, cost, which, rho=RHO_F32):
     return 2.0 * ((w * flip)[:, None] * np.abs(Sens)).sum(0)
 
 
-@pytest.mark.parametrize("form,cost,dominant,fit_I0", [
-    ("pwc", "mse", "I", True), ("pwc", "mse", "R", True), ("pwc", "mse", "D", True), ("pwc", "mae", "R", True),
-    ("pwc", "mape", "D", True), ("pwc", "mxse", "I", True), ("ramp", "mxse", "R", False), ("ramp", "mxse", "D", False),
-    ("ramp", "mse", "I", False), ("ramp", "mape", "R", True)])
-def test_ird_adjoint_f32_within_tolerance(form, cost, dominant, fit_I0):
+@pytest.mark.parametrize("form,cost,dominant,fit_I0,days", [
+    ("pwc", "mse", "I", True, 35), ("pwc", "mse", "R", True, 35), ("pwc", "mse", "D", True, 35),
+    ("pwc", "mae", "R", True, 35), ("pwc", "mape", "D", True, 35), ("pwc", "mxse", "I", True, 35),
+    ("ramp", "mxse", "R", False, 35), ("ramp", "mxse", "D", False, 35), ("ramp", "mse", "I", False, 35),
+    ("ramp", "mape", "R", True, 35),
+    # more than 1000 Euler steps: the trajectory's long-window mode in the forward pass
+    ("pwc", "mse", "D", True, 110), ("ramp", "mxse", "I", False, 110)])
+def test_ird_adjoint_f32_within_tolerance(form, cost, dominant, fit_I0, days):
     # the FP32 adjoint of F_IRD^C: its loss the FP32 evaluation's bit for bit, its gradient the
     # oracle's FP64 gradient at the same FP32-representable theta within
     #     |theta_j (g32_j - g64_j)| <= 1e-5 (|theta . g64|_inf + L) + ird_residual_bound_j,
     # on points where the dominant compartment is clear (top two costs more than 1e-4 apart)
-    yD, N, pb, th, common = dominated_problem(form, cost, dominant, fit_I0)
+    yD, N, pb, th, common = dominated_problem(form, cost, dominant, fit_I0, days)
     th = f32(th)
     cal = sird.Calibrator(yD, N, precision=32, **common)
     T = torch.from_numpy(np.ascontiguousarray(th.T).astype(np.float32)).cuda()
@@ -287,22 +290,31 @@ def test_ird_adjoint_f32_within_tolerance(form, cost, dominant, fit_I0):
     assert worst <= 1.0, worst
 
 
-def test_ird_fp32_polish_and_batch_polish():
-    # FP32 polish of F_IRD^MXSE (the paper's representative objective, ramp beta, initial state
-    # from the data): never worse than the swarm, reports the oracle's FP64 loss of its point, and a
-    # batch of windows polished together gives each window's one-window polish bit for bit
+@pytest.mark.parametrize("form,cost", [("ramp", "mxse"), ("pwc", "mse"), ("pwc", "mape")])
+def test_ird_fp32_polish_and_batch_polish(form, cost):
+    # FP32 polish of F_IRD (F_IRD^MXSE with the ramp and the data's initial state: the paper's
+    # representative setting): never worse than the swarm, reports the oracle's FP64 loss of its
+    # point, and a batch of windows polished together gives each window's one-window polish bit
+    # for bit
     ser = synth.reported_IR(synth.load_series("450d"), 2)
     lay = {"L": np.array([35, 35, 28]), "M": np.array([600, 900, 320]), "T": np.array([40, 160, 300])}
     wins = synth.rolling_window_problems(ser, lay)
-    lb, ub = configs.bounds_ramp(fit_I0=False)
-    kw = dict(K=1, spd=10, beta_form=sird.BETA_RAMP, fit_I0=False, cost=sird.COSTS["mxse"], objective=sird.FIT_IRD,
-              lb=lb, ub=ub, seed=5)
+    if form == "ramp":
+        lb, ub = configs.bounds_ramp(fit_I0=False)
+        kw = dict(K=1, beta_form=sird.BETA_RAMP)
+        okw = dict(beta_form=O.BETA_RAMP)
+    else:
+        lb, ub = configs.bounds(3, log=True)
+        lb, ub = lb[:-1], ub[:-1]  # the initial state from the data: no I0 dimension
+        kw = dict(K=3, beta_form=sird.BETA_PWC, log_scale=[1] * len(lb))
+        okw = dict(K=3)
+    kw.update(spd=10, fit_I0=False, cost=sird.COSTS[cost], objective=sird.FIT_IRD, lb=lb, ub=ub, seed=5)
     batch = sird.Batch(wins, iters=20, **kw)
     r0 = batch.calibrate()
     rb = batch.polish(k=4, iters=8, first_step=1e-2)
     for i, w in enumerate(wins):
         pb = O.Problem(yD=w["yD"], yI=w["yI"], yR=w["yR"], N=w["N"], R0=w["R0"], I0=w["I0"], fit_I0=False, spd=10,
-                       beta_form=O.BETA_RAMP, cost=O.MXSE, objective=O.FIT_IRD)
+                       cost=O.COSTS[cost], objective=O.FIT_IRD, **okw)
         assert rb[i]["loss"] <= r0[i]["loss"]
         assert rb[i]["loss"] == O.loss(pb, rb[i]["theta"])
         cal = sird.Calibrator(w["yD"], w["N"], R0=w["R0"], I0=w["I0"], yI=w["yI"], yR=w["yR"], particles=w["particles"],
