@@ -65,7 +65,7 @@ int InitializeInjectionNvtx2(NvtxGetExportTableFunc_t get) {
 const char* tool_log(void) { return log_buf; }
 """
 
-DRIVER = r"""
+CALLER = r"""
 import ctypes as C, os, sys
 sys.path.insert(0, sys.argv[1])
 from paper_2204_12346_gb300 import sird
@@ -91,9 +91,9 @@ def test_entry_points_open_and_close_their_ranges(tmp_path):
     r = subprocess.run([gcc, "-std=c11", "-shared", "-fPIC", "-I", CUDA_INCLUDE, str(tmp_path / "tool.c"), "-o",
                         str(tool), "-ldl"], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
-    (tmp_path / "driver.py").write_text(DRIVER)
+    (tmp_path / "caller.py").write_text(CALLER)
     env = dict(os.environ, NVTX_INJECTION64_PATH=str(tool))
-    run = subprocess.run([sys.executable, str(tmp_path / "driver.py"), ROOT], env=env, capture_output=True, text=True,
+    run = subprocess.run([sys.executable, str(tmp_path / "caller.py"), ROOT], env=env, capture_output=True, text=True,
                          timeout=300)
     assert run.returncode == 0, run.stderr
     events = [tuple(l.split()) for l in run.stdout.splitlines()]
