@@ -56,17 +56,21 @@ PROFILED = {
     "window60": {"files": ["pso_persistent.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
            "sha": "d2902a5aafa962f0", "traffic_bytes": 457216, "fma_pipe": 0.3575,
            "profile": "profiles/pso_f32_persistent_window60.md"},
-    "gradient90": {"files": ["adjoint_f32.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "4e59aa10f7c4bd00",
-           "traffic_bytes": 165888, "fma_pipe": 0.0737, "profile": "profiles/loss_grad_f32_gradient90.md"},
+    "gradient90": {"files": ["adjoint_f32.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
+           "sha": "5aaddeec214ad36e", "traffic_bytes": 182016, "fma_pipe": 0.0760,
+           "profile": "profiles/loss_grad_f32_gradient90.md"},
     "paper": {"files": ["batched.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
            "sha": "aea9ece54ea983f8", "traffic_bytes": 14973660000, "fma_pipe": 0.5684,
            "profile": "profiles/pso_batch_f32_paper.md"},
-    "paper_ird": {"files": ["batched_flat.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "e33e6bd7ec2fd256",
-           "traffic_bytes": 17636036000, "fma_pipe": 0.4623, "profile": "profiles/pso_flat_f32_paper_ird.md"},
-    "stability": {"files": ["batched.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "e33e6bd7ec2fd256",
-           "traffic_bytes": 300430231040, "fma_pipe": 0.5098, "profile": "profiles/pso_batch_f32_stability.md"},
-    "swarm2p20": {"files": ["pso_kernels.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"], "sha": "0fd47436f9d0b4cd",
-           "traffic_bytes": 276988160, "fma_pipe": 0.7481, "profile": "profiles/pso_f32_kernel_swarm2p20.md"},
+    "paper_ird": {"files": ["batched.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
+           "sha": "aea9ece54ea983f8", "traffic_bytes": 14900860000, "fma_pipe": 0.5664,
+           "profile": "profiles/pso_batch_f32_paper_ird.md"},
+    "stability": {"files": ["batched.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
+           "sha": "aea9ece54ea983f8", "traffic_bytes": 300467837184, "fma_pipe": 0.5892,
+           "profile": "profiles/pso_batch_f32_stability.md"},
+    "swarm2p20": {"files": ["pso_kernels.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
+           "sha": "ae88d79edec298bf", "traffic_bytes": 275589888, "fma_pipe": 0.7605,
+           "profile": "profiles/pso_f32_kernel_swarm2p20.md"},
 }
 
 
