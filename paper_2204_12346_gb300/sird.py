@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+from collections.abc import Sequence
 
 import numpy as np
 
@@ -69,6 +70,32 @@ class Result(C.Structure):
     def as_dict(self) -> dict:
         return {"theta": np.array(self.theta[: self.n_params]), "loss": self.loss, "loss_search": self.loss_search,
                 "r2_D": self.r2_D, "index": self.index, "iters_done": self.iters_done}
+
+
+class BatchResults(Sequence):
+    """Per-window results of a batched call, in window order: results[i] is window i's result dict
+    (as Result.as_dict gives it, built on first access and kept), so a caller that reads a few
+    windows of a large batch pays for those only."""
+
+    def __init__(self, raw):
+        self._raw = raw  # the ctypes Result array the library filled
+        self._dicts = {}
+
+    def __len__(self) -> int:
+        return len(self._raw)
+
+    def __getitem__(self, i):
+        if isinstance(i, slice):
+            return [self[j] for j in range(*i.indices(len(self)))]
+        n = len(self._raw)
+        if i < 0:
+            i += n
+        if not 0 <= i < n:
+            raise IndexError("window index out of range")
+        d = self._dicts.get(i)
+        if d is None:
+            d = self._dicts[i] = self._raw[i].as_dict()
+        return d
 
 
 _lib = None
@@ -488,20 +515,22 @@ class Batch:
         return int(nb.value)
 
     def calibrate(self):
+        """Calibrates every window (one graph launch); a BatchResults sequence of result dicts."""
         res = (Result * self.W)()
         st = self._lib.sird_batch_calibrate(self.h, res)
         if st != OK:
             raise SirdError(st, self._lib.sird_last_error(None).decode())
-        return [r.as_dict() for r in res]
+        return BatchResults(res)
 
     def polish(self, k=32, iters=40, first_step=1e-2):
         """L-BFGS polish of every window's k best personal bests (FP32 trials and adjoint, FP64
-        algebra and re-scoring), all windows together; one result dict per window."""
+        algebra and re-scoring), all windows together; a BatchResults sequence, one result dict
+        per window."""
         res = (Result * self.W)()
         st = self._lib.sird_batch_polish(self.h, int(k), int(iters), float(first_step), res)
         if st != OK:
             raise SirdError(st, self._lib.sird_last_error(None).decode())
-        return [r.as_dict() for r in res]
+        return BatchResults(res)
 
     def close(self):
         if getattr(self, "h", None):
