@@ -446,7 +446,10 @@ sird_status sird_pso_calibrate_batched(int W, const sird_problem* problems, cons
  *   problem, config  host structs as for sird_pso_create, checked the same way (precision
  *                    must be 32, objective F_D); y_D gives D0 = y_D[0], the zeros that MAPE
  *                    skips and, for MAPE, the reciprocals 1/y_D rounded to float
- *   d_obs            device [n_obs] float observations of D (the float values of y_D)
+ *   d_obs            device [n_obs] float observations of D: y_D[i] - y_D[0] rounded to float,
+ *                    as the handle stores them (only differences of consecutive entries are
+ *                    used, so the float values of y_D give the same results when y_D[0] = 0 or
+ *                    when y_D holds integers below 2^24)
  *   d_x, d_v, d_pbest  device [P][ld] float, read and written (layout of sird_pso_eval)
  *   d_pbest_f        device [ld] float, read and written
  *   d_gbest          device [P] float: read as the previous global best, rewritten

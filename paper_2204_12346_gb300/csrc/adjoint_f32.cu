@@ -178,6 +178,7 @@ __device__ __forceinline__ float cb_of_f32(const WindowDev& w, float beta) {
 // day (the first with the largest e^2).
 template <int COST>
 struct CkptObs {
+    static constexpr bool kWantsQ = true;  // day_start stores S = Q - I
     CostT<float, COST> c;
     const float* invys;
     float* ck;
@@ -210,6 +211,7 @@ struct CkptObs {
 // first day of each series' largest scaled e^2 (MXSE) and the dominant series (0 I, 1 R, 2 D).
 template <int COST>
 struct CkptObsIRD {
+    static constexpr bool kWantsQ = true;
     CostT<float, COST> cI, cR, cD;
     const float *ys, *invys;
     int ps, L;

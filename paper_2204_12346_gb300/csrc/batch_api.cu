@@ -297,7 +297,7 @@ sird_status batch_create(int W, const sird_problem* problems, const sird_pso_con
         const sird_problem& p = problems[i];
         double mean = 0.0;
         for (int j = 0; j < p.n_obs; ++j) {
-            yf[obs_off[i] + j] = (float)p.y_D[j];
+            yf[obs_off[i] + j] = obs_f32(p.y_D, j, true);
             invy[obs_off[i] + j] = p.y_D[j] != 0.0 ? (float)(1.0 / p.y_D[j]) : 0.f;
             yd[obs_off[i] + j] = p.y_D[j];
             if (p.objective == SIRD_FIT_IRD) {
@@ -305,7 +305,7 @@ sird_status batch_create(int W, const sird_problem* problems, const sird_pso_con
                 const double* ir[2] = {p.y_I, p.y_R};
                 for (int k = 0; k < 2; ++k) {
                     const int o = obs_off[i] + (k + 1) * ps + j;
-                    yf[o] = (float)ir[k][j];
+                    yf[o] = obs_f32(ir[k], j, k == 1);
                     invy[o] = ir[k][j] != 0.0 ? (float)(1.0 / ir[k][j]) : 0.f;
                     yd[o] = ir[k][j];
                 }
@@ -640,7 +640,7 @@ extern "C" sird_status sird_batch_set_observations(sird_batch_t b, const double*
             for (int j = 0; j < pr.n_obs; ++j) {
                 const int o = b->obs_off[i] + k * ps + j;
                 const double v = y[k * pr.n_obs + j];
-                yf[o] = (float)v;
+                yf[o] = obs_f32(y + k * pr.n_obs, j, k != 1);
                 invy[o] = v != 0.0 ? (float)(1.0 / v) : 0.f;
                 yd[o] = v;
             }

@@ -90,12 +90,18 @@ struct ResultDev {
     int count;  // candidates evaluated
 };
 
-// Observations on the device.
+// Observations on the device (series stacked D | I | R for F_IRD, each padded to obs_stride).
 struct ObsDev {
-    const float* yf;     // [n_obs]
+    const float* yf;     // [n_obs] FP32 copy, see obs_f32
     const float* invyf;  // [n_obs] 1/y or 0
     const double* yd;    // [n_obs]
 };
+
+// Entry i of a series' FP32 copy: the cumulative counts D and R as their difference from the
+// series' first value (the FP32 trajectory uses only differences of consecutive days, which are
+// then exact for integer counts that change by less than 2^24 over the window, at any level of
+// the series), I as its value.
+inline float obs_f32(const double* y, int i, bool diff) { return (float)(diff ? y[i] - y[0] : y[i]); }
 
 size_t smem_bytes_f32(const WindowDev& w, const ModelDev& m, int block, bool with_theta);
 

@@ -34,7 +34,7 @@ struct WindowDev {
     double N, I0, R0, D0, dt;
     float Nh, Nl;       // N = Nh + Nl
     float RD0h, RD0l;   // R0 + D0 = RD0h + RD0l
-    float I0f;
+    float I0f, I0l;     // a given I0 = I0f + I0l
     float cbn_h, cbn_l; // dt/N = cbn_h + cbn_l
     float dt_h, dt_l;   // dt = dt_h + dt_l
     // F_IRD (Sec. 3.1): the reported I and R series' ranges max - min (1 for a flat series) used by

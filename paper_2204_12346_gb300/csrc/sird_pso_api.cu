@@ -203,7 +203,9 @@ void sird_fill_window(const sird_problem* pb, WindowDev& w, ModelDev& m) {
     s = split(pb->R0 + pb->y_D[0]);
     w.RD0h = s.h;
     w.RD0l = s.l;
-    w.I0f = (float)pb->I0;
+    s = split(pb->I0);
+    w.I0f = s.h;
+    w.I0l = s.l;
     s = split(w.dt / pb->N);
     w.cbn_h = s.h;
     w.cbn_l = s.l;
@@ -265,7 +267,7 @@ static cudaError_t upload_obs(const sird_problem* pb, void** mem, ObsDev& o, cud
     for (int k = 0; k < nser; ++k)
         for (int i = 0; i < n; ++i) {
             const double y = series[k][i];
-            yf[k * ps + i] = (float)y;
+            yf[k * ps + i] = obs_f32(series[k], i, k != 1);
             inv[k * ps + i] = y != 0.0 ? (float)(1.0 / y) : 0.f;
             yd[k * ps + i] = y;
         }
@@ -565,7 +567,7 @@ extern "C" sird_status sird_pso_set_observations(sird_pso_t h, const double* y_D
     int kept = 0;
     double mean = 0.0, ss = 0.0;
     for (int i = 0; i < n_obs; ++i) {
-        yf[i] = (float)y_D[i];
+        yf[i] = obs_f32(y_D, i, true);
         inv[i] = y_D[i] != 0.0 ? (float)(1.0 / y_D[i]) : 0.f;
         yd[i] = y_D[i];
         kept += (y_D[i] != 0.0);

@@ -17,18 +17,24 @@
 //     error of the I update recovered exactly (fma(g, I, I - r)) into a low part Il.
 //   * The day's sum of I is needed to ~1e-9: it is spd Is + W - A, where Is is the day's first I
 //     (hi part), W = sum_k Il_k, and A = sum_k (spd - 1 - k) d_k with d_k = I_k - I_{k+1} (hi
-//     parts) the exact per-step decrements.  Products with it use spd-scaled coefficient pairs.
+//     parts) the exact per-step decrements.
 //   * Day end: Il receives the growth the steps could not apply (G's low part and cb's low part
-//     times the day's sum, and g times the low parts, G W) and is folded into I; Q and G take the
-//     day's removals (pairs); the deaths' misfit e = y - Dhat follows e_i = e_{i-1} + (y_i -
-//     y_{i-1}) - dm sum_day I, which keeps e's rounding relative to e itself (small at a good
-//     fit) rather than to D.
+//     times the day's sum, and g times the low parts, G W) and is folded into I; G takes the
+//     day's removals, G -= cb a (day's sum), as a pair; the deaths' misfit e = y - Dhat follows
+//     e_i = e_{i-1} + (y_i - y_{i-1}) - dm sum_day I, with y_i - y_{i-1} - dmh Psh in one
+//     rounding (it cancels at a good fit), which keeps e's rounding relative to e itself rather
+//     than to D.  The observations arrive as y_i - y_0 in FP32 (exact differences for counts
+//     below 2^24 over the window, whatever the level of y).
+//   * Q itself is needed only where a transmission segment starts: there it is recovered from
+//     the ending segment's G as Q = (G + a) / cb (a pair quotient).  Where that cb is 0, G says
+//     nothing about Q, and Q is carried through the segment's days instead (Q -= a day's sum);
+//     observers that read Q at day starts (the adjoint's checkpoints) get it carried every day.
 //   * A transmission segment that starts inside a day switches (G, cb) at its step; the part of
 //     the day run with the old constants is accounted for at the switch.
 //   * The ramp of eq. (beta) changes beta every step: G_k and cb_k follow the ramp per step
-//     (G1 + u_k HS between t1 and t2, G1 / G2 outside), from per-day pairs G1 = cb(beta1) Q - a,
-//     G2 = cb(beta2) Q - a and HS = d cb/dt Q; u_k = t_k - t1 is formed from the day (exact)
-//     and the step's offset.
+//     (G1 + u_k HS between t1 and t2, G1 / G2 outside), from the pairs G1 = cb(beta1) Q - a,
+//     G2 = cb(beta2) Q - a and HS = d cb/dt Q, set from the initial Q and then given each day's
+//     removals like G; u_k = t_k - t1 is formed from the day (exact) and the step's offset.
 //   * F_IRD carries the recovered series' misfit eR like e (dr = dt gamma) and compares I's
 //     (hi, lo) pair with the reported I.
 //
@@ -38,6 +44,7 @@
 #pragma once
 
 #include <climits>
+#include <type_traits>
 
 #include "device_common.cuh"
 
@@ -118,6 +125,45 @@ __device__ __forceinline__ void growth_pair(T cbh, T cbl, T Qh, T Ql, T ah, T al
     Gl = tadd(er, tsub(pe, al));
     tnorm(Gh, Gl);
 }
+
+// Q = (G + a) / cb from G = cb Q - a as a pair (cb != 0; the caller selects another Q where
+// cb = 0).  The residual of the quotient is formed exactly by the FMA.
+__device__ __forceinline__ float trcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ F2 trcp(F2 x) { return f2(__frcp_rn(f2lo(x)), __frcp_rn(f2hi(x))); }
+template <class T>
+__device__ __forceinline__ void q_from_growth(T Gh, T Gl, T cbh, T cbl, T ah, T al, T& Qh, T& Ql) {
+    T sh, se;
+    ttwo_sum(Gh, ah, sh, se);
+    se = tadd(se, tadd(Gl, al));
+    const T rc = trcp(cbh);
+    Qh = tmul(sh, rc);
+    const T nq = tneg(Qh);
+    Ql = tmul(tfma(nq, cbl, tadd(tfma(nq, cbh, sh), se)), rc);
+}
+// G -= c s for a coefficient pair c and the day's sum s = (Psh, Psl)
+template <class T, bool NORM>
+__device__ __forceinline__ void remove_pair(T ch, T cl, T Psh, T Psl, T& Gh, T& Gl) {
+    const T dd = tfma(ch, Psh, tfma(ch, Psl, tmul(cl, Psh)));
+    const T s = tsub(Gh, dd);
+    const T er = tsub(tsub(Gh, s), dd);
+    Gh = s;
+    Gl = tadd(Gl, er);
+    if (NORM) tnorm(Gh, Gl);
+}
+// (h, l) = x y for two pairs, to the pair's precision
+template <class T>
+__device__ __forceinline__ void tmul_pairs(T xh, T xl, T yh, T yl, T& h, T& l) {
+    tprod(xh, yh, h, l);
+    l = tfma(xh, yl, tfma(xl, yh, l));
+}
+__device__ __forceinline__ unsigned teq0(float a) { return a == 0.f ? 1u : 0u; }
+__device__ __forceinline__ unsigned teq0(F2 a) { return (f2lo(a) == 0.f ? 1u : 0u) | (f2hi(a) == 0.f ? 2u : 0u); }
+
+// An observer that reads Q = S + I at day starts declares kWantsQ = true; the others leave Q out.
+template <class O, class = void>
+struct obs_wants_q : std::false_type {};
+template <class O>
+struct obs_wants_q<O, std::void_t<decltype(O::kWantsQ)>> : std::integral_constant<bool, O::kWantsQ> {};
 
 // ---------------------------------------------------------------- Kahan sum of exact products
 template <class T>
@@ -239,7 +285,7 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
     const int gi = RAMP ? 4 : m.K;
     const T gam = th(gi), mu = th(gi + 1);
     T Ih = m.fit_I0 ? th(gi + 2) : tsplat<T>(w.I0f);
-    T Il = tsplat<T>(0.f);
+    T Il = tsplat<T>(m.fit_I0 ? 0.f : w.I0l);  // a given I0 enters as a pair
     const T dth = tsplat<T>(w.dt_h), dtl = tsplat<T>(w.dt_l);
     // a = dt (gamma + mu), dm = dt mu, dr = dt gamma as pairs, and spd times each
     T ah, al, dmh, dml, drh = tsplat<T>(0.f), drl = tsplat<T>(0.f);
@@ -258,6 +304,7 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
             tnorm(drh, drl);
         }
     }
+    const T ndmh = tneg(dmh), ndml = tneg(dml), ndrh = tneg(drh), ndrl = tneg(drl);
     const T cbnh = tsplat<T>(w.cbn_h), cbnl = tsplat<T>(w.cbn_l);
     auto cb_pair = [&](T beta, T& h, T& l) {  // cb = beta dt/N
         tprod(beta, cbnh, h, l);
@@ -266,8 +313,9 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
     };
 
     T Qh = tsplat<T>(w.Q0h), Ql = tsplat<T>(w.Q0l);
-    // e_0 = y_0 - D0 = 0 (Euler starts from the first observation); eR_0 = y_R0 - R0.  With
-    // DTRACK the observations are ignored and e = -D (its rounding then relative to D).
+    // e_0 = y_0 - D0 = 0 (Euler starts from the first observation); eR_0 = y_R0 - R0.  ysD and
+    // ysR hold y_i - y_0 (only their differences are used).  With DTRACK the observations are
+    // ignored, ysD[0] holds D0 and e = -D (its rounding then relative to D).
     T e = tsplat<T>(DTRACK ? -ysD[0] : 0.f), eR = tsplat<T>(IRD ? w.eR0 : 0.f);
     T el = tsplat<T>(0.f), eRl = el;  // low parts of e, eR (long-window mode)
     float yprev = ysD[0], yRprev = IRD ? ysR[0] : 0.f;
@@ -276,14 +324,14 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
 
     // day end: corrections, fold, removals into Q (and G), misfits.  The day's sum of I is
     // Psh + Psl with (Psh, Psl0) = spd Is exactly and Psl = Psl0 + W - A.
-    auto close_day = [&](int day, T Gh_, T Gl_, T ncbl_, T cbah_, T cbal_, T& Gh_upd, T& Gl_upd, bool upd_G) {
-        T Psh, Psl;
+    constexpr bool kQ = obs_wants_q<Obs>::value;
+    auto close_day = [&](int day, T Gh_, T Gl_, T ncbl_, bool trackQ, T& Psh, T& Psl) {
         tprod(fspd, Is, Psh, Psl);
         Psl = tadd(Psl, tsub(W, A));
         if (EXACTG) tnorm(Psh, Psl);  // short windows: Q's low part may grow, it is carried as is
         Il = tfma(Gh_, W, tfma(tfma(ncbl_, Is, Gl_), isum, Il));
         tnorm(Ih, Il);
-        {   // Q -= a (day's sum)
+        if (kQ || trackQ) {   // Q -= a (day's sum)
             T qh, ql;
             tprod(ah, Psh, qh, ql);
             ql = tfma(ah, Psl, tfma(al, Psh, ql));
@@ -292,44 +340,36 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
             Qh = s;
             Ql = tadd(Ql, tsub(er, ql));
         }
-        if (upd_G) {  // G -= cb a (day's sum)
-            const T dd = tfma(cbah_, Psh, tfma(cbah_, Psl, tmul(cbal_, Psh)));
-            const T s = tsub(Gh_upd, dd);
-            const T er = tsub(tsub(Gh_upd, s), dd);
-            Gh_upd = s;
-            Gl_upd = tadd(Gl_upd, er);
-            if (EXACTG) tnorm(Gh_upd, Gl_upd);
-        }
         {   // e += (y_day - y_{day-1}) - dm (day's sum)
-            T dh, dl;
-            tprod(dmh, Psh, dh, dl);
-            dl = tfma(dmh, Psl, tfma(dml, Psh, dl));
             const float y = (day <= L && !DTRACK) ? ysD[day] : yprev;
             const T dy = tsplat<T>(__fsub_rn(y, yprev));
             yprev = y;
             if (EXACTG) {
+                T dh, dl;
+                tprod(dmh, Psh, dh, dl);
+                dl = tfma(dmh, Psl, tfma(dml, Psh, dl));
                 T s, er;
                 ttwo_sum(e, tsub(dy, dh), s, er);
                 e = s;
                 el = tadd(el, tsub(er, dl));
-            } else {
-                e = tsub(tadd(e, tsub(dy, dh)), dl);
+            } else {  // dy - dmh Psh in one rounding (it cancels at a fit), then the low terms
+                e = tadd(e, tfma(ndml, Psh, tfma(ndmh, Psl, tfma(ndmh, Psh, dy))));
             }
         }
         if (IRD) {  // eR += (yR_day - yR_{day-1}) - dr (day's sum)
-            T rh, rl;
-            tprod(drh, Psh, rh, rl);
-            rl = tfma(drh, Psl, tfma(drl, Psh, rl));
             const float y = day <= L ? ysR[day] : yRprev;
             const T dy = tsplat<T>(__fsub_rn(y, yRprev));
             yRprev = y;
             if (EXACTG) {
+                T rh, rl;
+                tprod(drh, Psh, rh, rl);
+                rl = tfma(drh, Psl, tfma(drl, Psh, rl));
                 T s, er;
                 ttwo_sum(eR, tsub(dy, rh), s, er);
                 eR = s;
                 eRl = tadd(eRl, tsub(er, rl));
             } else {
-                eR = tsub(tadd(eR, tsub(dy, rh)), rl);
+                eR = tadd(eR, tfma(ndrl, Psh, tfma(ndrh, Psl, tfma(ndrh, Psh, dy))));
             }
         }
         if (EXACTG) obs.day_end(day, tadd(e, el), Ih, Il, tadd(eR, eRl));
@@ -343,6 +383,12 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
         const int K = m.K;
         T Gh = tsplat<T>(0.f), Gl = Gh, ncbh = Gh, ncbl = Gh, cbah = Gh, cbal = Gh;
         int k = 0, day = 0, in_day = 0;
+        unsigned zero = 0u;  // lanes whose segment has cb = 0: G does not determine Q there
+        auto end_day = [&]() {
+            T Psh, Psl;
+            close_day(day, Gh, Gl, ncbl, zero != 0u, Psh, Psl);
+            remove_pair<T, EXACTG>(cbah, cbal, Psh, Psl, Gh, Gl);
+        };
         // one step with weight spd-1-j for the day's sum (any j; the first step of a day finds
         // isum = W = A = 0)
         auto step = [&](T wj) {
@@ -374,6 +420,12 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
             const T beta = th(seg);
             T cbh, cbl;
             cb_pair(beta, cbh, cbl);
+            if (seg > 0) {  // the day-start Q from the ending segment's G where its cb is not 0
+                T qh, ql;
+                q_from_growth(Gh, Gl, tneg(ncbh), tneg(ncbl), ah, al, qh, ql);
+                Qh = tsel(zero, Qh, qh);
+                Ql = tsel(zero, Ql, ql);
+            }
             T cah, cal;
             tprod(cbh, ah, cah, cal);
             cal = tfma(cbh, al, tfma(cbl, ah, cal));
@@ -392,6 +444,7 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
             ncbl = tneg(cbl);
             cbah = cah;
             cbal = cal;
+            zero = teq0(cbh);
             // the last segment runs on past the window (forecast)
             const int kend = seg + 1 < K ? traj_segment_start(seg + 1, steps, K) : INT_MAX;
             while (in_day != 0 && k < kend) {  // finish a day begun by the previous segment
@@ -400,7 +453,7 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
                 if (++in_day == spd) {
                     ++day;
                     in_day = 0;
-                    close_day(day, Gh, Gl, ncbl, cbah, cbal, Gh, Gl, true);
+                    end_day();
                     if (day == last_day) return;
                 }
             }
@@ -416,7 +469,7 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
                 }
                 k += spd;
                 ++day;
-                close_day(day, Gh, Gl, ncbl, cbah, cbal, Gh, Gl, true);
+                end_day();
                 if (day == last_day) return;
             }
             while (k < kend) {  // start a day the next segment finishes
@@ -464,15 +517,20 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
         cb_pair(b2, c2h, c2l);
         const T nc1h = tneg(c1h), nc2h = tneg(c2h), nhh = tneg(hh);
         const T dtf = tsplat<T>(__fadd_rn(w.dt_h, w.dt_l));
-        // cb a spd pairs of the two plateaus and of the ramp's slope, for the removals' effect on G
-        // are not needed: G1, G2 are recomputed from Q every day.
+        // G1 = cb(beta1) Q - a, G2 = cb(beta2) Q - a and HS = d cb/dt Q from the initial Q, then
+        // each day's removals a (day's sum) applied to them through the pairs cb(beta1) a, cb(beta2) a
+        // and d cb/dt a
+        T G1h, G1l, G2h, G2l, HSh, HSl;
+        growth_pair(c1h, c1l, Qh, Ql, ah, al, G1h, G1l);
+        growth_pair(c2h, c2l, Qh, Ql, ah, al, G2h, G2l);
+        tprod(hh, Qh, HSh, HSl);
+        HSl = tfma(hh, Ql, tfma(hl, Qh, HSl));
+        tnorm(HSh, HSl);
+        T c1ah, c1al, c2ah, c2al, hah, hal;
+        tmul_pairs(c1h, c1l, ah, al, c1ah, c1al);
+        tmul_pairs(c2h, c2l, ah, al, c2ah, c2al);
+        tmul_pairs(hh, hl, ah, al, hah, hal);
         for (int day = 0; day < n_days; ++day) {
-            T G1h, G1l, G2h, G2l, HSh, HSl;
-            growth_pair(c1h, c1l, Qh, Ql, ah, al, G1h, G1l);
-            growth_pair(c2h, c2l, Qh, Ql, ah, al, G2h, G2l);
-            tprod(hh, Qh, HSh, HSl);
-            HSl = tfma(hh, Ql, tfma(hl, Qh, HSl));
-            tnorm(HSh, HSl);
             const T us = tsub(tsplat<T>((float)day), t1);  // t at the day's start minus t1
             obs.day_start(day, Qh, Ql, Ih, Il, EXACTG ? tadd(e, el) : e);
             auto step = [&](int j, T wj) {
@@ -505,8 +563,11 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
             const T Glm = tsel(before, G1l, tsel(after, G2l, tfma(um, HSl, G1l)));
             const T Ghm = tsel(before, G1h, tsel(after, G2h, tfma(um, HSh, G1h)));
             const T ncl = tneg(tsel(before, c1l, tsel(after, c2l, tfma(um, hl, c1l))));
-            T dummyh = Ghm, dummyl = Glm;
-            close_day(day + 1, Ghm, Glm, ncl, Ghm, Ghm, dummyh, dummyl, false);
+            T Psh, Psl;
+            close_day(day + 1, Ghm, Glm, ncl, false, Psh, Psl);
+            remove_pair<T, EXACTG>(c1ah, c1al, Psh, Psl, G1h, G1l);
+            remove_pair<T, EXACTG>(c2ah, c2al, Psh, Psl, G2h, G2l);
+            remove_pair<T, EXACTG>(hah, hal, Psh, Psl, HSh, HSl);
         }
     }
 }

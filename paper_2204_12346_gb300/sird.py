@@ -674,7 +674,9 @@ def step_f32_noalloc(yD, N, obs, x, v, pbest, pbest_f, gbest, iteration, *, gbes
                      lb=None, ub=None, log_scale=None, w=0.5, c1=0.5, c2=0.5, seed=0, stream_id=0, block_size=0):
     """One FP32 PSO iteration on caller-owned torch CUDA buffers, through the entry point that
     allocates nothing (sird_pso_step_f32_noalloc).  x, v, pbest: [P, ld] float32; pbest_f: [ld];
-    gbest: [P]; obs: [n_obs] float32 observations; gbest_index: optional int32 CUDA tensor [1]."""
+    gbest: [P]; obs: [n_obs] float32 observations of D as yD - yD[0], the handle's own copy (the
+    float values of yD give the same results when yD[0] = 0 or yD holds integers below 2^24);
+    gbest_index: optional int32 CUDA tensor [1]."""
     L = lib()
     pb, k1 = make_problem(yD, N, K, spd, R0, I0, fit_I0, beta_form, cost)
     P = n_params(K, beta_form, fit_I0)

@@ -95,6 +95,34 @@ def test_ird_fp32_calibration_reports_its_fp64_loss_and_batches_agree():
         assert r["loss"] == O.loss(pb, r["theta"])
 
 
+def test_ird_fp32_at_fits_where_the_reported_R_passes_2_to_the_24():
+    # Late windows of the paper's F_IRD^MXSE setting: the reported R is above 2^24 (float
+    # integers are then even numbers only) and at a fit R's misfit on the last day is ~1e-3 of R
+    # and sets the cost.  The FP32 path takes the series' day-to-day changes exactly (its copy of
+    # D and R holds y - y_0), so the search loss stays within 1e-5 of the oracle at the fitted
+    # points; rounding the levels themselves to float put four of these windows 6e-5 .. 3e-4 off.
+    c = configs.CONFIGS["paper_ird"]
+    ser = synth.reported_IR(synth.load_series(c["series"]), c["seed"])
+    lay = synth.rolling_windows(W=c["W"], L_min=c["L_min"], L_max=c["L_max"], M_min=c["M_min"], M_max=c["M_max"],
+                                delta=c["delta"], seed=c["seed"])
+    every = synth.rolling_window_problems(ser, lay)
+    wins = []
+    for i in (92, 110, 116, 136):  # with their Philox streams in the full 139-window batch
+        wins.append(dict(every[i], stream_id=i))
+    assert all(w["yR"].max() > 2 ** 24 for w in wins)
+    lb, ub = configs.bounds_ramp(fit_I0=False)
+    kw = dict(K=1, spd=10, beta_form=sird.BETA_RAMP, lb=lb, ub=ub, log_scale=None, fit_I0=False, seed=0,
+              objective=sird.FIT_IRD, cost=sird.COST_MXSE)
+    res = sird.Batch(wins, iters=100, **kw).calibrate()
+    got, want = [], []
+    for w, r in zip(wins, res):
+        pb = O.Problem(yD=w["yD"], yI=w["yI"], yR=w["yR"], N=w["N"], R0=w["R0"], I0=w["I0"], fit_I0=False,
+                       beta_form=O.BETA_RAMP, spd=10, cost=O.MXSE, objective=O.FIT_IRD)
+        got.append(r["loss_search"])
+        want.append(O.loss(pb, f32(r["theta"])))
+    print("largest relative error", assert_fp32_losses(got, want, "R above 2^24"))
+
+
 def test_ird_batch_set_observations_equals_a_fresh_batch():
     ser = synth.reported_IR(synth.load_series("450d"), 4)
     lay = {"L": np.array([25, 40]), "M": np.array([200, 450]), "T": np.array([30, 200])}

@@ -47,7 +47,7 @@ def test_noalloc_step_matches_handle_step(cost, integer):
     pbf = torch.zeros(ld, dtype=torch.float32, device=dev)
     gb = torch.zeros(sird.MAX_PARAMS, dtype=torch.float32, device=dev)
     gidx = torch.zeros(1, dtype=torch.int32, device=dev)
-    obs = torch.from_numpy(y.astype(np.float32)).to(dev)
+    obs = torch.from_numpy((y - y[0]).astype(np.float32)).to(dev)  # the handle's FP32 copy
 
     ref.init()
     for it in range(3):  # the initialisation, then two iterations in a row
