@@ -127,9 +127,14 @@ __device__ __forceinline__ void growth_pair(T cbh, T cbl, T Qh, T Ql, T ah, T al
 }
 
 // Q = (G + a) / cb from G = cb Q - a as a pair (cb != 0; the caller selects another Q where
-// cb = 0).  The residual of the quotient is formed exactly by the FMA.
-__device__ __forceinline__ float trcp(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ F2 trcp(F2 x) { return f2(__frcp_rn(f2lo(x)), __frcp_rn(f2hi(x))); }
+// cb = 0).  The quotient's residual is formed exactly by the FMA, so the hardware's approximate
+// reciprocal (a few ulp) serves: the pair still holds Q to ~2^-44.
+__device__ __forceinline__ float trcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ F2 trcp(F2 x) { return f2(trcp(f2lo(x)), trcp(f2hi(x))); }
 template <class T>
 __device__ __forceinline__ void q_from_growth(T Gh, T Gl, T cbh, T cbl, T ah, T al, T& Qh, T& Ql) {
     T sh, se;
@@ -322,15 +327,18 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
     T isum = tsplat<T>(0.f), W = isum, A = isum, Is = Ih;
     obs.day_end(0, e, Ih, Il, eR);
 
-    // day end: corrections, fold, removals into Q (and G), misfits.  The day's sum of I is
-    // Psh + Psl with (Psh, Psl0) = spd Is exactly and Psl = Psl0 + W - A.
+    // day end: corrections, fold, removals into the growth rates (remove(Psh, Psl)) and Q,
+    // misfits.  The day's sum of I is Psh + Psl with (Psh, Psl0) = spd Is exactly and Psl = Psl0
+    // + W - A.  The removals come first: the next day's first step waits for them.
     constexpr bool kQ = obs_wants_q<Obs>::value;
-    auto close_day = [&](int day, T Gh_, T Gl_, T ncbl_, bool trackQ, T& Psh, T& Psl) {
+    auto close_day = [&](int day, T Gh_, T Gl_, T ncbl_, bool trackQ, const auto& remove) {
+        T Psh, Psl;
         tprod(fspd, Is, Psh, Psl);
         Psl = tadd(Psl, tsub(W, A));
         if (EXACTG) tnorm(Psh, Psl);  // short windows: Q's low part may grow, it is carried as is
         Il = tfma(Gh_, W, tfma(tfma(ncbl_, Is, Gl_), isum, Il));
         tnorm(Ih, Il);
+        remove(Psh, Psl);
         if (kQ || trackQ) {   // Q -= a (day's sum)
             T qh, ql;
             tprod(ah, Psh, qh, ql);
@@ -353,7 +361,7 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
                 e = s;
                 el = tadd(el, tsub(er, dl));
             } else {  // dy - dmh Psh in one rounding (it cancels at a fit), then the low terms
-                e = tadd(e, tfma(ndml, Psh, tfma(ndmh, Psl, tfma(ndmh, Psh, dy))));
+                e = tadd(e, tfma(ndmh, Psl, tfma(ndml, Psh, tfma(ndmh, Psh, dy))));
             }
         }
         if (IRD) {  // eR += (yR_day - yR_{day-1}) - dr (day's sum)
@@ -369,7 +377,7 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
                 eR = s;
                 eRl = tadd(eRl, tsub(er, rl));
             } else {
-                eR = tadd(eR, tfma(ndrl, Psh, tfma(ndrh, Psl, tfma(ndrh, Psh, dy))));
+                eR = tadd(eR, tfma(ndrh, Psl, tfma(ndrl, Psh, tfma(ndrh, Psh, dy))));
             }
         }
         if (EXACTG) obs.day_end(day, tadd(e, el), Ih, Il, tadd(eR, eRl));
@@ -385,9 +393,8 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
         int k = 0, day = 0, in_day = 0;
         unsigned zero = 0u;  // lanes whose segment has cb = 0: G does not determine Q there
         auto end_day = [&]() {
-            T Psh, Psl;
-            close_day(day, Gh, Gl, ncbl, zero != 0u, Psh, Psl);
-            remove_pair<T, EXACTG>(cbah, cbal, Psh, Psl, Gh, Gl);
+            close_day(day, Gh, Gl, ncbl, zero != 0u,
+                      [&](T Psh, T Psl) { remove_pair<T, EXACTG>(cbah, cbal, Psh, Psl, Gh, Gl); });
         };
         // one step with weight spd-1-j for the day's sum (any j; the first step of a day finds
         // isum = W = A = 0)
@@ -563,11 +570,11 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
             const T Glm = tsel(before, G1l, tsel(after, G2l, tfma(um, HSl, G1l)));
             const T Ghm = tsel(before, G1h, tsel(after, G2h, tfma(um, HSh, G1h)));
             const T ncl = tneg(tsel(before, c1l, tsel(after, c2l, tfma(um, hl, c1l))));
-            T Psh, Psl;
-            close_day(day + 1, Ghm, Glm, ncl, false, Psh, Psl);
-            remove_pair<T, EXACTG>(c1ah, c1al, Psh, Psl, G1h, G1l);
-            remove_pair<T, EXACTG>(c2ah, c2al, Psh, Psl, G2h, G2l);
-            remove_pair<T, EXACTG>(hah, hal, Psh, Psl, HSh, HSl);
+            close_day(day + 1, Ghm, Glm, ncl, false, [&](T Psh, T Psl) {
+                remove_pair<T, EXACTG>(c1ah, c1al, Psh, Psl, G1h, G1l);
+                remove_pair<T, EXACTG>(c2ah, c2al, Psh, Psl, G2h, G2l);
+                remove_pair<T, EXACTG>(hah, hal, Psh, Psl, HSh, HSl);
+            });
         }
     }
 }
