@@ -51,25 +51,25 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 # kernel sources they were taken on (sha256[:16] of the files listed).
 PROFILED = {
     "batch512": {"files": ["batched.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "aea9ece54ea983f8", "traffic_bytes": 13024512, "fma_pipe": 0.6300,
+           "sha": "f064a4882c26dbb1", "traffic_bytes": 13829888, "fma_pipe": 0.6046,
            "profile": "profiles/pso_batch_f32_batch512.md"},
     "window60": {"files": ["pso_persistent.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "d2902a5aafa962f0", "traffic_bytes": 457216, "fma_pipe": 0.3575,
+           "sha": "ffe3992a5af3f265", "traffic_bytes": 445184, "fma_pipe": 0.3161,
            "profile": "profiles/pso_f32_persistent_window60.md"},
     "gradient90": {"files": ["adjoint_f32.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "5aaddeec214ad36e", "traffic_bytes": 182016, "fma_pipe": 0.0760,
+           "sha": "2523f68bad906781", "traffic_bytes": 182784, "fma_pipe": 0.0753,
            "profile": "profiles/loss_grad_f32_gradient90.md"},
     "paper": {"files": ["batched.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "aea9ece54ea983f8", "traffic_bytes": 14973660000, "fma_pipe": 0.5684,
+           "sha": "f064a4882c26dbb1", "traffic_bytes": 15202969000, "fma_pipe": 0.5154,
            "profile": "profiles/pso_batch_f32_paper.md"},
     "paper_ird": {"files": ["batched.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "aea9ece54ea983f8", "traffic_bytes": 14900860000, "fma_pipe": 0.5664,
+           "sha": "f064a4882c26dbb1", "traffic_bytes": 15565753000, "fma_pipe": 0.5188,
            "profile": "profiles/pso_batch_f32_paper_ird.md"},
     "stability": {"files": ["batched.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "aea9ece54ea983f8", "traffic_bytes": 300467837184, "fma_pipe": 0.5892,
+           "sha": "f064a4882c26dbb1", "traffic_bytes": 300881895936, "fma_pipe": 0.5314,
            "profile": "profiles/pso_batch_f32_stability.md"},
     "swarm2p20": {"files": ["pso_kernels.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "ae88d79edec298bf", "traffic_bytes": 275589888, "fma_pipe": 0.7605,
+           "sha": "9d36e629086dee78", "traffic_bytes": 276360192, "fma_pipe": 0.7654,
            "profile": "profiles/pso_f32_kernel_swarm2p20.md"},
 }
 
