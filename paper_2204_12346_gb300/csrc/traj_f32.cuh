@@ -391,9 +391,8 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
         const int K = m.K;
         T Gh = tsplat<T>(0.f), Gl = Gh, ncbh = Gh, ncbl = Gh, cbah = Gh, cbal = Gh;
         int k = 0, day = 0, in_day = 0;
-        unsigned zero = 0u;  // lanes whose segment has cb = 0: G does not determine Q there
         auto end_day = [&]() {
-            close_day(day, Gh, Gl, ncbl, zero != 0u,
+            close_day(day, Gh, Gl, ncbl, teq0(ncbh) != 0u,  // cb = 0: G does not determine Q
                       [&](T Psh, T Psl) { remove_pair<T, EXACTG>(cbah, cbal, Psh, Psl, Gh, Gl); });
         };
         // one step with weight spd-1-j for the day's sum (any j; the first step of a day finds
@@ -430,6 +429,7 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
             if (seg > 0) {  // the day-start Q from the ending segment's G where its cb is not 0
                 T qh, ql;
                 q_from_growth(Gh, Gl, tneg(ncbh), tneg(ncbl), ah, al, qh, ql);
+                const unsigned zero = teq0(ncbh);
                 Qh = tsel(zero, Qh, qh);
                 Ql = tsel(zero, Ql, ql);
             }
@@ -451,7 +451,6 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
             ncbl = tneg(cbl);
             cbah = cah;
             cbal = cal;
-            zero = teq0(cbh);
             // the last segment runs on past the window (forecast)
             const int kend = seg + 1 < K ? traj_segment_start(seg + 1, steps, K) : INT_MAX;
             while (in_day != 0 && k < kend) {  // finish a day begun by the previous segment

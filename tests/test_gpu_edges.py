@@ -158,6 +158,62 @@ def test_degenerate_parameters(cost):
         assert got64[j] == want[j]
 
 
+def zero_beta_thetas(K, seed):
+    """Segments with beta = 0 before, between and after ones with beta > 0, next to rows without
+    any: the FP32 trajectory recovers Q from G = cb Q - a where a segment starts, which says
+    nothing about Q after a segment with cb = 0 (Q is then carried through that segment)."""
+    patterns = [[0, .2, .2, .2], [.2, 0, .2, .2], [.2, .2, 0, .25], [0, .3, 0, .2], [.2, .2, .2, 0], [0, 0, .3, .2],
+                [.25, 0, 0, .2], [0, 0, 0, .3]]
+    rng = np.random.default_rng(seed)
+    rows = []
+    for p in patterns:
+        for _ in range(3):
+            rows.append(list(np.array(p) * rng.uniform(0.8, 1.2)) + [rng.uniform(0.05, 0.15), 0.002, 1e4])
+            rows.append(list(rng.uniform(0.1, 0.3, K)) + [0.1, 0.002, rng.uniform(5e3, 2e4)])
+    return f32(np.array(rows))
+
+
+@pytest.mark.parametrize("cost", ["mse", "mape"])
+def test_zero_beta_segments(cost):
+    y, N, _, _ = window("60d", 40)
+    K = 4
+    th = zero_beta_thetas(K, 3)
+    pb = O.Problem(yD=y, N=N, K=K, spd=10, cost=O.COSTS[cost])
+    want = O.losses(pb, th)
+    assert np.array_equal(gpu_eval(calibrator(y, N, K, 10, 64, sird.COSTS[cost]), th, 64), want)
+    cal = calibrator(y, N, K, 10, 32, sird.COSTS[cost])
+    got = gpu_eval(cal, th, 32)
+    print("largest relative error", assert_fp32_losses(got, want, cost))
+    # each lane of a packed pair on its own: other partners give the same bits
+    perm = np.random.default_rng(4).permutation(len(th))
+    assert np.array_equal(gpu_eval(cal, th[perm], 32), got[perm])
+    # the adjoint's forward pass carries Q every day (its checkpoints read it); its loss is still
+    # the evaluation's bit for bit
+    L, _, _, E = f32_loss_grad(cal, th)
+    assert np.array_equal(L, E) and np.array_equal(E.astype(np.float64), got)
+
+
+def test_swarm_clamped_at_beta_zero():
+    # a linear box with beta's lower bound 0: the swarm puts particles on beta = 0 exactly (the
+    # bound), in single segments and in whole packed pairs alike; their FP32 personal-best losses
+    # are the oracle's within 1e-5 and the batch form agrees with the single window bit for bit
+    y, N, _, _ = window("60d", 40)
+    K = 4
+    lb, ub = [0.0] * K + [0.02, 1e-4, 1e3], [0.5] * K + [0.3, 0.01, 5e4]
+    kw = dict(K=K, spd=10, lb=lb, ub=ub, seed=9)
+    cal = sird.Calibrator(y, N, particles=512, iters=6, precision=32, **kw)
+    r = cal.calibrate()
+    st = cal.get_state()
+    x = f32(st["x"].T)
+    assert np.any(x[:, :K] == 0.0), "no particle on beta = 0"
+    pb = O.Problem(yD=y, N=N, K=K, spd=10)
+    print("largest relative error", assert_fp32_losses(gpu_eval(cal, x, 32), O.losses(pb, x), "positions"))
+    pbest = f32(st["pbest"].T)
+    print("largest relative error", assert_fp32_losses(st["pbest_f"], O.losses(pb, pbest), "personal bests"))
+    res = sird.Batch([{"yD": y, "N": N, "particles": 512}], iters=6, **kw).calibrate()
+    assert res[0]["index"] == r["index"] and res[0]["loss"] == r["loss"]
+
+
 # ------------------------------------------------------------------ the shortest window, a batch of one
 
 @pytest.mark.parametrize("cost", ["mse", "mxse", "mae", "mape"])
