@@ -155,11 +155,11 @@ __global__ void __launch_bounds__(batch_launch_bound(COST)) pso_batch_f32(const 
                 float fa, fb;
                 if (Tw + tid < cnt) {
                     update(j1, B + tid);
-                    fitness_f32x2<SPD, COST>(w, m, ys, invys, th_s + tid, th_s + B + tid, B2, fa, fb);
+                    fitness_f32x2<SPD, COST, true>(w, m, ys, invys, th_s + tid, th_s + B + tid, B2, fa, fb);
                     settle(j0, tid, fa);
                     settle(j1, B + tid, fb);
                 } else {
-                    fa = fitness_f32<SPD, COST>(w, m, ys, invys, th_s + tid, B2);
+                    fa = fitness_f32<SPD, COST, true>(w, m, ys, invys, th_s + tid, B2);
                     settle(j0, tid, fa);
                 }
             }

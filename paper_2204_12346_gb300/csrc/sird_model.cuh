@@ -79,9 +79,11 @@ namespace sird {
 // ---------------------------------------------------------------- FP32
 // The trajectory itself lives in traj_f32.cuh; here are the losses built on it.
 
-// F_D^C (Sec. 3.1): the cost of the deaths' misfit e_i = y_i - Dhat_i over days 0..L.
-template <class T, int COST>
+// F_D^C (Sec. 3.1): the cost of the deaths' misfit e_i = y_i - Dhat_i over days 0..L.  LEAN:
+// the calling kernel is at its register bound (see obs_lean in traj_f32.cuh).
+template <class T, int COST, bool LEAN = false>
 struct LossObsD {
+    static constexpr bool kLeanRegs = LEAN;
     CostT<T, COST> c;
     const float* invys;
     __device__ __forceinline__ void day_start(int, T, T, T, T, T) {}
@@ -91,8 +93,9 @@ struct LossObsD {
 // F_IRD^C (Sec. 3.1): the cost of each of I, R, D against its reported series (errors divided
 // by the series' range, the min-max normalisation; MAPE on the raw values), the largest of the
 // three.  ys / invys hold the series stacked D | I | R with stride obs_stride(n).
-template <class T, int COST>
+template <class T, int COST, bool LEAN = false>
 struct LossObsIRD {
+    static constexpr bool kLeanRegs = LEAN;
     CostT<T, COST> cI, cR, cD;
     const float *ys, *invys;
     int ps;
@@ -131,14 +134,14 @@ __host__ __device__ __forceinline__ int form_of(const ModelDev& m) {
 
 // Losses of the vectors th (T = float: one, fa = fb; T = F2: two, one per lane); CV is the
 // variant (cost | form << 2), which must match m.
-template <class T, int SPD, int CV, class Th>
+template <class T, int SPD, int CV, bool LEAN, class Th>
 __device__ __forceinline__ void fitness_lanes(const WindowDev& w, const ModelDev& m, const float* __restrict__ ys,
                                               const float* __restrict__ invys, Th th, float& fa, float& fb) {
     constexpr int COST = variant_cost(CV), FORM = variant_form(CV);
     constexpr bool RAMP = FORM >= 2, IRD = (FORM & 1) != 0;
     const int L = w.n_obs - 1;
     if constexpr (IRD) {
-        LossObsIRD<T, COST> o;
+        LossObsIRD<T, COST, LEAN> o;
         o.cI.init();
         o.cR.init();
         o.cD.init();
@@ -159,7 +162,7 @@ __device__ __forceinline__ void fitness_lanes(const WindowDev& w, const ModelDev
         fa = max3(ia, ra, da);
         fb = max3(ib, rb, db);
     } else {
-        LossObsD<T, COST> o;
+        LossObsD<T, COST, LEAN> o;
         o.c.init();
         o.invys = invys;
         if (L * (SPD > 0 ? SPD : m.spd) > kExactGrowthSteps)
@@ -172,22 +175,22 @@ __device__ __forceinline__ void fitness_lanes(const WindowDev& w, const ModelDev
 
 // Loss of one parameter vector, theta_d at th[d*stride].  ys / invys: observations and their
 // reciprocals (0 where y == 0) in shared memory.  SPD > 0 fixes steps per day at compile time;
-// COST is the variant (cost | form << 2).
-template <int SPD, int COST>
+// COST is the variant (cost | form << 2); LEAN for kernels at their register bound (same losses).
+template <int SPD, int COST, bool LEAN = false>
 __device__ float fitness_f32(const WindowDev& w, const ModelDev& m, const float* __restrict__ ys,
                              const float* __restrict__ invys, const float* th, int stride) {
     float fa, fb;
-    fitness_lanes<float, SPD, COST>(w, m, ys, invys, ThetaF1{th, stride}, fa, fb);
+    fitness_lanes<float, SPD, COST, LEAN>(w, m, ys, invys, ThetaF1{th, stride}, fa, fb);
     return fa;
 }
 
 // Losses of two parameter vectors (theta_d at tha[d*stride], thb[d*stride]) integrated together
 // in packed f32x2 form; each equals fitness_f32's loss of that vector bit for bit.
-template <int SPD, int COST>
+template <int SPD, int COST, bool LEAN = false>
 __device__ void fitness_f32x2(const WindowDev& w, const ModelDev& m, const float* __restrict__ ys,
                               const float* __restrict__ invys, const float* tha, const float* thb, int stride,
                               float& fa, float& fb) {
-    fitness_lanes<F2, SPD, COST>(w, m, ys, invys, ThetaF2{tha, thb, stride}, fa, fb);
+    fitness_lanes<F2, SPD, COST, LEAN>(w, m, ys, invys, ThetaF2{tha, thb, stride}, fa, fb);
 }
 
 // One Euler step in the C-form (C = N - S carried, S = Sday - cday) with I's rounding error

@@ -169,6 +169,12 @@ template <class O, class = void>
 struct obs_wants_q : std::false_type {};
 template <class O>
 struct obs_wants_q<O, std::void_t<decltype(O::kWantsQ)>> : std::integral_constant<bool, O::kWantsQ> {};
+// An observer with kLeanRegs = true asks the trajectory to recompute per-segment masks where they
+// are used instead of keeping them live (for kernels at their register bound); same arithmetic.
+template <class O, class = void>
+struct obs_lean : std::false_type {};
+template <class O>
+struct obs_lean<O, std::void_t<decltype(O::kLeanRegs)>> : std::integral_constant<bool, O::kLeanRegs> {};
 
 // ---------------------------------------------------------------- Kahan sum of exact products
 template <class T>
@@ -391,8 +397,12 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
         const int K = m.K;
         T Gh = tsplat<T>(0.f), Gl = Gh, ncbh = Gh, ncbl = Gh, cbah = Gh, cbal = Gh;
         int k = 0, day = 0, in_day = 0;
+        // lanes whose segment has cb = 0, where G does not determine Q
+        constexpr bool kLean = obs_lean<Obs>::value;
+        unsigned zero = 0u;
+        auto cb_zero = [&]() { return kLean ? teq0(ncbh) : zero; };
         auto end_day = [&]() {
-            close_day(day, Gh, Gl, ncbl, teq0(ncbh) != 0u,  // cb = 0: G does not determine Q
+            close_day(day, Gh, Gl, ncbl, cb_zero() != 0u,
                       [&](T Psh, T Psl) { remove_pair<T, EXACTG>(cbah, cbal, Psh, Psl, Gh, Gl); });
         };
         // one step with weight spd-1-j for the day's sum (any j; the first step of a day finds
@@ -429,9 +439,9 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
             if (seg > 0) {  // the day-start Q from the ending segment's G where its cb is not 0
                 T qh, ql;
                 q_from_growth(Gh, Gl, tneg(ncbh), tneg(ncbl), ah, al, qh, ql);
-                const unsigned zero = teq0(ncbh);
-                Qh = tsel(zero, Qh, qh);
-                Ql = tsel(zero, Ql, ql);
+                const unsigned z = cb_zero();
+                Qh = tsel(z, Qh, qh);
+                Ql = tsel(z, Ql, ql);
             }
             T cah, cal;
             tprod(cbh, ah, cah, cal);
@@ -449,6 +459,7 @@ __device__ __forceinline__ void trajectory_f32(const WindowDev& w, const ModelDe
             Gl = nGl;
             ncbh = tneg(cbh);
             ncbl = tneg(cbl);
+            if (!kLean) zero = teq0(cbh);
             cbah = cah;
             cbal = cal;
             // the last segment runs on past the window (forecast)
