@@ -51,25 +51,25 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
 # kernel sources they were taken on (sha256[:16] of the files listed).
 PROFILED = {
     "batch512": {"files": ["batched.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "f064a4882c26dbb1", "traffic_bytes": 13829888, "fma_pipe": 0.6046,
+           "sha": "e82eef7ec000d386", "traffic_bytes": 12888576, "fma_pipe": 0.6128,
            "profile": "profiles/pso_batch_f32_batch512.md"},
     "window60": {"files": ["pso_persistent.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "ffe3992a5af3f265", "traffic_bytes": 445184, "fma_pipe": 0.3161,
+           "sha": "dc2f1813dbce77c6", "traffic_bytes": 478464, "fma_pipe": 0.3180,
            "profile": "profiles/pso_f32_persistent_window60.md"},
     "gradient90": {"files": ["adjoint_f32.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "2523f68bad906781", "traffic_bytes": 182784, "fma_pipe": 0.0753,
+           "sha": "69a9d7c0c61d445b", "traffic_bytes": 182784, "fma_pipe": 0.0751,
            "profile": "profiles/loss_grad_f32_gradient90.md"},
     "paper": {"files": ["batched.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "f064a4882c26dbb1", "traffic_bytes": 15202969000, "fma_pipe": 0.5154,
+           "sha": "e82eef7ec000d386", "traffic_bytes": 15183807000, "fma_pipe": 0.5143,
            "profile": "profiles/pso_batch_f32_paper.md"},
     "paper_ird": {"files": ["batched.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "f064a4882c26dbb1", "traffic_bytes": 15565753000, "fma_pipe": 0.5188,
+           "sha": "e82eef7ec000d386", "traffic_bytes": 15357156000, "fma_pipe": 0.5173,
            "profile": "profiles/pso_batch_f32_paper_ird.md"},
     "stability": {"files": ["batched.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "f064a4882c26dbb1", "traffic_bytes": 300881895936, "fma_pipe": 0.5314,
+           "sha": "e82eef7ec000d386", "traffic_bytes": 300685507328, "fma_pipe": 0.5305,
            "profile": "profiles/pso_batch_f32_stability.md"},
     "swarm2p20": {"files": ["pso_kernels.cu", "traj_f32.cuh", "sird_model.cuh", "device_common.cuh", "kernels.h"],
-           "sha": "9d36e629086dee78", "traffic_bytes": 276360192, "fma_pipe": 0.7654,
+           "sha": "4c27a2f29190ec1e", "traffic_bytes": 275710720, "fma_pipe": 0.7650,
            "profile": "profiles/pso_f32_kernel_swarm2p20.md"},
 }
 
