@@ -289,41 +289,52 @@ def timed_steps(args, world, stream, step_fn, kernel_events=None):
 # ------------------------------------------------------------------ seconds to calibrate
 
 def s_to_calibrate() -> dict:
-    """Single 60-day window: wall seconds of the plain FP64 swarm (its final loss is L_ref) vs the
-    FP32 swarm plus the FP32 L-BFGS polish until the FP64 loss is <= (1 + 1e-6) L_ref."""
+    """Single 60-day window: wall seconds of the plain FP64 swarm (1000 iterations; its final loss
+    is L_ref) vs the FP32 swarm plus the FP32 L-BFGS polish of its 32 best until the FP64 loss is
+    <= (1 + 1e-6) L_ref.  The FP32 swarm runs 100, 200, 500 or 1000 iterations; for each, the
+    polish iterations grow until the target is reached; the line reports the fastest setting that
+    reaches it (every trial is listed)."""
     import torch
 
     from paper_2204_12346_gb300 import sird
 
     c, ser, y, lb, ub = single_window("window60")
-    kw = dict(K=c["K"], spd=c["spd"], particles=c["M"], iters=c["iters"], lb=lb, ub=ub,
-              log_scale=[1] * len(lb), seed=c["seed"])
-    c64 = sird.Calibrator(y, ser["N"], precision=64, **kw)
+    kw = dict(K=c["K"], spd=c["spd"], particles=c["M"], lb=lb, ub=ub, log_scale=[1] * len(lb), seed=c["seed"])
+    c64 = sird.Calibrator(y, ser["N"], precision=64, iters=c["iters"], **kw)
     c64.calibrate()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     r64 = c64.calibrate()
     t64 = time.perf_counter() - t0
     target = r64["loss"] * (1 + 1e-6)
-    c32 = sird.Calibrator(y, ser["N"], precision=32, reeval_topk=32, **kw)
-    c32.calibrate()
-    out = {"window": "60 days, 4 segments, 4096 particles, 1000 PSO iterations, dt=0.1", "L_ref": r64["loss"],
-           "target": "(1 + 1e-6) L_ref", "fp64_pso_s": t64}
-    loss = float("inf")
-    for n in (0, 5, 10, 15, 20, 30, 40, 50, 75, 100, 150, 200, 300):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r32 = c32.calibrate()
-        loss = r32["loss"]
-        if n > 0:
-            rp = c32.polish(k=32, iters=n, first_step=1e-2, precision=32)
-            loss = min(loss, rp["loss"])
-        dt = time.perf_counter() - t0
-        if loss <= target:
-            out.update({"fp32_plus_polish_s": dt, "polish_iters": n, "loss_reached": loss,
-                        "speedup": t64 / dt, "reached": True})
-            return out
-    out.update({"reached": False, "loss_reached": loss})
+    out = {"window": "60 days, 4 segments, 4096 particles, 1000 FP64 PSO iterations, dt=0.1", "L_ref": r64["loss"],
+           "target": "(1 + 1e-6) L_ref", "fp64_pso_s": t64, "trials": []}
+    best = None
+    for iters in (100, 200, 500, c["iters"]):
+        c32 = sird.Calibrator(y, ser["N"], precision=32, iters=iters, reeval_topk=32, **kw)
+        c32.calibrate()
+        c32.polish(k=32, iters=5, first_step=1e-2, precision=32)  # warm-up: the first polish sets up its buffers
+        for n in (0, 5, 10, 15, 20, 30, 40, 50, 75, 100, 150, 200, 300):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r32 = c32.calibrate()
+            loss = r32["loss"]
+            if n > 0:
+                rp = c32.polish(k=32, iters=n, first_step=1e-2, precision=32)
+                loss = min(loss, rp["loss"])
+            dt = time.perf_counter() - t0
+            ok = loss <= target
+            out["trials"].append({"swarm_iters": iters, "polish_iters": n, "s": dt, "loss_over_L_ref": loss / r64["loss"],
+                                  "reached": ok})
+            if ok:
+                if best is None or dt < best["s"]:
+                    best = {"s": dt, "swarm_iters": iters, "polish_iters": n, "loss": loss}
+                break
+    if best is None:
+        out.update({"reached": False})
+        return out
+    out.update({"fp32_plus_polish_s": best["s"], "swarm_iters": best["swarm_iters"], "polish_iters": best["polish_iters"],
+                "loss_reached": best["loss"], "speedup": t64 / best["s"], "reached": True})
     return out
 
 
